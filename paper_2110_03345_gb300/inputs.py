@@ -1,0 +1,259 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only draws inputs: models (sound speed, density), transducer
+coordinates and source wavelets.  It holds none of the solver's arithmetic and
+is shared by the tests, the benchmark, the CUDA path and the oracle alike.
+
+The paper's datasets (the numerical breast database and MIDA head of Sec. 3.2
+and 3.3, the PVA phantom recordings, the kWave/ITRUSST results of Sec. 3.1) are
+not available; the phantoms below take their shapes, spacings and property
+ranges instead:
+
+  * ``config_homogeneous_2d``: the homogeneous accuracy setup of Sec. 3.1 on a
+    256^2 grid at 0.2 mm with a Ricker source (the paper used a tone burst).
+  * ``config_breast_2d``: a 2D breast-like slice (Sec. 3.2): water, an
+    ellipse of fatty tissue holding 20-40 random inclusions, smoothed noise,
+    a 256-element ring array; every second element fires.
+  * ``config_skull_3d``: a 3D head-like model (Sec. 3.3): water, an
+    ellipsoidal skull shell and soft-tissue interior, transducers on a
+    Fibonacci sphere (the Fibonacci layout of Sec. 3.1).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+def ricker(f0: float, dt: float, nt: int, t0: float | None = None, amp: float = 1.0):
+    """Ricker wavelet r(t) = (1 - 2 pi^2 f0^2 tau^2) exp(-pi^2 f0^2 tau^2), tau = t - t0."""
+    t0 = 1.5 / f0 if t0 is None else t0
+    t = np.arange(nt) * dt - t0
+    a = (np.pi * f0 * t) ** 2
+    return amp * (1.0 - 2.0 * a) * np.exp(-a)
+
+
+def ricker_fn(f0: float, t0: float | None = None, amp: float = 1.0):
+    """The same wavelet as a function of continuous time (for analytic checks)."""
+    t0 = 1.5 / f0 if t0 is None else t0
+
+    def q(t):
+        a = (np.pi * f0 * (np.asarray(t) - t0)) ** 2
+        return amp * (1.0 - 2.0 * a) * np.exp(-a)
+    return q
+
+
+def ring(n: int, centre, radius: float):
+    """n points on a circle; coordinates in axis order (y, x)."""
+    th = 2.0 * np.pi * np.arange(n) / n
+    return np.stack([centre[0] + radius * np.sin(th), centre[1] + radius * np.cos(th)], 1)
+
+
+def fibonacci_sphere(n: int, centre, radius: float):
+    """n nearly uniform points on a sphere (Fibonacci spiral); axis order (z, y, x)."""
+    k = np.arange(n) + 0.5
+    z = 1.0 - 2.0 * k / n
+    r = np.sqrt(1.0 - z * z)
+    phi = np.pi * (1.0 + 5.0 ** 0.5) * k
+    pts = np.stack([z, r * np.sin(phi), r * np.cos(phi)], 1)
+    return np.asarray(centre)[None, :] + radius * pts
+
+
+def cfl_dt(dx: float, c_max: float, cfl: float = 0.4) -> float:
+    return cfl * dx / c_max
+
+
+@dataclass
+class Problem:
+    """One synthetic problem: model, geometry, wavelets and time axis.
+
+    vp, rho: float64 arrays of the grid shape (slowest axis first).
+    src_xyz: [nshots][nsrc][ndim] metres; rec_xyz: [nrec][ndim] metres (shared).
+    wavelet: [nshots][nsrc][nt]."""
+    name: str
+    shape: tuple
+    spacing: float
+    dt: float
+    nt: int
+    order: int
+    nb: int
+    vp: np.ndarray
+    rho: np.ndarray | None
+    src_xyz: np.ndarray
+    rec_xyz: np.ndarray
+    wavelet: np.ndarray
+    c_ref: float = 1500.0
+    vp_true: np.ndarray | None = None   # model that generates observed data
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def ndim(self):
+        return len(self.shape)
+
+    @property
+    def nshots(self):
+        return self.src_xyz.shape[0]
+
+    @property
+    def npoints(self):
+        return int(np.prod(self.shape))
+
+
+def config_homogeneous_2d(n=256, dx=0.2e-3, nt=1000, nrec=64, radius=20e-3, f0=500e3,
+                          c=1500.0, rho=1000.0, order=8, nb=20, variable_density=False):
+    """Homogeneous 2D setup: on-node Ricker source at the centre node, a ring of
+    receivers (default: 256^2, 0.2 mm, 64 receivers at 20 mm, 1000 steps)."""
+    dt = cfl_dt(dx, c)
+    shape = (n, n)
+    vp = np.full(shape, c)
+    rh = np.full(shape, rho) if variable_density else None
+    ctr = (n // 2) * dx
+    src = np.array([[[ctr, ctr]]])
+    rec = ring(nrec, (ctr, ctr), radius)
+    wav = ricker(f0, dt, nt)[None, None, :]
+    return Problem("homogeneous_2d", shape, dx, dt, nt, order, nb, vp, rh, src, rec, wav,
+                   c_ref=c)
+
+
+def _ellipse_mask(Y, X, cy, cx, ay, ax, theta):
+    ct, st = math.cos(theta), math.sin(theta)
+    yy, xx = Y - cy, X - cx
+    u = ct * xx + st * yy
+    v = -st * xx + ct * yy
+    return (u / ax) ** 2 + (v / ay) ** 2 <= 1.0
+
+
+def _smooth(a, sigma_pts):
+    from scipy.ndimage import gaussian_filter
+    return gaussian_filter(a, sigma_pts, mode="nearest")
+
+
+def breast_model_2d(n: int, dx: float, seed: int, scale: float = 1.0):
+    """Breast-like 2D slice: water (1500 m/s, 1000 kg/m^3); an ellipse of fatty
+    tissue (semi-axes ~35-40 mm x scale) holding 20-40 random inclusions with
+    c ~ U[1400, 1600], rho ~ U[950, 1100]; smoothed noise of std 5 m/s;
+    clipped to [1400, 1600] / [950, 1100].  Returns (vp, rho)."""
+    rng = np.random.default_rng(seed)
+    y = (np.arange(n) + 0.5 - n / 2) * dx
+    Y, X = np.meshgrid(y, y, indexing="ij")
+    vp = np.full((n, n), 1500.0)
+    rho = np.full((n, n), 1000.0)
+    ay, ax = rng.uniform(35e-3, 40e-3, 2) * scale
+    breast = _ellipse_mask(Y, X, 0.0, 0.0, ay, ax, rng.uniform(0, np.pi))
+    vp[breast] = rng.uniform(1430, 1470)
+    rho[breast] = rng.uniform(950, 980)
+    for _ in range(int(rng.integers(20, 41))):
+        r = math.sqrt(rng.uniform(0.0, 1.0)) * 0.8
+        ang = rng.uniform(0, 2 * np.pi)
+        cy, cx = r * ay * math.sin(ang), r * ax * math.cos(ang)
+        sy, sx = rng.uniform(2e-3, 15e-3, 2) * scale
+        m = _ellipse_mask(Y, X, cy, cx, sy, sx, rng.uniform(0, np.pi)) & breast
+        vp[m] = rng.uniform(1400, 1600)
+        rho[m] = rng.uniform(950, 1100)
+    noise = _smooth(rng.standard_normal((n, n)), 0.5e-3 / dx)
+    noise *= 5.0 / max(noise.std(), 1e-12)
+    vp = np.where(breast, vp + noise, vp)
+    vp = np.clip(vp, 1400.0, 1600.0)
+    rho = np.clip(rho, 950.0, 1100.0)
+    return vp, rho
+
+
+def gaussian_blobs(shape, dx, seed, n=3, amp=20.0, sigma=3e-3, extent=0.3):
+    """Sum of n Gaussian blobs of amplitude +-amp m/s and width sigma, centres
+    within +-extent of the domain size about the centre."""
+    rng = np.random.default_rng(seed)
+    axes = [(np.arange(s) + 0.5 - s / 2) * dx for s in shape]
+    grids = np.meshgrid(*axes, indexing="ij")
+    out = np.zeros(shape)
+    L = np.array(shape) * dx
+    for _ in range(n):
+        c = rng.uniform(-extent, extent, len(shape)) * L
+        a = amp * rng.choice([-1.0, 1.0])
+        r2 = sum((g - ci) ** 2 for g, ci in zip(grids, c))
+        out += a * np.exp(-0.5 * r2 / sigma ** 2)
+    return out
+
+
+def config_breast_2d(n=1024, dx=0.1e-3, nt=4000, nelem=256, radius=45e-3, f0=500e3,
+                     order=8, nb=20, seed=2, shots=None, c_max=1600.0):
+    """Breast-like 2D problem: n^2 grid, 256-element ring of radius 45 mm about
+    the centre; shots fire elements 0, 2, ..., all elements receive.  The
+    observed data come from the model plus 3 Gaussian blobs (+-20 m/s,
+    3 mm, seed 20).  Defaults are the full-size workload (1024^2, 0.1 mm,
+    128 shots of 4000 steps, dt = 25 ns).  Smaller n scales the geometry."""
+    scale = n * dx / (1024 * 0.1e-3)
+    vp, rho = breast_model_2d(n, dx, seed, scale=scale)
+    dt = cfl_dt(dx, c_max)
+    ctr = (n / 2) * dx
+    elems = ring(nelem, (ctr, ctr), radius * scale)
+    fire = np.arange(0, nelem, 2) if shots is None else np.asarray(shots)
+    src = elems[fire][:, None, :]
+    w = ricker(f0, dt, nt)
+    wav = np.broadcast_to(w, (len(fire), 1, nt)).copy()
+    vp_true = np.clip(vp + gaussian_blobs((n, n), dx, 20, sigma=3e-3 * scale), 1400.0, 1600.0)
+    return Problem("breast_2d", (n, n), dx, dt, nt, order, nb, vp, rho, src, elems, wav,
+                   c_ref=c_max, vp_true=vp_true)
+
+
+def skull_model_3d(n: int, dx: float, scale: float = 1.0):
+    """Head-like 3D model: water; an ellipsoidal skull shell with outer
+    semi-axes (20, 23, 19) mm x scale and 6 mm x scale thickness (2800 m/s,
+    1900 kg/m^3) around soft tissue (1540 m/s, 1040 kg/m^3)."""
+    z = (np.arange(n) + 0.5 - n / 2) * dx
+    Z, Y, X = np.meshgrid(z, z, z, indexing="ij")
+    a = np.array([20e-3, 23e-3, 19e-3]) * scale
+    t = 6e-3 * scale
+    outer = (Z / a[0]) ** 2 + (Y / a[1]) ** 2 + (X / a[2]) ** 2 <= 1.0
+    inner = (Z / (a[0] - t)) ** 2 + (Y / (a[1] - t)) ** 2 + (X / (a[2] - t)) ** 2 <= 1.0
+    vp = np.full((n, n, n), 1500.0)
+    rho = np.full((n, n, n), 1000.0)
+    vp[outer] = 2800.0
+    rho[outer] = 1900.0
+    vp[inner] = 1540.0
+    rho[inner] = 1040.0
+    return vp, rho
+
+
+def config_skull_3d(n=256, dx=0.25e-3, nt=2000, nrec=512, every=16, radius=25e-3,
+                    f0=500e3, order=10, nb=20, c_max=2800.0, shots=None):
+    """3D skull problem: n^3 grid, 512 receivers on a Fibonacci sphere of
+    radius 25 mm; 32 shots fire every 16th receiver.  Defaults are the full
+    size (256^3, 0.25 mm, 2000 steps, dt = 35.71 ns).  Smaller n scales the
+    geometry."""
+    scale = n * dx / (256 * 0.25e-3)
+    vp, rho = skull_model_3d(n, dx, scale)
+    dt = cfl_dt(dx, c_max)
+    ctr = (n / 2) * dx
+    rec = fibonacci_sphere(nrec, (ctr, ctr, ctr), radius * scale)
+    fire = np.arange(0, nrec, every) if shots is None else np.asarray(shots)
+    src = rec[fire][:, None, :]
+    w = ricker(f0, dt, nt)
+    wav = np.broadcast_to(w, (len(fire), 1, nt)).copy()
+    vp_true = vp.copy()
+    inner = (vp == 1540.0)
+    vp_true = np.where(inner, vp + gaussian_blobs(vp.shape, dx, 30, sigma=3e-3 * scale), vp)
+    return Problem("skull_3d", (n, n, n), dx, dt, nt, order, nb, vp, rho, src, rec, wav,
+                   c_ref=c_max, vp_true=vp_true)
+
+
+def random_smooth_model(shape, dx, seed, c_range=(1400.0, 1600.0), rho_range=(950.0, 1100.0),
+                        sigma=1e-3):
+    """Smooth random heterogeneous model (for parity tests on small grids)."""
+    rng = np.random.default_rng(seed)
+    sp = sigma / dx
+    a = _smooth(rng.standard_normal(shape), sp)
+    b = _smooth(rng.standard_normal(shape), sp)
+    a = (a - a.min()) / max(a.max() - a.min(), 1e-12)
+    b = (b - b.min()) / max(b.max() - b.min(), 1e-12)
+    vp = c_range[0] + (c_range[1] - c_range[0]) * a
+    rho = rho_range[0] + (rho_range[1] - rho_range[0]) * b
+    return vp, rho
+
+
+def random_points(n, shape, dx, seed, margin):
+    """n random off-grid points at least `margin` grid points inside each edge."""
+    rng = np.random.default_rng(seed)
+    lo = margin * dx
+    hi = (np.array(shape) - 1 - margin) * dx
+    return rng.uniform(lo, hi, (n, len(shape)))
