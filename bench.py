@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark of the acoustic FWI hot path on GB300.
+
+One step = one full misfit gradient (Sec. 2.2 Eqs. 5-9; one forward and one
+adjoint propagation per shot, imaging fused into the adjoint) of the 2D
+breast-like workload: 1024 x 1024 grid at 0.1 mm, variable density, 8th
+order, 128 shots of 4000 steps, 256 receivers (synthetic inputs, seed 2).
+
+Prints one JSON line: grid-point updates per second (Gpts/s, counting one
+update per grid point per time step per propagation: 2 propagations per
+shot), the HBM roofline of the dominant kernel (CUDA events on the plan's
+stream), the FP64 oracle timed on a bounded sample on the host cores, and an
+end-to-end figure through the public API with host buffers.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Algorithmic HBM bytes per grid-point update (FP32 fields, no halo re-reads):
+# forward step with history store, adjoint step with fused imaging.
+BYTES_PER_UPDATE = {("fwd", True): 24, ("fwd", False): 20, ("adj", True): 32, ("adj", False): 28}
+
+WORKLOADS = {
+    "breast2d": "2D breast-like phantom 1024x1024, dx=0.1 mm, vd, o8, 128 shots x 4000 steps, 256 receivers",
+    "skull3d": "3D skull phantom 256^3, dx=0.25 mm, vd, o10, 32 shots x 2000 steps, 512 receivers",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--workload", default="breast2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--shots", type=int, default=0, help="override shot count (testing only)")
+    ap.add_argument("--nt", type=int, default=0, help="override time steps (testing only)")
+    ap.add_argument("--n", type=int, default=0, help="override grid side (testing only)")
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--ckpt", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def make_problem(args):
+    from paper_2110_03345_gb300 import inputs
+    if args.workload == "breast2d":
+        n = args.n or 1024
+        nt = args.nt or 4000
+        dx = 0.1e-3 * 1024 / n
+        p = inputs.config_breast_2d(n=n, dx=dx, nt=nt)
+    else:
+        n = args.n or 256
+        nt = args.nt or 2000
+        dx = 0.25e-3 * 256 / n
+        p = inputs.config_skull_3d(n=n, dx=dx, nt=nt)
+    if args.shots:
+        p.src_xyz = p.src_xyz[:args.shots]
+        p.wavelet = p.wavelet[:args.shots]
+    return p
+
+
+def useful_updates(p) -> int:
+    """2 propagations x grid points x leapfrog steps x shots."""
+    return 2 * p.npoints * (p.nt - 1) * p.nshots
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [l.strip().split(", ") for l in self.f.read().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_uuid():
+    try:
+        import torch
+        u = torch.cuda.get_device_properties(torch.cuda.current_device()).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        return None
+
+
+def measured_hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_record(kernel_kind):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu summary,
+    or None when absent or taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(kernel_kind)
+    except Exception:
+        return None
+    if not rec:
+        return None
+    import hashlib
+    src = os.path.join(ROOT, "paper_2110_03345_gb300", "csrc", rec.get("source", "kernels2d.cu"))
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if h != rec.get("source_sha256_16"):
+        return None
+    return rec
+
+
+# ---------------------------------------------------------------- CPU baseline
+
+def cpu_baseline(p, budget_s: float):
+    """The FP64 oracle, as it stands, on one shot of the workload with the time
+    axis cut so that the run takes about budget_s seconds."""
+    import oracle
+    oracle.build()
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+    def run(nt):
+        g = oracle.Grid(p.shape, p.spacing, dt=p.dt, nt=nt, order=p.order, nb=p.nb, c_ref=p.c_ref)
+        obs = np.zeros((1, p.rec_xyz.shape[0], nt))
+        t0 = time.perf_counter()
+        oracle.gradient(g, p.vp, p.rho, p.src_xyz[:1], p.wavelet[:1, :, :nt], p.rec_xyz, obs,
+                        ckpt_every=max(2, int(np.sqrt(2 * nt))))
+        return time.perf_counter() - t0
+
+    t_small = run(12)
+    per_step = t_small / 11
+    nt = int(min(p.nt, max(12, budget_s / max(per_step, 1e-6))))
+    t = run(nt)
+    upd = 2 * p.npoints * (nt - 1)
+    return {"value": upd / t / 1e9, "unit": "Gpts/s", "cores": cores, "kind": "oracle",
+            "sample": f"1 shot of {p.nshots}, {nt} of {p.nt} steps, full grid "
+                      f"{'x'.join(map(str, p.shape))}, FP64 C oracle (OpenMP), observed data = 0, "
+                      f"checkpointed gradient; {t:.1f} s"}
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    p = make_problem(args)
+    steps = []
+    per = max(3.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(p, per)
+        if i >= args.warmup:
+            steps.append(r)
+    val = statistics.median(s["value"] for s in steps)
+    upd = useful_updates(p)
+    line = {
+        "impl": "reference", "metric": "Gpts/s (grid-point updates per second, gradient: forward + adjoint)",
+        "value": val, "unit": "Gpts/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": upd / (val * 1e9) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "shots": p.nshots, "nt": p.nt,
+                   "grid": list(p.shape), "sample": steps[-1]["sample"]},
+        "cpu_baseline": {"value": val, "unit": "Gpts/s", "cores": steps[-1]["cores"],
+                         "kind": "oracle", "sample": steps[-1]["sample"]},
+        "e2e": {"value": val, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_mine(args):
+    import torch
+    from paper_2110_03345_gb300 import binding
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    p = make_problem(args)
+    vd = p.rho is not None
+    f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    vp_h = torch.from_numpy(f32(p.vp)).pin_memory()
+    rho_h = torch.from_numpy(f32(p.rho)).pin_memory()
+    wav_h = torch.from_numpy(f32(p.wavelet)).pin_memory()
+    vp, rho, wav = vp_h.to(dev), rho_h.to(dev), wav_h.to(dev)
+    geo = binding.Geometry(p.src_xyz, p.rec_xyz)
+    stream = torch.cuda.current_stream()
+    plan = binding.Plan(p.shape, p.spacing, p.nt, p.dt, order=p.order, sponge=p.nb, c_ref=p.c_ref,
+                        stream=stream)
+    # observed data: the same solver on the perturbed model (bench input only)
+    obs = plan.forward(torch.from_numpy(f32(p.vp_true)).to(dev), rho, geo, wav)
+    obs_h = obs.cpu().pin_memory()
+    grad = torch.empty(p.shape, device=dev, dtype=torch.float32)
+    plan.set_options(batch=args.batch, tile=args.tile, ckpt_every=args.ckpt, profile=True)
+
+    for _ in range(args.warmup):
+        plan.gradient(vp, rho, geo, wav, obs, grad=grad)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(gpu_uuid())
+    acc = {"fwd_ms": 0.0, "adj_ms": 0.0, "fwd_launches": 0, "adj_launches": 0, "fwd_points": 0,
+           "adj_points": 0, "launches": 0}
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    J = None
+    for _ in range(args.steps):
+        J, _, _ = plan.gradient(vp, rho, geo, wav, obs, grad=grad)
+        s = plan.stats()
+        for k in acc:
+            acc[k] += s[k]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        # data-parallel gradient combination across ranks (the paper's sum over shots)
+        dist.all_reduce(grad)
+    stats = plan.stats()
+
+    upd = useful_updates(p)
+    value = world * upd / (ms * 1e-3) / 1e9
+    # roofline of the dominant kernel
+    kind = "adj" if acc["adj_ms"] >= acc["fwd_ms"] else "fwd"
+    n_l = max(acc[f"{kind}_launches"], 1)
+    t_launch = acc[f"{kind}_ms"] / n_l * 1e-3
+    pts_launch = acc[f"{kind}_points"] / n_l
+    bpu = BYTES_PER_UPDATE[(kind, vd)]
+    achieved = bpu * pts_launch / t_launch / 1e9
+    peak, peak_src = measured_hbm_peak()
+    tr = traffic_record(kind)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": (tr["dram_bytes_per_point"] * pts_launch) if tr else None,
+            "kernel": "k_step2d adjoint+imaging" if kind == "adj" else "k_step2d forward+store",
+            "bytes_per_update": bpu, "points_per_launch": int(pts_launch),
+            "launch_ms": t_launch * 1e3, "peak_source": peak_src,
+            "share_of_step": acc[f"{kind}_ms"] / args.steps / ms}
+
+    e2e = None
+    if not args.no_e2e:
+        gh = torch.empty(p.shape, dtype=torch.float32).pin_memory()
+        nb = vp_h.numel() * 4 + rho_h.numel() * 4 + wav_h.numel() * 4 + obs_h.numel() * 4
+        ke = 1
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            vp_d = vp_h.to(dev, non_blocking=True)
+            rho_d = rho_h.to(dev, non_blocking=True)
+            wav_d = wav_h.to(dev, non_blocking=True)
+            obs_d = obs_h.to(dev, non_blocking=True)
+            Je, gd, _ = plan.gradient(vp_d, rho_d, geo, wav_d, obs_d)
+            gh.copy_(gd, non_blocking=True)
+            torch.cuda.synchronize()
+        te = (time.perf_counter() - t0) / ke
+        e2e = {"value": world * upd / te / 1e9, "unit": "Gpts/s", "h2d_bytes_per_step": nb,
+               "d2h_bytes_per_step": gh.numel() * 4 + 8, "steps": ke}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(p, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": "Gpts/s (grid-point updates per second, gradient: forward + adjoint)",
+            "value": value, "unit": "Gpts/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "grid": list(p.shape),
+                       "shots": p.nshots, "nt": p.nt, "receivers": int(p.rec_xyz.shape[0]),
+                       "order": p.order, "variable_density": vd,
+                       "batch": stats["batch"], "ckpt_every": stats["ckpt_every"], "tile": stats["tile"],
+                       "l2": "inputs larger than L2 (history of every batch streams through HBM)",
+                       "misfit": J},
+            "shots_per_s": world * p.nshots / (ms * 1e-3),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(acc["launches"]),
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_mine(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

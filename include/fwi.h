@@ -1,0 +1,164 @@
+/*
+ * fwi.h -- C ABI of the GB300 acoustic full-waveform-inversion solver.
+ *
+ * The library solves the acoustic wave equation of Sec. 2.4, Eq. 10 of the
+ * Stride paper (arXiv 2110.03345) without attenuation,
+ *     (1/vp^2) p_tt = rho div(rho^-1 grad p) + s,
+ * with a second-order leapfrog in time, 8th- or 10th-order central stencils
+ * in space, a sponge absorbing layer and off-grid (bi-/tri-linear) sources
+ * and receivers (Sec. 2.4, last paragraphs).  It returns receiver traces
+ * (forward modelling, Sec. 3.1) and the L2 trace misfit with its gradient
+ * with respect to the squared slowness m = 1/vp^2, computed by the
+ * adjoint-state method of Sec. 2.2, Eqs. 5-9 on the discrete scheme (one
+ * forward and one adjoint propagation per shot, Sec. 3.2).
+ *
+ * Conventions shared by every call:
+ *  - Arrays are C order, the LAST axis fastest: 2D fields are [ny][nx],
+ *    3D fields are [nz][ny][nx].  Coordinates are given in the same axis
+ *    order (slowest first), in metres, with node i of axis d at i*spacing[d].
+ *  - "device" pointers are CUDA global memory visible to the plan's device;
+ *    "host" pointers are ordinary CPU memory.  The caller owns every array
+ *    passed in; the library never frees or retains them after a call returns.
+ *  - Fields are FP32; the misfit is accumulated in FP64.
+ *  - Every call returns a status; nothing aborts.  fwi_last_error() gives a
+ *    message for the last failing call on the calling thread.
+ *  - Work is enqueued on the plan's CUDA stream.  fwi_forward returns after
+ *    enqueueing (the traces are ready when the stream reaches that point);
+ *    fwi_gradient synchronises the stream before it returns (the misfit is a
+ *    host value).  Both synchronise once at entry to validate the model.
+ */
+#ifndef FWI_H
+#define FWI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FWI_OK = 0,
+    FWI_ERR_INVALID_ARG = 1,  /* bad sizes, pointers, coordinates or options */
+    FWI_ERR_UNSTABLE_CFL = 2, /* dt above 0.95 x the leapfrog stability limit */
+    FWI_ERR_BUDGET = 3,       /* workspace does not fit the plan's HBM budget */
+    FWI_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+    FWI_ERR_NONFINITE = 5,    /* the model or the result holds Inf/NaN */
+    FWI_ERR_TIMEOUT = 6,      /* a bounded device wait gave up */
+    FWI_ERR_UNSUPPORTED = 7   /* valid request this build does not implement */
+} fwi_status;
+
+/* Regular grid and spatial discretisation (Sec. 2.3 Listing 5, Sec. 2.4). */
+typedef struct {
+    int ndim;           /* 2 or 3 */
+    int64_t shape[3];   /* points per axis, slowest first; unused entries ignored */
+    double spacing[3];  /* metres per axis, same order */
+    int order;          /* spatial order: 8 or 10 (stencil radius 4 or 5) */
+    int sponge;         /* sponge width in points on every face, >= 0, < shape/2 */
+    double c_ref;       /* sponge reference speed (m/s); <= 0: the maximum vp of
+                           the first model the plan sees, then kept fixed */
+} fwi_grid;
+
+/* Medium (Sec. 2.3 Listing 6): sound speed and optional density. */
+typedef struct {
+    const float* vp;    /* device [N] m/s, N = prod(shape); > 0 and finite */
+    const float* rho;   /* device [N] kg/m^3, > 0; NULL selects constant density */
+} fwi_model;
+
+/* Acquisition geometry (Sec. 2.3 Listings 7-8): nshots shots, each with nsrc
+ * point sources; nrec receivers shared by every shot.  Points must lie inside
+ * the grid: 0 <= x_d <= (shape[d]-1)*spacing[d]. */
+typedef struct {
+    int nshots;               /* >= 1 */
+    int nsrc;                 /* sources per shot, >= 1 */
+    int nrec;                 /* receivers, >= 1 */
+    const double* src_xyz;    /* host [nshots][nsrc][ndim] metres */
+    const double* rec_xyz;    /* host [nrec][ndim] metres */
+} fwi_geometry;
+
+typedef struct fwi_plan fwi_plan;
+
+/* Execution options; zero-initialise and set what you need.  Every field has
+ * a default chosen by the plan when left at 0. */
+typedef struct {
+    int batch;          /* shots propagated concurrently (0: largest the budget allows) */
+    int ckpt_every;     /* gradient: 0 = full history if it fits, else sqrt(2 nt)
+                           checkpoints; > 0 forces checkpoints every ckpt_every
+                           steps; -1 forces the full history */
+    int tile;           /* kernel tile variant (0: default; see fwi_plan_stats) */
+    int profile;        /* 1: time every stencil launch with CUDA events */
+    int use_graphs;     /* 1: capture the time loop into CUDA graphs */
+} fwi_options;
+
+/* Counters of the last forward/gradient call on a plan. */
+typedef struct {
+    int batch;                  /* shots per launch used */
+    int ckpt_every;             /* 0 = full history, else checkpoint interval */
+    int tile;                   /* tile variant used */
+    size_t workspace_bytes;     /* device bytes held by the plan */
+    int64_t launches;           /* kernels launched by the last call */
+    int64_t updates;            /* grid-point updates in the last call (all kernels) */
+    int64_t fwd_launches;       /* forward stencil launches (incl. recompute) */
+    int64_t adj_launches;       /* adjoint stencil launches */
+    double fwd_ms;              /* summed CUDA-event time of forward stencil launches (profile=1) */
+    double adj_ms;              /* same for adjoint stencil launches */
+    int64_t fwd_points;         /* grid points (incl. padding-free interior) per forward launch, summed */
+    int64_t adj_points;
+} fwi_stats;
+
+/* Create a plan for one grid and time axis (nt samples of step dt seconds).
+ * The plan holds the device workspace, allocated on first use and kept
+ * within hbm_budget_bytes (0: 90% of the free device memory at creation).
+ * stream: a cudaStream_t (NULL = legacy default stream) the plan enqueues on.
+ * Errors: FWI_ERR_INVALID_ARG for a bad grid, nt < 1 or dt <= 0. */
+fwi_status fwi_plan_create(fwi_plan** plan, const fwi_grid* grid, int nt, double dt,
+                           size_t hbm_budget_bytes, void* stream);
+
+/* Set execution options (see fwi_options).  Takes effect on the next call. */
+fwi_status fwi_plan_set_options(fwi_plan* plan, const fwi_options* opt);
+
+/* Counters of the last call. */
+fwi_status fwi_plan_stats(const fwi_plan* plan, fwi_stats* out);
+
+/* Device bytes one forward (gradient = 0) or gradient (gradient = 1) call
+ * with this geometry would hold, at the batch and checkpoint policy the plan
+ * would choose.  No device work. */
+fwi_status fwi_plan_estimate(const fwi_plan* plan, const fwi_geometry* geom, int gradient,
+                             size_t* bytes);
+
+/* Release the workspace and the plan.  NULL is ignored. */
+void fwi_plan_destroy(fwi_plan* plan);
+
+/* Forward modelling (Sec. 2.4; Sec. 3.2 Listing 13 `pde(wavelets, vp)`).
+ *   wavelet: device [nshots][nsrc][nt] source time functions q^n.
+ *   traces:  device [nshots][nrec][nt] output, d^n = P u^n, n = 0..nt-1.
+ * nt and dt must equal the plan's (they are repeated for checking).
+ * u^0 = u^-1 = 0; step n injects q^n and produces u^{n+1}; d^0 = 0. */
+fwi_status fwi_forward(fwi_plan* plan, const fwi_model* model, const fwi_geometry* geom,
+                       const float* wavelet, int nt, double dt, float* traces);
+
+/* Misfit and gradient (Sec. 2.2 Eqs. 5-9; Sec. 3.2 Listing 13 `loss`,
+ * `fun.adjoint()`).
+ *   observed:   device [nshots][nrec][nt] observed data d_obs.
+ *   misfit:     host out, J = 1/2 sum_shots sum_rec sum_n (d - d_obs)^2.
+ *   grad_m:     device [N] out (overwritten), dJ/dm with m = 1/vp^2, summed
+ *               over shots, defined on the whole grid (sponge included).
+ *   traces_opt: device [nshots][nrec][nt] out for the modelled traces, or NULL.
+ * The paper's vp.grad follows as -2 grad_m / vp^3. */
+fwi_status fwi_gradient(fwi_plan* plan, const fwi_model* model, const fwi_geometry* geom,
+                        const float* wavelet, const float* observed, double* misfit,
+                        float* grad_m, float* traces_opt);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char* fwi_last_error(void);
+
+/* Leapfrog stability limit of c*dt/h for this order and dimension:
+ * 2/sqrt(ndim * lambda_max), lambda_max = |sum_j (-1)^j w2_j| of the
+ * second-derivative stencil.  Returns a negative value for bad input. */
+double fwi_cfl_limit(int ndim, int order);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FWI_H */

@@ -1,0 +1,237 @@
+"""ctypes binding of libfwi.so (include/fwi.h): argument marshalling only.
+
+Every step of the solver runs in the CUDA library; this module converts torch
+tensors and numpy arrays into the pointers and sizes of the C ABI and turns
+status codes into exceptions.  There is no CPU fallback: if the library is
+missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+FWI_OK = 0
+STATUS = {0: "FWI_OK", 1: "FWI_ERR_INVALID_ARG", 2: "FWI_ERR_UNSTABLE_CFL", 3: "FWI_ERR_BUDGET",
+          4: "FWI_ERR_CUDA", 5: "FWI_ERR_NONFINITE", 6: "FWI_ERR_TIMEOUT",
+          7: "FWI_ERR_UNSUPPORTED"}
+
+# Every symbol include/fwi.h declares (checked by the tests).
+EXPORTS = ("fwi_plan_create", "fwi_plan_set_options", "fwi_plan_stats", "fwi_plan_estimate",
+           "fwi_plan_destroy", "fwi_forward", "fwi_gradient", "fwi_last_error", "fwi_cfl_limit")
+
+
+class FwiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class CGrid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("shape", ctypes.c_int64 * 3),
+                ("spacing", ctypes.c_double * 3), ("order", ctypes.c_int),
+                ("sponge", ctypes.c_int), ("c_ref", ctypes.c_double)]
+
+
+class CModel(ctypes.Structure):
+    _fields_ = [("vp", ctypes.c_void_p), ("rho", ctypes.c_void_p)]
+
+
+class CGeometry(ctypes.Structure):
+    _fields_ = [("nshots", ctypes.c_int), ("nsrc", ctypes.c_int), ("nrec", ctypes.c_int),
+                ("src_xyz", ctypes.POINTER(ctypes.c_double)),
+                ("rec_xyz", ctypes.POINTER(ctypes.c_double))]
+
+
+class COptions(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int), ("ckpt_every", ctypes.c_int), ("tile", ctypes.c_int),
+                ("profile", ctypes.c_int), ("use_graphs", ctypes.c_int)]
+
+
+class CStats(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int), ("ckpt_every", ctypes.c_int), ("tile", ctypes.c_int),
+                ("workspace_bytes", ctypes.c_size_t), ("launches", ctypes.c_int64),
+                ("updates", ctypes.c_int64), ("fwd_launches", ctypes.c_int64),
+                ("adj_launches", ctypes.c_int64), ("fwd_ms", ctypes.c_double),
+                ("adj_ms", ctypes.c_double), ("fwd_points", ctypes.c_int64),
+                ("adj_points", ctypes.c_int64)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libfwi.so (building it first if it is missing and nvcc is present)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise FwiError(4, f"{path} is missing; run the build first")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        P = ctypes.POINTER
+        vp = ctypes.c_void_p
+        lib.fwi_plan_create.argtypes = [P(vp), P(CGrid), ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_size_t, vp]
+        lib.fwi_plan_create.restype = ctypes.c_int
+        lib.fwi_plan_set_options.argtypes = [vp, P(COptions)]
+        lib.fwi_plan_set_options.restype = ctypes.c_int
+        lib.fwi_plan_stats.argtypes = [vp, P(CStats)]
+        lib.fwi_plan_stats.restype = ctypes.c_int
+        lib.fwi_plan_estimate.argtypes = [vp, P(CGeometry), ctypes.c_int, P(ctypes.c_size_t)]
+        lib.fwi_plan_estimate.restype = ctypes.c_int
+        lib.fwi_plan_destroy.argtypes = [vp]
+        lib.fwi_plan_destroy.restype = None
+        lib.fwi_forward.argtypes = [vp, P(CModel), P(CGeometry), vp, ctypes.c_int, ctypes.c_double, vp]
+        lib.fwi_forward.restype = ctypes.c_int
+        lib.fwi_gradient.argtypes = [vp, P(CModel), P(CGeometry), vp, vp, P(ctypes.c_double), vp, vp]
+        lib.fwi_gradient.restype = ctypes.c_int
+        lib.fwi_last_error.argtypes = []
+        lib.fwi_last_error.restype = ctypes.c_char_p
+        lib.fwi_cfl_limit.argtypes = [ctypes.c_int, ctypes.c_int]
+        lib.fwi_cfl_limit.restype = ctypes.c_double
+        _lib = lib
+        return lib
+
+
+def _check(status: int):
+    if status != FWI_OK:
+        msg = load().fwi_last_error().decode(errors="replace")
+        raise FwiError(status, msg)
+
+
+def cfl_limit(ndim: int, order: int) -> float:
+    return float(load().fwi_cfl_limit(ndim, order))
+
+
+def _ptr(t):
+    """Device pointer of a CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float32 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Geometry:
+    """Host-side acquisition geometry: src_xyz [nshots][nsrc][ndim], rec_xyz [nrec][ndim]."""
+
+    def __init__(self, src_xyz, rec_xyz):
+        self.src = np.ascontiguousarray(src_xyz, dtype=np.float64)
+        self.rec = np.ascontiguousarray(rec_xyz, dtype=np.float64)
+        if self.src.ndim == 2:
+            self.src = self.src[None]
+        assert self.src.ndim == 3 and self.rec.ndim == 2
+        dp = ctypes.POINTER(ctypes.c_double)
+        self.c = CGeometry(self.src.shape[0], self.src.shape[1], self.rec.shape[0],
+                           self.src.ctypes.data_as(dp), self.rec.ctypes.data_as(dp))
+
+    @property
+    def nshots(self):
+        return self.src.shape[0]
+
+    @property
+    def nsrc(self):
+        return self.src.shape[1]
+
+    @property
+    def nrec(self):
+        return self.rec.shape[0]
+
+
+class Plan:
+    """A solver plan for one grid and time axis (fwi_plan_create)."""
+
+    def __init__(self, shape, spacing, nt, dt, order=8, sponge=20, c_ref=0.0, budget=0,
+                 stream=None):
+        import torch
+        lib = load()
+        shape = tuple(int(s) for s in shape)
+        nd = len(shape)
+        if np.isscalar(spacing):
+            spacing = (float(spacing),) * nd
+        g = CGrid()
+        g.ndim = nd
+        for i in range(nd):
+            g.shape[i] = shape[i]
+            g.spacing[i] = float(spacing[i])
+        g.order, g.sponge, g.c_ref = int(order), int(sponge), float(c_ref)
+        self.shape, self.spacing, self.nt, self.dt = shape, tuple(spacing), int(nt), float(dt)
+        self.order, self.sponge = order, sponge
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(lib.fwi_plan_create(ctypes.byref(h), ctypes.byref(g), self.nt, self.dt,
+                                   int(budget), ctypes.c_void_p(stream.cuda_stream)))
+        self._h = h
+        self._opts = COptions()
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().fwi_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    __del__ = close
+
+    def set_options(self, batch=0, ckpt_every=0, tile=0, profile=False, use_graphs=False):
+        self._opts = COptions(int(batch), int(ckpt_every), int(tile), int(bool(profile)),
+                              int(bool(use_graphs)))
+        _check(load().fwi_plan_set_options(self._h, ctypes.byref(self._opts)))
+
+    def stats(self) -> dict:
+        s = CStats()
+        _check(load().fwi_plan_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in CStats._fields_}
+
+    def estimate(self, geometry: Geometry, gradient: bool) -> int:
+        b = ctypes.c_size_t()
+        _check(load().fwi_plan_estimate(self._h, ctypes.byref(geometry.c), int(gradient),
+                                        ctypes.byref(b)))
+        return int(b.value)
+
+    def _model(self, vp, rho):
+        return CModel(_ptr(vp), _ptr(rho))
+
+    def forward(self, vp, rho, geometry: Geometry, wavelet, traces=None):
+        """Traces [nshots][nrec][nt] (CUDA float32) for the given wavelets."""
+        import torch
+        if traces is None:
+            traces = torch.empty((geometry.nshots, geometry.nrec, self.nt), device=vp.device,
+                                 dtype=torch.float32)
+        m = self._model(vp, rho)
+        _check(load().fwi_forward(self._h, ctypes.byref(m), ctypes.byref(geometry.c),
+                                  _ptr(wavelet), self.nt, self.dt, _ptr(traces)))
+        return traces
+
+    def gradient(self, vp, rho, geometry: Geometry, wavelet, observed, grad=None, traces=False):
+        """(J, grad_m, traces or None): L2 misfit and its gradient w.r.t. m = 1/vp^2."""
+        import torch
+        if grad is None:
+            grad = torch.empty(vp.shape, device=vp.device, dtype=torch.float32)
+        tr = None
+        if traces is True:
+            tr = torch.empty((geometry.nshots, geometry.nrec, self.nt), device=vp.device,
+                             dtype=torch.float32)
+        elif traces is not False and traces is not None:
+            tr = traces
+        J = ctypes.c_double()
+        m = self._model(vp, rho)
+        _check(load().fwi_gradient(self._h, ctypes.byref(m), ctypes.byref(geometry.c),
+                                   _ptr(wavelet), _ptr(observed), ctypes.byref(J), _ptr(grad),
+                                   _ptr(tr)))
+        return J.value, grad, tr

@@ -1,0 +1,135 @@
+// Internal declarations of the GB300 acoustic FWI library (not part of the ABI).
+//
+// Device data layout (one "field" = one FP32 array over the padded grid):
+//   x (last axis) is padded by OX = 8 floats on the left and rounded up to a
+//   multiple of 128 plus 8 on the right, so every row starts 32-byte aligned
+//   and float4 loads of a tile plus its halo never leave the allocation;
+//   y and z are padded by the stencil radius R on both sides and rounded up
+//   to a multiple of 64 (the largest tile height).  The padding holds zeros,
+//   which is the u = 0 boundary condition behind the sponge, so stencil
+//   loads need no bounds checks.  Per-shot fields are stacked [B][fstride].
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fwi {
+
+constexpr int OX = 8;          // x padding (floats) before the interior
+constexpr int TILE_X = 128;    // tile width of the 2D kernels (32 threads x float4)
+constexpr int ROUND_Y = 64;    // y (and z) extents are rounded to this
+constexpr int MAX_SLOT_TILES = 1 << 20;
+
+struct Layout {
+  int ndim;
+  int nx, ny, nz;        // interior extents (nz = 1 in 2D)
+  int R;                 // stencil radius
+  int ox, oy, oz;        // interior origin in padded coordinates
+  int sx;                // row stride (floats)
+  int rows;              // padded rows (y)
+  int planes;            // padded planes (z; 1 in 2D)
+  long long sxy;         // plane stride (floats)
+  long long fstride;     // floats per field
+  int nx_r, ny_r, nz_r;  // rounded interior extents covered by tiles
+  __host__ __device__ long long index(int z, int y, int x) const {
+    return (long long)(z + oz) * sxy + (long long)(y + oy) * sx + (x + ox);
+  }
+};
+
+// Scaled stencil weights for one axis: w2[j] / h^2 and w1[j] / h.
+struct AxisW {
+  float w2[6];
+  float w1[6];
+};
+
+// Parameters of one stencil launch (forward or adjoint step).
+struct StepParams {
+  const float* u;      // u^n (adjoint: lambda^k), [B][fstride]
+  float* up;           // in: u^{n-1} (lambda^{k+1}); out: u^{n+1} (lambda^{k-1})
+  const float* kf;     // k = (vp dt)^2, [fstride]
+  const float* bx;     // density gradient d(ln rho)/dx etc. (variable density)
+  const float* by;
+  const float* bz;
+  const float* spx;    // sponge a_d(i) = sigma_d(i) dt / 2, per axis, rounded length
+  const float* spy;
+  const float* spz;
+  float* hist;         // forward: store k(L u + s) here (or null); adjoint: read h^k
+  float* g;            // adjoint imaging accumulator [B][fstride] (or null)
+  long long fstride;
+  long long sxy;
+  int sx;
+  int nx, ny, nz;
+  int ox, oy, oz;
+  AxisW wx, wy, wz;
+  // sparse injection, bucketed by (slot, tile): entries e in [off[s*T+t], off[s*T+t+1])
+  const int* inj_off;
+  const int* inj_loc;    // tile-local linear index (2D: ly*TX+lx; 3D: (lz*TY+ly)*TX+lx)
+  const int* inj_vidx;   // index into vals (before step_off)
+  const float* inj_w;    // weight (source: w/dV; receiver residual: w)
+  const float* vals;
+  long long step_off;
+  int ntiles;            // tiles per slot
+  // receiver sampling of u (forward only): out[smp_off + b*nrec + r]
+  const int* smp_node;   // [nrec][ncorner] padded index within a shot field
+  const float* smp_w;
+  float* smp_out;
+  long long smp_off;
+  int nrec;
+  int ncorner;
+  int B;                 // shot slots in this launch
+  int image;             // adjoint: accumulate g -= lambda^k h^k
+  int zchunk;            // 3D: planes per CTA
+  int nzc;               // 3D: z chunks
+};
+
+// Tile variants of the 2D kernels: rows per thread x thread rows.
+struct Tile2 { int ry, by; };
+constexpr int NUM_TILE2 = 4;
+__host__ __device__ inline Tile2 tile2_variant(int v) {
+  switch (v) {
+    case 1: return {2, 16};
+    case 2: return {4, 4};
+    case 3: return {2, 8};
+    default: return {4, 8};
+  }
+}
+// 3D tile variants: thread rows (tile 32 x by) and z chunk
+struct Tile3 { int by, zc; };
+constexpr int NUM_TILE3 = 4;
+__host__ __device__ inline Tile3 tile3_variant(int v) {
+  switch (v) {
+    case 1: return {8, 64};
+    case 2: return {16, 32};
+    case 3: return {8, 32};
+    default: return {16, 64};
+  }
+}
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_step2d(const StepParams& p, int R, bool vd, bool adj, int tile,
+                          cudaStream_t st);
+cudaError_t launch_step3d(const StepParams& p, int R, bool vd, bool adj, int tile,
+                          cudaStream_t st);
+size_t step2d_smem(int R, bool vd, bool adj, int tile);
+size_t step3d_smem(int R, bool vd, bool adj, int tile);
+
+// Auxiliary kernels (aux_kernels.cu)
+cudaError_t launch_model_prep(const Layout& L, const float* vp, const float* rho, double dt,
+                              float* kf, float* lnr, unsigned int* stats, cudaStream_t st);
+cudaError_t launch_density_grad(const Layout& L, const float* lnr, const AxisW& wx,
+                                const AxisW& wy, const AxisW& wz, float* bx, float* by,
+                                float* bz, cudaStream_t st);
+cudaError_t launch_sample(const StepParams& p, cudaStream_t st);
+cudaError_t launch_misfit(const float* d_ws, const float* obs, float* traces_out, int B,
+                          int shot0, int nshots_batch, int nrec, int nt, double* partials,
+                          int* nonfinite, int npartials, cudaStream_t st);
+int misfit_blocks(int nshots_batch, int nrec, int nt);
+cudaError_t launch_sum_partials(const double* partials, int n, double* out, cudaStream_t st);
+cudaError_t launch_traces_out(const float* d_ws, float* traces_out, int B, int shot0,
+                              int nshots_batch, int nrec, int nt, int* nonfinite,
+                              cudaStream_t st);
+cudaError_t launch_image_only(const Layout& L, const float* lam, const float* hist, float* g,
+                              int B, cudaStream_t st);
+cudaError_t launch_grad_finalize(const Layout& L, const float* g, int B, double inv_dt2,
+                                 float* grad_out, int* nonfinite, cudaStream_t st);
+
+}  // namespace fwi

@@ -175,25 +175,45 @@ def gaussian_blobs(shape, dx, seed, n=3, amp=20.0, sigma=3e-3, extent=0.3):
     return out
 
 
-def config_breast_2d(n=1024, dx=0.1e-3, nt=4000, nelem=256, radius=45e-3, f0=500e3,
-                     order=8, nb=20, seed=2, shots=None, c_max=1600.0):
-    """Breast-like 2D problem: n^2 grid, 256-element ring of radius 45 mm about
-    the centre; shots fire elements 0, 2, ..., all elements receive.  The
-    observed data come from the model plus 3 Gaussian blobs (+-20 m/s,
-    3 mm, seed 20).  Defaults are the full-size workload (1024^2, 0.1 mm,
-    128 shots of 4000 steps, dt = 25 ns).  Smaller n scales the geometry."""
-    scale = n * dx / (1024 * 0.1e-3)
-    vp, rho = breast_model_2d(n, dx, seed, scale=scale)
+def breast_problem(shape, dx, nt, nelem=256, shots=None, order=8, nb=20, seed=2, f0=500e3,
+                   c_max=1600.0, radius=None, perturb_seed=20):
+    """Breast-like 2D problem on a (possibly non-square) grid: the phantom of
+    ``breast_model_2d`` scaled to the smaller side and centre-cropped, a ring of
+    ``nelem`` elements about the centre (default radius: 0.4395 x the smaller
+    side, i.e. 45 mm on a 1024 x 0.1 mm grid); shots fire the
+    given elements (default every second one); all elements receive.  The
+    observed-data model adds 3 Gaussian blobs (+-20 m/s, 3 mm x scale)."""
+    ny, nx = (int(s) for s in shape)
+    m, full = min(ny, nx), max(ny, nx)
+    scale = m * dx / (1024 * 0.1e-3)
+    vpf, rhof = breast_model_2d(full, dx, seed, scale=scale)
+    oy, ox = (full - ny) // 2, (full - nx) // 2
+    vp = vpf[oy:oy + ny, ox:ox + nx].copy()
+    rho = rhof[oy:oy + ny, ox:ox + nx].copy()
     dt = cfl_dt(dx, c_max)
-    ctr = (n / 2) * dx
-    elems = ring(nelem, (ctr, ctr), radius * scale)
+    ctr = ((ny / 2) * dx, (nx / 2) * dx)
+    rad = 0.4395 * m * dx if radius is None else radius
+    elems = ring(nelem, ctr, rad)
     fire = np.arange(0, nelem, 2) if shots is None else np.asarray(shots)
     src = elems[fire][:, None, :]
     w = ricker(f0, dt, nt)
     wav = np.broadcast_to(w, (len(fire), 1, nt)).copy()
-    vp_true = np.clip(vp + gaussian_blobs((n, n), dx, 20, sigma=3e-3 * scale), 1400.0, 1600.0)
-    return Problem("breast_2d", (n, n), dx, dt, nt, order, nb, vp, rho, src, elems, wav,
+    blobs = gaussian_blobs((full, full), dx, perturb_seed, sigma=3e-3 * scale)[oy:oy + ny, ox:ox + nx]
+    vp_true = np.clip(vp + blobs, 1400.0, 1600.0)
+    return Problem("breast_2d", (ny, nx), dx, dt, nt, order, nb, vp, rho, src, elems, wav,
                    c_ref=c_max, vp_true=vp_true)
+
+
+def config_breast_2d(n=1024, dx=0.1e-3, nt=4000, nelem=256, radius=45e-3, f0=500e3,
+                     order=8, nb=20, seed=2, shots=None, c_max=1600.0):
+    """Breast-like 2D problem: n^2 grid, 256-element ring of radius 45 mm (scaled
+    with n dx) about the centre; shots fire elements 0, 2, ..., all elements
+    receive.  The observed-data model is the phantom plus 3 Gaussian blobs
+    (+-20 m/s, 3 mm, seed 20).  Defaults are the full-size workload (1024^2,
+    0.1 mm, 128 shots of 4000 steps, dt = 25 ns)."""
+    scale = n * dx / (1024 * 0.1e-3)
+    return breast_problem((n, n), dx, nt, nelem=nelem, shots=shots, order=order, nb=nb,
+                          seed=seed, f0=f0, c_max=c_max, radius=radius * scale)
 
 
 def skull_model_3d(n: int, dx: float, scale: float = 1.0):
@@ -215,26 +235,43 @@ def skull_model_3d(n: int, dx: float, scale: float = 1.0):
     return vp, rho
 
 
-def config_skull_3d(n=256, dx=0.25e-3, nt=2000, nrec=512, every=16, radius=25e-3,
-                    f0=500e3, order=10, nb=20, c_max=2800.0, shots=None):
-    """3D skull problem: n^3 grid, 512 receivers on a Fibonacci sphere of
-    radius 25 mm; 32 shots fire every 16th receiver.  Defaults are the full
-    size (256^3, 0.25 mm, 2000 steps, dt = 35.71 ns).  Smaller n scales the
-    geometry."""
-    scale = n * dx / (256 * 0.25e-3)
-    vp, rho = skull_model_3d(n, dx, scale)
+def skull_problem(shape, dx, nt, nrec=512, every=16, order=10, nb=20, f0=500e3, c_max=2800.0,
+                  radius=None, shots=None, perturb_seed=30):
+    """Head-like 3D problem on a (possibly non-cubic) grid: the model of
+    ``skull_model_3d`` scaled to the smallest side and centre-cropped,
+    ``nrec`` receivers on a Fibonacci sphere (default radius 25 mm x scale),
+    shots firing every ``every``-th receiver.  Observed-data model: Gaussian
+    blobs (+-20 m/s, 3 mm x scale) in the soft tissue."""
+    shape = tuple(int(s) for s in shape)
+    m, full = min(shape), max(shape)
+    scale = m * dx / (256 * 0.25e-3)
+    vpf, rhof = skull_model_3d(full, dx, scale)
+    o = [(full - s) // 2 for s in shape]
+    sl = tuple(slice(oi, oi + s) for oi, s in zip(o, shape))
+    vp, rho = vpf[sl].copy(), rhof[sl].copy()
     dt = cfl_dt(dx, c_max)
-    ctr = (n / 2) * dx
-    rec = fibonacci_sphere(nrec, (ctr, ctr, ctr), radius * scale)
+    ctr = tuple((s / 2) * dx for s in shape)
+    rad = 25e-3 * scale if radius is None else radius
+    rec = fibonacci_sphere(nrec, ctr, rad)
     fire = np.arange(0, nrec, every) if shots is None else np.asarray(shots)
     src = rec[fire][:, None, :]
     w = ricker(f0, dt, nt)
     wav = np.broadcast_to(w, (len(fire), 1, nt)).copy()
-    vp_true = vp.copy()
     inner = (vp == 1540.0)
-    vp_true = np.where(inner, vp + gaussian_blobs(vp.shape, dx, 30, sigma=3e-3 * scale), vp)
-    return Problem("skull_3d", (n, n, n), dx, dt, nt, order, nb, vp, rho, src, rec, wav,
+    blobs = gaussian_blobs((full,) * 3, dx, perturb_seed, sigma=3e-3 * scale)[sl]
+    vp_true = np.where(inner, vp + blobs, vp)
+    return Problem("skull_3d", shape, dx, dt, nt, order, nb, vp, rho, src, rec, wav,
                    c_ref=c_max, vp_true=vp_true)
+
+
+def config_skull_3d(n=256, dx=0.25e-3, nt=2000, nrec=512, every=16, radius=25e-3,
+                    f0=500e3, order=10, nb=20, c_max=2800.0, shots=None):
+    """3D skull problem: n^3 grid, 512 receivers on a Fibonacci sphere of
+    radius 25 mm (scaled with n dx); 32 shots fire every 16th receiver.
+    Defaults are the full size (256^3, 0.25 mm, 2000 steps, dt = 35.71 ns)."""
+    scale = n * dx / (256 * 0.25e-3)
+    return skull_problem((n, n, n), dx, nt, nrec=nrec, every=every, order=order, nb=nb, f0=f0,
+                         c_max=c_max, radius=radius * scale, shots=shots)
 
 
 def random_smooth_model(shape, dx, seed, c_range=(1400.0, 1600.0), rho_range=(950.0, 1100.0),

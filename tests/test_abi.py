@@ -1,0 +1,63 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds for
+sm_103a, loads, and exports every function include/fwi.h declares; the
+leapfrog stability limit it reports matches an independent computation."""
+import ctypes
+import os
+import re
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_2110_03345_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "fwi.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fwi_[a-z_]+)\s*\(", src)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    names = declared_functions()
+    assert len(names) >= 9
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(binding.EXPORTS)
+
+
+def test_library_is_built_for_sm_103a():
+    # the fatbin of an sm_103a build carries the architecture name
+    data = open(build.build(), "rb").read()
+    assert b"sm_103a" in data or b"sm_103" in data
+
+
+def test_last_error_empty_and_cfl_limits():
+    lib = binding.load()
+    assert isinstance(lib.fwi_last_error(), bytes)
+    # lambda_max of the exact central weights (Fornberg) -> 2/sqrt(d lambda)
+    for order, w in ((8, [Fraction(-205, 72), Fraction(8, 5), Fraction(-1, 5), Fraction(8, 315),
+                          Fraction(-1, 560)]),
+                     (10, [Fraction(-5269, 1800), Fraction(5, 3), Fraction(-5, 21),
+                           Fraction(5, 126), Fraction(-5, 1008), Fraction(1, 3150)])):
+        lam = abs(w[0] + 2 * sum((-1) ** j * w[j] for j in range(1, len(w))))
+        for d in (2, 3):
+            assert binding.cfl_limit(d, order) == pytest.approx(2 / np.sqrt(d * float(lam)), rel=1e-14)
+    assert binding.cfl_limit(4, 8) < 0 and binding.cfl_limit(2, 6) < 0
+
+
+def test_paper_homogeneous_setup_is_within_the_limit():
+    """Sec. 3.1 runs the homogeneous case at c = 1500 m/s, 0.250 mm and 0.060 us
+    (the paper's CFL 0.36, see tests/golden/paper_sec31_setup.txt); that CFL
+    is stable for this leapfrog in 2D and 3D at both orders."""
+    rows = [l.split() for l in open(os.path.join(ROOT, "tests", "golden", "paper_sec31_setup.txt"))
+            if l.strip() and not l.startswith("#")]
+    for c, dx, dt, cfl in ((float(a), float(b), float(c_), float(d)) for a, b, c_, d in rows):
+        assert c * dt / dx == pytest.approx(cfl, abs=5e-3)
+        for d in (2, 3):
+            for order in (8, 10):
+                assert cfl < binding.cfl_limit(d, order)

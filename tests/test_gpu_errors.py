@@ -1,0 +1,81 @@
+"""Error handling of the C ABI on a GPU: every failure is a status code and a
+message; the CUDA context stays usable afterwards.  No test faults the GPU:
+the failures are bad arguments caught on the host or values flagged by the
+model-validation kernel."""
+import numpy as np
+import pytest
+
+from paper_2110_03345_gb300 import binding, inputs
+from _helpers import gpu_forward, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem():
+    return inputs.breast_problem((64, 80), 0.5e-3, 60, nelem=16, shots=[0, 8], nb=8,
+                                 radius=0.3 * 64 * 0.5e-3)
+
+
+def _expect(status, fn):
+    with pytest.raises(binding.FwiError) as ei:
+        fn()
+    assert ei.value.status == status, str(ei.value)
+    assert len(str(ei.value)) > 20
+
+
+def test_invalid_grid():
+    _expect(1, lambda: binding.Plan((64, 80), 0.5e-3, 60, 1e-7, order=6))
+    _expect(1, lambda: binding.Plan((64, 80), 0.5e-3, 60, 1e-7, sponge=40))
+    _expect(1, lambda: binding.Plan((64, 80), 0.5e-3, 0, 1e-7))
+    _expect(1, lambda: binding.Plan((64, 80), 0.5e-3, 60, -1.0))
+
+
+def test_point_outside_grid():
+    p = _problem()
+    plan = binding.Plan(p.shape, p.spacing, p.nt, p.dt, sponge=p.nb, c_ref=1500.0)
+    bad = p.src_xyz.copy()
+    bad[0, 0, 1] = 1.0   # 1 m: far outside
+    geo = binding.Geometry(bad, p.rec_xyz)
+    _expect(1, lambda: plan.forward(to_dev(p.vp), None, geo, to_dev(p.wavelet)))
+
+
+def test_unstable_cfl_rejected():
+    p = _problem()
+    plan = binding.Plan(p.shape, p.spacing, p.nt, p.dt * 1.5, sponge=p.nb, c_ref=1500.0)
+    geo = binding.Geometry(p.src_xyz, p.rec_xyz)
+    _expect(2, lambda: plan.forward(to_dev(p.vp), None, geo, to_dev(p.wavelet)))
+
+
+def test_budget_exceeded():
+    p = _problem()
+    plan = binding.Plan(p.shape, p.spacing, p.nt, p.dt, sponge=p.nb, c_ref=1500.0, budget=1 << 16)
+    geo = binding.Geometry(p.src_xyz, p.rec_xyz)
+    _expect(3, lambda: plan.forward(to_dev(p.vp), None, geo, to_dev(p.wavelet)))
+
+
+def test_nonfinite_and_nonpositive_model():
+    p = _problem()
+    plan = binding.Plan(p.shape, p.spacing, p.nt, p.dt, sponge=p.nb, c_ref=1500.0)
+    geo = binding.Geometry(p.src_xyz, p.rec_xyz)
+    vp = p.vp.copy()
+    vp[10, 10] = np.nan
+    _expect(5, lambda: plan.forward(to_dev(vp), None, geo, to_dev(p.wavelet)))
+    rho = p.rho.copy()
+    rho[3, 4] = 0.0
+    _expect(5, lambda: plan.forward(to_dev(p.vp), to_dev(rho), geo, to_dev(p.wavelet)))
+    # the plan and the context still work
+    tr = plan.forward(to_dev(p.vp), to_dev(p.rho), geo, to_dev(p.wavelet))
+    assert np.isfinite(tr.cpu().numpy()).all()
+
+
+def test_estimate_and_stats():
+    p = _problem()
+    plan = binding.Plan(p.shape, p.spacing, p.nt, p.dt, sponge=p.nb, c_ref=1500.0)
+    geo = binding.Geometry(p.src_xyz, p.rec_xyz)
+    est_f = plan.estimate(geo, gradient=False)
+    est_g = plan.estimate(geo, gradient=True)
+    assert 0 < est_f < est_g
+    _, plan = gpu_forward(p, plan=plan)
+    s = plan.stats()
+    assert s["fwd_launches"] == p.nt - 1 and s["batch"] == 2
+    assert s["updates"] == 2 * 64 * 80 * (p.nt - 1)
