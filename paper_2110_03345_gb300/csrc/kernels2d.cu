@@ -131,12 +131,19 @@ k_step2d(const StepParams p) {
 
     float acc[4];
     float d1x[4], d1y[4];
+    // Second derivatives in the zero-sum form sum_j w_j (u_{+j} + u_{-j} - 2 u_0):
+    // a constant field gives exactly 0 whatever the rounding of the FP32
+    // weights (with w_0 written out, the rounded weights leave a residual of
+    // ~1e-7 w_0 that acts as a spurious reaction term and shifts the phase
+    // coherently over thousands of steps).
+    float c2[4];
 #pragma unroll
     for (int ix = 0; ix < 4; ++ix) {
       const int c = 4 * NL + ix;
-      float s = (p.wx.w2[0] + p.wy.w2[0]) * v[c];
+      c2[ix] = v[c] + v[c];
+      float s = 0.f;
 #pragma unroll
-      for (int j = 1; j <= R; ++j) s = fmaf(p.wx.w2[j], v[c + j] + v[c - j], s);
+      for (int j = 1; j <= R; ++j) s = fmaf(p.wx.w2[j], (v[c + j] + v[c - j]) - c2[ix], s);
       acc[ix] = s;
       if (VD && !ADJ) {
         float d = 0.f;
@@ -150,10 +157,10 @@ k_step2d(const StepParams p) {
     for (int j = 1; j <= R; ++j) {
       const float4 a = s_u[(srow - j) * SW + tx + NL];
       const float4 c = s_u[(srow + j) * SW + tx + NL];
-      acc[0] = fmaf(p.wy.w2[j], a.x + c.x, acc[0]);
-      acc[1] = fmaf(p.wy.w2[j], a.y + c.y, acc[1]);
-      acc[2] = fmaf(p.wy.w2[j], a.z + c.z, acc[2]);
-      acc[3] = fmaf(p.wy.w2[j], a.w + c.w, acc[3]);
+      acc[0] = fmaf(p.wy.w2[j], (a.x + c.x) - c2[0], acc[0]);
+      acc[1] = fmaf(p.wy.w2[j], (a.y + c.y) - c2[1], acc[1]);
+      acc[2] = fmaf(p.wy.w2[j], (a.z + c.z) - c2[2], acc[2]);
+      acc[3] = fmaf(p.wy.w2[j], (a.w + c.w) - c2[3], acc[3]);
       if (VD && !ADJ) {
         d1y[0] = fmaf(p.wy.w1[j], c.x - a.x, d1y[0]);
         d1y[1] = fmaf(p.wy.w1[j], c.y - a.y, d1y[1]);

@@ -115,13 +115,15 @@ k_step3d(const StepParams p) {
     }
     __syncthreads();
 
+    // zero-sum form sum_j w_j (u_{+j} + u_{-j} - 2 u_0): exact 0 on constants
     const float cen = q[R];
-    float acc = (p.wx.w2[0] + p.wy.w2[0] + p.wz.w2[0]) * cen;
+    const float c2 = cen + cen;
+    float acc = 0.f;
 #pragma unroll
     for (int j = 1; j <= R; ++j) {
-      acc = fmaf(p.wx.w2[j], s_u[ty + R][tx + R + j] + s_u[ty + R][tx + R - j], acc);
-      acc = fmaf(p.wy.w2[j], s_u[ty + R + j][tx + R] + s_u[ty + R - j][tx + R], acc);
-      acc = fmaf(p.wz.w2[j], q[R + j] + q[R - j], acc);
+      acc = fmaf(p.wx.w2[j], (s_u[ty + R][tx + R + j] + s_u[ty + R][tx + R - j]) - c2, acc);
+      acc = fmaf(p.wy.w2[j], (s_u[ty + R + j][tx + R] + s_u[ty + R - j][tx + R]) - c2, acc);
+      acc = fmaf(p.wz.w2[j], (q[R + j] + q[R - j]) - c2, acc);
     }
     const long long idx = col + pz;
     if (VD && !ADJ) {
