@@ -22,10 +22,10 @@
  *  - Fields are FP32; the misfit is accumulated in FP64.
  *  - Every call returns a status; nothing aborts.  fwi_last_error() gives a
  *    message for the last failing call on the calling thread.
- *  - Work is enqueued on the plan's CUDA stream.  fwi_forward returns after
- *    enqueueing (the traces are ready when the stream reaches that point);
- *    fwi_gradient synchronises the stream before it returns (the misfit is a
- *    host value).  Both synchronise once at entry to validate the model.
+ *  - Work is enqueued on the plan's CUDA stream.  fwi_forward and
+ *    fwi_gradient synchronise that stream once after validating the model and
+ *    again before they return (results are complete, the misfit is a host
+ *    value, and non-finite results are reported).
  */
 #ifndef FWI_H
 #define FWI_H
@@ -148,6 +148,35 @@ fwi_status fwi_forward(fwi_plan* plan, const fwi_model* model, const fwi_geometr
 fwi_status fwi_gradient(fwi_plan* plan, const fwi_model* model, const fwi_geometry* geom,
                         const float* wavelet, const float* observed, double* misfit,
                         float* grad_m, float* traces_opt);
+
+/* Size of the fixed device scratch used by fwi_forward_noalloc (64 MiB). */
+#define FWI_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/* Forward modelling that allocates no device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- a service that reserves its device memory at start-up and must
+ * not allocate while serving, a plugin whose host application owns the
+ * device allocator, or code that must avoid the implicit synchronisation of
+ * cudaMalloc/cudaFree.  It computes what fwi_forward computes (same kernels,
+ * same results), without a plan: the workspace lives in one static device
+ * array of FWI_NOALLOC_SCRATCH_BYTES that every device loading this library
+ * holds until the process exits.
+ *   grid, nt, dt: as for fwi_plan_create (the sponge reference speed c_ref
+ *     <= 0 takes the maximum vp of this call's model).
+ *   model, geom, wavelet, traces: as for fwi_forward; the caller allocates the
+ *     inputs and the output.  Shots run in batches that fit the scratch.
+ *   stream: cudaStream_t to enqueue on; the call synchronises it before
+ *     returning.
+ * The first call on a device looks up the scratch address (once per device,
+ * with that device current); make that first call before any stream capture.
+ * All calls share the scratch and keep the last call's contents, so calls
+ * that overlap on the GPU race; each call clears what must start at zero.
+ * Errors: FWI_ERR_BUDGET (with the required and available sizes in
+ * fwi_last_error) when one shot of the grid does not fit the scratch, plus
+ * the errors of fwi_plan_create and fwi_forward. */
+fwi_status fwi_forward_noalloc(const fwi_grid* grid, int nt, double dt, const fwi_model* model,
+                               const fwi_geometry* geom, const float* wavelet, float* traces,
+                               void* stream);
 
 /* Message describing the last error on the calling thread ("" if none). */
 const char* fwi_last_error(void);

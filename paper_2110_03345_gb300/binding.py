@@ -25,7 +25,8 @@ STATUS = {0: "FWI_OK", 1: "FWI_ERR_INVALID_ARG", 2: "FWI_ERR_UNSTABLE_CFL", 3: "
 
 # Every symbol include/fwi.h declares (checked by the tests).
 EXPORTS = ("fwi_plan_create", "fwi_plan_set_options", "fwi_plan_stats", "fwi_plan_estimate",
-           "fwi_plan_destroy", "fwi_forward", "fwi_gradient", "fwi_last_error", "fwi_cfl_limit")
+           "fwi_plan_destroy", "fwi_forward", "fwi_gradient", "fwi_last_error", "fwi_cfl_limit",
+           "fwi_forward_noalloc")
 
 
 class FwiError(RuntimeError):
@@ -101,6 +102,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.fwi_last_error.restype = ctypes.c_char_p
         lib.fwi_cfl_limit.argtypes = [ctypes.c_int, ctypes.c_int]
         lib.fwi_cfl_limit.restype = ctypes.c_double
+        lib.fwi_forward_noalloc.argtypes = [P(CGrid), ctypes.c_int, ctypes.c_double, P(CModel),
+                                            P(CGeometry), vp, vp, vp]
+        lib.fwi_forward_noalloc.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -113,6 +117,39 @@ def _check(status: int):
 
 def cfl_limit(ndim: int, order: int) -> float:
     return float(load().fwi_cfl_limit(ndim, order))
+
+
+def make_grid(shape, spacing, order=8, sponge=20, c_ref=0.0) -> CGrid:
+    shape = tuple(int(v) for v in shape)
+    if np.isscalar(spacing):
+        spacing = (float(spacing),) * len(shape)
+    g = CGrid()
+    g.ndim = len(shape)
+    for i in range(len(shape)):
+        g.shape[i] = shape[i]
+        g.spacing[i] = float(spacing[i])
+    g.order, g.sponge, g.c_ref = int(order), int(sponge), float(c_ref)
+    return g
+
+
+def forward_noalloc(shape, spacing, nt, dt, vp, rho, geometry, wavelet, traces=None, order=8,
+                    sponge=20, c_ref=0.0, stream=None):
+    """fwi_forward_noalloc: forward modelling whose workspace is the library's
+    fixed device scratch (no device allocation inside the call).  For callers
+    that must not allocate device memory while they run; the caller still
+    provides the inputs and the traces array."""
+    import torch
+    if traces is None:
+        traces = torch.empty((geometry.nshots, geometry.nrec, int(nt)), device=vp.device,
+                             dtype=torch.float32)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    g = make_grid(shape, spacing, order, sponge, c_ref)
+    m = CModel(_ptr(vp), _ptr(rho))
+    _check(load().fwi_forward_noalloc(ctypes.byref(g), int(nt), float(dt), ctypes.byref(m),
+                                      ctypes.byref(geometry.c), _ptr(wavelet), _ptr(traces),
+                                      ctypes.c_void_p(stream.cuda_stream)))
+    return traces
 
 
 def _ptr(t):
