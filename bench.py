@@ -37,6 +37,8 @@ BYTES_PER_UPDATE = {("fwd", True): 24, ("fwd", False): 20, ("adj", True): 32, ("
 WORKLOADS = {
     "breast2d": "2D breast-like phantom 1024x1024, dx=0.1 mm, vd, o8, 128 shots x 4000 steps, 256 receivers",
     "skull3d": "3D skull phantom 256^3, dx=0.25 mm, vd, o10, 32 shots x 2000 steps, 512 receivers",
+    "uneven": "64 independent 2D problems, side U{256..1024}, 500-4000 steps, 1-16 shots, vd, o8 (forward)",
+    "serving": "Poisson stream (20 req/s) of forward/gradient requests, 75% 2D 512^2-1024^2, 25% 3D 128^3-192^3, 1000-3000 steps",
 }
 
 
@@ -53,9 +55,13 @@ def parse():
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--ckpt", type=int, default=0)
+    ap.add_argument("--spc", type=int, default=0, help="shots per CTA (TMA kernels)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving samples")
+    ap.add_argument("--nprob", type=int, default=0, help="uneven: problems (default 64)")
+    ap.add_argument("--nreq", type=int, default=0, help="serving: requests (default 650)")
     return ap.parse_args()
 
 
@@ -227,6 +233,112 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- batched and serving
+
+def uneven_batch(nprob=64, seed=4, reps=2, **kw):
+    """Uneven set of independent 2D problems: one multi-problem launch per
+    step captured in one CUDA graph, against one plan (one launch per step)
+    per problem run one after another.  Device time of the runs, inputs and
+    workspaces resident (created outside the timed region)."""
+    import torch
+    from paper_2110_03345_gb300 import binding, inputs
+    ps = inputs.config_uneven_batch(nprob=nprob, seed=seed, **kw)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev)
+    entries = [dict(shape=p.shape, spacing=p.spacing, nt=p.nt, dt=p.dt, order=p.order, sponge=p.nb,
+                    c_ref=p.c_ref, vp=f32(p.vp), rho=f32(p.rho),
+                    geometry=binding.Geometry(p.src_xyz, p.rec_xyz), wavelet=f32(p.wavelet))
+               for p in ps]
+    shots = sum(p.nshots for p in ps)
+    updates = sum(p.nshots * p.npoints * (p.nt - 1) for p in ps)
+    batch = binding.Batch(entries, use_graph=True)
+    batch.run()
+    t_b = []
+    for _ in range(reps):
+        batch.run()
+        t_b.append(batch.stats()["run_ms"] * 1e-3)
+    nodes = batch.stats()["launches"]
+    batch.close()
+    plans = []
+    for e in entries:
+        pl = binding.Plan(e["shape"], e["spacing"], e["nt"], e["dt"], order=e["order"],
+                          sponge=e["sponge"], c_ref=e["c_ref"])
+        pl.set_options(batch=e["geometry"].nshots)
+        plans.append(pl)
+    outs = [torch.empty((e["geometry"].nshots, e["geometry"].nrec, e["nt"]), device=dev) for e in entries]
+    for pl, e, o in zip(plans, entries, outs):
+        pl.forward(e["vp"], e["rho"], e["geometry"], e["wavelet"], traces=o)
+    t_p = []
+    launches_plain = 0
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for pl, e, o in zip(plans, entries, outs):
+            pl.forward(e["vp"], e["rho"], e["geometry"], e["wavelet"], traces=o)
+            launches_plain += pl.stats()["launches"]
+        torch.cuda.synchronize()
+        t_p.append(time.perf_counter() - t0)
+    for pl in plans:
+        pl.close()
+    tb, tp = min(t_b), min(t_p)
+    return {"problems": nprob, "shots": shots, "updates": updates,
+            "batched": {"shots_per_s": shots / tb, "gpts": updates / tb / 1e9, "s": tb,
+                        "graph_nodes": nodes, "launches": 1},
+            "plain": {"shots_per_s": shots / tp, "gpts": updates / tp / 1e9, "s": tp,
+                      "launches": launches_plain // reps},
+            "speedup": tp / tb}
+
+
+def serving_stream(nreq=650, warm=50, seed=5, lanes=4, rate=20.0, **kw):
+    """Poisson request stream through the serving loop (continuous admission
+    onto `lanes` concurrent streams under an HBM budget) and through the plain
+    solver (one request at a time, first come first served).  Latency =
+    completion - arrival (host clock); the first `warm` requests are not
+    counted."""
+    import torch
+    from paper_2110_03345_gb300 import binding, inputs, serve
+    dev = torch.device("cuda", torch.cuda.current_device())
+    f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev)
+    stream = inputs.config_serving(nreq=nreq, seed=seed, rate=rate, **kw)
+    models = {}
+    reqs = []
+    for t, kind, p in stream:
+        key = (p.shape, id(p))
+        vp, rho = f32(p.vp), f32(p.rho)          # device-resident models
+        obs = None
+        if kind == "gradient":
+            obs = torch.zeros((p.nshots, p.rec_xyz.shape[0], p.nt), device=dev)
+        reqs.append((t, dict(shape=p.shape, spacing=p.spacing, nt=p.nt, dt=p.dt, vp=vp, rho=rho,
+                             geometry=binding.Geometry(p.src_xyz, p.rec_xyz), wavelet=f32(p.wavelet),
+                             observed=obs, order=p.order, sponge=p.nb, c_ref=p.c_ref)))
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.7 * free)
+
+    def play(nlanes):
+        server = serve.Server(budget_bytes=budget, lanes=nlanes, request_cap=budget // 4)
+        objs = [serve.Request(**r) for _, r in reqs]
+        futs = []
+        t0 = time.perf_counter()
+        for (t, _), o in zip(reqs, objs):
+            now = time.perf_counter() - t0
+            if now < t:
+                time.sleep(t - now)
+            futs.append(server.submit(o))
+        for f in futs:
+            f.result()
+        server.drain()
+        server.close()
+        counted = objs[warm:] if len(objs) > warm else objs
+        st = serve.latency_stats(counted)
+        st["peak_running"] = server.peak_running
+        return st
+
+    cont = play(lanes)
+    plain = play(1)
+    return {"requests": nreq, "warmup": warm, "rate_per_s": rate, "lanes": lanes,
+            "continuous": cont, "plain": plain}
+
+
 # ---------------------------------------------------------------- GPU arm
 
 def run_mine(args):
@@ -264,7 +376,8 @@ def run_mine(args):
     obs = plan.forward(torch.from_numpy(f32(p.vp_true)).to(dev), rho, geo, wav)
     obs_h = obs.cpu().pin_memory()
     grad = torch.empty(p.shape, device=dev, dtype=torch.float32)
-    plan.set_options(batch=args.batch, tile=args.tile, ckpt_every=args.ckpt, profile=True)
+    plan.set_options(batch=args.batch, tile=args.tile, ckpt_every=args.ckpt, profile=True,
+                     shots_per_cta=args.spc)
 
     for _ in range(args.warmup):
         plan.gradient(vp, rho, geo, wav, obs, grad=grad)
@@ -336,6 +449,12 @@ def run_mine(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(p, args.cpu_seconds)
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        # reduced samples of the uneven-batch and serving patterns (full size:
+        # --workload uneven / serving)
+        extras["batched"] = uneven_batch(nprob=16, seed=4, reps=1)
+        extras["serving"] = serving_stream(nreq=80, warm=10, seed=5)
 
     if rank == 0:
         line = {
@@ -356,6 +475,7 @@ def run_mine(args):
             "gpu_launches": int(acc["launches"]),
             "clocks": clk,
         }
+        line.update(extras)
         print(json.dumps(line))
     plan.close()
     if dist is not None:
@@ -363,10 +483,32 @@ def run_mine(args):
     return 0
 
 
+def run_extra_workload(args):
+    """--workload uneven | serving: one JSON line for that workload alone."""
+    import torch
+    torch.cuda.set_device(0)
+    if args.workload == "uneven":
+        r = uneven_batch(nprob=args.nprob or 64)
+        line = {"metric": "shots/s (uneven batch, one CUDA graph vs one plan per problem)",
+                "value": r["batched"]["shots_per_s"], "unit": "shots/s", "n_gpus": 1,
+                "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOADS["uneven"]}, "uneven": r}
+    else:
+        r = serving_stream(nreq=args.nreq or 650)
+        line = {"metric": "p99 latency (s) and shots/s, continuous admission vs plain",
+                "value": r["continuous"]["p99_s"], "unit": "s", "n_gpus": 1,
+                "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOADS["serving"]}, "serving": r}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in ("uneven", "serving"):
+        return run_extra_workload(args)
     return run_mine(args)
 
 

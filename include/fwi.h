@@ -61,9 +61,15 @@ typedef struct {
 
 /* Medium (Sec. 2.3 Listing 6): sound speed and optional density. */
 typedef struct {
-    const float* vp;    /* device [N] m/s, N = prod(shape); > 0 and finite */
+    const float* vp;    /* device [N], N = prod(shape): the sound speed in m/s, or
+                           the squared slowness m = 1/vp^2 in s^2/m^2 when
+                           param = FWI_PARAM_M; > 0 and finite */
     const float* rho;   /* device [N] kg/m^3, > 0; NULL selects constant density */
+    int param;          /* FWI_PARAM_VP (0) or FWI_PARAM_M (1) */
 } fwi_model;
+
+#define FWI_PARAM_VP 0
+#define FWI_PARAM_M 1
 
 /* Acquisition geometry (Sec. 2.3 Listings 7-8): nshots shots, each with nsrc
  * point sources; nrec receivers shared by every shot.  Points must lie inside
@@ -85,9 +91,12 @@ typedef struct {
     int ckpt_every;     /* gradient: 0 = full history if it fits, else sqrt(2 nt)
                            checkpoints; > 0 forces checkpoints every ckpt_every
                            steps; -1 forces the full history */
-    int tile;           /* kernel tile variant (0: default; see fwi_plan_stats) */
+    int tile;           /* kernel variant: -1 = default; 2D: 0-3 shared-memory staged,
+                           one shot per CTA; 4-7 TMA-staged, shots looped inside
+                           a CTA (same four tile shapes); 3D: 0-3 */
     int profile;        /* 1: time every stencil launch with CUDA events */
     int use_graphs;     /* 1: capture the time loop into CUDA graphs */
+    int shots_per_cta;  /* TMA variants: shots per CTA (0: chosen from the SM count) */
 } fwi_options;
 
 /* Counters of the last forward/gradient call on a plan. */
@@ -148,6 +157,69 @@ fwi_status fwi_forward(fwi_plan* plan, const fwi_model* model, const fwi_geometr
 fwi_status fwi_gradient(fwi_plan* plan, const fwi_model* model, const fwi_geometry* geom,
                         const float* wavelet, const float* observed, double* misfit,
                         float* grad_m, float* traces_opt);
+
+/* The gradient of fwi_gradient split in its two halves, for reverse-mode
+ * automatic differentiation (Sec. 2.2: a forward evaluation that records what
+ * the adjoint needs, then the adjoint sweep).
+ *
+ * fwi_misfit_forward runs the forward propagation of every shot, computes the
+ * misfit (host out) and optionally the traces, and keeps in the plan what the
+ * adjoint needs: for every shot either the history h^n or, when that does not
+ * fit the budget (or ckpt_every > 0), checkpoints (u^n, u^{n-1}) every K
+ * steps (default K = ceil(sqrt(2 nt))), plus the residual traces.  The
+ * model, wavelet and observed device arrays must stay allocated and unchanged
+ * until fwi_misfit_backward; any other call on the plan drops the state.
+ *
+ * fwi_misfit_backward runs the adjoint propagation of those shots with the
+ * imaging condition, recomputing each checkpoint segment forward first, and
+ * writes grad_m as fwi_gradient does.  It can be called once per forward. */
+fwi_status fwi_misfit_forward(fwi_plan* plan, const fwi_model* model, const fwi_geometry* geom,
+                              const float* wavelet, const float* observed, double* misfit,
+                              float* traces_opt);
+fwi_status fwi_misfit_backward(fwi_plan* plan, float* grad_m);
+
+/* ---- Uneven batches (many independent problems in one CUDA graph) ---- */
+
+/* One independent forward-modelling problem of a batch: its own grid, time
+ * axis, model, geometry, wavelets (device [nshots][nsrc][nt]) and traces
+ * (device out [nshots][nrec][nt]); the arrays follow fwi_forward. */
+typedef struct {
+    fwi_grid grid;
+    int nt;
+    double dt;
+    fwi_model model;
+    fwi_geometry geom;
+    const float* wavelet;
+    float* traces;
+} fwi_problem;
+
+typedef struct {
+    int problems;
+    int64_t units;       /* (problem, tile, shot) work units of one step */
+    int64_t launches;    /* kernel launches (graph nodes) of one run */
+    int64_t updates;     /* grid-point updates of one run */
+    double run_ms;       /* device time of the last fwi_batch_run */
+} fwi_batch_stats;
+
+typedef struct fwi_batch fwi_batch;
+
+/* Prepare a batch of 2D problems that share the stencil order and density
+ * mode but differ in grid, time axis, shot count and geometry (the shot-level
+ * parallelism of Sec. 2.5 / 3.3, applied to independent problems on one
+ * GPU).  Each problem's model is validated (CFL) and prepared, its tables
+ * built and its workspace allocated (all its shots at once; the total must
+ * fit hbm_budget_bytes, 0 = free memory).  Every time step of every problem
+ * then runs in ONE launch of a multi-problem kernel per step (units =
+ * problem x tile x shot; problems that have finished drop out), and with
+ * use_graph = 1 the whole sequence, including the final sampling and trace
+ * transposition, is captured once into a CUDA graph.  The problem arrays
+ * must stay valid until fwi_batch_destroy. */
+fwi_status fwi_batch_create(fwi_batch** batch, int nprob, const fwi_problem* probs,
+                            size_t hbm_budget_bytes, void* stream, int use_graph);
+/* Run the batch (one graph launch); synchronises the stream. */
+fwi_status fwi_batch_run(fwi_batch* batch);
+fwi_status fwi_batch_stats_get(const fwi_batch* batch, fwi_batch_stats* out);
+void fwi_batch_destroy(fwi_batch* batch);
 
 /* Size of the fixed device scratch used by fwi_forward_noalloc (64 MiB). */
 #define FWI_NOALLOC_SCRATCH_BYTES (64u << 20)

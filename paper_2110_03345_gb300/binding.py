@@ -26,7 +26,8 @@ STATUS = {0: "FWI_OK", 1: "FWI_ERR_INVALID_ARG", 2: "FWI_ERR_UNSTABLE_CFL", 3: "
 # Every symbol include/fwi.h declares (checked by the tests).
 EXPORTS = ("fwi_plan_create", "fwi_plan_set_options", "fwi_plan_stats", "fwi_plan_estimate",
            "fwi_plan_destroy", "fwi_forward", "fwi_gradient", "fwi_last_error", "fwi_cfl_limit",
-           "fwi_forward_noalloc")
+           "fwi_forward_noalloc", "fwi_misfit_forward", "fwi_misfit_backward",
+           "fwi_batch_create", "fwi_batch_run", "fwi_batch_stats_get", "fwi_batch_destroy")
 
 
 class FwiError(RuntimeError):
@@ -41,8 +42,11 @@ class CGrid(ctypes.Structure):
                 ("sponge", ctypes.c_int), ("c_ref", ctypes.c_double)]
 
 
+PARAM_VP, PARAM_M = 0, 1
+
+
 class CModel(ctypes.Structure):
-    _fields_ = [("vp", ctypes.c_void_p), ("rho", ctypes.c_void_p)]
+    _fields_ = [("vp", ctypes.c_void_p), ("rho", ctypes.c_void_p), ("param", ctypes.c_int)]
 
 
 class CGeometry(ctypes.Structure):
@@ -51,9 +55,22 @@ class CGeometry(ctypes.Structure):
                 ("rec_xyz", ctypes.POINTER(ctypes.c_double))]
 
 
+class CProblem(ctypes.Structure):
+    _fields_ = [("grid", CGrid), ("nt", ctypes.c_int), ("dt", ctypes.c_double),
+                ("model", CModel), ("geom", CGeometry), ("wavelet", ctypes.c_void_p),
+                ("traces", ctypes.c_void_p)]
+
+
+class CBatchStats(ctypes.Structure):
+    _fields_ = [("problems", ctypes.c_int), ("units", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("updates", ctypes.c_int64),
+                ("run_ms", ctypes.c_double)]
+
+
 class COptions(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int), ("ckpt_every", ctypes.c_int), ("tile", ctypes.c_int),
-                ("profile", ctypes.c_int), ("use_graphs", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("use_graphs", ctypes.c_int),
+                ("shots_per_cta", ctypes.c_int)]
 
 
 class CStats(ctypes.Structure):
@@ -105,6 +122,19 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.fwi_forward_noalloc.argtypes = [P(CGrid), ctypes.c_int, ctypes.c_double, P(CModel),
                                             P(CGeometry), vp, vp, vp]
         lib.fwi_forward_noalloc.restype = ctypes.c_int
+        lib.fwi_misfit_forward.argtypes = [vp, P(CModel), P(CGeometry), vp, vp, P(ctypes.c_double), vp]
+        lib.fwi_misfit_forward.restype = ctypes.c_int
+        lib.fwi_misfit_backward.argtypes = [vp, vp]
+        lib.fwi_misfit_backward.restype = ctypes.c_int
+        lib.fwi_batch_create.argtypes = [P(vp), ctypes.c_int, P(CProblem), ctypes.c_size_t, vp,
+                                         ctypes.c_int]
+        lib.fwi_batch_create.restype = ctypes.c_int
+        lib.fwi_batch_run.argtypes = [vp]
+        lib.fwi_batch_run.restype = ctypes.c_int
+        lib.fwi_batch_stats_get.argtypes = [vp, P(CBatchStats)]
+        lib.fwi_batch_stats_get.restype = ctypes.c_int
+        lib.fwi_batch_destroy.argtypes = [vp]
+        lib.fwi_batch_destroy.restype = None
         _lib = lib
         return lib
 
@@ -225,9 +255,12 @@ class Plan:
 
     __del__ = close
 
-    def set_options(self, batch=0, ckpt_every=0, tile=0, profile=False, use_graphs=False):
+    def set_options(self, batch=0, ckpt_every=0, tile=0, profile=False, use_graphs=False,
+                    shots_per_cta=0):
+        """tile: 0 default; 2D 1-4 shared-memory staged (one shot per CTA), 5-8
+        TMA-staged with shots looped inside a CTA; 3D 1-4."""
         self._opts = COptions(int(batch), int(ckpt_every), int(tile), int(bool(profile)),
-                              int(bool(use_graphs)))
+                              int(bool(use_graphs)), int(shots_per_cta))
         _check(load().fwi_plan_set_options(self._h, ctypes.byref(self._opts)))
 
     def stats(self) -> dict:
@@ -241,8 +274,8 @@ class Plan:
                                         ctypes.byref(b)))
         return int(b.value)
 
-    def _model(self, vp, rho):
-        return CModel(_ptr(vp), _ptr(rho))
+    def _model(self, vp, rho, param=PARAM_VP):
+        return CModel(_ptr(vp), _ptr(rho), int(param))
 
     def forward(self, vp, rho, geometry: Geometry, wavelet, traces=None):
         """Traces [nshots][nrec][nt] (CUDA float32) for the given wavelets."""
@@ -254,6 +287,36 @@ class Plan:
         _check(load().fwi_forward(self._h, ctypes.byref(m), ctypes.byref(geometry.c),
                                   _ptr(wavelet), self.nt, self.dt, _ptr(traces)))
         return traces
+
+    def misfit_forward(self, vp, rho, geometry: Geometry, wavelet, observed, traces=False,
+                       param=PARAM_VP):
+        """J (and the traces if asked); keeps what misfit_backward needs in the plan.
+        param=PARAM_M: `vp` holds the squared slowness m = 1/vp^2 instead."""
+        import torch
+        tr = None
+        if traces is True:
+            tr = torch.empty((geometry.nshots, geometry.nrec, self.nt), device=vp.device,
+                             dtype=torch.float32)
+        J = ctypes.c_double()
+        m = self._model(vp, rho, param)
+        self._kept = (vp, rho, geometry, wavelet, observed)   # must outlive the backward
+        _check(load().fwi_misfit_forward(self._h, ctypes.byref(m), ctypes.byref(geometry.c),
+                                         _ptr(wavelet), _ptr(observed), ctypes.byref(J), _ptr(tr)))
+        return J.value, tr
+
+    def misfit_backward(self, grad=None):
+        """Gradient w.r.t. m = 1/vp^2 of the misfit of the last misfit_forward."""
+        import torch
+        if getattr(self, "_kept", None) is None:
+            raise FwiError(1, "no pending misfit_forward on this plan")
+        vp = self._kept[0]
+        if grad is None:
+            grad = torch.empty(vp.shape, device=vp.device, dtype=torch.float32)
+        try:
+            _check(load().fwi_misfit_backward(self._h, _ptr(grad)))
+        finally:
+            self._kept = None
+        return grad
 
     def gradient(self, vp, rho, geometry: Geometry, wavelet, observed, grad=None, traces=False):
         """(J, grad_m, traces or None): L2 misfit and its gradient w.r.t. m = 1/vp^2."""
@@ -272,3 +335,57 @@ class Plan:
                                    _ptr(wavelet), _ptr(observed), ctypes.byref(J), _ptr(grad),
                                    _ptr(tr)))
         return J.value, grad, tr
+
+
+class Batch:
+    """fwi_batch: many independent 2D problems advanced together, one
+    multi-problem launch per time step, optionally one CUDA graph per run.
+
+    problems: list of dicts with keys shape, spacing, nt, dt, order, sponge,
+    c_ref, vp, rho (CUDA tensors or None), geometry (Geometry), wavelet (CUDA
+    tensor [shots][src][nt]).  Traces are allocated here (self.traces)."""
+
+    def __init__(self, problems, budget=0, stream=None, use_graph=True):
+        import torch
+        lib = load()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self._keep = []
+        self.traces = []
+        arr = (CProblem * len(problems))()
+        for i, pr in enumerate(problems):
+            geo = pr["geometry"]
+            tr = torch.empty((geo.nshots, geo.nrec, int(pr["nt"])), device=pr["vp"].device,
+                             dtype=torch.float32)
+            self.traces.append(tr)
+            self._keep.append((pr["vp"], pr.get("rho"), geo, pr["wavelet"], tr))
+            arr[i].grid = make_grid(pr["shape"], pr["spacing"], pr.get("order", 8),
+                                    pr.get("sponge", 20), pr.get("c_ref", 0.0))
+            arr[i].nt = int(pr["nt"])
+            arr[i].dt = float(pr["dt"])
+            arr[i].model = CModel(_ptr(pr["vp"]), _ptr(pr.get("rho")), 0)
+            arr[i].geom = geo.c
+            arr[i].wavelet = _ptr(pr["wavelet"])
+            arr[i].traces = _ptr(tr)
+        self._arr = arr
+        h = ctypes.c_void_p()
+        _check(lib.fwi_batch_create(ctypes.byref(h), len(problems), arr, int(budget),
+                                    ctypes.c_void_p(stream.cuda_stream), int(bool(use_graph))))
+        self._h = h
+
+    def run(self):
+        _check(load().fwi_batch_run(self._h))
+        return self.traces
+
+    def stats(self) -> dict:
+        s = CBatchStats()
+        _check(load().fwi_batch_stats_get(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in CBatchStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().fwi_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    __del__ = close

@@ -13,8 +13,9 @@ namespace fwi {
 namespace {
 
 // stats[0] = max vp bits, stats[1] = min vp bits, stats[2] = bad-value count
+// vp holds the sound speed (param 0) or the squared slowness m = 1/vp^2 (param 1).
 __global__ void k_model_prep(Layout L, const float* __restrict__ vp, const float* __restrict__ rho,
-                             double dt, float* __restrict__ kf, float* __restrict__ lnr,
+                             double dt, int param, float* __restrict__ kf, float* __restrict__ lnr,
                              unsigned int* __restrict__ stats) {
   const long long N = (long long)L.nx * L.ny * L.nz;
   unsigned int vmax = 0u, vmin = 0x7f800000u, bad = 0u;
@@ -25,13 +26,15 @@ __global__ void k_model_prep(Layout L, const float* __restrict__ vp, const float
     const int y = (int)(t % L.ny);
     const int z = (int)(t / L.ny);
     const long long pi = L.index(z, y, x);
-    const float c = vp[i];
-    if (!(c > 0.f) || !isfinite(c)) {
+    const float in = vp[i];
+    if (!(in > 0.f) || !isfinite(in)) {
       ++bad;
       kf[pi] = 0.f;
     } else {
-      const double cd = (double)c * dt;
-      kf[pi] = (float)(cd * cd);
+      // k = (vp dt)^2 = dt^2 / m
+      const double k = param ? dt * dt / (double)in : ((double)in * dt) * ((double)in * dt);
+      kf[pi] = (float)k;
+      const float c = param ? (float)(1.0 / sqrt((double)in)) : in;
       const unsigned int bits = __float_as_uint(c);
       vmax = max(vmax, bits);
       vmin = min(vmin, bits);
@@ -172,16 +175,20 @@ __global__ void k_sum_partials(const double* __restrict__ partials, int n, doubl
 }
 
 __global__ void k_image_only(const float4* __restrict__ lam, const float4* __restrict__ hist,
-                             float4* __restrict__ g, long long n4) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
+                             float4* __restrict__ g, long long f4, int nb, int S) {
+  // f4: float4 per field; slots in fixed order so the sum is deterministic
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < f4;
        i += (long long)gridDim.x * blockDim.x) {
-    const float4 l = lam[i], h = hist[i];
-    float4 v = g[i];
-    v.x = fmaf(-l.x, h.x, v.x);
-    v.y = fmaf(-l.y, h.y, v.y);
-    v.z = fmaf(-l.z, h.z, v.z);
-    v.w = fmaf(-l.w, h.w, v.w);
-    g[i] = v;
+    for (int b = 0; b < nb; ++b) {
+      const float4 l = lam[b * f4 + i], h = hist[b * f4 + i];
+      float4* gp = g + (long long)(b / S) * f4 + i;
+      float4 v = *gp;
+      v.x = fmaf(-l.x, h.x, v.x);
+      v.y = fmaf(-l.y, h.y, v.y);
+      v.z = fmaf(-l.z, h.z, v.z);
+      v.w = fmaf(-l.w, h.w, v.w);
+      *gp = v;
+    }
   }
 }
 
@@ -215,9 +222,10 @@ int grid_for(long long n, int threads) {
 }  // namespace
 
 cudaError_t launch_model_prep(const Layout& L, const float* vp, const float* rho, double dt,
-                              float* kf, float* lnr, unsigned int* stats, cudaStream_t st) {
+                              int param, float* kf, float* lnr, unsigned int* stats,
+                              cudaStream_t st) {
   const long long N = (long long)L.nx * L.ny * L.nz;
-  k_model_prep<<<grid_for(N, 256), 256, 0, st>>>(L, vp, rho, dt, kf, lnr, stats);
+  k_model_prep<<<grid_for(N, 256), 256, 0, st>>>(L, vp, rho, dt, param, kf, lnr, stats);
   return cudaGetLastError();
 }
 
@@ -265,11 +273,11 @@ cudaError_t launch_sum_partials(const double* partials, int n, double* out, cuda
 }
 
 cudaError_t launch_image_only(const Layout& L, const float* lam, const float* hist, float* g,
-                              int B, cudaStream_t st) {
-  const long long n4 = (long long)B * L.fstride / 4;
-  k_image_only<<<grid_for(n4, 256), 256, 0, st>>>(reinterpret_cast<const float4*>(lam),
+                              int nb, int S, cudaStream_t st) {
+  const long long f4 = L.fstride / 4;
+  k_image_only<<<grid_for(f4, 256), 256, 0, st>>>(reinterpret_cast<const float4*>(lam),
                                                   reinterpret_cast<const float4*>(hist),
-                                                  reinterpret_cast<float4*>(g), n4);
+                                                  reinterpret_cast<float4*>(g), f4, nb, S);
   return cudaGetLastError();
 }
 

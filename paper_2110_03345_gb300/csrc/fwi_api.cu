@@ -10,6 +10,8 @@
 #include "fwi.h"
 #include "fwi_internal.cuh"
 
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -62,6 +64,11 @@ int round_up(int v, int a) { return (v + a - 1) / a * a; }
 
 }  // namespace
 
+namespace {
+struct SavedGrad;
+void delete_saved(SavedGrad* s);
+}  // namespace
+
 struct fwi_plan {
   fwi_grid grid{};
   int nt = 0;
@@ -69,6 +76,7 @@ struct fwi_plan {
   size_t budget = 0;
   cudaStream_t st = nullptr;
   int device = 0;
+  int nsm = 152;            // SM count of the device
   fwi_options opt{};
   fwi_stats stats{};
   Layout L{};
@@ -93,6 +101,9 @@ struct fwi_plan {
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_kind;  // 0 forward, 1 adjoint
   size_t ev_used = 0;
+  SavedGrad* saved = nullptr;  // state kept by fwi_misfit_forward for fwi_misfit_backward
+  bool fixed_memory = false;   // buffers supplied by the caller: never allocate
+  ~fwi_plan() { delete_saved(saved); }
 };
 
 namespace {
@@ -110,15 +121,19 @@ struct Carve {
   }
 };
 
+// Plan memory comes from the stream-ordered allocator on the plan's stream:
+// unlike cudaMalloc/cudaFree it never synchronises the device, so plans on
+// different streams (concurrent requests) do not serialise each other.
 fwi_status ensure_arena(fwi_plan* P, size_t bytes) {
   if (bytes <= P->arena_cap) return FWI_OK;
+  if (P->fixed_memory)
+    return fail(FWI_ERR_BUDGET, "workspace of " + std::to_string(bytes) + " bytes exceeds the fixed scratch");
   if (P->arena) {
-    CUDA_TRY(cudaStreamSynchronize(P->st));
-    CUDA_TRY(cudaFree(P->arena));
+    CUDA_TRY(cudaFreeAsync(P->arena, P->st));
     P->arena = nullptr;
     P->arena_cap = 0;
   }
-  cudaError_t e = cudaMalloc(&P->arena, bytes);
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&P->arena), bytes, P->st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     P->arena = nullptr;
@@ -131,13 +146,14 @@ fwi_status ensure_arena(fwi_plan* P, size_t bytes) {
 
 fwi_status ensure_tab(fwi_plan* P, size_t bytes) {
   if (bytes <= P->tab_cap) return FWI_OK;
+  if (P->fixed_memory)
+    return fail(FWI_ERR_BUDGET, "tables of " + std::to_string(bytes) + " bytes exceed the fixed scratch");
   if (P->tab) {
-    CUDA_TRY(cudaStreamSynchronize(P->st));
-    CUDA_TRY(cudaFree(P->tab));
+    CUDA_TRY(cudaFreeAsync(P->tab, P->st));
     P->tab = nullptr;
   }
   bytes = std::max(bytes, (size_t)1 << 20);
-  CUDA_TRY(cudaMalloc(&P->tab, bytes));
+  CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&P->tab), bytes, P->st));
   P->tab_cap = bytes;
   return FWI_OK;
 }
@@ -185,10 +201,10 @@ struct TileGeo {
   int ntiles() const { return gx * gy * nzc; }
 };
 
-TileGeo tile_geo(const fwi_plan* P, int tile) {
+TileGeo tile_geo(const fwi_plan* P, int tile, bool tma) {
   TileGeo T{};
   if (P->grid.ndim == 2) {
-    const Tile2 t = tile2_variant(tile);
+    const Tile2 t = tma ? tile2_tma_variant(tile) : tile2_variant(tile);
     T.tx = TILE_X;
     T.ty = t.ry * t.by;
     T.zc = 1;
@@ -371,8 +387,9 @@ fwi_status build_sponge(fwi_plan* P) {
         v[i] = (float)(smax * r * r * P->dt * 0.5);
       }
     }
-    if (!*dst[a]) CUDA_TRY(cudaMalloc(dst[a], v.size() * sizeof(float)));
-    CUDA_TRY(cudaMemcpy(*dst[a], v.data(), v.size() * sizeof(float), cudaMemcpyHostToDevice));
+    if (!*dst[a]) CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(dst[a]), v.size() * sizeof(float), P->st));
+    CUDA_TRY(cudaMemcpyAsync(*dst[a], v.data(), v.size() * sizeof(float), cudaMemcpyHostToDevice, P->st));
+    CUDA_TRY(cudaStreamSynchronize(P->st));   // v is a host temporary
   }
   P->sponge_ready = true;
   return FWI_OK;
@@ -409,9 +426,31 @@ struct Plan {
   int K = 0;            // 0: full history; else checkpoint interval
   int nck = 0;          // checkpoints per shot
   bool gradient = false;
-  int tile = 0;
+  int tile = 0;         // resolved variant id (as in fwi_options.tile, never 0)
+  int shape = 0;        // tile shape 0..3
+  bool tma = false;     // 2D TMA-staged kernels with shots looped inside a CTA
+  int S = 1;            // shots per CTA; gradient slot of shot s is s / S
+  bool split = false;   // forward and adjoint in separate calls: keep every batch's state
+  int nbatches = 1;
   size_t bytes = 0;
 };
+
+// Resolve fwi_options.tile: 0 selects the default variant.
+bool resolve_tile(const fwi_plan* P, int t, int* id, int* shape, bool* tma) {
+  if (P->grid.ndim == 2) {
+    if (t == 0) t = 6;   // TMA-staged, one row per thread, 128 x 16 tiles
+    if (t < 1 || t > 2 * NUM_TILE2) return false;
+    *tma = t > NUM_TILE2;
+    *shape = (t - 1) % NUM_TILE2;
+  } else {
+    if (t == 0) t = 1;
+    if (t < 1 || t > NUM_TILE3) return false;
+    *tma = false;
+    *shape = t - 1;
+  }
+  *id = t;
+  return true;
+}
 
 size_t field_bytes(const fwi_plan* P) { return (size_t)P->L.fstride * sizeof(float); }
 
@@ -436,21 +475,43 @@ size_t slot_bytes(const fwi_plan* P, const fwi_geometry* g, bool grad, int K) {
   return b;
 }
 
+// Split gradient: bytes kept per shot between the two calls (checkpoints or
+// history, and the residual traces), and the per-slot working set.
+size_t persist_bytes_per_shot(const fwi_plan* P, const fwi_geometry* g, int K) {
+  const size_t f = align_up(field_bytes(P), 256);
+  const size_t traces = (size_t)P->nt * g->nrec * sizeof(float);
+  if (K == 0) return (size_t)std::max(P->nt - 1, 1) * f + traces;
+  const int nck = (P->nt - 2) / K + 1;
+  return 2 * (size_t)nck * f + traces;
+}
+
+size_t split_slot_bytes(const fwi_plan* P, int K) {
+  const size_t f = align_up(field_bytes(P), 256);
+  return 5 * f + (K ? (size_t)K * f : 0) + 4096;
+}
+
 size_t fixed_bytes(const fwi_plan* P, const fwi_geometry* g, bool vd, int B) {
   const size_t misfit = align_up((size_t)misfit_blocks(B, g->nrec, P->nt) * 8, 256);
   return model_bytes(P, vd) + misfit + (4u << 20);
 }
 
-fwi_status choose_plan(const fwi_plan* P, const fwi_geometry* g, bool vd, bool grad, Plan& out) {
+fwi_status choose_plan(const fwi_plan* P, const fwi_geometry* g, bool vd, bool grad, Plan& out,
+                       bool split = false) {
   const int ns = g->nshots;
   const size_t budget = P->budget;
   const int K_auto = std::max(2, (int)std::ceil(std::sqrt(2.0 * std::max(P->nt, 2))));
   const long long N = (long long)P->L.nx * P->L.ny * P->L.nz;
   const int B_fill = (int)std::max(1LL, (8LL << 20) / std::max(N, 1LL));  // slots that fill the GPU
   auto fit = [&](int K) {
-    const size_t fixed = fixed_bytes(P, g, vd, ns);
+    size_t fixed = fixed_bytes(P, g, vd, ns);
+    size_t per = slot_bytes(P, g, grad, K);
+    if (split) {
+      // nbatches * B <= ns + B - 1 shots of kept state
+      const size_t keep = persist_bytes_per_shot(P, g, K);
+      fixed += (size_t)ns * keep;
+      per = split_slot_bytes(P, K) + keep;
+    }
     if (budget <= fixed) return 0;
-    const size_t per = slot_bytes(P, g, grad, K);
     return (int)std::min<size_t>((size_t)ns, (budget - fixed) / per);
   };
   int K = 0;
@@ -472,8 +533,27 @@ fwi_status choose_plan(const fwi_plan* P, const fwi_geometry* g, bool vd, bool g
   out.K = K;
   out.nck = K ? (P->nt - 2) / K + 1 : 0;
   out.gradient = grad;
-  out.tile = P->opt.tile;
+  out.split = split;
+  out.nbatches = (ns + B - 1) / B;
+  if (!resolve_tile(P, P->opt.tile, &out.tile, &out.shape, &out.tma))
+    return fail(FWI_ERR_INVALID_ARG, "tile variant out of range");
+  out.S = 1;
+  if (out.tma) {
+    if (P->opt.shots_per_cta > 0) {
+      out.S = std::min(P->opt.shots_per_cta, B);
+    } else {
+      // six shots share a tile's model loads and gradient update; at least
+      // four waves of CTAs (two resident per SM) keep the SMs balanced
+      const int T = tile_geo(P, out.shape, true).ntiles();
+      int S = std::min(B, 6);
+      while (S > 1 && (long long)T * ((B + S - 1) / S) < 8LL * P->nsm) --S;
+      out.S = S;
+    }
+  }
   out.bytes = fixed_bytes(P, g, vd, B) + (size_t)B * slot_bytes(P, g, grad, K);
+  if (split)
+    out.bytes = fixed_bytes(P, g, vd, B) + (size_t)B * split_slot_bytes(P, K) +
+                (size_t)out.nbatches * B * persist_bytes_per_shot(P, g, K) + (4u << 20);
   return FWI_OK;
 }
 
@@ -500,18 +580,57 @@ void carve_work(fwi_plan* P, const Plan& pl, const fwi_geometry* g, bool vd, Car
   W.partials = C.take<double>(W.npartials);
   W.U0 = C.take<float>(fs * B);
   W.U1 = C.take<float>(fs * B);
-  W.D = C.take<float>((size_t)P->nt * B * g->nrec);
+  const size_t nbk = pl.split ? (size_t)pl.nbatches : 1;   // batches whose state is kept
+  W.D = C.take<float>((size_t)P->nt * B * g->nrec * nbk);
   if (pl.gradient) {
     W.G = C.take<float>(fs * B);
     if (pl.K == 0) {
-      W.H = C.take<float>(fs * B * (size_t)std::max(P->nt - 1, 1));
+      W.H = C.take<float>(fs * B * (size_t)std::max(P->nt - 1, 1) * nbk);
     } else {
       W.F0 = C.take<float>(fs * B);
       W.F1 = C.take<float>(fs * B);
-      W.CK = C.take<float>(fs * B * 2 * (size_t)pl.nck);
+      W.CK = C.take<float>(fs * B * 2 * (size_t)pl.nck * nbk);
       W.H = C.take<float>(fs * B * (size_t)pl.K);
     }
   }
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no -lcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 3D tensor map over nslots padded 2D fields: dims (x = sx, y = rows, slot),
+// box = one tile plus its halo of one slot.
+fwi_status make_tensor_map(const fwi_plan* P, const float* base, int nslots, int shape,
+                           CUtensorMap* out) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  int bx = 0, by = 0;
+  tma_box2d(P->R, shape, &bx, &by);
+  const cuuint64_t dims[3] = {(cuuint64_t)P->L.sx, (cuuint64_t)P->L.rows, (cuuint64_t)nslots};
+  const cuuint64_t strides[2] = {(cuuint64_t)P->L.sx * sizeof(float),
+                                 (cuuint64_t)P->L.fstride * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1u};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  const CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+  return FWI_OK;
 }
 
 struct Call {
@@ -527,7 +646,13 @@ struct Call {
   const int* smp_node = nullptr;
   const float* smp_w = nullptr;
   DevTable rec_tab;   // adjoint residual injection, per slot
+  float* D = nullptr; // trace / residual buffer [nt][B][nrec] of the current batch
   int ncorner = 4;
+  struct MapEnt {
+    const float* base;
+    CUtensorMap map;
+  };
+  std::vector<MapEnt> maps;   // TMA descriptors of the wavefield buffers
   int64_t launches = 0;
   int64_t fwd_launches = 0, adj_launches = 0;
   int64_t fwd_points = 0, adj_points = 0;
@@ -581,8 +706,16 @@ StepParams base_params(Call& c) {
 }
 
 long long launch_threads(const Call& c, int B) {
-  const int by = (c.P->grid.ndim == 2) ? tile2_variant(c.pl.tile).by : tile3_variant(c.pl.tile).by;
-  return (long long)c.T.ntiles() * B * 32 * by;
+  const int by = (c.P->grid.ndim == 3) ? tile3_variant(c.pl.shape).by
+                 : c.pl.tma ? tile2_tma_variant(c.pl.shape).by : tile2_variant(c.pl.shape).by;
+  const int ctas_z = c.pl.tma ? (B + c.pl.S - 1) / c.pl.S : B;
+  return (long long)c.T.ntiles() * ctas_z * 32 * by;
+}
+
+const CUtensorMap* find_map(const Call& c, const float* base) {
+  for (const auto& m : c.maps)
+    if (m.base == base) return &m.map;
+  return nullptr;
 }
 
 fwi_status launch_step(Call& c, const StepParams& p_in, bool adj) {
@@ -596,9 +729,18 @@ fwi_status launch_step(Call& c, const StepParams& p_in, bool adj) {
     p.nrec = 0;
   }
   const bool prof = P->opt.profile != 0;
+  p.flags = P->d_flags + 1;
+  p.S = c.pl.S;
+  const CUtensorMap* map = nullptr;
+  if (c.pl.tma) {
+    map = find_map(c, p.u);
+    if (!map) return fail(FWI_ERR_INVALID_ARG, "internal: no tensor map for the wavefield buffer");
+  }
   if (prof) FWI_TRY(record_event(P, adj ? 1 : 0));
-  cudaError_t e = (P->grid.ndim == 2) ? launch_step2d(p, P->R, c.vd, adj, c.pl.tile, P->st)
-                                      : launch_step3d(p, P->R, c.vd, adj, c.pl.tile, P->st);
+  cudaError_t e;
+  if (P->grid.ndim == 3) e = launch_step3d(p, P->R, c.vd, adj, c.pl.shape, P->st);
+  else if (c.pl.tma) e = launch_step2d_tma(p, *map, P->R, c.vd, adj, c.pl.shape, P->st);
+  else e = launch_step2d(p, P->R, c.vd, adj, c.pl.shape, P->st);
   if (e != cudaSuccess) return fail(FWI_ERR_CUDA, std::string("stencil launch: ") + cudaGetErrorString(e));
   if (prof) FWI_TRY(record_event(P, adj ? 1 : 0));
   c.launches++;
@@ -625,7 +767,7 @@ fwi_status forward_steps(Call& c, int nb, int shot0, const DevTable& src, float*
   p.vals = c.wavelet;
   p.smp_node = c.smp_node;
   p.smp_w = c.smp_w;
-  p.smp_out = c.W.D;
+  p.smp_out = c.D;
   p.nrec = sample ? c.geom->nrec : 0;
   for (int n = n0; n < n1; ++n) {
     if (K_ckpt > 0 && n % K_ckpt == 0) {
@@ -654,7 +796,7 @@ fwi_status final_sample(Call& c, int nb, const float* A, int n) {
   p.u = A;
   p.smp_node = c.smp_node;
   p.smp_w = c.smp_w;
-  p.smp_out = c.W.D;
+  p.smp_out = c.D;
   p.nrec = c.geom->nrec;
   p.smp_off = (long long)n * c.pl.B * c.geom->nrec;
   cudaError_t e = launch_sample(p, P->st);
@@ -688,7 +830,7 @@ fwi_status prepare_common(Call& c, Carve& tabC) {
   const fwi_geometry* g = c.geom;
   const int nd = P->grid.ndim;
   c.ncorner = 1 << nd;
-  c.T = tile_geo(P, c.pl.tile);
+  c.T = tile_geo(P, c.pl.shape, c.pl.tma);
   // receiver sampling table
   std::vector<int> node((size_t)g->nrec * c.ncorner);
   std::vector<float> w((size_t)g->nrec * c.ncorner);
@@ -719,7 +861,7 @@ fwi_status prepare_common(Call& c, Carve& tabC) {
 }
 
 size_t tables_bound(const fwi_plan* P, const fwi_geometry* g, const Plan& pl) {
-  const TileGeo T = tile_geo(P, pl.tile);
+  const TileGeo T = tile_geo(P, pl.shape, pl.tma);
   const int nc = 1 << P->grid.ndim;
   const size_t nb = (size_t)pl.B * T.ntiles() + 1;
   const size_t src = (size_t)pl.B * g->nsrc * nc;
@@ -737,8 +879,10 @@ fwi_status prepare_model(Call& c) {
   unsigned int init[3] = {0u, 0x7f800000u, 0u};
   CUDA_TRY(cudaMemcpyAsync(P->d_stats, init, sizeof(init), cudaMemcpyHostToDevice, P->st));
   if (c.vd) CUDA_TRY(cudaMemsetAsync(c.W.lnr, 0, fs * sizeof(float), P->st));
-  cudaError_t e = launch_model_prep(P->L, m->vp, m->rho, P->dt, c.W.kf, c.vd ? c.W.lnr : nullptr,
-                                    P->d_stats, P->st);
+  if (m->param != FWI_PARAM_VP && m->param != FWI_PARAM_M)
+    return fail(FWI_ERR_INVALID_ARG, "model param must be FWI_PARAM_VP or FWI_PARAM_M");
+  cudaError_t e = launch_model_prep(P->L, m->vp, m->rho, P->dt, m->param, c.W.kf,
+                                    c.vd ? c.W.lnr : nullptr, P->d_stats, P->st);
   if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
   unsigned int st[3];
   CUDA_TRY(cudaMemcpyAsync(st, P->d_stats, sizeof(st), cudaMemcpyDeviceToHost, P->st));
@@ -773,7 +917,7 @@ fwi_status prepare_model(Call& c) {
 }
 
 fwi_status begin_call(fwi_plan* P, const fwi_model* model, const fwi_geometry* geom,
-                      const float* wavelet, bool grad, Call& c, Carve& tabC) {
+                      const float* wavelet, bool grad, Call& c, Carve& tabC, bool split = false) {
   if (!model || !model->vp) return fail(FWI_ERR_INVALID_ARG, "model or vp is NULL");
   if (!wavelet) return fail(FWI_ERR_INVALID_ARG, "wavelet is NULL");
   FWI_TRY(validate_geometry(P, geom));
@@ -783,23 +927,35 @@ fwi_status begin_call(fwi_plan* P, const fwi_model* model, const fwi_geometry* g
   c.geom = geom;
   c.wavelet = wavelet;
   c.vd = model->rho != nullptr;
-  const int ntile = P->grid.ndim == 2 ? NUM_TILE2 : NUM_TILE3;
-  if (P->opt.tile < 0 || P->opt.tile >= ntile) return fail(FWI_ERR_INVALID_ARG, "tile variant out of range");
-  FWI_TRY(choose_plan(P, geom, c.vd, grad, c.pl));
+  if (P->saved) {   // any new call drops the state of a pending split gradient
+    delete_saved(P->saved);
+    P->saved = nullptr;
+  }
+  FWI_TRY(choose_plan(P, geom, c.vd, grad, c.pl, split));
   FWI_TRY(ensure_arena(P, c.pl.bytes));
   Carve C(P->arena);
   carve_work(P, c.pl, geom, c.vd, C, c.W);
   if (C.off > P->arena_cap) return fail(FWI_ERR_BUDGET, "workspace carve exceeds allocation");
+  if (c.pl.tma) {
+    for (float* buf : {c.W.U0, c.W.U1, c.W.F0, c.W.F1}) {
+      if (!buf) continue;
+      Call::MapEnt m{buf, {}};
+      FWI_TRY(make_tensor_map(P, buf, c.pl.B, c.pl.shape, &m.map));
+      c.maps.push_back(m);
+    }
+  }
   FWI_TRY(ensure_tab(P, tables_bound(P, geom, c.pl) * 2));
   tabC = Carve(P->tab);
   const int nbatches = (geom->nshots + c.pl.B - 1) / c.pl.B;
   if (nbatches > P->d_J_cap) {
-    if (P->d_J) CUDA_TRY(cudaFree(P->d_J));
-    CUDA_TRY(cudaMalloc(&P->d_J, sizeof(double) * nbatches));
+    if (P->fixed_memory) return fail(FWI_ERR_BUDGET, "too many shot batches for the fixed scratch");
+    if (P->d_J) CUDA_TRY(cudaFreeAsync(P->d_J, P->st));
+    CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&P->d_J), sizeof(double) * nbatches, P->st));
     P->d_J_cap = nbatches;
   }
   CUDA_TRY(cudaMemsetAsync(P->d_flags, 0, sizeof(int) * 4, P->st));
   P->ev_used = 0;
+  c.D = c.W.D;
   FWI_TRY(prepare_model(c));
   FWI_TRY(prepare_common(c, tabC));
   return FWI_OK;
@@ -828,7 +984,148 @@ fwi_status finish_call(Call& c) {
     if (P->ev_kind[i] == 0) s.fwd_ms += ms;
     else s.adj_ms += ms;
   }
+  if (flags[1] & 2) return fail(FWI_ERR_TIMEOUT, "a bounded wait on a TMA copy timed out");
   if (flags[0]) return fail(FWI_ERR_NONFINITE, "non-finite values in the result (unstable run?)");
+  return FWI_OK;
+}
+
+// State kept between fwi_misfit_forward and fwi_misfit_backward.
+struct SavedGrad {
+  Call c;
+  Carve tabC{nullptr};
+  std::vector<double> src, rec;
+  fwi_geometry geom{};
+  fwi_model model{};
+  int nbatches = 0;
+  double J = 0.0;
+};
+
+void delete_saved(SavedGrad* s) { delete s; }
+
+// Pointers of batch j's kept state: traces/residuals, checkpoints, history.
+struct BatchBufs {
+  float* D;
+  float* CK;
+  float* H;
+};
+
+BatchBufs batch_bufs(const Call& c, int j) {
+  const size_t fs = (size_t)c.P->L.fstride;
+  const size_t B = (size_t)c.pl.B;
+  const size_t k = c.pl.split ? (size_t)j : 0;
+  const int nt = c.P->nt;
+  BatchBufs b;
+  b.D = c.W.D + k * (size_t)nt * B * c.geom->nrec;
+  b.CK = c.W.CK ? c.W.CK + k * fs * B * 2 * (size_t)c.pl.nck : nullptr;
+  b.H = (c.pl.K == 0) ? c.W.H + k * fs * B * (size_t)std::max(nt - 1, 1) : c.W.H;
+  return b;
+}
+
+// Forward sweep of batch j (history or checkpoints), last trace sample,
+// residual and misfit of the batch (into d_J[j]).
+fwi_status gradient_forward_batch(Call& c, int j, int shot0, int nb, const DevTable& src,
+                                  const float* observed, float* traces_opt) {
+  fwi_plan* P = c.P;
+  const size_t fs = (size_t)P->L.fstride;
+  const int nt = P->nt;
+  const int K = c.pl.K;
+  const BatchBufs bb = batch_bufs(c, j);
+  c.D = bb.D;
+  float* A = c.W.U0;
+  float* Bf = c.W.U1;
+  CUDA_TRY(cudaMemsetAsync(A, 0, fs * nb * sizeof(float), P->st));
+  CUDA_TRY(cudaMemsetAsync(Bf, 0, fs * nb * sizeof(float), P->st));
+  FWI_TRY(forward_steps(c, nb, shot0, src, A, Bf, 0, nt - 1, K == 0 ? bb.H : nullptr, 0, true,
+                        K, bb.CK));
+  FWI_TRY(final_sample(c, nb, A, nt - 1));
+  cudaError_t e = launch_misfit(c.D, observed, traces_opt, c.pl.B, shot0, nb, c.geom->nrec, nt,
+                                c.W.partials, P->d_flags, c.W.npartials, P->st);
+  if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
+  e = launch_sum_partials(c.W.partials, misfit_blocks(nb, c.geom->nrec, nt), P->d_J + j, P->st);
+  if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
+  c.launches += 2;
+  return FWI_OK;
+}
+
+// Adjoint sweep of batch j with the imaging condition, from the kept history
+// or by recomputing each checkpoint segment; accumulates into the slots of G.
+fwi_status gradient_adjoint_batch(Call& c, int j, int shot0, int nb, const DevTable& src) {
+  fwi_plan* P = c.P;
+  const size_t fs = (size_t)P->L.fstride;
+  const int B = c.pl.B;
+  const int nt = P->nt;
+  const int K = c.pl.K;
+  const BatchBufs bb = batch_bufs(c, j);
+  c.D = bb.D;
+  // lambda^{nt-1} = lambda^{nt} = 0
+  float* LA = (K == 0) ? c.W.U0 : c.W.F0;
+  float* LB = (K == 0) ? c.W.U1 : c.W.F1;
+  CUDA_TRY(cudaMemsetAsync(LA, 0, fs * nb * sizeof(float), P->st));
+  CUDA_TRY(cudaMemsetAsync(LB, 0, fs * nb * sizeof(float), P->st));
+  StepParams p = base_params(c);
+  p.B = nb;
+  p.inj_off = c.rec_tab.off;
+  p.inj_loc = c.rec_tab.loc;
+  p.inj_vidx = c.rec_tab.vidx;
+  p.inj_w = c.rec_tab.w;
+  p.vals = c.D;
+  p.g = c.W.G;
+  p.nrec = 0;
+  int seg_lo = -1, seg_hi = -1;
+  auto hist_at = [&](int n) -> float* {
+    if (K == 0) return bb.H + (size_t)n * fs * B;
+    return bb.H + (size_t)(n - seg_lo) * fs * B;
+  };
+  auto ensure_segment = [&](int n) -> fwi_status {
+    if (K == 0 || (n >= seg_lo && n < seg_hi)) return FWI_OK;
+    const int js = n / K;
+    seg_lo = js * K;
+    seg_hi = std::min(seg_lo + K, nt - 1);
+    float* FA = c.W.U0;
+    float* FB = c.W.U1;
+    const float* ck = bb.CK + 2 * (size_t)js * fs * B;
+    CUDA_TRY(cudaMemcpyAsync(FA, ck, fs * nb * sizeof(float), cudaMemcpyDeviceToDevice, P->st));
+    CUDA_TRY(cudaMemcpyAsync(FB, ck + fs * B, fs * nb * sizeof(float), cudaMemcpyDeviceToDevice, P->st));
+    return forward_steps(c, nb, shot0, src, FA, FB, seg_lo, seg_hi, bb.H, seg_lo, false, 0, nullptr);
+  };
+  for (int k = nt - 1; k >= 1; --k) {
+    p.image = (k <= nt - 2) ? 1 : 0;
+    if (p.image) {
+      FWI_TRY(ensure_segment(k));
+      p.hist = hist_at(k);
+    } else {
+      p.hist = nullptr;
+    }
+    p.u = LA;
+    p.up = LB;
+    p.step_off = (long long)k * B * c.geom->nrec;
+    FWI_TRY(launch_step(c, p, true));
+    std::swap(LA, LB);
+  }
+  if (nt >= 2) {   // imaging term of lambda^0
+    FWI_TRY(ensure_segment(0));
+    cudaError_t e = launch_image_only(P->L, LA, hist_at(0), c.W.G, nb, c.pl.S, P->st);
+    if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
+    c.launches++;
+  }
+  return FWI_OK;
+}
+
+// Sum the gradient slots into grad_m (scaled by 1/dt^2), read the misfit of
+// `batches` batches (0: none) and finish the call.
+fwi_status gradient_finish(Call& c, int batches, double* misfit, float* grad_m) {
+  fwi_plan* P = c.P;
+  const int G = (c.pl.B + c.pl.S - 1) / c.pl.S;   // gradient slots in use
+  cudaError_t e = launch_grad_finalize(P->L, c.W.G, G, 1.0 / (P->dt * P->dt), grad_m, P->d_flags, P->st);
+  if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
+  c.launches++;
+  std::vector<double> J(std::max(batches, 1));
+  if (batches > 0)
+    CUDA_TRY(cudaMemcpyAsync(J.data(), P->d_J, sizeof(double) * batches, cudaMemcpyDeviceToHost, P->st));
+  FWI_TRY(finish_call(c));
+  double tot = 0.0;
+  for (int i = 0; i < batches; ++i) tot += J[i];
+  if (batches > 0) *misfit = tot;
   return FWI_OK;
 }
 
@@ -864,7 +1161,22 @@ fwi_status fwi_plan_create(fwi_plan** plan, const fwi_grid* grid, int nt, double
   e = cudaMemGetInfo(&fr, &tot);
   if (e != cudaSuccess) return cleanup(fail(FWI_ERR_CUDA, cudaGetErrorString(e)));
   P->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)fr);
-  if (cudaMalloc(&P->d_stats, 64) != cudaSuccess || cudaMalloc(&P->d_flags, 64) != cudaSuccess)
+  if (cudaDeviceGetAttribute(&P->nsm, cudaDevAttrMultiProcessorCount, P->device) != cudaSuccess) {
+    cudaGetLastError();
+    P->nsm = 152;
+  }
+  {
+    // keep freed plan memory cached in the default pool (no return to the OS
+    // between requests); this is a per-process allocator setting
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, P->device) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+  }
+  if (cudaMallocAsync(reinterpret_cast<void**>(&P->d_stats), 64, P->st) != cudaSuccess ||
+      cudaMallocAsync(reinterpret_cast<void**>(&P->d_flags), 64, P->st) != cudaSuccess)
     return cleanup(fail(FWI_ERR_CUDA, "small allocation failed"));
   if (P->c_ref > 0.0) {
     fwi_status s = build_sponge(P);
@@ -900,16 +1212,11 @@ fwi_status fwi_plan_estimate(const fwi_plan* plan, const fwi_geometry* geom, int
 void fwi_plan_destroy(fwi_plan* P) {
   if (!P) return;
   cudaSetDevice(P->device);
-  if (P->st) cudaStreamSynchronize(P->st);
-  else cudaDeviceSynchronize();
-  cudaFree(P->arena);
-  cudaFree(P->tab);
-  cudaFree(P->spx);
-  cudaFree(P->spy);
-  cudaFree(P->spz);
-  cudaFree(P->d_stats);
-  cudaFree(P->d_flags);
-  cudaFree(P->d_J);
+  for (void* q : {(void*)P->arena, (void*)P->tab, (void*)P->spx, (void*)P->spy, (void*)P->spz,
+                  (void*)P->d_stats, (void*)P->d_flags, (void*)P->d_J})
+    if (q) cudaFreeAsync(q, P->st);
+  cudaStreamSynchronize(P->st);
+  cudaGetLastError();
   for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
   delete P;
 }
@@ -953,95 +1260,371 @@ fwi_status fwi_gradient(fwi_plan* P, const fwi_model* model, const fwi_geometry*
   Carve tabC(nullptr);
   FWI_TRY(begin_call(P, model, geom, wavelet, true, c, tabC));
   const size_t fs = (size_t)P->L.fstride;
-  const int B = c.pl.B;
-  const int nt = P->nt;
-  const int K = c.pl.K;
-  CUDA_TRY(cudaMemsetAsync(c.W.G, 0, fs * B * sizeof(float), P->st));
+  CUDA_TRY(cudaMemsetAsync(c.W.G, 0, fs * c.pl.B * sizeof(float), P->st));
   int batch = 0;
-  for (int shot0 = 0; shot0 < geom->nshots; shot0 += B, ++batch) {
-    const int nb = std::min(B, geom->nshots - shot0);
+  for (int shot0 = 0; shot0 < geom->nshots; shot0 += c.pl.B, ++batch) {
+    const int nb = std::min(c.pl.B, geom->nshots - shot0);
     Carve srcC = tabC;
     DevTable src;
     FWI_TRY(build_source_table(c, shot0, nb, srcC, src));
-    float* A = c.W.U0;
-    float* Bf = c.W.U1;
-    CUDA_TRY(cudaMemsetAsync(A, 0, fs * nb * sizeof(float), P->st));
-    CUDA_TRY(cudaMemsetAsync(Bf, 0, fs * nb * sizeof(float), P->st));
-    // forward sweep with history (K = 0) or checkpoints (K > 0)
-    FWI_TRY(forward_steps(c, nb, shot0, src, A, Bf, 0, nt - 1, K == 0 ? c.W.H : nullptr, 0, true,
-                          K, c.W.CK));
-    FWI_TRY(final_sample(c, nb, A, nt - 1));
-    // residual and misfit of this batch
-    cudaError_t e = launch_misfit(c.W.D, observed, traces_opt, B, shot0, nb, geom->nrec, nt,
-                                  c.W.partials, P->d_flags, c.W.npartials, P->st);
-    if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
-    e = launch_sum_partials(c.W.partials, misfit_blocks(nb, geom->nrec, nt), P->d_J + batch, P->st);
-    if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
-    c.launches += 2;
-    // adjoint sweep: lambda^{nt-1} = lambda^{nt} = 0
-    float* LA = (K == 0) ? c.W.U0 : c.W.F0;
-    float* LB = (K == 0) ? c.W.U1 : c.W.F1;
-    CUDA_TRY(cudaMemsetAsync(LA, 0, fs * nb * sizeof(float), P->st));
-    CUDA_TRY(cudaMemsetAsync(LB, 0, fs * nb * sizeof(float), P->st));
-    StepParams p = base_params(c);
-    p.B = nb;
-    p.inj_off = c.rec_tab.off;
-    p.inj_loc = c.rec_tab.loc;
-    p.inj_vidx = c.rec_tab.vidx;
-    p.inj_w = c.rec_tab.w;
-    p.vals = c.W.D;
-    p.g = c.W.G;
-    p.nrec = 0;
-    int seg_lo = -1, seg_hi = -1;
-    auto hist_at = [&](int n) -> float* {
-      if (K == 0) return c.W.H + (size_t)n * fs * B;
-      return c.W.H + (size_t)(n - seg_lo) * fs * B;
-    };
-    auto ensure_segment = [&](int n) -> fwi_status {
-      if (K == 0 || (n >= seg_lo && n < seg_hi)) return FWI_OK;
-      const int j = n / K;
-      seg_lo = j * K;
-      seg_hi = std::min(seg_lo + K, nt - 1);
-      float* FA = c.W.U0;
-      float* FB = c.W.U1;
-      const float* ck = c.W.CK + 2 * (size_t)j * fs * B;
-      CUDA_TRY(cudaMemcpyAsync(FA, ck, fs * nb * sizeof(float), cudaMemcpyDeviceToDevice, P->st));
-      CUDA_TRY(cudaMemcpyAsync(FB, ck + fs * B, fs * nb * sizeof(float), cudaMemcpyDeviceToDevice, P->st));
-      return forward_steps(c, nb, shot0, src, FA, FB, seg_lo, seg_hi, c.W.H, seg_lo, false, 0,
-                           nullptr);
-    };
-    for (int k = nt - 1; k >= 1; --k) {
-      p.image = (k <= nt - 2) ? 1 : 0;
-      if (p.image) {
-        FWI_TRY(ensure_segment(k));
-        p.hist = hist_at(k);
-      } else {
-        p.hist = nullptr;
-      }
-      p.u = LA;
-      p.up = LB;
-      p.step_off = (long long)k * B * geom->nrec;
-      FWI_TRY(launch_step(c, p, true));
-      std::swap(LA, LB);
-    }
-    if (nt >= 2) {   // imaging term of lambda^0
-      FWI_TRY(ensure_segment(0));
-      e = launch_image_only(P->L, LA, hist_at(0), c.W.G, nb, P->st);
-      if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
-      c.launches++;
-    }
-    if (shot0 + B < geom->nshots) CUDA_TRY(cudaStreamSynchronize(P->st));
+    FWI_TRY(gradient_forward_batch(c, batch, shot0, nb, src, observed, traces_opt));
+    FWI_TRY(gradient_adjoint_batch(c, batch, shot0, nb, src));
+    if (shot0 + c.pl.B < geom->nshots) CUDA_TRY(cudaStreamSynchronize(P->st));
   }
-  cudaError_t e = launch_grad_finalize(P->L, c.W.G, B, 1.0 / (P->dt * P->dt), grad_m, P->d_flags, P->st);
-  if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
-  c.launches++;
+  return gradient_finish(c, batch, misfit, grad_m);
+}
+
+fwi_status fwi_misfit_forward(fwi_plan* P, const fwi_model* model, const fwi_geometry* geom,
+                              const float* wavelet, const float* observed, double* misfit,
+                              float* traces_opt) {
+  if (!P) return fail(FWI_ERR_INVALID_ARG, "plan is NULL");
+  if (!observed || !misfit) return fail(FWI_ERR_INVALID_ARG, "observed or misfit is NULL");
+  if (!model || !geom) return fail(FWI_ERR_INVALID_ARG, "model or geometry is NULL");
+  // keep host copies of the geometry; device arrays stay the caller's
+  SavedGrad* S = new SavedGrad();
+  S->src.assign(geom->src_xyz, geom->src_xyz + (size_t)geom->nshots * geom->nsrc * P->grid.ndim);
+  S->rec.assign(geom->rec_xyz, geom->rec_xyz + (size_t)geom->nrec * P->grid.ndim);
+  S->geom = *geom;
+  S->geom.src_xyz = S->src.data();
+  S->geom.rec_xyz = S->rec.data();
+  S->model = *model;
+  Call& c = S->c;
+  fwi_status st = begin_call(P, &S->model, &S->geom, wavelet, true, c, S->tabC, true);
+  if (st != FWI_OK) {
+    delete_saved(S);
+    return st;
+  }
+  int batch = 0;
+  for (int shot0 = 0; shot0 < geom->nshots && st == FWI_OK; shot0 += c.pl.B, ++batch) {
+    const int nb = std::min(c.pl.B, geom->nshots - shot0);
+    Carve srcC = S->tabC;
+    DevTable src;
+    st = build_source_table(c, shot0, nb, srcC, src);
+    if (st == FWI_OK) st = gradient_forward_batch(c, batch, shot0, nb, src, observed, traces_opt);
+    if (st == FWI_OK && shot0 + c.pl.B < geom->nshots) {
+      cudaError_t e = cudaStreamSynchronize(P->st);
+      if (e != cudaSuccess) st = fail(FWI_ERR_CUDA, cudaGetErrorString(e));
+    }
+  }
   std::vector<double> J(batch);
-  CUDA_TRY(cudaMemcpyAsync(J.data(), P->d_J, sizeof(double) * batch, cudaMemcpyDeviceToHost, P->st));
-  FWI_TRY(finish_call(c));
+  if (st == FWI_OK) {
+    cudaError_t e = cudaMemcpyAsync(J.data(), P->d_J, sizeof(double) * batch, cudaMemcpyDeviceToHost, P->st);
+    if (e != cudaSuccess) st = fail(FWI_ERR_CUDA, cudaGetErrorString(e));
+  }
+  if (st == FWI_OK) st = finish_call(c);
+  if (st != FWI_OK) {
+    delete_saved(S);
+    return st;
+  }
   double tot = 0.0;
   for (int i = 0; i < batch; ++i) tot += J[i];
   *misfit = tot;
+  S->nbatches = batch;
+  S->J = tot;
+  P->saved = S;
   return FWI_OK;
+}
+
+fwi_status fwi_misfit_backward(fwi_plan* P, float* grad_m) {
+  if (!P || !grad_m) return fail(FWI_ERR_INVALID_ARG, "plan or grad_m is NULL");
+  SavedGrad* S = P->saved;
+  if (!S) return fail(FWI_ERR_INVALID_ARG, "no pending fwi_misfit_forward on this plan");
+  P->saved = nullptr;   // the state is used once
+  Call& c = S->c;
+  CUDA_TRY(cudaSetDevice(P->device));
+  const size_t fs = (size_t)P->L.fstride;
+  c.launches = c.fwd_launches = c.adj_launches = c.fwd_points = c.adj_points = 0;
+  P->ev_used = 0;
+  fwi_status st = FWI_OK;
+  cudaError_t e = cudaMemsetAsync(c.W.G, 0, fs * c.pl.B * sizeof(float), P->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->d_flags, 0, sizeof(int) * 4, P->st);
+  if (e != cudaSuccess) st = fail(FWI_ERR_CUDA, cudaGetErrorString(e));
+  int batch = 0;
+  for (int shot0 = 0; shot0 < S->geom.nshots && st == FWI_OK; shot0 += c.pl.B, ++batch) {
+    const int nb = std::min(c.pl.B, S->geom.nshots - shot0);
+    Carve srcC = S->tabC;
+    DevTable src;
+    st = build_source_table(c, shot0, nb, srcC, src);
+    if (st == FWI_OK) st = gradient_adjoint_batch(c, batch, shot0, nb, src);
+    if (st == FWI_OK && shot0 + c.pl.B < S->geom.nshots) {
+      e = cudaStreamSynchronize(P->st);
+      if (e != cudaSuccess) st = fail(FWI_ERR_CUDA, cudaGetErrorString(e));
+    }
+  }
+  double J = 0.0;
+  if (st == FWI_OK) st = gradient_finish(c, 0, &J, grad_m);
+  delete_saved(S);
+  return st;
+}
+
+}  // extern "C"
+
+#define FWI_TRY_B(call)              \
+  do {                               \
+    fwi_status s_ = (call);          \
+    if (s_ != FWI_OK) return bail(s_); \
+  } while (0)
+
+#define CUDA_TRY_B(call)                                                                     \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return bail(fail(FWI_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)));   \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Uneven batches of independent 2D problems (forward modelling).
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BatchProblem {
+  fwi_plan* P = nullptr;
+  Call c;
+  Carve tabC{nullptr};
+  DevTable src;
+  fwi_problem prob{};
+  std::vector<double> srcxyz, recxyz;
+};
+
+}  // namespace
+
+struct fwi_batch {
+  std::vector<BatchProblem*> items;   // sorted by nt, longest first
+  cudaStream_t st = nullptr;          // the caller's stream
+  cudaStream_t ws = nullptr;          // internal non-blocking stream the runs (and the capture) use
+  cudaEvent_t ready = nullptr;
+  int device = 0;
+  int R = 4;
+  bool vd = false;
+  MultiDesc* d_desc = nullptr;
+  MultiUnit* d_units = nullptr;
+  std::vector<int> active_units;      // units of the problems still running at step n
+  int max_steps = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool use_graph = true;
+  fwi_batch_stats stats{};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ~fwi_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaFree(d_desc);
+    cudaFree(d_units);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (ready) cudaEventDestroy(ready);
+    if (ws) cudaStreamDestroy(ws);
+    for (BatchProblem* b : items) {
+      fwi_plan_destroy(b->P);
+      delete b;
+    }
+  }
+};
+
+namespace {
+
+// Every step of every problem (and the final sampling / trace transposition)
+// enqueued on b->st; captured into a graph when b->use_graph.
+fwi_status batch_enqueue(fwi_batch* b) {
+  int64_t launches = 0, updates = 0;
+  for (int n = 0; n < b->max_steps; ++n) {
+    cudaError_t e = launch_step2d_multi(b->d_desc, b->d_units, b->active_units[n], n, b->R, b->vd, b->ws);
+    if (e != cudaSuccess) return fail(FWI_ERR_CUDA, std::string("multi-problem step: ") + cudaGetErrorString(e));
+    ++launches;
+  }
+  for (BatchProblem* it : b->items) {
+    Call& c = it->c;
+    const int nt = it->prob.nt;
+    const int ns = it->prob.geom.nshots;
+    float* last = ((nt - 1) & 1) ? c.W.U1 : c.W.U0;   // u^{nt-1}
+    StepParams p = base_params(c);
+    p.B = ns;
+    p.u = last;
+    p.smp_node = c.smp_node;
+    p.smp_w = c.smp_w;
+    p.smp_out = c.W.D;
+    p.nrec = it->prob.geom.nrec;
+    p.smp_off = (long long)(nt - 1) * c.pl.B * it->prob.geom.nrec;
+    cudaError_t e = launch_sample(p, b->ws);
+    if (e == cudaSuccess)
+      e = launch_traces_out(c.W.D, it->prob.traces, c.pl.B, 0, ns, it->prob.geom.nrec, nt,
+                            it->P->d_flags, b->ws);
+    if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
+    launches += 2;
+    updates += (int64_t)ns * it->P->L.nx * it->P->L.ny * (nt - 1);
+  }
+  b->stats.launches = launches;
+  b->stats.updates = updates;
+  return FWI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fwi_status fwi_batch_create(fwi_batch** out, int nprob, const fwi_problem* probs,
+                            size_t hbm_budget_bytes, void* stream, int use_graph) {
+  if (!out || !probs || nprob < 1) return fail(FWI_ERR_INVALID_ARG, "bad batch arguments");
+  *out = nullptr;
+  fwi_batch* b = new fwi_batch();
+  b->st = reinterpret_cast<cudaStream_t>(stream);
+  b->use_graph = use_graph != 0;
+  auto bail = [&](fwi_status s) { delete b; return s; };
+  if (cudaGetDevice(&b->device) != cudaSuccess) return bail(fail(FWI_ERR_CUDA, "no CUDA device"));
+  size_t used = 0;
+  for (int i = 0; i < nprob; ++i) {
+    const fwi_problem& pr = probs[i];
+    if (pr.grid.ndim != 2) return bail(fail(FWI_ERR_UNSUPPORTED, "batches hold 2D problems"));
+    if (i == 0) {
+      b->R = pr.grid.order / 2;
+      b->vd = pr.model.rho != nullptr;
+    } else if (pr.grid.order / 2 != b->R || (pr.model.rho != nullptr) != b->vd) {
+      return bail(fail(FWI_ERR_UNSUPPORTED, "a batch shares one stencil order and density mode"));
+    }
+    if (!pr.traces || !pr.wavelet) return bail(fail(FWI_ERR_INVALID_ARG, "problem arrays are NULL"));
+    BatchProblem* it = new BatchProblem();
+    b->items.push_back(it);
+    it->prob = pr;
+    if (!pr.geom.src_xyz || !pr.geom.rec_xyz) return bail(fail(FWI_ERR_INVALID_ARG, "coordinates are NULL"));
+    it->srcxyz.assign(pr.geom.src_xyz, pr.geom.src_xyz + (size_t)pr.geom.nshots * pr.geom.nsrc * 2);
+    it->recxyz.assign(pr.geom.rec_xyz, pr.geom.rec_xyz + (size_t)pr.geom.nrec * 2);
+    it->prob.geom.src_xyz = it->srcxyz.data();
+    it->prob.geom.rec_xyz = it->recxyz.data();
+    const size_t left = hbm_budget_bytes ? (hbm_budget_bytes > used ? hbm_budget_bytes - used : 1) : 0;
+    FWI_TRY_B(fwi_plan_create(&it->P, &pr.grid, pr.nt, pr.dt, left, stream));
+    fwi_options o{};
+    o.batch = pr.geom.nshots;   // every shot of the problem in one batch
+    o.tile = 1;                 // shared-memory-staged 128 x 32 tiles (the multi-problem kernel's)
+    it->P->opt = o;
+    FWI_TRY_B(begin_call(it->P, &it->prob.model, &it->prob.geom, pr.wavelet, false, it->c, it->tabC));
+    if (it->c.pl.B != pr.geom.nshots)
+      return bail(fail(FWI_ERR_BUDGET, "problem " + std::to_string(i) + " does not fit the budget with all its shots"));
+    Carve srcC = it->tabC;
+    FWI_TRY_B(build_source_table(it->c, 0, pr.geom.nshots, srcC, it->src));
+    const size_t fs = (size_t)it->P->L.fstride;
+    CUDA_TRY_B(cudaMemsetAsync(it->c.W.U0, 0, fs * pr.geom.nshots * sizeof(float), b->st));
+    CUDA_TRY_B(cudaMemsetAsync(it->c.W.U1, 0, fs * pr.geom.nshots * sizeof(float), b->st));
+    used += it->c.pl.bytes;
+  }
+  std::stable_sort(b->items.begin(), b->items.end(),
+                   [](const BatchProblem* a, const BatchProblem* c) { return a->prob.nt > c->prob.nt; });
+  // descriptors and units (problems longest first: the running ones are a prefix)
+  std::vector<MultiDesc> desc(b->items.size());
+  std::vector<MultiUnit> units;
+  std::vector<int> prefix;
+  for (size_t k = 0; k < b->items.size(); ++k) {
+    BatchProblem* it = b->items[k];
+    Call& c = it->c;
+    StepParams p = base_params(c);
+    p.B = it->prob.geom.nshots;
+    p.inj_off = it->src.off;
+    p.inj_loc = it->src.loc;
+    p.inj_vidx = it->src.vidx;
+    p.inj_w = it->src.w;
+    p.vals = it->prob.wavelet;
+    p.smp_node = c.smp_node;
+    p.smp_w = c.smp_w;
+    p.smp_out = c.W.D;
+    p.nrec = it->prob.geom.nrec;
+    p.S = 1;
+    p.flags = it->P->d_flags + 1;
+    desc[k].p = p;
+    desc[k].U0 = c.W.U0;
+    desc[k].U1 = c.W.U1;
+    desc[k].gx = c.T.gx;
+    desc[k].nt = it->prob.nt;
+    long long rank = 0;
+    for (int sl = 0; sl < p.B; ++sl)
+      for (int ty = 0; ty < c.T.gy; ++ty)
+        for (int tx = 0; tx < c.T.gx; ++tx) units.push_back({(int)k, tx, ty, sl, rank++});
+    prefix.push_back((int)units.size());
+  }
+  b->max_steps = b->items.empty() ? 0 : b->items[0]->prob.nt - 1;
+  b->active_units.assign(std::max(b->max_steps, 0), 0);
+  for (int n = 0; n < b->max_steps; ++n) {
+    int cnt = 0;
+    for (size_t k = 0; k < b->items.size(); ++k)
+      if (n < b->items[k]->prob.nt - 1) cnt = prefix[k];
+    b->active_units[n] = cnt;
+  }
+  CUDA_TRY_B(cudaMalloc(&b->d_desc, desc.size() * sizeof(MultiDesc)));
+  CUDA_TRY_B(cudaMalloc(&b->d_units, std::max<size_t>(units.size(), 1) * sizeof(MultiUnit)));
+  CUDA_TRY_B(cudaMemcpy(b->d_desc, desc.data(), desc.size() * sizeof(MultiDesc), cudaMemcpyHostToDevice));
+  if (!units.empty())
+    CUDA_TRY_B(cudaMemcpy(b->d_units, units.data(), units.size() * sizeof(MultiUnit), cudaMemcpyHostToDevice));
+  CUDA_TRY_B(cudaEventCreate(&b->e0));
+  CUDA_TRY_B(cudaEventCreate(&b->e1));
+  CUDA_TRY_B(cudaEventCreateWithFlags(&b->ready, cudaEventDisableTiming));
+  CUDA_TRY_B(cudaStreamCreateWithFlags(&b->ws, cudaStreamNonBlocking));
+  CUDA_TRY_B(cudaStreamSynchronize(b->st));
+  if (b->use_graph) {
+    // set the kernels' attributes outside the capture (zero-unit launch), then
+    // capture every launch of a run
+    {
+      cudaError_t e = launch_step2d_multi(b->d_desc, b->d_units, 0, 0, b->R, b->vd, b->ws);
+      if (e != cudaSuccess) return bail(fail(FWI_ERR_CUDA, cudaGetErrorString(e)));
+    }
+    CUDA_TRY_B(cudaStreamBeginCapture(b->ws, cudaStreamCaptureModeThreadLocal));
+    fwi_status s = batch_enqueue(b);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->ws, &g);
+    if (s != FWI_OK) {
+      if (g) cudaGraphDestroy(g);
+      return bail(s);
+    }
+    if (e != cudaSuccess) return bail(fail(FWI_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e)));
+    b->graph = g;
+    CUDA_TRY_B(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  }
+  b->stats.problems = (int)b->items.size();
+  b->stats.units = (int64_t)units.size();
+  *out = b;
+  return FWI_OK;
+}
+
+fwi_status fwi_batch_run(fwi_batch* b) {
+  if (!b) return fail(FWI_ERR_INVALID_ARG, "batch is NULL");
+  CUDA_TRY(cudaSetDevice(b->device));
+  // the run follows whatever the caller enqueued on its stream (inputs)
+  CUDA_TRY(cudaEventRecord(b->ready, b->st));
+  CUDA_TRY(cudaStreamWaitEvent(b->ws, b->ready, 0));
+  for (BatchProblem* it : b->items) {
+    const size_t fs = (size_t)it->P->L.fstride;
+    const int ns = it->prob.geom.nshots;
+    CUDA_TRY(cudaMemsetAsync(it->c.W.U0, 0, fs * ns * sizeof(float), b->ws));
+    CUDA_TRY(cudaMemsetAsync(it->c.W.U1, 0, fs * ns * sizeof(float), b->ws));
+    CUDA_TRY(cudaMemsetAsync(it->P->d_flags, 0, sizeof(int) * 4, b->ws));
+  }
+  CUDA_TRY(cudaEventRecord(b->e0, b->ws));
+  if (b->use_graph) {
+    CUDA_TRY(cudaGraphLaunch(b->exec, b->ws));
+  } else {
+    FWI_TRY(batch_enqueue(b));
+  }
+  CUDA_TRY(cudaEventRecord(b->e1, b->ws));
+  CUDA_TRY(cudaStreamSynchronize(b->ws));
+  float ms = 0.f;
+  CUDA_TRY(cudaEventElapsedTime(&ms, b->e0, b->e1));
+  b->stats.run_ms = ms;
+  for (BatchProblem* it : b->items) {
+    int flags[4];
+    CUDA_TRY(cudaMemcpy(flags, it->P->d_flags, sizeof(flags), cudaMemcpyDeviceToHost));
+    if (flags[0]) return fail(FWI_ERR_NONFINITE, "non-finite traces in a batched problem");
+  }
+  return FWI_OK;
+}
+
+fwi_status fwi_batch_stats_get(const fwi_batch* b, fwi_batch_stats* out) {
+  if (!b || !out) return fail(FWI_ERR_INVALID_ARG, "NULL argument");
+  *out = b->stats;
+  return FWI_OK;
+}
+
+void fwi_batch_destroy(fwi_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  cudaStreamSynchronize(b->st);
+  delete b;
 }
 
 }  // extern "C"
@@ -1066,6 +1649,11 @@ fwi_status forward_in_buffer(const fwi_grid* grid, int nt, double dt, const fwi_
   P.st = reinterpret_cast<cudaStream_t>(stream);
   P.device = device;
   P.c_ref = grid->c_ref;
+  P.fixed_memory = true;
+  if (cudaDeviceGetAttribute(&P.nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    cudaGetLastError();
+    P.nsm = 152;
+  }
   build_layout(&P);
   FWI_TRY(validate_geometry(&P, geom));
   constexpr int JCAP = 4096;
@@ -1077,8 +1665,10 @@ fwi_status forward_in_buffer(const fwi_grid* grid, int nt, double dt, const fwi_
   P.spx = C.take<float>(P.L.nx_r + 8);
   P.spy = C.take<float>(P.L.ny_r + 8);
   P.spz = C.take<float>(std::max(P.L.nz, 1) + 8);
-  Plan all;
+  Plan all;   // table bound for every shot in one batch, at the tile variant the call will use
   all.B = geom->nshots;
+  if (!resolve_tile(&P, P.opt.tile, &all.tile, &all.shape, &all.tma))
+    return fail(FWI_ERR_INVALID_ARG, "tile variant out of range");
   const size_t tab = align_up(tables_bound(&P, geom, all) * 2, 256);
   P.tab = C.take<char>(tab);
   P.tab_cap = tab;

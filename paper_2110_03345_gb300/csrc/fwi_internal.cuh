@@ -9,6 +9,7 @@
 //   which is the u = 0 boundary condition behind the sponge, so stencil
 //   loads need no bounds checks.  Per-shot fields are stacked [B][fstride].
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -79,6 +80,24 @@ struct StepParams {
   int image;             // adjoint: accumulate g -= lambda^k h^k
   int zchunk;            // 3D: planes per CTA
   int nzc;               // 3D: z chunks
+  int S;                 // shots per CTA (TMA kernels); gradient slot of shot s is s / S
+  int* flags;            // device error flags (bit 1: a bounded wait timed out)
+};
+
+// Multi-problem forward step (kernels2d.cu): one launch advances every unit
+// (problem, tile, shot slot) of the table by one time step.  The descriptor
+// holds the problem's StepParams except the per-step fields, which the kernel
+// derives from the global step n and the two wavefield buffers.
+struct MultiDesc {
+  StepParams p;
+  float* U0;   // u^n for even n (then u^{n-1} for odd n), [B][fstride]
+  float* U1;
+  int gx;      // tiles along x
+  int nt;      // time samples of the problem (active while n < nt - 1)
+};
+struct MultiUnit {
+  int prob, tx, ty, slot;
+  long long rank;  // CTA rank among the problem's units (receiver sampling)
 };
 
 // Tile variants of the 2D kernels: rows per thread x thread rows.
@@ -90,6 +109,16 @@ __host__ __device__ inline Tile2 tile2_variant(int v) {
     case 2: return {4, 4};
     case 3: return {2, 8};
     default: return {4, 8};
+  }
+}
+// Tile shapes of the TMA-staged 2D kernels (one or two rows per thread keep
+// registers at <= 64 so that 32-64 warps per SM hide the memory latency).
+__host__ __device__ inline Tile2 tile2_tma_variant(int v) {
+  switch (v) {
+    case 1: return {1, 16};
+    case 2: return {2, 16};
+    case 3: return {2, 8};
+    default: return {1, 32};
   }
 }
 // 3D tile variants: thread rows (tile 32 x by) and z chunk
@@ -110,11 +139,20 @@ cudaError_t launch_step2d(const StepParams& p, int R, bool vd, bool adj, int til
 cudaError_t launch_step3d(const StepParams& p, int R, bool vd, bool adj, int tile,
                           cudaStream_t st);
 size_t step2d_smem(int R, bool vd, bool adj, int tile);
+// Multi-problem forward step over `nunits` units (128 x 32 tiles, one shot per CTA).
+cudaError_t launch_step2d_multi(const MultiDesc* descs, const MultiUnit* units, int nunits, int n,
+                                int R, bool vd, cudaStream_t st);
+// TMA-staged 2D kernels with a loop over p.S shots per CTA (kernels2d_tma.cu);
+// tile = 0..NUM_TILE2-1 selects the same tile shapes as tile2_variant.
+cudaError_t launch_step2d_tma(const StepParams& p, const CUtensorMap& map, int R, bool vd, bool adj,
+                              int tile, cudaStream_t st);
+void tma_box2d(int R, int tile, int* bx, int* by);
 size_t step3d_smem(int R, bool vd, bool adj, int tile);
 
 // Auxiliary kernels (aux_kernels.cu)
 cudaError_t launch_model_prep(const Layout& L, const float* vp, const float* rho, double dt,
-                              float* kf, float* lnr, unsigned int* stats, cudaStream_t st);
+                              int param, float* kf, float* lnr, unsigned int* stats,
+                              cudaStream_t st);
 cudaError_t launch_density_grad(const Layout& L, const float* lnr, const AxisW& wx,
                                 const AxisW& wy, const AxisW& wz, float* bx, float* by,
                                 float* bz, cudaStream_t st);
@@ -127,9 +165,11 @@ cudaError_t launch_sum_partials(const double* partials, int n, double* out, cuda
 cudaError_t launch_traces_out(const float* d_ws, float* traces_out, int B, int shot0,
                               int nshots_batch, int nrec, int nt, int* nonfinite,
                               cudaStream_t st);
+// g[b / S] -= lam[b] * hist[b] for the nb shot slots of a batch
 cudaError_t launch_image_only(const Layout& L, const float* lam, const float* hist, float* g,
-                              int B, cudaStream_t st);
-cudaError_t launch_grad_finalize(const Layout& L, const float* g, int B, double inv_dt2,
+                              int nb, int S, cudaStream_t st);
+// grad_out = (sum of the G gradient slots) * inv_dt2 on the interior
+cudaError_t launch_grad_finalize(const Layout& L, const float* g, int G, double inv_dt2,
                                  float* grad_out, int* nonfinite, cudaStream_t st);
 
 }  // namespace fwi

@@ -58,9 +58,13 @@ __device__ __forceinline__ void sample_prologue(const StepParams& p, long long g
   }
 }
 
+// One tile (bxi, byi) of shot slot b: the body shared by the single-problem
+// kernel (indices from the launch grid) and the multi-problem kernel (indices
+// from a unit table).  samp_rank is the CTA's rank among the CTAs of its
+// problem, gx the problem's tile count along x.
 template <int R, bool VD, bool ADJ, int RY, int BY>
-__global__ void __launch_bounds__(32 * BY)
-k_step2d(const StepParams p) {
+__device__ __forceinline__ void step2d_tile(const StepParams& p, int bxi, int byi, int gx, int b,
+                                            long long samp_rank, float4* smem) {
   constexpr int TX = TILE_X;
   constexpr int TY = RY * BY;
   constexpr int XH = (R <= 4) ? 4 : 8;   // x halo in floats (float4 aligned)
@@ -71,22 +75,17 @@ k_step2d(const StepParams p) {
   constexpr int NV = 4 + 8 * NL;         // floats in one thread's x window
   constexpr int QW = TX / 4;             // psi_y row width in float4
 
-  extern __shared__ float4 smem[];
   float4* s_u = smem;                    // [SH][SW]
   float4* s_px = s_u + SH * SW;          // adjoint, variable density: [TY][SW]
   float4* s_py = s_px + TY * SW;         // adjoint, variable density: [SH][QW]
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * 32 + tx;
-  const int b = blockIdx.z;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int x0 = bxi * TX, y0 = byi * TY;
   const long long fo = (long long)b * p.fstride;
   const float* __restrict__ u = p.u + fo;
 
-  if (!ADJ && p.nrec > 0) {
-    const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    sample_prologue(p, blk * NT + tid);
-  }
+  if (!ADJ && p.nrec > 0) sample_prologue(p, samp_rank * NT + tid);
 
   // Stage the tile and its halo.
   const long long base = (long long)(y0 + p.oy - R) * p.sx + (x0 + p.ox - XH);
@@ -114,7 +113,7 @@ k_step2d(const StepParams p) {
   const float4 ax4 = ldg4(p.spx + xg);
   int e0 = 0, e1 = 0;
   if (p.inj_off) {
-    const int t = b * p.ntiles + blockIdx.y * gridDim.x + blockIdx.x;
+    const int t = b * p.ntiles + byi * gx + bxi;
     e0 = p.inj_off[t];
     e1 = p.inj_off[t + 1];
   }
@@ -249,6 +248,42 @@ k_step2d(const StepParams p) {
 }
 
 template <int R, bool VD, bool ADJ, int RY, int BY>
+__global__ void __launch_bounds__(32 * BY)
+k_step2d(const StepParams p) {
+  extern __shared__ float4 smem[];
+  const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  step2d_tile<R, VD, ADJ, RY, BY>(p, blockIdx.x, blockIdx.y, gridDim.x, blockIdx.z, blk, smem);
+}
+
+// Multi-problem step: CTA i advances unit units[i] (problem, tile, shot slot)
+// by one time step of that problem, described by descs[problem]; the step
+// index n is global (every problem started at n = 0).  The descriptor is copied
+// to shared memory and completed with the fields that depend on n.
+template <int R, bool VD, int RY, int BY>
+__global__ void __launch_bounds__(32 * BY)
+k_step2d_multi(const MultiDesc* __restrict__ descs, const MultiUnit* __restrict__ units, int n) {
+  extern __shared__ float4 smem[];
+  __shared__ StepParams sp;
+  const MultiUnit un = units[blockIdx.x];
+  {
+    const int* src = reinterpret_cast<const int*>(&descs[un.prob].p);
+    int* dst = reinterpret_cast<int*>(&sp);
+    for (int i = threadIdx.y * 32 + threadIdx.x; i < (int)(sizeof(StepParams) / 4); i += 32 * BY)
+      dst[i] = src[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    const MultiDesc& d = descs[un.prob];
+    sp.u = (n & 1) ? d.U1 : d.U0;
+    sp.up = (n & 1) ? d.U0 : d.U1;
+    sp.step_off = n;
+    sp.smp_off = (long long)n * sp.B * sp.nrec;
+  }
+  __syncthreads();
+  step2d_tile<R, VD, false, RY, BY>(sp, un.tx, un.ty, descs[un.prob].gx, un.slot, un.rank, smem);
+}
+
+template <int R, bool VD, bool ADJ, int RY, int BY>
 constexpr size_t smem_bytes() {
   constexpr int TY = RY * BY;
   constexpr int NL = (R <= 4) ? 1 : 2;
@@ -296,7 +331,31 @@ size_t smem_tile(int tile) {
   }
 }
 
+template <int R, bool VD>
+cudaError_t launch_multi_t(const MultiDesc* descs, const MultiUnit* units, int nunits, int n,
+                           cudaStream_t st) {
+  constexpr size_t smem = smem_bytes<R, VD, false, 4, 8>();
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_step2d_multi<R, VD, 4, 8>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  if (nunits <= 0) return cudaSuccess;
+  k_step2d_multi<R, VD, 4, 8><<<nunits, dim3(32, 8), smem, st>>>(descs, units, n);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_step2d_multi(const MultiDesc* descs, const MultiUnit* units, int nunits, int n,
+                                int R, bool vd, cudaStream_t st) {
+  if (R == 4) return vd ? launch_multi_t<4, true>(descs, units, nunits, n, st)
+                        : launch_multi_t<4, false>(descs, units, nunits, n, st);
+  return vd ? launch_multi_t<5, true>(descs, units, nunits, n, st)
+            : launch_multi_t<5, false>(descs, units, nunits, n, st);
+}
 
 cudaError_t launch_step2d(const StepParams& p, int R, bool vd, bool adj, int tile,
                           cudaStream_t st) {

@@ -1,0 +1,406 @@
+// 2D leapfrog step kernels, TMA-staged and looping over shots inside a CTA.
+//
+// Same arithmetic as kernels2d.cu (damped leapfrog for Eq. 10 of Sec. 2.4,
+// exact discrete adjoint, imaging condition of Sec. 2.2 Eq. 8 fused into the
+// adjoint), organised for HBM traffic:
+//
+//  * A CTA owns one 128 x (RY*BY) tile for a group of S shots of the batch.
+//    The model fields of the tile (k, and for the variable-density adjoint
+//    the b_x / b_y tiles with their halos) are loaded once and reused for the
+//    S shots; the adjoint's imaging term sum_s lambda_s h_s is accumulated in
+//    registers and added to the group's gradient slot once.  Per shot and
+//    grid point the compulsory traffic is then u^n, u^{n-1}, u^{n+1} and h
+//    (16 bytes) plus the shared fields divided by S.
+//  * Each shot's wavefield tile plus halo (radius R in y, 4 or 8 floats in x)
+//    is fetched by one thread with a 3D TMA copy (cp.async.bulk.tensor) into
+//    one of two shared-memory buffers, completion tracked by an mbarrier;
+//    the copy for shot k+2 is issued as soon as every thread is done with
+//    shot k, so loads overlap the stencil of the next shot.  Every mbarrier
+//    wait is bounded: on time-out the CTA sets an error flag and returns.
+#include "fwi_internal.cuh"
+
+#include <cuda.h>
+
+namespace fwi {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after ~2^22 polls (each poll may suspend briefly).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ float4 ldg4(const float* p) {
+  return __ldg(reinterpret_cast<const float4*>(p));
+}
+__device__ __forceinline__ float4 ld4(const float* p) {
+  return *reinterpret_cast<const float4*>(p);
+}
+__device__ __forceinline__ void st4(float* p, const float4& v) {
+  *reinterpret_cast<float4*>(p) = v;
+}
+__device__ __forceinline__ float get(const float4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ void unpack(const float4& t, float* v) {
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+
+template <int R, int RY, int BY>
+struct Geo {
+  static constexpr int TX = TILE_X;
+  static constexpr int TY = RY * BY;
+  static constexpr int XH = (R <= 4) ? 4 : 8;
+  static constexpr int NL = XH / 4;
+  static constexpr int SW = TX / 4 + 2 * NL;  // float4 per shared row
+  static constexpr int SH = TY + 2 * R;
+  static constexpr int QW = TX / 4;
+  static constexpr uint32_t TILE_BYTES = (uint32_t)SH * SW * 16;
+};
+
+template <int R, bool VD, bool ADJ, int RY, int BY>
+__global__ void __launch_bounds__(32 * BY, (RY == 1 ? 1024 : 512) / (32 * BY))
+k_step2d_tma(const StepParams p, const __grid_constant__ CUtensorMap tmap) {
+  using G = Geo<R, RY, BY>;
+  constexpr int TX = G::TX, TY = G::TY, NL = G::NL, SW = G::SW, SH = G::SH, QW = G::QW;
+  constexpr int NT = 32 * BY;
+  constexpr int NV = 4 + 8 * NL;
+
+  extern __shared__ __align__(128) float4 smem[];
+  float4* s_t0 = smem;                 // wavefield tile, buffer 0 [SH][SW]
+  float4* s_t1 = smem + SH * SW;       // buffer 1
+  float4* s_bx = smem + 2 * SH * SW;   // adjoint vd: b_x on tile rows with x halo [TY][SW]
+  float4* s_by = s_bx + TY * SW;       // adjoint vd: b_y on tile columns with y halo [SH][QW]
+  __shared__ uint64_t bar[2];
+
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * 32 + tx;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int s0 = blockIdx.z * p.S;
+  const int ns = min(p.S, p.B - s0);
+  const int tile_id = blockIdx.y * gridDim.x + blockIdx.x;
+
+  if (!ADJ && p.nrec > 0) {
+    // receiver sampling of u^n (not written during this step), one thread per slot x receiver
+    const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const long long gid = blk * NT + tid;
+    if (gid < (long long)p.B * p.nrec) {
+      const int bb = (int)(gid / p.nrec);
+      const int r = (int)(gid - (long long)bb * p.nrec);
+      const float* ub = p.u + (long long)bb * p.fstride;
+      float acc = 0.f;
+      for (int c = 0; c < p.ncorner; ++c)
+        acc = fmaf(p.smp_w[r * p.ncorner + c], ub[p.smp_node[r * p.ncorner + c]], acc);
+      p.smp_out[p.smp_off + (long long)bb * p.nrec + r] = acc;
+    }
+  }
+  if (ns <= 0) return;
+
+  const int tmx = x0 + p.ox - G::XH;   // multiple of 4 floats: 16-byte aligned box start
+  const int tmy = y0 + p.oy - R;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    mbar_arrive_expect_tx(&bar[0], G::TILE_BYTES);
+    tma_load_3d(s_t0, &tmap, &bar[0], tmx, tmy, s0);
+    if (ns > 1) {
+      mbar_arrive_expect_tx(&bar[1], G::TILE_BYTES);
+      tma_load_3d(s_t1, &tmap, &bar[1], tmx, tmy, s0 + 1);
+    }
+  }
+
+  // Shared model data of the tile, loaded once for the S shots.  Offsets
+  // inside one field fit in 32 bits; slot bases are formed once per shot.
+  const int xg = x0 + 4 * tx;
+  const int base = (y0 + p.oy - R) * p.sx + (x0 + p.ox - G::XH);
+  const float4 ax4 = ldg4(p.spx + xg);
+  int pix[RY];
+  float4 kk[RY];
+  float ay[RY];
+#pragma unroll
+  for (int iy = 0; iy < RY; ++iy) {
+    const int yg = y0 + ty * RY + iy;
+    pix[iy] = (yg + p.oy) * p.sx + (xg + p.ox);
+    kk[iy] = ldg4(p.kf + pix[iy]);
+    ay[iy] = p.spy[yg];
+  }
+  if (VD && ADJ) {
+    for (int i = tid; i < TY * SW; i += NT) {
+      const int r = i / SW, c = i - r * SW;
+      s_bx[i] = ldg4(p.bx + base + (r + R) * p.sx + 4 * c);
+    }
+    for (int i = tid; i < SH * QW; i += NT) {
+      const int r = i / QW, c = i - r * QW;
+      s_by[i] = ldg4(p.by + base + r * p.sx + 4 * (c + NL));
+    }
+  }
+  float gs[RY][4];
+#pragma unroll
+  for (int iy = 0; iy < RY; ++iy)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) gs[iy][q] = 0.f;
+  __syncthreads();   // the b_x / b_y tiles above are read by other threads
+
+  for (int k = 0; k < ns; ++k) {
+    const int s = s0 + k;
+    const int buf = k & 1;
+    const float4* s_u = buf ? s_t1 : s_t0;
+    float* const up_s = p.up + (size_t)s * p.fstride;
+    float* const h_s = p.hist ? p.hist + (size_t)s * p.fstride : nullptr;
+    // adjoint: this shot's global operands are issued before the tile wait
+    // (the forward loads u^{n-1} where it is used, to stay within 64 registers)
+    float4 uo[ADJ ? RY : 1], hv[ADJ ? RY : 1];
+    if (ADJ) {
+#pragma unroll
+      for (int iy = 0; iy < RY; ++iy) {
+        uo[iy] = ld4(up_s + pix[iy]);
+        if (p.image) hv[iy] = __ldcs(reinterpret_cast<const float4*>(h_s + pix[iy]));
+      }
+    }
+    // A wait that times out flags the error and carries on (no early exit, so
+    // no thread can miss a later barrier); the host reports FWI_ERR_TIMEOUT.
+    if (!mbar_wait_bounded(&bar[buf], (uint32_t)((k >> 1) & 1)) && p.flags) atomicOr(p.flags, 2);
+    int e0 = 0, e1 = 0;
+    if (p.inj_off) {
+      e0 = p.inj_off[s * p.ntiles + tile_id];
+      e1 = p.inj_off[s * p.ntiles + tile_id + 1];
+    }
+
+#pragma unroll
+    for (int iy = 0; iy < RY; ++iy) {
+      const int ly = ty * RY + iy;
+      const int yg = y0 + ly;
+      const int srow = ly + R;
+      float v[NV];
+#pragma unroll
+      for (int q = 0; q <= 2 * NL; ++q) unpack(s_u[srow * SW + tx + q], v + 4 * q);
+
+      // second derivatives in the zero-sum form sum_j w_j (u_{+j} + u_{-j} - 2 u_0)
+      float acc[4], c2[4], d1x[4], d1y[4];
+#pragma unroll
+      for (int ix = 0; ix < 4; ++ix) {
+        const int c = 4 * NL + ix;
+        c2[ix] = v[c] + v[c];
+        float t = 0.f;
+#pragma unroll
+        for (int j = 1; j <= R; ++j) t = fmaf(p.wx.w2[j], (v[c + j] + v[c - j]) - c2[ix], t);
+        acc[ix] = t;
+        d1x[ix] = 0.f;
+        d1y[ix] = 0.f;
+        if (VD && !ADJ) {
+#pragma unroll
+          for (int j = 1; j <= R; ++j) d1x[ix] = fmaf(p.wx.w1[j], v[c + j] - v[c - j], d1x[ix]);
+        }
+      }
+      if (VD && ADJ) {
+        // D1x(b_x lambda) from the b_x and lambda windows of this row
+        float bw[NV];
+#pragma unroll
+        for (int q = 0; q <= 2 * NL; ++q) unpack(s_bx[ly * SW + tx + q], bw + 4 * q);
+#pragma unroll
+        for (int ix = 0; ix < 4; ++ix) {
+          const int c = 4 * NL + ix;
+          float d = 0.f;
+#pragma unroll
+          for (int j = 1; j <= R; ++j)
+            d = fmaf(p.wx.w1[j], bw[c + j] * v[c + j] - bw[c - j] * v[c - j], d);
+          acc[ix] += d;
+        }
+      }
+#pragma unroll
+      for (int j = 1; j <= R; ++j) {
+        const float4 a = s_u[(srow - j) * SW + tx + NL];
+        const float4 c = s_u[(srow + j) * SW + tx + NL];
+        acc[0] = fmaf(p.wy.w2[j], (a.x + c.x) - c2[0], acc[0]);
+        acc[1] = fmaf(p.wy.w2[j], (a.y + c.y) - c2[1], acc[1]);
+        acc[2] = fmaf(p.wy.w2[j], (a.z + c.z) - c2[2], acc[2]);
+        acc[3] = fmaf(p.wy.w2[j], (a.w + c.w) - c2[3], acc[3]);
+        if (VD && !ADJ) {
+          d1y[0] = fmaf(p.wy.w1[j], c.x - a.x, d1y[0]);
+          d1y[1] = fmaf(p.wy.w1[j], c.y - a.y, d1y[1]);
+          d1y[2] = fmaf(p.wy.w1[j], c.z - a.z, d1y[2]);
+          d1y[3] = fmaf(p.wy.w1[j], c.w - a.w, d1y[3]);
+        }
+        if (VD && ADJ) {
+          // D1y(b_y lambda)
+          const float4 ba = s_by[(srow - j) * QW + tx];
+          const float4 bc = s_by[(srow + j) * QW + tx];
+          acc[0] = fmaf(p.wy.w1[j], bc.x * c.x - ba.x * a.x, acc[0]);
+          acc[1] = fmaf(p.wy.w1[j], bc.y * c.y - ba.y * a.y, acc[1]);
+          acc[2] = fmaf(p.wy.w1[j], bc.z * c.z - ba.z * a.z, acc[2]);
+          acc[3] = fmaf(p.wy.w1[j], bc.w * c.w - ba.w * a.w, acc[3]);
+        }
+      }
+      if (VD && !ADJ) {
+        // b_x, b_y are re-read per shot (L1 hits after the first shot)
+        const float4 bxv = ldg4(p.bx + pix[iy]), byv = ldg4(p.by + pix[iy]);
+#pragma unroll
+        for (int ix = 0; ix < 4; ++ix)
+          acc[ix] -= get(bxv, ix) * d1x[ix] + get(byv, ix) * d1y[ix];
+      }
+      if (e1 > e0) {
+        for (int e = e0; e < e1; ++e) {
+          const int loc = p.inj_loc[e];
+          const int ely = loc / TX, elx = loc - ely * TX;
+          if (ely == ly && (elx >> 2) == tx) {
+            const float val = p.inj_w[e] * p.vals[p.inj_vidx[e] + p.step_off];
+            const int ix = elx & 3;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] += (q == ix) ? val : 0.f;
+          }
+        }
+      }
+      float* upp = up_s + pix[iy];
+      const float4 uoi = ADJ ? uo[ADJ ? iy : 0] : ld4(upp);
+      float res[4], upd[4];
+#pragma unroll
+      for (int ix = 0; ix < 4; ++ix) {
+        const float a = get(ax4, ix) + ay[iy];
+        const float h = get(kk[iy], ix) * acc[ix];
+        const float cen = v[4 * NL + ix];
+        const float r = (2.f * cen - (1.f - a) * get(uoi, ix) + h) * __frcp_rn(1.f + a);
+        const bool in = (yg < p.ny) && (xg + ix < p.nx);
+        res[ix] = in ? r : 0.f;
+        upd[ix] = in ? h : 0.f;
+      }
+      st4(upp, make_float4(res[0], res[1], res[2], res[3]));
+      if (!ADJ) {
+        if (h_s)
+          __stcs(reinterpret_cast<float4*>(h_s + pix[iy]),
+                 make_float4(upd[0], upd[1], upd[2], upd[3]));
+      } else if (p.image) {
+        gs[iy][0] = fmaf(v[4 * NL + 0], hv[iy].x, gs[iy][0]);
+        gs[iy][1] = fmaf(v[4 * NL + 1], hv[iy].y, gs[iy][1]);
+        gs[iy][2] = fmaf(v[4 * NL + 2], hv[iy].z, gs[iy][2]);
+        gs[iy][3] = fmaf(v[4 * NL + 3], hv[iy].w, gs[iy][3]);
+      }
+    }
+    __syncthreads();   // every thread is done with this buffer
+    if (tid == 0 && k + 2 < ns) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&bar[buf], G::TILE_BYTES);
+      tma_load_3d(buf ? s_t1 : s_t0, &tmap, &bar[buf], tmx, tmy, s + 2);
+    }
+  }
+  if (ADJ && p.image) {
+    // g_group -= sum over this group's shots of lambda^k h^k
+    float* gbase = p.g + (size_t)blockIdx.z * p.fstride;
+#pragma unroll
+    for (int iy = 0; iy < RY; ++iy) {
+      float* gp = gbase + pix[iy];
+      float4 g = ld4(gp);
+      g.x -= gs[iy][0];
+      g.y -= gs[iy][1];
+      g.z -= gs[iy][2];
+      g.w -= gs[iy][3];
+      st4(gp, g);
+    }
+  }
+}
+
+template <int R, bool VD, bool ADJ, int RY, int BY>
+constexpr size_t smem_bytes() {
+  using G = Geo<R, RY, BY>;
+  size_t n = 2 * (size_t)G::SH * G::SW;
+  if (VD && ADJ) n += (size_t)G::TY * G::SW + (size_t)G::SH * G::QW;
+  return n * sizeof(float4);
+}
+
+template <int R, bool VD, bool ADJ, int RY, int BY>
+cudaError_t launch_t(const StepParams& p, const CUtensorMap& map, cudaStream_t st) {
+  constexpr int TY = RY * BY;
+  constexpr size_t smem = smem_bytes<R, VD, ADJ, RY, BY>();
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_step2d_tma<R, VD, ADJ, RY, BY>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_step2d_tma<R, VD, ADJ, RY, BY>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  dim3 grid((p.nx + TILE_X - 1) / TILE_X, (p.ny + TY - 1) / TY, (p.B + p.S - 1) / p.S);
+  dim3 block(32, BY);
+  k_step2d_tma<R, VD, ADJ, RY, BY><<<grid, block, smem, st>>>(p, map);
+  return cudaGetLastError();
+}
+
+template <int R, bool VD, bool ADJ>
+cudaError_t launch_tile(const StepParams& p, const CUtensorMap& map, int tile, cudaStream_t st) {
+  switch (tile) {
+    case 1: return launch_t<R, VD, ADJ, 1, 16>(p, map, st);
+    case 2: return launch_t<R, VD, ADJ, 2, 16>(p, map, st);
+    case 3: return launch_t<R, VD, ADJ, 2, 8>(p, map, st);
+    default: return launch_t<R, VD, ADJ, 1, 32>(p, map, st);
+  }
+}
+
+}  // namespace
+
+// tile: 0..3, the shapes of tile2_tma_variant
+cudaError_t launch_step2d_tma(const StepParams& p, const CUtensorMap& map, int R, bool vd, bool adj,
+                              int tile, cudaStream_t st) {
+  if (R == 4) {
+    if (vd) return adj ? launch_tile<4, true, true>(p, map, tile, st) : launch_tile<4, true, false>(p, map, tile, st);
+    return adj ? launch_tile<4, false, true>(p, map, tile, st) : launch_tile<4, false, false>(p, map, tile, st);
+  }
+  if (vd) return adj ? launch_tile<5, true, true>(p, map, tile, st) : launch_tile<5, true, false>(p, map, tile, st);
+  return adj ? launch_tile<5, false, true>(p, map, tile, st) : launch_tile<5, false, false>(p, map, tile, st);
+}
+
+// TMA box (floats) of a tile variant: {x extent, y extent}.
+void tma_box2d(int R, int tile, int* bx, int* by) {
+  const Tile2 t = tile2_tma_variant(tile);
+  const int XH = (R <= 4) ? 4 : 8;
+  *bx = TILE_X + 2 * XH;
+  *by = t.ry * t.by + 2 * R;
+}
+
+}  // namespace fwi

@@ -274,6 +274,53 @@ def config_skull_3d(n=256, dx=0.25e-3, nt=2000, nrec=512, every=16, radius=25e-3
                          c_max=c_max, radius=radius * scale, shots=shots)
 
 
+def config_uneven_batch(nprob=64, seed=4, side=(256, 1024), nt=(500, 4000), shots=(1, 16),
+                        dx=0.1e-3, order=8, nb=20, nelem=64, f0=500e3):
+    """Uneven set of independent 2D problems: square grids with side drawn
+    uniformly from `side` (multiples of 4), time axes from `nt`, shot counts
+    from `shots`; breast-like models as in ``breast_problem`` scaled to a ring
+    of radius 0.42 x side x dx; dt at CFL 0.4 of 1600 m/s."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(nprob):
+        n = 4 * int(rng.integers(side[0] // 4, side[1] // 4 + 1))
+        steps = int(rng.integers(nt[0], nt[1] + 1))
+        ns = int(rng.integers(shots[0], shots[1] + 1))
+        fire = np.linspace(0, nelem, ns, endpoint=False).astype(int)
+        p = breast_problem((n, n), dx, steps, nelem=nelem, shots=fire, order=order, nb=nb,
+                           seed=seed * 1000 + i, f0=f0, radius=0.42 * n * dx)
+        out.append(p)
+    return out
+
+
+def config_serving(nreq=650, seed=5, rate=20.0, frac_2d=0.75, frac_fwd=0.5,
+                   side2d=(512, 1024), side3d=(128, 192), nt=(1000, 3000)):
+    """Request stream for the serving pattern: Poisson arrivals (mean `rate`
+    per second), 75% 2D (side ~ U[512, 1024], multiple of 4, dx 0.1 mm,
+    breast-like) and 25% 3D (side ~ U[128, 192], dx 0.25 mm, skull-like),
+    half forward and half gradient, one shot each, nt ~ U[1000, 3000].
+    Returns a list of (arrival time in s, kind, Problem)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(nreq):
+        t += rng.exponential(1.0 / rate)
+        two_d = rng.uniform() < frac_2d
+        kind = "forward" if rng.uniform() < frac_fwd else "gradient"
+        steps = int(rng.integers(nt[0], nt[1] + 1))
+        if two_d:
+            n = 4 * int(rng.integers(side2d[0] // 4, side2d[1] // 4 + 1))
+            shot = [int(rng.integers(0, 64))]
+            p = breast_problem((n, n), 0.1e-3, steps, nelem=64, shots=shot, nb=20,
+                               seed=5000 + (i % 8), radius=0.42 * n * 0.1e-3)
+        else:
+            n = 4 * int(rng.integers(side3d[0] // 4, side3d[1] // 4 + 1))
+            p = skull_problem((n, n, n), 0.25e-3, steps, nrec=128, every=128,
+                              shots=[int(rng.integers(0, 128))], nb=16)
+        out.append((t, kind, p))
+    return out
+
+
 def random_smooth_model(shape, dx, seed, c_range=(1400.0, 1600.0), rho_range=(950.0, 1100.0),
                         sigma=1e-3):
     """Smooth random heterogeneous model (for parity tests on small grids)."""

@@ -87,18 +87,50 @@ def test_forward_3d_ragged(order, vd):
     assert rel_l2(got, ref) <= TOL_TRACES
 
 
-@pytest.mark.parametrize("tile", [0, 1, 2, 3])
-def test_tile_variants_bitwise_equal_2d(tile):
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_tile_variants_2d(tile):
+    """Shared-memory-staged variants (1-4) agree bit for bit among themselves,
+    TMA-staged shot-loop variants (5-8) likewise; the two families differ only
+    in the order of the variable-density adjoint terms (rounding)."""
     p = small_breast(nt=300)
-    base, _ = gpu_forward(p, tile=0)
-    got, _ = gpu_forward(p, tile=tile)
+    fam = 1 if tile <= 4 else 5
+    base, _ = gpu_forward(p, tile=fam)
+    got, plan = gpu_forward(p, tile=tile)
+    assert plan.stats()["tile"] == tile
     assert np.array_equal(got, base)
+    other, _ = gpu_forward(p, tile=6 - fam if fam == 1 else 1)
+    assert rel_l2(got, other) < 1e-6
 
 
-@pytest.mark.parametrize("tile", [0, 1, 2, 3])
+@pytest.mark.parametrize("spc", [1, 2, 3])
+def test_shots_per_cta_2d(spc):
+    """Looping 1, 2 or 3 shots inside a CTA changes nothing in the traces and
+    only the summation order of the gradient."""
+    p = small_breast(n=(130, 140), nt=150, shots=(0, 30, 64, 90))
+    obs = observed_from_oracle(p)
+    J0, g0, d0, _ = gpu_gradient(p, obs, tile=5, shots_per_cta=4)
+    J1, g1, d1, _ = gpu_gradient(p, obs, tile=5, shots_per_cta=spc)
+    assert np.array_equal(d1, d0)
+    assert rel_l2(g1, g0) < 1e-6
+    assert abs(J1 - J0) <= 1e-12 * abs(J0)
+
+
+@pytest.mark.parametrize("vd", [False, True])
+def test_gradient_2d_smem_family(vd):
+    """The shared-memory-staged kernels (one shot per CTA) against the oracle."""
+    p = small_breast(n=(150, 171), nt=400, shots=(0, 64), order=10)
+    obs = observed_from_oracle(p, variable_density=vd)
+    J_ref, g_ref, d_ref = oracle.gradient(oracle_grid(p), p.vp, p.rho if vd else None, p.src_xyz,
+                                          p.wavelet, p.rec_xyz, obs)
+    J, g, d, _ = gpu_gradient(p, obs, variable_density=vd, tile=2)
+    assert rel_l2(d, d_ref) <= TOL_TRACES
+    assert rel_l2(g, g_ref) <= TOL_GRAD
+
+
+@pytest.mark.parametrize("tile", [1, 2, 3, 4])
 def test_tile_variants_bitwise_equal_3d(tile):
     p = small_skull(nt=120)
-    base, _ = gpu_forward(p, tile=0)
+    base, _ = gpu_forward(p, tile=1)
     got, _ = gpu_forward(p, tile=tile)
     assert np.array_equal(got, base)
 
