@@ -212,10 +212,13 @@ typedef struct fwi_batch fwi_batch;
  * then runs in ONE launch of a multi-problem kernel per step (units =
  * problem x tile x shot; problems that have finished drop out), and with
  * use_graph = 1 the whole sequence, including the final sampling and trace
- * transposition, is captured once into a CUDA graph.  The problem arrays
- * must stay valid until fwi_batch_destroy. */
+ * transposition, is captured once into a CUDA graph.  opt (or NULL) selects
+ * the kernel variant (tile, shots_per_cta; 2D TMA variants 5-8 or variant 1)
+ * for every problem.  The problem arrays must stay valid until
+ * fwi_batch_destroy. */
 fwi_status fwi_batch_create(fwi_batch** batch, int nprob, const fwi_problem* probs,
-                            size_t hbm_budget_bytes, void* stream, int use_graph);
+                            const fwi_options* opt, size_t hbm_budget_bytes, void* stream,
+                            int use_graph);
 /* Run the batch (one graph launch); synchronises the stream. */
 fwi_status fwi_batch_run(fwi_batch* batch);
 fwi_status fwi_batch_stats_get(const fwi_batch* batch, fwi_batch_stats* out);

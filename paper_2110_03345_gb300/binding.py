@@ -126,8 +126,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.fwi_misfit_forward.restype = ctypes.c_int
         lib.fwi_misfit_backward.argtypes = [vp, vp]
         lib.fwi_misfit_backward.restype = ctypes.c_int
-        lib.fwi_batch_create.argtypes = [P(vp), ctypes.c_int, P(CProblem), ctypes.c_size_t, vp,
-                                         ctypes.c_int]
+        lib.fwi_batch_create.argtypes = [P(vp), ctypes.c_int, P(CProblem), P(COptions),
+                                         ctypes.c_size_t, vp, ctypes.c_int]
         lib.fwi_batch_create.restype = ctypes.c_int
         lib.fwi_batch_run.argtypes = [vp]
         lib.fwi_batch_run.restype = ctypes.c_int
@@ -345,7 +345,7 @@ class Batch:
     c_ref, vp, rho (CUDA tensors or None), geometry (Geometry), wavelet (CUDA
     tensor [shots][src][nt]).  Traces are allocated here (self.traces)."""
 
-    def __init__(self, problems, budget=0, stream=None, use_graph=True):
+    def __init__(self, problems, budget=0, stream=None, use_graph=True, tile=0, shots_per_cta=0):
         import torch
         lib = load()
         if stream is None:
@@ -369,9 +369,11 @@ class Batch:
             arr[i].wavelet = _ptr(pr["wavelet"])
             arr[i].traces = _ptr(tr)
         self._arr = arr
+        self._opts = COptions(0, 0, int(tile), 0, 0, int(shots_per_cta))
         h = ctypes.c_void_p()
-        _check(lib.fwi_batch_create(ctypes.byref(h), len(problems), arr, int(budget),
-                                    ctypes.c_void_p(stream.cuda_stream), int(bool(use_graph))))
+        _check(lib.fwi_batch_create(ctypes.byref(h), len(problems), arr, ctypes.byref(self._opts),
+                                    int(budget), ctypes.c_void_p(stream.cuda_stream),
+                                    int(bool(use_graph))))
         self._h = h
 
     def run(self):

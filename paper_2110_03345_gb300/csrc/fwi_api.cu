@@ -443,10 +443,10 @@ bool resolve_tile(const fwi_plan* P, int t, int* id, int* shape, bool* tma) {
     *tma = t > NUM_TILE2;
     *shape = (t - 1) % NUM_TILE2;
   } else {
-    if (t == 0) t = 1;
-    if (t < 1 || t > NUM_TILE3) return false;
-    *tma = false;
-    *shape = t - 1;
+    if (t == 0) t = 8;   // TMA-staged plane ring, 32 x 8 columns, 32-plane chunks
+    if (t < 1 || t > 2 * NUM_TILE3) return false;
+    *tma = t > NUM_TILE3;
+    *shape = (t - 1) % NUM_TILE3;
   }
   *id = t;
   return true;
@@ -633,6 +633,28 @@ fwi_status make_tensor_map(const fwi_plan* P, const float* base, int nslots, int
   return FWI_OK;
 }
 
+// 4D tensor map over nslots padded 3D fields: dims (x, y, z, slot); box = a
+// 48-float-wide x-y tile (16-byte aligned start) with its y halo, one plane.
+fwi_status make_tensor_map_3d(const fwi_plan* P, const float* base, int nslots, int shape,
+                              CUtensorMap* out) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  const cuuint64_t dims[4] = {(cuuint64_t)P->L.sx, (cuuint64_t)P->L.rows, (cuuint64_t)P->L.planes,
+                              (cuuint64_t)nslots};
+  const cuuint64_t strides[3] = {(cuuint64_t)P->L.sx * sizeof(float),
+                                 (cuuint64_t)P->L.sxy * sizeof(float),
+                                 (cuuint64_t)P->L.fstride * sizeof(float)};
+  const cuuint32_t box[4] = {48u, (cuuint32_t)tma_box3d_rows(P->R, shape), 1u, 1u};
+  const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+  const CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled (3D) failed with code " + std::to_string((int)r));
+  return FWI_OK;
+}
+
 struct Call {
   fwi_plan* P;
   const fwi_model* model;
@@ -738,7 +760,12 @@ fwi_status launch_step(Call& c, const StepParams& p_in, bool adj) {
   }
   if (prof) FWI_TRY(record_event(P, adj ? 1 : 0));
   cudaError_t e;
-  if (P->grid.ndim == 3) e = launch_step3d(p, P->R, c.vd, adj, c.pl.shape, P->st);
+  if (P->grid.ndim == 3 && c.pl.tma) {
+    const CUtensorMap* bxm = c.vd ? find_map(c, c.W.bx) : map;
+    const CUtensorMap* bym = c.vd ? find_map(c, c.W.by) : map;
+    if (!bxm || !bym) return fail(FWI_ERR_INVALID_ARG, "internal: no tensor map for b_x / b_y");
+    e = launch_step3d_tma(p, *map, *bxm, *bym, P->R, c.vd, adj, c.pl.shape, P->st);
+  } else if (P->grid.ndim == 3) e = launch_step3d(p, P->R, c.vd, adj, c.pl.shape, P->st);
   else if (c.pl.tma) e = launch_step2d_tma(p, *map, P->R, c.vd, adj, c.pl.shape, P->st);
   else e = launch_step2d(p, P->R, c.vd, adj, c.pl.shape, P->st);
   if (e != cudaSuccess) return fail(FWI_ERR_CUDA, std::string("stencil launch: ") + cudaGetErrorString(e));
@@ -937,11 +964,20 @@ fwi_status begin_call(fwi_plan* P, const fwi_model* model, const fwi_geometry* g
   carve_work(P, c.pl, geom, c.vd, C, c.W);
   if (C.off > P->arena_cap) return fail(FWI_ERR_BUDGET, "workspace carve exceeds allocation");
   if (c.pl.tma) {
+    const bool three = P->grid.ndim == 3;
     for (float* buf : {c.W.U0, c.W.U1, c.W.F0, c.W.F1}) {
       if (!buf) continue;
       Call::MapEnt m{buf, {}};
-      FWI_TRY(make_tensor_map(P, buf, c.pl.B, c.pl.shape, &m.map));
+      if (three) FWI_TRY(make_tensor_map_3d(P, buf, c.pl.B, c.pl.shape, &m.map));
+      else FWI_TRY(make_tensor_map(P, buf, c.pl.B, c.pl.shape, &m.map));
       c.maps.push_back(m);
+    }
+    if (three && c.vd) {
+      for (float* buf : {c.W.bx, c.W.by}) {
+        Call::MapEnt m{buf, {}};
+        FWI_TRY(make_tensor_map_3d(P, buf, 1, c.pl.shape, &m.map));
+        c.maps.push_back(m);
+      }
     }
   }
   FWI_TRY(ensure_tab(P, tables_bound(P, geom, c.pl) * 2));
@@ -1396,6 +1432,8 @@ struct fwi_batch {
   int device = 0;
   int R = 4;
   bool vd = false;
+  bool tma = true;      // TMA-staged multi-problem kernel (else shared-memory staged)
+  int shape = 0;        // tile shape of the batch's kernels
   MultiDesc* d_desc = nullptr;
   MultiUnit* d_units = nullptr;
   std::vector<int> active_units;      // units of the problems still running at step n
@@ -1428,7 +1466,10 @@ namespace {
 fwi_status batch_enqueue(fwi_batch* b) {
   int64_t launches = 0, updates = 0;
   for (int n = 0; n < b->max_steps; ++n) {
-    cudaError_t e = launch_step2d_multi(b->d_desc, b->d_units, b->active_units[n], n, b->R, b->vd, b->ws);
+    cudaError_t e = b->tma ? launch_step2d_tma_multi(b->d_desc, b->d_units, b->active_units[n], n,
+                                                     b->R, b->vd, b->shape, b->ws)
+                           : launch_step2d_multi(b->d_desc, b->d_units, b->active_units[n], n,
+                                                 b->R, b->vd, b->ws);
     if (e != cudaSuccess) return fail(FWI_ERR_CUDA, std::string("multi-problem step: ") + cudaGetErrorString(e));
     ++launches;
   }
@@ -1463,7 +1504,8 @@ fwi_status batch_enqueue(fwi_batch* b) {
 extern "C" {
 
 fwi_status fwi_batch_create(fwi_batch** out, int nprob, const fwi_problem* probs,
-                            size_t hbm_budget_bytes, void* stream, int use_graph) {
+                            const fwi_options* opt, size_t hbm_budget_bytes, void* stream,
+                            int use_graph) {
   if (!out || !probs || nprob < 1) return fail(FWI_ERR_INVALID_ARG, "bad batch arguments");
   *out = nullptr;
   fwi_batch* b = new fwi_batch();
@@ -1494,11 +1536,18 @@ fwi_status fwi_batch_create(fwi_batch** out, int nprob, const fwi_problem* probs
     FWI_TRY_B(fwi_plan_create(&it->P, &pr.grid, pr.nt, pr.dt, left, stream));
     fwi_options o{};
     o.batch = pr.geom.nshots;   // every shot of the problem in one batch
-    o.tile = 1;                 // shared-memory-staged 128 x 32 tiles (the multi-problem kernel's)
+    o.tile = opt ? opt->tile : 0;                  // 0: the default (TMA-staged) variant
+    o.shots_per_cta = opt ? opt->shots_per_cta : 0;
     it->P->opt = o;
     FWI_TRY_B(begin_call(it->P, &it->prob.model, &it->prob.geom, pr.wavelet, false, it->c, it->tabC));
     if (it->c.pl.B != pr.geom.nshots)
       return bail(fail(FWI_ERR_BUDGET, "problem " + std::to_string(i) + " does not fit the budget with all its shots"));
+    if (i == 0) {
+      b->tma = it->c.pl.tma;
+      b->shape = it->c.pl.shape;
+      if (!b->tma && b->shape != 0)
+        return bail(fail(FWI_ERR_UNSUPPORTED, "batches run the TMA variants or shared-memory variant 1"));
+    }
     Carve srcC = it->tabC;
     FWI_TRY_B(build_source_table(it->c, 0, pr.geom.nshots, srcC, it->src));
     const size_t fs = (size_t)it->P->L.fstride;
@@ -1528,15 +1577,25 @@ fwi_status fwi_batch_create(fwi_batch** out, int nprob, const fwi_problem* probs
     p.nrec = it->prob.geom.nrec;
     p.S = 1;
     p.flags = it->P->d_flags + 1;
+    p.S = c.pl.S;
     desc[k].p = p;
     desc[k].U0 = c.W.U0;
     desc[k].U1 = c.W.U1;
     desc[k].gx = c.T.gx;
     desc[k].nt = it->prob.nt;
+    if (b->tma) {
+      const CUtensorMap* m0 = find_map(c, c.W.U0);
+      const CUtensorMap* m1 = find_map(c, c.W.U1);
+      if (!m0 || !m1) return bail(fail(FWI_ERR_INVALID_ARG, "internal: missing tensor maps"));
+      desc[k].map0 = *m0;
+      desc[k].map1 = *m1;
+    }
+    // units: one per tile and shot group (TMA kernels loop S shots in a CTA)
+    const int groups = b->tma ? (p.B + p.S - 1) / p.S : p.B;
     long long rank = 0;
-    for (int sl = 0; sl < p.B; ++sl)
+    for (int gr = 0; gr < groups; ++gr)
       for (int ty = 0; ty < c.T.gy; ++ty)
-        for (int tx = 0; tx < c.T.gx; ++tx) units.push_back({(int)k, tx, ty, sl, rank++});
+        for (int tx = 0; tx < c.T.gx; ++tx) units.push_back({(int)k, tx, ty, gr, rank++});
     prefix.push_back((int)units.size());
   }
   b->max_steps = b->items.empty() ? 0 : b->items[0]->prob.nt - 1;
@@ -1561,7 +1620,9 @@ fwi_status fwi_batch_create(fwi_batch** out, int nprob, const fwi_problem* probs
     // set the kernels' attributes outside the capture (zero-unit launch), then
     // capture every launch of a run
     {
-      cudaError_t e = launch_step2d_multi(b->d_desc, b->d_units, 0, 0, b->R, b->vd, b->ws);
+      cudaError_t e = b->tma ? launch_step2d_tma_multi(b->d_desc, b->d_units, 0, 0, b->R, b->vd,
+                                                       b->shape, b->ws)
+                             : launch_step2d_multi(b->d_desc, b->d_units, 0, 0, b->R, b->vd, b->ws);
       if (e != cudaSuccess) return bail(fail(FWI_ERR_CUDA, cudaGetErrorString(e)));
     }
     CUDA_TRY_B(cudaStreamBeginCapture(b->ws, cudaStreamCaptureModeThreadLocal));

@@ -89,6 +89,8 @@ struct StepParams {
 // holds the problem's StepParams except the per-step fields, which the kernel
 // derives from the global step n and the two wavefield buffers.
 struct MultiDesc {
+  CUtensorMap map0;   // TMA descriptors of U0 and U1 (TMA-staged kernels)
+  CUtensorMap map1;
   StepParams p;
   float* U0;   // u^n for even n (then u^{n-1} for odd n), [B][fstride]
   float* U1;
@@ -139,6 +141,10 @@ cudaError_t launch_step2d(const StepParams& p, int R, bool vd, bool adj, int til
 cudaError_t launch_step3d(const StepParams& p, int R, bool vd, bool adj, int tile,
                           cudaStream_t st);
 size_t step2d_smem(int R, bool vd, bool adj, int tile);
+// Multi-problem forward step, TMA-staged (kernels2d_tma.cu); units are
+// (problem, tile, shot group) with the tile shape tile2_tma_variant(tile).
+cudaError_t launch_step2d_tma_multi(const MultiDesc* descs, const MultiUnit* units, int nunits,
+                                    int n, int R, bool vd, int tile, cudaStream_t st);
 // Multi-problem forward step over `nunits` units (128 x 32 tiles, one shot per CTA).
 cudaError_t launch_step2d_multi(const MultiDesc* descs, const MultiUnit* units, int nunits, int n,
                                 int R, bool vd, cudaStream_t st);
@@ -148,6 +154,13 @@ cudaError_t launch_step2d_tma(const StepParams& p, const CUtensorMap& map, int R
                               int tile, cudaStream_t st);
 void tma_box2d(int R, int tile, int* bx, int* by);
 size_t step3d_smem(int R, bool vd, bool adj, int tile);
+// TMA-staged 3D kernels (kernels3d_tma.cu): um maps the wavefield buffer p.u
+// as (x, y, z, slot); bxm / bym map the b_x / b_y fields (variable-density
+// adjoint only).  tile = 0..NUM_TILE3-1 as tile3_variant.
+cudaError_t launch_step3d_tma(const StepParams& p, const CUtensorMap& um, const CUtensorMap& bxm,
+                              const CUtensorMap& bym, int R, bool vd, bool adj, int tile,
+                              cudaStream_t st);
+int tma_box3d_rows(int R, int tile);
 
 // Auxiliary kernels (aux_kernels.cu)
 cudaError_t launch_model_prep(const Layout& L, const float* vp, const float* rho, double dt,

@@ -18,6 +18,7 @@
 //    shot k, so loads overlap the stencil of the next shot.  Every mbarrier
 //    wait is bounded: on time-out the CTA sets an error flag and returns.
 #include "fwi_internal.cuh"
+#include "tma_util.cuh"
 
 #include <cuda.h>
 
@@ -25,51 +26,7 @@ namespace fwi {
 
 namespace {
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n"
-      " .reg .pred p;\n"
-      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n"
-      "}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: gives up after ~2^22 polls (each poll may suspend briefly).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < (1u << 22); ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int x, int y, int z) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-      : "memory");
-}
+using namespace tma;
 
 __device__ __forceinline__ float4 ldg4(const float* p) {
   return __ldg(reinterpret_cast<const float4*>(p));
@@ -99,32 +56,35 @@ struct Geo {
   static constexpr uint32_t TILE_BYTES = (uint32_t)SH * SW * 16;
 };
 
+// One tile (bxi, byi) for shot group grp (shots grp*S .. grp*S+S-1): the body
+// shared by the single-problem kernel and the multi-problem kernel.  tmap is
+// the tensor map of the wavefield buffer p.u (param or global memory);
+// samp_rank is the CTA's rank among its problem's CTAs, gx the problem's tile
+// count along x.
 template <int R, bool VD, bool ADJ, int RY, int BY>
-__global__ void __launch_bounds__(32 * BY, (RY == 1 ? 1024 : 512) / (32 * BY))
-k_step2d_tma(const StepParams p, const __grid_constant__ CUtensorMap tmap) {
+__device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const CUtensorMap* tmap,
+                                                int bxi, int byi, int gx, int grp,
+                                                long long samp_rank, float4* smem, uint64_t* bar) {
   using G = Geo<R, RY, BY>;
   constexpr int TX = G::TX, TY = G::TY, NL = G::NL, SW = G::SW, SH = G::SH, QW = G::QW;
   constexpr int NT = 32 * BY;
   constexpr int NV = 4 + 8 * NL;
 
-  extern __shared__ __align__(128) float4 smem[];
   float4* s_t0 = smem;                 // wavefield tile, buffer 0 [SH][SW]
   float4* s_t1 = smem + SH * SW;       // buffer 1
   float4* s_bx = smem + 2 * SH * SW;   // adjoint vd: b_x on tile rows with x halo [TY][SW]
   float4* s_by = s_bx + TY * SW;       // adjoint vd: b_y on tile columns with y halo [SH][QW]
-  __shared__ uint64_t bar[2];
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * 32 + tx;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int s0 = blockIdx.z * p.S;
+  const int x0 = bxi * TX, y0 = byi * TY;
+  const int s0 = grp * p.S;
   const int ns = min(p.S, p.B - s0);
-  const int tile_id = blockIdx.y * gridDim.x + blockIdx.x;
+  const int tile_id = byi * gx + bxi;
 
   if (!ADJ && p.nrec > 0) {
     // receiver sampling of u^n (not written during this step), one thread per slot x receiver
-    const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    const long long gid = blk * NT + tid;
+    const long long gid = samp_rank * NT + tid;
     if (gid < (long long)p.B * p.nrec) {
       const int bb = (int)(gid / p.nrec);
       const int r = (int)(gid - (long long)bb * p.nrec);
@@ -147,10 +107,10 @@ k_step2d_tma(const StepParams p, const __grid_constant__ CUtensorMap tmap) {
   __syncthreads();
   if (tid == 0) {
     mbar_arrive_expect_tx(&bar[0], G::TILE_BYTES);
-    tma_load_3d(s_t0, &tmap, &bar[0], tmx, tmy, s0);
+    tma_load_3d(s_t0, tmap, &bar[0], tmx, tmy, s0);
     if (ns > 1) {
       mbar_arrive_expect_tx(&bar[1], G::TILE_BYTES);
-      tma_load_3d(s_t1, &tmap, &bar[1], tmx, tmy, s0 + 1);
+      tma_load_3d(s_t1, tmap, &bar[1], tmx, tmy, s0 + 1);
     }
   }
 
@@ -253,28 +213,42 @@ k_step2d_tma(const StepParams p, const __grid_constant__ CUtensorMap tmap) {
         }
       }
 #pragma unroll
-      for (int j = 1; j <= R; ++j) {
-        const float4 a = s_u[(srow - j) * SW + tx + NL];
-        const float4 c = s_u[(srow + j) * SW + tx + NL];
-        acc[0] = fmaf(p.wy.w2[j], (a.x + c.x) - c2[0], acc[0]);
-        acc[1] = fmaf(p.wy.w2[j], (a.y + c.y) - c2[1], acc[1]);
-        acc[2] = fmaf(p.wy.w2[j], (a.z + c.z) - c2[2], acc[2]);
-        acc[3] = fmaf(p.wy.w2[j], (a.w + c.w) - c2[3], acc[3]);
-        if (VD && !ADJ) {
-          d1y[0] = fmaf(p.wy.w1[j], c.x - a.x, d1y[0]);
-          d1y[1] = fmaf(p.wy.w1[j], c.y - a.y, d1y[1]);
-          d1y[2] = fmaf(p.wy.w1[j], c.z - a.z, d1y[2]);
-          d1y[3] = fmaf(p.wy.w1[j], c.w - a.w, d1y[3]);
+      {
+        // y-direction taps on the (x, y) and (z, w) halves of the float4 rows as
+        // packed FP32x2 operations: one instruction serves two grid points
+        // (round-to-nearest per lane, the same results as the scalar sequence).
+        float2 A0 = make_float2(acc[0], acc[1]), A1 = make_float2(acc[2], acc[3]);
+        const float2 n0 = make_float2(-c2[0], -c2[1]), n1 = make_float2(-c2[2], -c2[3]);
+        float2 D0 = make_float2(0.f, 0.f), D1 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 1; j <= R; ++j) {
+          const float4 a = s_u[(srow - j) * SW + tx + NL];
+          const float4 c = s_u[(srow + j) * SW + tx + NL];
+          const float2 a0 = make_float2(a.x, a.y), a1 = make_float2(a.z, a.w);
+          const float2 c0 = make_float2(c.x, c.y), c1 = make_float2(c.z, c.w);
+          const float2 w2 = make_float2(p.wy.w2[j], p.wy.w2[j]);
+          A0 = __ffma2_rn(w2, __fadd2_rn(__fadd2_rn(a0, c0), n0), A0);
+          A1 = __ffma2_rn(w2, __fadd2_rn(__fadd2_rn(a1, c1), n1), A1);
+          if (VD) {
+            const float2 w1 = make_float2(p.wy.w1[j], p.wy.w1[j]);
+            if (!ADJ) {
+              D0 = __ffma2_rn(w1, __fadd2_rn(c0, make_float2(-a0.x, -a0.y)), D0);
+              D1 = __ffma2_rn(w1, __fadd2_rn(c1, make_float2(-a1.x, -a1.y)), D1);
+            } else {
+              // D1y(b_y lambda): b_y(+j) lambda(+j) - b_y(-j) lambda(-j)
+              const float4 ba = s_by[(srow - j) * QW + tx];
+              const float4 bc = s_by[(srow + j) * QW + tx];
+              const float2 t0 = __ffma2_rn(make_float2(-ba.x, -ba.y), a0,
+                                           __fmul2_rn(make_float2(bc.x, bc.y), c0));
+              const float2 t1 = __ffma2_rn(make_float2(-ba.z, -ba.w), a1,
+                                           __fmul2_rn(make_float2(bc.z, bc.w), c1));
+              A0 = __ffma2_rn(w1, t0, A0);
+              A1 = __ffma2_rn(w1, t1, A1);
+            }
+          }
         }
-        if (VD && ADJ) {
-          // D1y(b_y lambda)
-          const float4 ba = s_by[(srow - j) * QW + tx];
-          const float4 bc = s_by[(srow + j) * QW + tx];
-          acc[0] = fmaf(p.wy.w1[j], bc.x * c.x - ba.x * a.x, acc[0]);
-          acc[1] = fmaf(p.wy.w1[j], bc.y * c.y - ba.y * a.y, acc[1]);
-          acc[2] = fmaf(p.wy.w1[j], bc.z * c.z - ba.z * a.z, acc[2]);
-          acc[3] = fmaf(p.wy.w1[j], bc.w * c.w - ba.w * a.w, acc[3]);
-        }
+        acc[0] = A0.x; acc[1] = A0.y; acc[2] = A1.x; acc[3] = A1.y;
+        d1y[0] = D0.x; d1y[1] = D0.y; d1y[2] = D1.x; d1y[3] = D1.y;
       }
       if (VD && !ADJ) {
         // b_x, b_y are re-read per shot (L1 hits after the first shot)
@@ -324,12 +298,12 @@ k_step2d_tma(const StepParams p, const __grid_constant__ CUtensorMap tmap) {
     if (tid == 0 && k + 2 < ns) {
       fence_proxy_async_smem();
       mbar_arrive_expect_tx(&bar[buf], G::TILE_BYTES);
-      tma_load_3d(buf ? s_t1 : s_t0, &tmap, &bar[buf], tmx, tmy, s + 2);
+      tma_load_3d(buf ? s_t1 : s_t0, tmap, &bar[buf], tmx, tmy, s + 2);
     }
   }
   if (ADJ && p.image) {
     // g_group -= sum over this group's shots of lambda^k h^k
-    float* gbase = p.g + (size_t)blockIdx.z * p.fstride;
+    float* gbase = p.g + (size_t)grp * p.fstride;
 #pragma unroll
     for (int iy = 0; iy < RY; ++iy) {
       float* gp = gbase + pix[iy];
@@ -341,6 +315,45 @@ k_step2d_tma(const StepParams p, const __grid_constant__ CUtensorMap tmap) {
       st4(gp, g);
     }
   }
+}
+
+template <int R, bool VD, bool ADJ, int RY, int BY>
+__global__ void __launch_bounds__(32 * BY, (RY == 1 ? 1024 : 512) / (32 * BY))
+k_step2d_tma(const StepParams p, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(128) float4 smem[];
+  __shared__ uint64_t bar[2];
+  const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  step2d_tma_tile<R, VD, ADJ, RY, BY>(p, &tmap, blockIdx.x, blockIdx.y, gridDim.x, blockIdx.z,
+                                      blk, smem, bar);
+}
+
+// Multi-problem forward step with TMA staging: CTA i advances unit units[i]
+// (problem, tile, shot group) by one step; the problem's StepParams and the
+// tensor maps of its two wavefield buffers come from descs (global memory).
+template <int R, bool VD, int RY, int BY>
+__global__ void __launch_bounds__(32 * BY, (RY == 1 ? 1024 : 512) / (32 * BY))
+k_step2d_tma_multi(const MultiDesc* __restrict__ descs, const MultiUnit* __restrict__ units, int n) {
+  extern __shared__ __align__(128) float4 smem[];
+  __shared__ uint64_t bar[2];
+  __shared__ StepParams sp;
+  const MultiUnit un = units[blockIdx.x];
+  const MultiDesc* d = descs + un.prob;
+  {
+    const int* src = reinterpret_cast<const int*>(&d->p);
+    int* dst = reinterpret_cast<int*>(&sp);
+    for (int i = threadIdx.y * 32 + threadIdx.x; i < (int)(sizeof(StepParams) / 4); i += 32 * BY)
+      dst[i] = src[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    sp.u = (n & 1) ? d->U1 : d->U0;
+    sp.up = (n & 1) ? d->U0 : d->U1;
+    sp.step_off = n;
+    sp.smp_off = (long long)n * sp.B * sp.nrec;
+  }
+  __syncthreads();
+  const CUtensorMap* map = (n & 1) ? &d->map1 : &d->map0;
+  step2d_tma_tile<R, VD, false, RY, BY>(sp, map, un.tx, un.ty, d->gx, un.slot, un.rank, smem, bar);
 }
 
 template <int R, bool VD, bool ADJ, int RY, int BY>
@@ -382,7 +395,46 @@ cudaError_t launch_tile(const StepParams& p, const CUtensorMap& map, int tile, c
   }
 }
 
+template <int R, bool VD, int RY, int BY>
+cudaError_t launch_multi_t(const MultiDesc* descs, const MultiUnit* units, int nunits, int n,
+                           cudaStream_t st) {
+  constexpr size_t smem = smem_bytes<R, VD, false, RY, BY>();
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_step2d_tma_multi<R, VD, RY, BY>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_step2d_tma_multi<R, VD, RY, BY>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  if (nunits <= 0) return cudaSuccess;
+  k_step2d_tma_multi<R, VD, RY, BY><<<nunits, dim3(32, BY), smem, st>>>(descs, units, n);
+  return cudaGetLastError();
+}
+
+template <int R, bool VD>
+cudaError_t launch_multi_tile(const MultiDesc* descs, const MultiUnit* units, int nunits, int n,
+                              int tile, cudaStream_t st) {
+  switch (tile) {
+    case 1: return launch_multi_t<R, VD, 1, 16>(descs, units, nunits, n, st);
+    case 2: return launch_multi_t<R, VD, 2, 16>(descs, units, nunits, n, st);
+    case 3: return launch_multi_t<R, VD, 2, 8>(descs, units, nunits, n, st);
+    default: return launch_multi_t<R, VD, 1, 32>(descs, units, nunits, n, st);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_step2d_tma_multi(const MultiDesc* descs, const MultiUnit* units, int nunits,
+                                    int n, int R, bool vd, int tile, cudaStream_t st) {
+  if (R == 4) return vd ? launch_multi_tile<4, true>(descs, units, nunits, n, tile, st)
+                        : launch_multi_tile<4, false>(descs, units, nunits, n, tile, st);
+  return vd ? launch_multi_tile<5, true>(descs, units, nunits, n, tile, st)
+            : launch_multi_tile<5, false>(descs, units, nunits, n, tile, st);
+}
 
 // tile: 0..3, the shapes of tile2_tma_variant
 cudaError_t launch_step2d_tma(const StepParams& p, const CUtensorMap& map, int R, bool vd, bool adj,

@@ -1,0 +1,307 @@
+// 3D leapfrog step kernels, TMA-staged (2.5D blocking with a plane ring).
+//
+// Same arithmetic as kernels3d.cu (Eq. 10 of Sec. 2.4 without attenuation,
+// damped leapfrog, exact discrete adjoint, imaging condition of Sec. 2.2
+// Eq. 8 fused into the adjoint).  A CTA of 32 x BY threads owns a 32 x BY
+// column of one shot and streams along z over a chunk of planes:
+//
+//  * each x-y plane of the column, with its halo, arrives by a 4D TMA copy
+//    (x, y, z, shot) into a ring of 2R+2 shared-memory planes, so the copies
+//    of the next planes run while the current plane is computed;
+//  * a thread keeps the 2R+1 values of its own column in a register queue,
+//    filled from the ring as each plane arrives (z derivatives in registers),
+//    and reads the x / y neighbours of the centre plane from the ring;
+//  * the variable-density adjoint also needs b_x, b_y with their halos on the
+//    centre plane: they come through a second, two-stage TMA ring; b_z
+//    lambda is queued like lambda.
+// Every mbarrier wait is bounded (on time-out the error flag is set and the
+// kernel carries on, so no thread skips a barrier).
+#include "fwi_internal.cuh"
+#include "tma_util.cuh"
+
+#include <cuda.h>
+
+namespace fwi {
+
+namespace {
+
+using namespace tma;
+
+template <int R, int BY>
+struct Geo3 {
+  static constexpr int BXW = 48;             // floats per staged row: x0-8 .. x0+39
+  static constexpr int XOFF = 8;             // column of x0 in a staged row
+  static constexpr int BYH = BY + 2 * R;     // staged rows: y0-R .. y0+BY+R-1
+  static constexpr int PLANE = BYH * BXW;    // floats per staged plane
+  static constexpr int NSU = 2 * R + 2;      // ring depth (centre .. lead + 1 prefetch)
+  static constexpr uint32_t PLANE_BYTES = PLANE * 4;
+};
+
+template <int R, bool VD, bool ADJ, int BY>
+__global__ void __launch_bounds__(32 * BY)
+k_step3d_tma(const StepParams p, const __grid_constant__ CUtensorMap umap,
+             const __grid_constant__ CUtensorMap bxmap, const __grid_constant__ CUtensorMap bymap) {
+  using G = Geo3<R, BY>;
+  constexpr int TX = 32, TY = BY;
+  constexpr int NT = 32 * BY;
+  constexpr int Q = 2 * R + 1;
+  constexpr bool PSI = VD && ADJ;
+  constexpr int NSU = G::NSU;
+  extern __shared__ __align__(128) float smem3[];
+  float* ring = smem3;                       // [NSU][BYH][BXW]
+  float* bring = ring + NSU * G::PLANE;      // PSI: [2 stages][b_x, b_y][BYH][BXW]
+  __shared__ uint64_t bar[NSU];
+  __shared__ uint64_t bbar[2];
+
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * 32 + tx;
+  const int b = blockIdx.z / p.nzc;
+  const int zc = blockIdx.z - b * p.nzc;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int z0 = zc * p.zchunk;
+  const int z1 = min(z0 + p.zchunk, p.nz);
+  const int nz_c = z1 - z0;
+  const int nplanes = nz_c + 2 * R;
+  const size_t fo = (size_t)b * p.fstride;
+  const int xg = x0 + tx, yg = y0 + ty;
+  const long long col = (long long)(yg + p.oy) * p.sx + (xg + p.ox);
+
+  if (!ADJ && p.nrec > 0) {
+    const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const long long gid = blk * NT + tid;
+    if (gid < (long long)p.B * p.nrec) {
+      const int bb = (int)(gid / p.nrec);
+      const int r = (int)(gid - (long long)bb * p.nrec);
+      const float* ub = p.u + (long long)bb * p.fstride;
+      float acc = 0.f;
+      for (int c = 0; c < p.ncorner; ++c)
+        acc = fmaf(p.smp_w[r * p.ncorner + c], ub[p.smp_node[r * p.ncorner + c]], acc);
+      p.smp_out[p.smp_off + (long long)bb * p.nrec + r] = acc;
+    }
+  }
+  if (nz_c <= 0) return;
+
+  const int tmx = x0 + p.ox - G::XOFF;     // 16-byte aligned box start
+  const int tmy = y0 + p.oy - R;
+  const int pz0 = z0 - R + p.oz;           // padded z of staged plane 0
+  if (tid == 0) {
+    for (int k = 0; k < NSU; ++k) mbar_init(&bar[k], 1);
+    mbar_init(&bbar[0], 1);
+    mbar_init(&bbar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int lp = 0; lp < NSU && lp < nplanes; ++lp) {
+      mbar_arrive_expect_tx(&bar[lp], G::PLANE_BYTES);
+      tma_load_4d(ring + lp * G::PLANE, &umap, &bar[lp], tmx, tmy, pz0 + lp, b);
+    }
+    if (PSI) {
+      for (int i = 0; i < 2 && i < nz_c; ++i) {
+        mbar_arrive_expect_tx(&bbar[i], 2 * G::PLANE_BYTES);
+        tma_load_4d(bring + (2 * i) * G::PLANE, &bxmap, &bbar[i], tmx, tmy, z0 + i + p.oz, 0);
+        tma_load_4d(bring + (2 * i + 1) * G::PLANE, &bymap, &bbar[i], tmx, tmy, z0 + i + p.oz, 0);
+      }
+    }
+  }
+
+  const int own = (ty + R) * G::BXW + tx + G::XOFF;   // own column in a staged plane
+  bool timed_out = false;
+  // register queues: q[j] = u at plane z - R + j of this column
+  float q[Q];
+  float qz[PSI ? Q : 1];
+#pragma unroll
+  for (int lp = 0; lp < Q - 1; ++lp) {
+    if (!mbar_wait_bounded(&bar[lp], 0)) timed_out = true;
+    q[lp] = ring[lp * G::PLANE + own];
+    if (PSI) qz[lp] = __ldg(p.bz + (long long)(pz0 + lp) * p.sxy + col) * q[lp];
+  }
+  __syncthreads();   // planes 0..R-1 are halo-only: their buffers take planes NSU..NSU+R-1
+  if (tid == 0) {
+    for (int lp = NSU; lp < NSU + R && lp < nplanes; ++lp) {
+      const int k = lp % NSU;
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&bar[k], G::PLANE_BYTES);
+      tma_load_4d(ring + k * G::PLANE, &umap, &bar[k], tmx, tmy, pz0 + lp, b);
+    }
+  }
+
+  const float axy = p.spx[xg] + p.spy[yg];
+  const bool in_xy = (xg < p.nx) && (yg < p.ny);
+  int e0 = 0, e1 = 0;
+  if (p.inj_off) {
+    const int t = b * p.ntiles + (zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    e0 = p.inj_off[t];
+    e1 = p.inj_off[t + 1];
+  }
+  const int r0 = ty + R, c0 = tx + G::XOFF;
+
+  // Global operands of a point (u^{n-1}, k, h, b) are loaded one plane ahead
+  // (software pipelining in registers), so their latency overlaps a plane.
+  struct Ops {
+    float uo, kk, hv, bx, by, bz, bzl;
+  };
+  auto load_ops = [&](int ii) {
+    Ops o{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const long long id = (long long)(z0 + ii + p.oz) * p.sxy + col;
+    o.uo = p.up[fo + id];
+    o.kk = __ldg(p.kf + id);
+    if (ADJ && p.image) o.hv = __ldcs(p.hist + fo + id);
+    if (VD && !ADJ) {
+      o.bx = __ldg(p.bx + id);
+      o.by = __ldg(p.by + id);
+      o.bz = __ldg(p.bz + id);
+    }
+    if (PSI) o.bzl = __ldg(p.bz + (long long)(pz0 + ii + 2 * R) * p.sxy + col);
+    return o;
+  };
+  Ops nxt = load_ops(0);
+
+  for (int i = 0; i < nz_c; ++i) {
+    const int z = z0 + i;
+    const long long idx = (long long)(z + p.oz) * p.sxy + col;
+    const Ops cur = nxt;
+    if (i + 1 < nz_c) nxt = load_ops(i + 1);
+    const float uo = cur.uo, kk = cur.kk, hv = cur.hv, bxv = cur.bx, byv = cur.by, bzv = cur.bz;
+    // the lead plane z + R completes the queue
+    const int lead = i + 2 * R;
+    if (!mbar_wait_bounded(&bar[lead % NSU], (uint32_t)((lead / NSU) & 1))) timed_out = true;
+    q[Q - 1] = ring[(lead % NSU) * G::PLANE + own];
+    if (PSI) qz[Q - 1] = cur.bzl * q[Q - 1];
+    const float* cp = ring + ((i + R) % NSU) * G::PLANE;   // centre plane z
+    const float* bxp = bring + (2 * (i & 1)) * G::PLANE;
+    const float* byp = bxp + G::PLANE;
+    if (PSI && !mbar_wait_bounded(&bbar[i & 1], (uint32_t)((i >> 1) & 1))) timed_out = true;
+
+    // zero-sum second derivatives, sum_j w_j (u_{+j} + u_{-j} - 2 u_0)
+    const float cen = q[R];
+    const float c2 = cen + cen;
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 1; j <= R; ++j) {
+      acc = fmaf(p.wx.w2[j], (cp[r0 * G::BXW + c0 + j] + cp[r0 * G::BXW + c0 - j]) - c2, acc);
+      acc = fmaf(p.wy.w2[j], (cp[(r0 + j) * G::BXW + c0] + cp[(r0 - j) * G::BXW + c0]) - c2, acc);
+      acc = fmaf(p.wz.w2[j], (q[R + j] + q[R - j]) - c2, acc);
+    }
+    if (VD && !ADJ) {
+      float dx = 0.f, dy = 0.f, dz = 0.f;
+#pragma unroll
+      for (int j = 1; j <= R; ++j) {
+        dx = fmaf(p.wx.w1[j], cp[r0 * G::BXW + c0 + j] - cp[r0 * G::BXW + c0 - j], dx);
+        dy = fmaf(p.wy.w1[j], cp[(r0 + j) * G::BXW + c0] - cp[(r0 - j) * G::BXW + c0], dy);
+        dz = fmaf(p.wz.w1[j], q[R + j] - q[R - j], dz);
+      }
+      acc -= bxv * dx + byv * dy + bzv * dz;
+    }
+    if (PSI) {
+#pragma unroll
+      for (int j = 1; j <= R; ++j) {
+        const int xp = r0 * G::BXW + c0 + j, xm = r0 * G::BXW + c0 - j;
+        const int yp = (r0 + j) * G::BXW + c0, ym = (r0 - j) * G::BXW + c0;
+        acc = fmaf(p.wx.w1[j], bxp[xp] * cp[xp] - bxp[xm] * cp[xm], acc);
+        acc = fmaf(p.wy.w1[j], byp[yp] * cp[yp] - byp[ym] * cp[ym], acc);
+        acc = fmaf(p.wz.w1[j], qz[R + j] - qz[R - j], acc);
+      }
+    }
+    if (e1 > e0) {
+      const int lz = z - z0;
+      for (int e = e0; e < e1; ++e) {
+        const int loc = p.inj_loc[e];
+        if (loc == (lz * TY + ty) * TX + tx)
+          acc += p.inj_w[e] * p.vals[p.inj_vidx[e] + p.step_off];
+      }
+    }
+    const float a = axy + p.spz[z];
+    const float h = kk * acc;
+    const float r = (2.f * cen - (1.f - a) * uo + h) * __frcp_rn(1.f + a);
+    if (in_xy) {
+      p.up[fo + idx] = r;
+      if (!ADJ) {
+        if (p.hist) __stcs(p.hist + fo + idx, h);
+      } else if (p.image) {
+        float* gp = p.g + fo + idx;
+        *gp = fmaf(-cen, hv, *gp);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < Q - 1; ++j) {
+      q[j] = q[j + 1];
+      if (PSI) qz[j] = qz[j + 1];
+    }
+    __syncthreads();   // every thread is done with the centre plane and this b stage
+    if (tid == 0) {
+      const int nxt = i + R + NSU;   // the centre plane's buffer takes plane nxt
+      if (nxt < nplanes) {
+        const int k = nxt % NSU;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bar[k], G::PLANE_BYTES);
+        tma_load_4d(ring + k * G::PLANE, &umap, &bar[k], tmx, tmy, pz0 + nxt, b);
+      }
+      if (PSI && i + 2 < nz_c) {
+        const int st = i & 1;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bbar[st], 2 * G::PLANE_BYTES);
+        tma_load_4d(bring + (2 * st) * G::PLANE, &bxmap, &bbar[st], tmx, tmy, z + 2 + p.oz, 0);
+        tma_load_4d(bring + (2 * st + 1) * G::PLANE, &bymap, &bbar[st], tmx, tmy, z + 2 + p.oz, 0);
+      }
+    }
+  }
+  if (timed_out && p.flags) atomicOr(p.flags, 2);
+}
+
+template <int R, bool VD, bool ADJ, int BY>
+constexpr size_t smem_bytes3() {
+  using G = Geo3<R, BY>;
+  size_t n = (size_t)G::NSU * G::PLANE;
+  if (VD && ADJ) n += 4 * (size_t)G::PLANE;
+  return n * sizeof(float);
+}
+
+template <int R, bool VD, bool ADJ, int BY>
+cudaError_t launch_t(const StepParams& p, const CUtensorMap& um, const CUtensorMap& bxm,
+                     const CUtensorMap& bym, cudaStream_t st) {
+  constexpr size_t smem = smem_bytes3<R, VD, ADJ, BY>();
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_step3d_tma<R, VD, ADJ, BY>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_step3d_tma<R, VD, ADJ, BY>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  dim3 grid((p.nx + 31) / 32, (p.ny + BY - 1) / BY, p.B * p.nzc);
+  k_step3d_tma<R, VD, ADJ, BY><<<grid, dim3(32, BY), smem, st>>>(p, um, bxm, bym);
+  return cudaGetLastError();
+}
+
+template <int R, bool VD, bool ADJ>
+cudaError_t launch_tile(const StepParams& p, const CUtensorMap& um, const CUtensorMap& bxm,
+                        const CUtensorMap& bym, int tile, cudaStream_t st) {
+  return tile3_variant(tile).by == 8 ? launch_t<R, VD, ADJ, 8>(p, um, bxm, bym, st)
+                                     : launch_t<R, VD, ADJ, 16>(p, um, bxm, bym, st);
+}
+
+}  // namespace
+
+cudaError_t launch_step3d_tma(const StepParams& p, const CUtensorMap& um, const CUtensorMap& bxm,
+                              const CUtensorMap& bym, int R, bool vd, bool adj, int tile,
+                              cudaStream_t st) {
+  if (R == 4) {
+    if (vd) return adj ? launch_tile<4, true, true>(p, um, bxm, bym, tile, st)
+                       : launch_tile<4, true, false>(p, um, bxm, bym, tile, st);
+    return adj ? launch_tile<4, false, true>(p, um, bxm, bym, tile, st)
+               : launch_tile<4, false, false>(p, um, bxm, bym, tile, st);
+  }
+  if (vd) return adj ? launch_tile<5, true, true>(p, um, bxm, bym, tile, st)
+                     : launch_tile<5, true, false>(p, um, bxm, bym, tile, st);
+  return adj ? launch_tile<5, false, true>(p, um, bxm, bym, tile, st)
+             : launch_tile<5, false, false>(p, um, bxm, bym, tile, st);
+}
+
+// TMA box rows (y extent) of a 3D tile variant.
+int tma_box3d_rows(int R, int tile) { return tile3_variant(tile).by + 2 * R; }
+
+}  // namespace fwi

@@ -32,7 +32,7 @@ def test_batch_matches_single_problem_runs(use_graph):
     b = binding.Batch(as_batch_entries(ps), use_graph=use_graph)
     got = [t.cpu().numpy().astype(np.float64) for t in b.run()]
     for p, g in zip(ps, got):
-        ref, _ = gpu_forward(p, tile=1)
+        ref, _ = gpu_forward(p)   # the default (TMA-staged) variant, as in the batch
         assert np.array_equal(g, ref)
     # a second run (graph replay) gives the same traces
     again = [t.cpu().numpy().astype(np.float64) for t in b.run()]

@@ -127,12 +127,30 @@ def test_gradient_2d_smem_family(vd):
     assert rel_l2(g, g_ref) <= TOL_GRAD
 
 
-@pytest.mark.parametrize("tile", [1, 2, 3, 4])
-def test_tile_variants_bitwise_equal_3d(tile):
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("vd", [False, True])
+def test_tile_variants_3d(tile, vd):
+    """3D: shared-memory-staged variants (1-4) and TMA plane-ring variants (5-8)
+    each agree bit for bit within their family and to rounding across."""
     p = small_skull(nt=120)
-    base, _ = gpu_forward(p, tile=1)
-    got, _ = gpu_forward(p, tile=tile)
+    fam = 1 if tile <= 4 else 5
+    base, _ = gpu_forward(p, tile=fam, variable_density=vd)
+    got, plan = gpu_forward(p, tile=tile, variable_density=vd)
+    assert plan.stats()["tile"] == tile
     assert np.array_equal(got, base)
+    other, _ = gpu_forward(p, tile=6 - fam if fam == 1 else 1, variable_density=vd)
+    assert rel_l2(got, other) < 1e-6
+
+
+@pytest.mark.parametrize("tile", [1, 5])
+def test_gradient_3d_both_families(tile):
+    p = small_skull(n=(36, 38, 41), nt=160, order=10)
+    obs = observed_from_oracle(p)
+    J_ref, g_ref, d_ref = oracle.gradient(oracle_grid(p), p.vp, p.rho, p.src_xyz, p.wavelet,
+                                          p.rec_xyz, obs)
+    J, g, d, _ = gpu_gradient(p, obs, tile=tile)
+    assert rel_l2(d, d_ref) <= TOL_TRACES
+    assert rel_l2(g, g_ref) <= TOL_GRAD
 
 
 def test_batch_invariance_and_determinism():
