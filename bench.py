@@ -154,15 +154,16 @@ def measured_hbm_peak():
         return 6800.0, "fallback"
 
 
-def traffic_record(kernel_kind):
-    """DRAM bytes per launch of the dominant kernel from a committed ncu summary,
-    or None when absent or taken on a different kernel source."""
+def traffic_record(kernel_kind, tile):
+    """DRAM bytes per point of the dominant kernel from a committed ncu summary,
+    or None when absent, taken on another kernel variant or on a different
+    kernel source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path)).get(kernel_kind)
     except Exception:
         return None
-    if not rec:
+    if not rec or rec.get("tile") != tile:
         return None
     import hashlib
     src = os.path.join(ROOT, "paper_2110_03345_gb300", "csrc", rec.get("source", "kernels2d.cu"))
@@ -237,9 +238,11 @@ def run_reference(args):
 
 def uneven_batch(nprob=64, seed=4, reps=2, **kw):
     """Uneven set of independent 2D problems: one multi-problem launch per
-    step captured in one CUDA graph, against one plan (one launch per step)
-    per problem run one after another.  Device time of the runs, inputs and
-    workspaces resident (created outside the timed region)."""
+    step captured in one CUDA graph (tile variant and shots per CTA from the
+    batch autotuner), against the plain solver run problem after problem with
+    one shot per launch ("plain") and with all of a problem's shots per launch
+    ("per_problem").  Inputs and workspaces resident (created outside the
+    timed region)."""
     import torch
     from paper_2110_03345_gb300 import binding, inputs
     ps = inputs.config_uneven_batch(nprob=nprob, seed=seed, **kw)
@@ -251,7 +254,9 @@ def uneven_batch(nprob=64, seed=4, reps=2, **kw):
                for p in ps]
     shots = sum(p.nshots for p in ps)
     updates = sum(p.nshots * p.npoints * (p.nt - 1) for p in ps)
-    batch = binding.Batch(entries, use_graph=True)
+    from paper_2110_03345_gb300 import autotune
+    tuned = autotune.tune_batch(entries)
+    batch = binding.Batch(entries, use_graph=True, **tuned)
     batch.run()
     t_b = []
     for _ in range(reps):
@@ -259,34 +264,44 @@ def uneven_batch(nprob=64, seed=4, reps=2, **kw):
         t_b.append(batch.stats()["run_ms"] * 1e-3)
     nodes = batch.stats()["launches"]
     batch.close()
-    plans = []
-    for e in entries:
-        pl = binding.Plan(e["shape"], e["spacing"], e["nt"], e["dt"], order=e["order"],
-                          sponge=e["sponge"], c_ref=e["c_ref"])
-        pl.set_options(batch=e["geometry"].nshots)
-        plans.append(pl)
-    outs = [torch.empty((e["geometry"].nshots, e["geometry"].nrec, e["nt"]), device=dev) for e in entries]
-    for pl, e, o in zip(plans, entries, outs):
-        pl.forward(e["vp"], e["rho"], e["geometry"], e["wavelet"], traces=o)
-    t_p = []
-    launches_plain = 0
-    for _ in range(reps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+
+    def plain(per_launch, nrep):
+        """Each problem on its own plan, one problem after another: all its
+        shots per launch (per_launch = 0) or one shot per launch (1)."""
+        plans = []
+        for e in entries:
+            pl = binding.Plan(e["shape"], e["spacing"], e["nt"], e["dt"], order=e["order"],
+                              sponge=e["sponge"], c_ref=e["c_ref"])
+            pl.set_options(batch=per_launch or e["geometry"].nshots)
+            plans.append(pl)
+        outs = [torch.empty((e["geometry"].nshots, e["geometry"].nrec, e["nt"]), device=dev)
+                for e in entries]
         for pl, e, o in zip(plans, entries, outs):
             pl.forward(e["vp"], e["rho"], e["geometry"], e["wavelet"], traces=o)
-            launches_plain += pl.stats()["launches"]
-        torch.cuda.synchronize()
-        t_p.append(time.perf_counter() - t0)
-    for pl in plans:
-        pl.close()
-    tb, tp = min(t_b), min(t_p)
+        t_p = []
+        launches = 0
+        for _ in range(nrep):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for pl, e, o in zip(plans, entries, outs):
+                pl.forward(e["vp"], e["rho"], e["geometry"], e["wavelet"], traces=o)
+                launches += pl.stats()["launches"]
+            torch.cuda.synchronize()
+            t_p.append(time.perf_counter() - t0)
+        for pl in plans:
+            pl.close()
+        tp = min(t_p)
+        return {"shots_per_s": shots / tp, "gpts": updates / tp / 1e9, "s": tp,
+                "launches": launches // nrep}
+
+    per_problem = plain(0, reps)
+    one_shot = plain(1, 1)
+    tb = min(t_b)
     return {"problems": nprob, "shots": shots, "updates": updates,
             "batched": {"shots_per_s": shots / tb, "gpts": updates / tb / 1e9, "s": tb,
-                        "graph_nodes": nodes, "launches": 1},
-            "plain": {"shots_per_s": shots / tp, "gpts": updates / tp / 1e9, "s": tp,
-                      "launches": launches_plain // reps},
-            "speedup": tp / tb}
+                        "graph_nodes": nodes, "launches": 1, "options": tuned},
+            "plain": one_shot, "per_problem": per_problem,
+            "speedup": one_shot["s"] / tb, "speedup_vs_per_problem": per_problem["s"] / tb}
 
 
 def serving_stream(nreq=650, warm=50, seed=5, lanes=4, rate=20.0, **kw):
@@ -429,7 +444,7 @@ def run_mine(args):
     bpu = BYTES_PER_UPDATE[(kind, vd)]
     achieved = bpu * pts_launch / t_launch / 1e9
     peak, peak_src = measured_hbm_peak()
-    tr = traffic_record(kind)
+    tr = traffic_record(f"{p.ndim}d-{kind}", stats["tile"])
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": (tr["dram_bytes_per_point"] * pts_launch) if tr else None,
             "kernel": ("k_step%dd_tma %s" % (p.ndim, "adjoint+imaging" if kind == "adj"
@@ -460,6 +475,10 @@ def run_mine(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(p, args.cpu_seconds)
+    # the samples below admit work by free device memory: release this workload's
+    plan.close()
+    del vp, rho, wav, obs, grad
+    torch.cuda.empty_cache()
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras:
         # reduced samples of the uneven-batch and serving patterns (full size:
@@ -489,7 +508,6 @@ def run_mine(args):
         }
         line.update(extras)
         print(json.dumps(line))
-    plan.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0

@@ -91,12 +91,15 @@ typedef struct {
     int ckpt_every;     /* gradient: 0 = full history if it fits, else sqrt(2 nt)
                            checkpoints; > 0 forces checkpoints every ckpt_every
                            steps; -1 forces the full history */
-    int tile;           /* kernel variant: -1 = default; 2D: 0-3 shared-memory staged,
-                           one shot per CTA; 4-7 TMA-staged, shots looped inside
-                           a CTA (same four tile shapes); 3D: 0-3 */
+    int tile;           /* kernel variant: 0 = default; 2D: 1-4 shared-memory staged,
+                           one shot per CTA; 5-8 TMA-staged, shots looped inside
+                           a CTA (same four tile shapes); 3D: 1-4 shared-memory
+                           staged, 5-8 TMA plane ring (32 x points per CTA row),
+                           9-12 TMA plane ring with two x points per thread (64);
+                           the TMA families give bit-identical results */
     int profile;        /* 1: time every stencil launch with CUDA events */
     int use_graphs;     /* 1: capture the time loop into CUDA graphs */
-    int shots_per_cta;  /* TMA variants: shots per CTA (0: chosen from the SM count) */
+    int shots_per_cta;  /* 2D TMA variants: shots per CTA (0: chosen from the SM count; 3D: 1) */
 } fwi_options;
 
 /* Counters of the last forward/gradient call on a plan. */

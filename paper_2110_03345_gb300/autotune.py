@@ -24,7 +24,7 @@ _lock = threading.Lock()
 
 CANDIDATES_2D = [dict(tile=t, shots_per_cta=s) for t in (5, 6, 7, 8) for s in (2, 3, 4, 5, 6, 8)] + \
                 [dict(tile=t) for t in (1, 2, 3, 4)]
-CANDIDATES_3D = [dict(tile=t) for t in (1, 2, 3, 4, 5, 6, 7, 8)]
+CANDIDATES_3D = [dict(tile=t) for t in (5, 6, 7, 8, 9, 10, 11, 12)]
 
 
 def problem_key(shape, order, variable_density, gradient, shots):
@@ -96,6 +96,62 @@ def tune(shape, spacing, dt, order, sponge, c_ref, vp, rho, geometry, wavelet, o
     with _lock:
         cache = _load_cache(cache_path)
         cache[key] = {"options": best[1], "ms_per_step": best[0],
+                      "tried": [[r[0], r[1]] for r in results]}
+        _store_cache(cache_path, cache)
+    return dict(best[1])
+
+
+BATCH_CANDIDATES = [dict(tile=t, shots_per_cta=s) for t in (5, 6, 7, 8) for s in (0, 2, 4, 6)]
+
+
+def batch_key(problems):
+    """Problem class of an uneven batch: order, density mode, problem count,
+    total shots and the grid-point volume (rounded)."""
+    pts = sum(int(np.prod(pr["shape"])) * pr["geometry"].nshots for pr in problems)
+    first = problems[0]
+    return f"batch-o{first.get('order', 8)}-{'vd' if first.get('rho') is not None else 'cd'}-" \
+           f"p{len(problems)}-s{sum(pr['geometry'].nshots for pr in problems)}-" \
+           f"v{int(round(np.log2(max(pts, 1)) * 4))}"
+
+
+def tune_batch(problems, steps=80, candidates=None, cache_path=_CACHE, refresh=False,
+               verbose=False):
+    """Tile variant and shots per CTA of an uneven batch (binding.Batch
+    problems).  Every problem is cut to its first `steps` time samples, so the
+    candidates are timed with every problem running (graph replays, device
+    time from the batch's events)."""
+    key = batch_key(problems)
+    with _lock:
+        cache = _load_cache(cache_path)
+        if not refresh and key in cache:
+            return dict(cache[key]["options"])
+    cut = []
+    for pr in problems:
+        q = dict(pr)
+        q["nt"] = int(min(steps, pr["nt"]))
+        q["wavelet"] = pr["wavelet"][..., :q["nt"]].contiguous()
+        cut.append(q)
+    results = []
+    for cand in candidates or BATCH_CANDIDATES:
+        try:
+            b = binding.Batch(cut, use_graph=True, **cand)
+        except binding.FwiError:
+            continue
+        try:
+            b.run()
+            b.run()
+            ms = b.stats()["run_ms"]
+        finally:
+            b.close()
+        results.append((ms, cand))
+        if verbose:
+            print(f"autotune {key} {cand}: {ms:.2f} ms")
+    if not results:
+        return {}
+    best = min(results, key=lambda r: r[0])
+    with _lock:
+        cache = _load_cache(cache_path)
+        cache[key] = {"options": best[1], "ms_per_run": best[0],
                       "tried": [[r[0], r[1]] for r in results]}
         _store_cache(cache_path, cache)
     return dict(best[1])

@@ -201,7 +201,7 @@ struct TileGeo {
   int ntiles() const { return gx * gy * nzc; }
 };
 
-TileGeo tile_geo(const fwi_plan* P, int tile, bool tma) {
+TileGeo tile_geo(const fwi_plan* P, int tile, bool tma, bool x2 = false) {
   TileGeo T{};
   if (P->grid.ndim == 2) {
     const Tile2 t = tma ? tile2_tma_variant(tile) : tile2_variant(tile);
@@ -213,10 +213,10 @@ TileGeo tile_geo(const fwi_plan* P, int tile, bool tma) {
     T.nzc = 1;
   } else {
     const Tile3 t = tile3_variant(tile);
-    T.tx = 32;
+    T.tx = x2 ? 64 : 32;   // the two-point kernels cover 64 x points per CTA row
     T.ty = t.by;
     T.zc = t.zc;
-    T.gx = (P->L.nx + 31) / 32;
+    T.gx = (P->L.nx + T.tx - 1) / T.tx;
     T.gy = (P->L.ny + T.ty - 1) / T.ty;
     T.nzc = (P->L.nz + T.zc - 1) / T.zc;
   }
@@ -428,7 +428,8 @@ struct Plan {
   bool gradient = false;
   int tile = 0;         // resolved variant id (as in fwi_options.tile, never 0)
   int shape = 0;        // tile shape 0..3
-  bool tma = false;     // 2D TMA-staged kernels with shots looped inside a CTA
+  bool tma = false;     // TMA-staged kernels (2D: shots looped inside a CTA)
+  bool x2 = false;      // 3D: two x points per thread (variants 9-12)
   int S = 1;            // shots per CTA; gradient slot of shot s is s / S
   bool split = false;   // forward and adjoint in separate calls: keep every batch's state
   int nbatches = 1;
@@ -436,7 +437,8 @@ struct Plan {
 };
 
 // Resolve fwi_options.tile: 0 selects the default variant.
-bool resolve_tile(const fwi_plan* P, int t, int* id, int* shape, bool* tma) {
+bool resolve_tile(const fwi_plan* P, int t, int* id, int* shape, bool* tma, bool* x2 = nullptr) {
+  if (x2) *x2 = false;
   if (P->grid.ndim == 2) {
     if (t == 0) t = 6;   // TMA-staged, one row per thread, 128 x 16 tiles
     if (t < 1 || t > 2 * NUM_TILE2) return false;
@@ -444,8 +446,9 @@ bool resolve_tile(const fwi_plan* P, int t, int* id, int* shape, bool* tma) {
     *shape = (t - 1) % NUM_TILE2;
   } else {
     if (t == 0) t = 8;   // TMA-staged plane ring, 32 x 8 columns, 32-plane chunks
-    if (t < 1 || t > 2 * NUM_TILE3) return false;
+    if (t < 1 || t > 3 * NUM_TILE3) return false;
     *tma = t > NUM_TILE3;
+    if (x2) *x2 = t > 2 * NUM_TILE3;
     *shape = (t - 1) % NUM_TILE3;
   }
   *id = t;
@@ -535,10 +538,10 @@ fwi_status choose_plan(const fwi_plan* P, const fwi_geometry* g, bool vd, bool g
   out.gradient = grad;
   out.split = split;
   out.nbatches = (ns + B - 1) / B;
-  if (!resolve_tile(P, P->opt.tile, &out.tile, &out.shape, &out.tma))
+  if (!resolve_tile(P, P->opt.tile, &out.tile, &out.shape, &out.tma, &out.x2))
     return fail(FWI_ERR_INVALID_ARG, "tile variant out of range");
   out.S = 1;
-  if (out.tma) {
+  if (out.tma && P->grid.ndim == 2) {   // the 3D kernels take one shot per CTA
     if (P->opt.shots_per_cta > 0) {
       out.S = std::min(P->opt.shots_per_cta, B);
     } else {
@@ -634,9 +637,10 @@ fwi_status make_tensor_map(const fwi_plan* P, const float* base, int nslots, int
 }
 
 // 4D tensor map over nslots padded 3D fields: dims (x, y, z, slot); box = a
-// 48-float-wide x-y tile (16-byte aligned start) with its y halo, one plane.
+// 48-float-wide (80 for the two-point kernels) x-y tile (16-byte aligned
+// start) with its y halo, one plane.
 fwi_status make_tensor_map_3d(const fwi_plan* P, const float* base, int nslots, int shape,
-                              CUtensorMap* out) {
+                              bool x2, CUtensorMap* out) {
   auto enc = tensor_map_encoder();
   if (!enc) return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
   const cuuint64_t dims[4] = {(cuuint64_t)P->L.sx, (cuuint64_t)P->L.rows, (cuuint64_t)P->L.planes,
@@ -644,7 +648,7 @@ fwi_status make_tensor_map_3d(const fwi_plan* P, const float* base, int nslots, 
   const cuuint64_t strides[3] = {(cuuint64_t)P->L.sx * sizeof(float),
                                  (cuuint64_t)P->L.sxy * sizeof(float),
                                  (cuuint64_t)P->L.fstride * sizeof(float)};
-  const cuuint32_t box[4] = {48u, (cuuint32_t)tma_box3d_rows(P->R, shape), 1u, 1u};
+  const cuuint32_t box[4] = {x2 ? 80u : 48u, (cuuint32_t)tma_box3d_rows(P->R, shape), 1u, 1u};
   const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
   const CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims,
                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -730,7 +734,7 @@ StepParams base_params(Call& c) {
 long long launch_threads(const Call& c, int B) {
   const int by = (c.P->grid.ndim == 3) ? tile3_variant(c.pl.shape).by
                  : c.pl.tma ? tile2_tma_variant(c.pl.shape).by : tile2_variant(c.pl.shape).by;
-  const int ctas_z = c.pl.tma ? (B + c.pl.S - 1) / c.pl.S : B;
+  const int ctas_z = (B + c.pl.S - 1) / c.pl.S;
   return (long long)c.T.ntiles() * ctas_z * 32 * by;
 }
 
@@ -764,7 +768,8 @@ fwi_status launch_step(Call& c, const StepParams& p_in, bool adj) {
     const CUtensorMap* bxm = c.vd ? find_map(c, c.W.bx) : map;
     const CUtensorMap* bym = c.vd ? find_map(c, c.W.by) : map;
     if (!bxm || !bym) return fail(FWI_ERR_INVALID_ARG, "internal: no tensor map for b_x / b_y");
-    e = launch_step3d_tma(p, *map, *bxm, *bym, P->R, c.vd, adj, c.pl.shape, P->st);
+    e = c.pl.x2 ? launch_step3d_x2(p, *map, *bxm, *bym, P->R, c.vd, adj, c.pl.shape, P->st)
+                : launch_step3d_tma(p, *map, *bxm, *bym, P->R, c.vd, adj, c.pl.shape, P->st);
   } else if (P->grid.ndim == 3) e = launch_step3d(p, P->R, c.vd, adj, c.pl.shape, P->st);
   else if (c.pl.tma) e = launch_step2d_tma(p, *map, P->R, c.vd, adj, c.pl.shape, P->st);
   else e = launch_step2d(p, P->R, c.vd, adj, c.pl.shape, P->st);
@@ -857,7 +862,7 @@ fwi_status prepare_common(Call& c, Carve& tabC) {
   const fwi_geometry* g = c.geom;
   const int nd = P->grid.ndim;
   c.ncorner = 1 << nd;
-  c.T = tile_geo(P, c.pl.shape, c.pl.tma);
+  c.T = tile_geo(P, c.pl.shape, c.pl.tma, c.pl.x2);
   // receiver sampling table
   std::vector<int> node((size_t)g->nrec * c.ncorner);
   std::vector<float> w((size_t)g->nrec * c.ncorner);
@@ -888,7 +893,7 @@ fwi_status prepare_common(Call& c, Carve& tabC) {
 }
 
 size_t tables_bound(const fwi_plan* P, const fwi_geometry* g, const Plan& pl) {
-  const TileGeo T = tile_geo(P, pl.shape, pl.tma);
+  const TileGeo T = tile_geo(P, pl.shape, pl.tma, pl.x2);
   const int nc = 1 << P->grid.ndim;
   const size_t nb = (size_t)pl.B * T.ntiles() + 1;
   const size_t src = (size_t)pl.B * g->nsrc * nc;
@@ -968,14 +973,14 @@ fwi_status begin_call(fwi_plan* P, const fwi_model* model, const fwi_geometry* g
     for (float* buf : {c.W.U0, c.W.U1, c.W.F0, c.W.F1}) {
       if (!buf) continue;
       Call::MapEnt m{buf, {}};
-      if (three) FWI_TRY(make_tensor_map_3d(P, buf, c.pl.B, c.pl.shape, &m.map));
+      if (three) FWI_TRY(make_tensor_map_3d(P, buf, c.pl.B, c.pl.shape, c.pl.x2, &m.map));
       else FWI_TRY(make_tensor_map(P, buf, c.pl.B, c.pl.shape, &m.map));
       c.maps.push_back(m);
     }
     if (three && c.vd) {
       for (float* buf : {c.W.bx, c.W.by}) {
         Call::MapEnt m{buf, {}};
-        FWI_TRY(make_tensor_map_3d(P, buf, 1, c.pl.shape, &m.map));
+        FWI_TRY(make_tensor_map_3d(P, buf, 1, c.pl.shape, c.pl.x2, &m.map));
         c.maps.push_back(m);
       }
     }
@@ -1434,6 +1439,8 @@ struct fwi_batch {
   bool vd = false;
   bool tma = true;      // TMA-staged multi-problem kernel (else shared-memory staged)
   int shape = 0;        // tile shape of the batch's kernels
+  bool uniform_w = false;   // every problem has the same stencil weights
+  AxisW w[2] = {};          // {x, y} weights when uniform_w
   MultiDesc* d_desc = nullptr;
   MultiUnit* d_units = nullptr;
   std::vector<int> active_units;      // units of the problems still running at step n
@@ -1467,7 +1474,8 @@ fwi_status batch_enqueue(fwi_batch* b) {
   int64_t launches = 0, updates = 0;
   for (int n = 0; n < b->max_steps; ++n) {
     cudaError_t e = b->tma ? launch_step2d_tma_multi(b->d_desc, b->d_units, b->active_units[n], n,
-                                                     b->R, b->vd, b->shape, b->ws)
+                                                     b->R, b->vd, b->shape,
+                                                     b->uniform_w ? b->w : nullptr, b->ws)
                            : launch_step2d_multi(b->d_desc, b->d_units, b->active_units[n], n,
                                                  b->R, b->vd, b->ws);
     if (e != cudaSuccess) return fail(FWI_ERR_CUDA, std::string("multi-problem step: ") + cudaGetErrorString(e));
@@ -1557,6 +1565,15 @@ fwi_status fwi_batch_create(fwi_batch** out, int nprob, const fwi_problem* probs
   }
   std::stable_sort(b->items.begin(), b->items.end(),
                    [](const BatchProblem* a, const BatchProblem* c) { return a->prob.nt > c->prob.nt; });
+  if (!b->items.empty()) {
+    b->w[0] = b->items[0]->P->wx;
+    b->w[1] = b->items[0]->P->wy;
+    b->uniform_w = true;
+    for (const BatchProblem* it : b->items)
+      if (std::memcmp(&it->P->wx, &b->w[0], sizeof(AxisW)) != 0 ||
+          std::memcmp(&it->P->wy, &b->w[1], sizeof(AxisW)) != 0)
+        b->uniform_w = false;
+  }
   // descriptors and units (problems longest first: the running ones are a prefix)
   std::vector<MultiDesc> desc(b->items.size());
   std::vector<MultiUnit> units;
@@ -1621,7 +1638,8 @@ fwi_status fwi_batch_create(fwi_batch** out, int nprob, const fwi_problem* probs
     // capture every launch of a run
     {
       cudaError_t e = b->tma ? launch_step2d_tma_multi(b->d_desc, b->d_units, 0, 0, b->R, b->vd,
-                                                       b->shape, b->ws)
+                                                       b->shape, b->uniform_w ? b->w : nullptr,
+                                                       b->ws)
                              : launch_step2d_multi(b->d_desc, b->d_units, 0, 0, b->R, b->vd, b->ws);
       if (e != cudaSuccess) return bail(fail(FWI_ERR_CUDA, cudaGetErrorString(e)));
     }
@@ -1728,7 +1746,7 @@ fwi_status forward_in_buffer(const fwi_grid* grid, int nt, double dt, const fwi_
   P.spz = C.take<float>(std::max(P.L.nz, 1) + 8);
   Plan all;   // table bound for every shot in one batch, at the tile variant the call will use
   all.B = geom->nshots;
-  if (!resolve_tile(&P, P.opt.tile, &all.tile, &all.shape, &all.tma))
+  if (!resolve_tile(&P, P.opt.tile, &all.tile, &all.shape, &all.tma, &all.x2))
     return fail(FWI_ERR_INVALID_ARG, "tile variant out of range");
   const size_t tab = align_up(tables_bound(&P, geom, all) * 2, 256);
   P.tab = C.take<char>(tab);

@@ -143,8 +143,10 @@ cudaError_t launch_step3d(const StepParams& p, int R, bool vd, bool adj, int til
 size_t step2d_smem(int R, bool vd, bool adj, int tile);
 // Multi-problem forward step, TMA-staged (kernels2d_tma.cu); units are
 // (problem, tile, shot group) with the tile shape tile2_tma_variant(tile).
+// w: {x, y} stencil weights shared by every problem, or null when they differ.
 cudaError_t launch_step2d_tma_multi(const MultiDesc* descs, const MultiUnit* units, int nunits,
-                                    int n, int R, bool vd, int tile, cudaStream_t st);
+                                    int n, int R, bool vd, int tile, const AxisW* w,
+                                    cudaStream_t st);
 // Multi-problem forward step over `nunits` units (128 x 32 tiles, one shot per CTA).
 cudaError_t launch_step2d_multi(const MultiDesc* descs, const MultiUnit* units, int nunits, int n,
                                 int R, bool vd, cudaStream_t st);
@@ -161,6 +163,11 @@ cudaError_t launch_step3d_tma(const StepParams& p, const CUtensorMap& um, const 
                               const CUtensorMap& bym, int R, bool vd, bool adj, int tile,
                               cudaStream_t st);
 int tma_box3d_rows(int R, int tile);
+// Two-point TMA-staged 3D kernels (kernels3d_x2.cu): 64 x BY columns, the
+// same tensor maps with an 80-float-wide box; bit-identical to the above.
+cudaError_t launch_step3d_x2(const StepParams& p, const CUtensorMap& um, const CUtensorMap& bxm,
+                             const CUtensorMap& bym, int R, bool vd, bool adj, int tile,
+                             cudaStream_t st);
 
 // Auxiliary kernels (aux_kernels.cu)
 cudaError_t launch_model_prep(const Layout& L, const float* vp, const float* rho, double dt,

@@ -62,7 +62,8 @@ struct Geo {
 // samp_rank is the CTA's rank among its problem's CTAs, gx the problem's tile
 // count along x.
 template <int R, bool VD, bool ADJ, int RY, int BY>
-__device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const CUtensorMap* tmap,
+__device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW& wx,
+                                                const AxisW& wy, const CUtensorMap* tmap,
                                                 int bxi, int byi, int gx, int grp,
                                                 long long samp_rank, float4* smem, uint64_t* bar) {
   using G = Geo<R, RY, BY>;
@@ -188,13 +189,13 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const CUten
         c2[ix] = v[c] + v[c];
         float t = 0.f;
 #pragma unroll
-        for (int j = 1; j <= R; ++j) t = fmaf(p.wx.w2[j], (v[c + j] + v[c - j]) - c2[ix], t);
+        for (int j = 1; j <= R; ++j) t = fmaf(wx.w2[j], (v[c + j] + v[c - j]) - c2[ix], t);
         acc[ix] = t;
         d1x[ix] = 0.f;
         d1y[ix] = 0.f;
         if (VD && !ADJ) {
 #pragma unroll
-          for (int j = 1; j <= R; ++j) d1x[ix] = fmaf(p.wx.w1[j], v[c + j] - v[c - j], d1x[ix]);
+          for (int j = 1; j <= R; ++j) d1x[ix] = fmaf(wx.w1[j], v[c + j] - v[c - j], d1x[ix]);
         }
       }
       if (VD && ADJ) {
@@ -208,7 +209,7 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const CUten
           float d = 0.f;
 #pragma unroll
           for (int j = 1; j <= R; ++j)
-            d = fmaf(p.wx.w1[j], bw[c + j] * v[c + j] - bw[c - j] * v[c - j], d);
+            d = fmaf(wx.w1[j], bw[c + j] * v[c + j] - bw[c - j] * v[c - j], d);
           acc[ix] += d;
         }
       }
@@ -226,11 +227,11 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const CUten
           const float4 c = s_u[(srow + j) * SW + tx + NL];
           const float2 a0 = make_float2(a.x, a.y), a1 = make_float2(a.z, a.w);
           const float2 c0 = make_float2(c.x, c.y), c1 = make_float2(c.z, c.w);
-          const float2 w2 = make_float2(p.wy.w2[j], p.wy.w2[j]);
+          const float2 w2 = make_float2(wy.w2[j], wy.w2[j]);
           A0 = __ffma2_rn(w2, __fadd2_rn(__fadd2_rn(a0, c0), n0), A0);
           A1 = __ffma2_rn(w2, __fadd2_rn(__fadd2_rn(a1, c1), n1), A1);
           if (VD) {
-            const float2 w1 = make_float2(p.wy.w1[j], p.wy.w1[j]);
+            const float2 w1 = make_float2(wy.w1[j], wy.w1[j]);
             if (!ADJ) {
               D0 = __ffma2_rn(w1, __fadd2_rn(c0, make_float2(-a0.x, -a0.y)), D0);
               D1 = __ffma2_rn(w1, __fadd2_rn(c1, make_float2(-a1.x, -a1.y)), D1);
@@ -323,16 +324,21 @@ k_step2d_tma(const StepParams p, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) float4 smem[];
   __shared__ uint64_t bar[2];
   const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  step2d_tma_tile<R, VD, ADJ, RY, BY>(p, &tmap, blockIdx.x, blockIdx.y, gridDim.x, blockIdx.z,
-                                      blk, smem, bar);
+  step2d_tma_tile<R, VD, ADJ, RY, BY>(p, p.wx, p.wy, &tmap, blockIdx.x, blockIdx.y, gridDim.x,
+                                      blockIdx.z, blk, smem, bar);
 }
 
 // Multi-problem forward step with TMA staging: CTA i advances unit units[i]
 // (problem, tile, shot group) by one step; the problem's StepParams and the
 // tensor maps of its two wavefield buffers come from descs (global memory).
-template <int R, bool VD, int RY, int BY>
+// UW: every problem of the batch has the same stencil weights (same order and
+// spacing), passed as kernel parameters so that the stencil reads them as
+// constant operands; otherwise each CTA reads its problem's weights from the
+// shared-memory copy of its StepParams.
+template <int R, bool VD, int RY, int BY, bool UW>
 __global__ void __launch_bounds__(32 * BY, (RY == 1 ? 1024 : 512) / (32 * BY))
-k_step2d_tma_multi(const MultiDesc* __restrict__ descs, const MultiUnit* __restrict__ units, int n) {
+k_step2d_tma_multi(const MultiDesc* __restrict__ descs, const MultiUnit* __restrict__ units, int n,
+                   const AxisW wx, const AxisW wy) {
   extern __shared__ __align__(128) float4 smem[];
   __shared__ uint64_t bar[2];
   __shared__ StepParams sp;
@@ -353,7 +359,8 @@ k_step2d_tma_multi(const MultiDesc* __restrict__ descs, const MultiUnit* __restr
   }
   __syncthreads();
   const CUtensorMap* map = (n & 1) ? &d->map1 : &d->map0;
-  step2d_tma_tile<R, VD, false, RY, BY>(sp, map, un.tx, un.ty, d->gx, un.slot, un.rank, smem, bar);
+  step2d_tma_tile<R, VD, false, RY, BY>(sp, UW ? wx : sp.wx, UW ? wy : sp.wy, map, un.tx, un.ty,
+                                        d->gx, un.slot, un.rank, smem, bar);
 }
 
 template <int R, bool VD, bool ADJ, int RY, int BY>
@@ -395,45 +402,55 @@ cudaError_t launch_tile(const StepParams& p, const CUtensorMap& map, int tile, c
   }
 }
 
-template <int R, bool VD, int RY, int BY>
-cudaError_t launch_multi_t(const MultiDesc* descs, const MultiUnit* units, int nunits, int n,
-                           cudaStream_t st) {
+template <int R, bool VD, int RY, int BY, bool UW>
+cudaError_t launch_multi_u(const MultiDesc* descs, const MultiUnit* units, int nunits, int n,
+                           const AxisW* w, cudaStream_t st) {
   constexpr size_t smem = smem_bytes<R, VD, false, RY, BY>();
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_step2d_tma_multi<R, VD, RY, BY>,
+    cudaError_t e = cudaFuncSetAttribute(k_step2d_tma_multi<R, VD, RY, BY, UW>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_step2d_tma_multi<R, VD, RY, BY>,
+    e = cudaFuncSetAttribute(k_step2d_tma_multi<R, VD, RY, BY, UW>,
                              cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   if (nunits <= 0) return cudaSuccess;
-  k_step2d_tma_multi<R, VD, RY, BY><<<nunits, dim3(32, BY), smem, st>>>(descs, units, n);
+  const AxisW zero{};
+  k_step2d_tma_multi<R, VD, RY, BY, UW><<<nunits, dim3(32, BY), smem, st>>>(
+      descs, units, n, w ? w[0] : zero, w ? w[1] : zero);
   return cudaGetLastError();
+}
+
+template <int R, bool VD, int RY, int BY>
+cudaError_t launch_multi_t(const MultiDesc* descs, const MultiUnit* units, int nunits, int n,
+                           const AxisW* w, cudaStream_t st) {
+  return w ? launch_multi_u<R, VD, RY, BY, true>(descs, units, nunits, n, w, st)
+           : launch_multi_u<R, VD, RY, BY, false>(descs, units, nunits, n, w, st);
 }
 
 template <int R, bool VD>
 cudaError_t launch_multi_tile(const MultiDesc* descs, const MultiUnit* units, int nunits, int n,
-                              int tile, cudaStream_t st) {
+                              int tile, const AxisW* w, cudaStream_t st) {
   switch (tile) {
-    case 1: return launch_multi_t<R, VD, 1, 16>(descs, units, nunits, n, st);
-    case 2: return launch_multi_t<R, VD, 2, 16>(descs, units, nunits, n, st);
-    case 3: return launch_multi_t<R, VD, 2, 8>(descs, units, nunits, n, st);
-    default: return launch_multi_t<R, VD, 1, 32>(descs, units, nunits, n, st);
+    case 1: return launch_multi_t<R, VD, 1, 16>(descs, units, nunits, n, w, st);
+    case 2: return launch_multi_t<R, VD, 2, 16>(descs, units, nunits, n, w, st);
+    case 3: return launch_multi_t<R, VD, 2, 8>(descs, units, nunits, n, w, st);
+    default: return launch_multi_t<R, VD, 1, 32>(descs, units, nunits, n, w, st);
   }
 }
 
 }  // namespace
 
 cudaError_t launch_step2d_tma_multi(const MultiDesc* descs, const MultiUnit* units, int nunits,
-                                    int n, int R, bool vd, int tile, cudaStream_t st) {
-  if (R == 4) return vd ? launch_multi_tile<4, true>(descs, units, nunits, n, tile, st)
-                        : launch_multi_tile<4, false>(descs, units, nunits, n, tile, st);
-  return vd ? launch_multi_tile<5, true>(descs, units, nunits, n, tile, st)
-            : launch_multi_tile<5, false>(descs, units, nunits, n, tile, st);
+                                    int n, int R, bool vd, int tile, const AxisW* w,
+                                    cudaStream_t st) {
+  if (R == 4) return vd ? launch_multi_tile<4, true>(descs, units, nunits, n, tile, w, st)
+                        : launch_multi_tile<4, false>(descs, units, nunits, n, tile, w, st);
+  return vd ? launch_multi_tile<5, true>(descs, units, nunits, n, tile, w, st)
+            : launch_multi_tile<5, false>(descs, units, nunits, n, tile, w, st);
 }
 
 // tile: 0..3, the shapes of tile2_tma_variant

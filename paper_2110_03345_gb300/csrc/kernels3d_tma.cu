@@ -114,7 +114,7 @@ k_step3d_tma(const StepParams p, const __grid_constant__ CUtensorMap umap,
   for (int lp = 0; lp < Q - 1; ++lp) {
     if (!mbar_wait_bounded(&bar[lp], 0)) timed_out = true;
     q[lp] = ring[lp * G::PLANE + own];
-    if (PSI) qz[lp] = __ldg(p.bz + (long long)(pz0 + lp) * p.sxy + col) * q[lp];
+    if (PSI) qz[lp] = __fmul_rn(__ldg(p.bz + (long long)(pz0 + lp) * p.sxy + col), q[lp]);
   }
   __syncthreads();   // planes 0..R-1 are halo-only: their buffers take planes NSU..NSU+R-1
   if (tid == 0) {
@@ -167,7 +167,7 @@ k_step3d_tma(const StepParams p, const __grid_constant__ CUtensorMap umap,
     const int lead = i + 2 * R;
     if (!mbar_wait_bounded(&bar[lead % NSU], (uint32_t)((lead / NSU) & 1))) timed_out = true;
     q[Q - 1] = ring[(lead % NSU) * G::PLANE + own];
-    if (PSI) qz[Q - 1] = cur.bzl * q[Q - 1];
+    if (PSI) qz[Q - 1] = __fmul_rn(cur.bzl, q[Q - 1]);
     const float* cp = ring + ((i + R) % NSU) * G::PLANE;   // centre plane z
     const float* bxp = bring + (2 * (i & 1)) * G::PLANE;
     const float* byp = bxp + G::PLANE;
@@ -191,15 +191,18 @@ k_step3d_tma(const StepParams p, const __grid_constant__ CUtensorMap umap,
         dy = fmaf(p.wy.w1[j], cp[(r0 + j) * G::BXW + c0] - cp[(r0 - j) * G::BXW + c0], dy);
         dz = fmaf(p.wz.w1[j], q[R + j] - q[R - j], dz);
       }
-      acc -= bxv * dx + byv * dy + bzv * dz;
+      float t = __fmul_rn(bxv, dx);
+      t = fmaf(byv, dy, t);
+      t = fmaf(bzv, dz, t);
+      acc = acc - t;
     }
     if (PSI) {
 #pragma unroll
       for (int j = 1; j <= R; ++j) {
         const int xp = r0 * G::BXW + c0 + j, xm = r0 * G::BXW + c0 - j;
         const int yp = (r0 + j) * G::BXW + c0, ym = (r0 - j) * G::BXW + c0;
-        acc = fmaf(p.wx.w1[j], bxp[xp] * cp[xp] - bxp[xm] * cp[xm], acc);
-        acc = fmaf(p.wy.w1[j], byp[yp] * cp[yp] - byp[ym] * cp[ym], acc);
+        acc = fmaf(p.wx.w1[j], __fmul_rn(bxp[xp], cp[xp]) - __fmul_rn(bxp[xm], cp[xm]), acc);
+        acc = fmaf(p.wy.w1[j], __fmul_rn(byp[yp], cp[yp]) - __fmul_rn(byp[ym], cp[ym]), acc);
         acc = fmaf(p.wz.w1[j], qz[R + j] - qz[R - j], acc);
       }
     }
@@ -208,12 +211,16 @@ k_step3d_tma(const StepParams p, const __grid_constant__ CUtensorMap umap,
       for (int e = e0; e < e1; ++e) {
         const int loc = p.inj_loc[e];
         if (loc == (lz * TY + ty) * TX + tx)
-          acc += p.inj_w[e] * p.vals[p.inj_vidx[e] + p.step_off];
+          acc = fmaf(p.inj_w[e], p.vals[p.inj_vidx[e] + p.step_off], acc);
       }
     }
     const float a = axy + p.spz[z];
-    const float h = kk * acc;
-    const float r = (2.f * cen - (1.f - a) * uo + h) * __frcp_rn(1.f + a);
+    // explicit rounding order (no contraction left to the compiler), shared
+    // with the two-point kernels of kernels3d_x2.cu
+    const float h = __fmul_rn(kk, acc);
+    float t = fmaf(-(1.f - a), uo, 2.f * cen);
+    t = __fadd_rn(t, h);
+    const float r = __fmul_rn(t, __frcp_rn(1.f + a));
     if (in_xy) {
       p.up[fo + idx] = r;
       if (!ADJ) {

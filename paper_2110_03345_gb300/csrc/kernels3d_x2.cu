@@ -1,0 +1,385 @@
+// 3D leapfrog step kernels, TMA-staged, two x points per thread.
+//
+// Same arithmetic, in the same order, as the plane-ring kernels of
+// kernels3d_tma.cu (Eq. 10 of Sec. 2.4 without attenuation, damped leapfrog,
+// exact discrete adjoint, imaging condition of Sec. 2.2 Eq. 8 fused into the
+// adjoint), so both give bit-identical results.  What differs is the work
+// per instruction:
+//
+//  * a thread owns two adjacent x points, so a CTA of 32 x BY threads covers
+//    a 64 x BY column; every shared-memory read is an 8-byte pair and the
+//    arithmetic runs on packed FP32x2 instructions (two lanes, each rounded
+//    as the scalar operation);
+//  * the z loop is unrolled by the queue length 2R+1, so the register queue
+//    of the column rotates by renaming and costs no moves;
+//  * the x-y planes (80 floats wide: x0-8 .. x0+71, 16-byte aligned) arrive by
+//    4D TMA copies into a ring of R+1+PF planes (the centre, the R planes up
+//    to the lead, PF planes in flight); the variable-density adjoint streams
+//    b_x, b_y planes through a second two-stage ring as before.
+// Every mbarrier wait is bounded: on time-out the error flag is set and the
+// kernel carries on, so no thread skips a barrier.
+#include "fwi_internal.cuh"
+#include "tma_util.cuh"
+
+#include <cuda.h>
+
+namespace fwi {
+
+namespace {
+
+using namespace tma;
+
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 lds2(const float* p) {
+  return *reinterpret_cast<const float2*>(p);
+}
+
+template <int R, int BY>
+struct GeoX2 {
+  static constexpr int TXP = 64;            // x points of a CTA row (32 threads x 2)
+  static constexpr int BXW = 80;            // floats per staged row: x0-8 .. x0+71
+  static constexpr int XOFF = 8;            // column of x0 in a staged row
+  static constexpr int BYH = BY + 2 * R;    // staged rows: y0-R .. y0+BY+R-1
+  static constexpr int PLANE = BYH * BXW;   // floats per staged plane (a multiple of 32)
+  static constexpr int PF = 3;              // planes in flight ahead of the lead
+  static constexpr int NSU = R + 1 + PF;    // ring depth
+  static constexpr int M = (R + 1) / 2;     // x pairs on each side of the own pair
+  static constexpr uint32_t PLANE_BYTES = PLANE * 4;
+};
+
+template <int R, bool VD, bool ADJ, int BY>
+__global__ void __launch_bounds__(32 * BY, 512 / (32 * BY))
+k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
+            const __grid_constant__ CUtensorMap bxmap, const __grid_constant__ CUtensorMap bymap) {
+  using G = GeoX2<R, BY>;
+  constexpr int TY = BY;
+  constexpr int NT = 32 * BY;
+  constexpr int Q = 2 * R + 1;
+  constexpr int NSU = G::NSU;
+  constexpr int M = G::M;
+  constexpr int BXW = G::BXW;
+  constexpr bool PSI = VD && ADJ;
+  extern __shared__ __align__(128) float smem3x[];
+  float* ring = smem3x;                       // [NSU][BYH][BXW]
+  float* bring = ring + NSU * G::PLANE;       // PSI: [2 stages][b_x, b_y][BYH][BXW]
+  __shared__ uint64_t bar[NSU];
+  __shared__ uint64_t bbar[2];
+
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * 32 + tx;
+  const int b = blockIdx.z / p.nzc;
+  const int zc = blockIdx.z - b * p.nzc;
+  const int x0 = blockIdx.x * G::TXP, y0 = blockIdx.y * TY;
+  const int z0 = zc * p.zchunk;
+  const int z1 = min(z0 + p.zchunk, p.nz);
+  const int nz_c = z1 - z0;
+  const int nplanes = nz_c + 2 * R;
+  const size_t fo = (size_t)b * p.fstride;
+  const int xg = x0 + 2 * tx, yg = y0 + ty;
+  const long long col = (long long)(yg + p.oy) * p.sx + (xg + p.ox);   // even: 8-byte pairs
+
+  if (!ADJ && p.nrec > 0) {
+    // receiver sampling of u^n (not written during this step), one thread per slot x receiver
+    const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const long long gid = blk * NT + tid;
+    if (gid < (long long)p.B * p.nrec) {
+      const int bb = (int)(gid / p.nrec);
+      const int r = (int)(gid - (long long)bb * p.nrec);
+      const float* ub = p.u + (long long)bb * p.fstride;
+      float acc = 0.f;
+      for (int c = 0; c < p.ncorner; ++c)
+        acc = fmaf(p.smp_w[r * p.ncorner + c], ub[p.smp_node[r * p.ncorner + c]], acc);
+      p.smp_out[p.smp_off + (long long)bb * p.nrec + r] = acc;
+    }
+  }
+  if (nz_c <= 0) return;
+
+  const int tmx = x0 + p.ox - G::XOFF;      // 16-byte aligned box start
+  const int tmy = y0 + p.oy - R;
+  const int pz0 = z0 - R + p.oz;            // padded z of staged plane 0
+  if (tid == 0) {
+    for (int k = 0; k < NSU; ++k) mbar_init(&bar[k], 1);
+    mbar_init(&bbar[0], 1);
+    mbar_init(&bbar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int lp = 0; lp < NSU && lp < nplanes; ++lp) {
+      mbar_arrive_expect_tx(&bar[lp], G::PLANE_BYTES);
+      tma_load_4d(ring + lp * G::PLANE, &umap, &bar[lp], tmx, tmy, pz0 + lp, b);
+    }
+    if (PSI) {
+      for (int i = 0; i < 2 && i < nz_c; ++i) {
+        mbar_arrive_expect_tx(&bbar[i], 2 * G::PLANE_BYTES);
+        tma_load_4d(bring + (2 * i) * G::PLANE, &bxmap, &bbar[i], tmx, tmy, z0 + i + p.oz, 0);
+        tma_load_4d(bring + (2 * i + 1) * G::PLANE, &bymap, &bbar[i], tmx, tmy, z0 + i + p.oz, 0);
+      }
+    }
+  }
+
+  const int c0 = G::XOFF + 2 * tx;          // own pair's column in a staged row (even)
+  const int own = (ty + R) * BXW + c0;
+  bool timed_out = false;
+  // register queue: plane z - R + j of iteration i (z = z0 + i) sits in
+  // q[(i + j) % Q]; with the loop unrolled by Q the slots are constants.
+  float2 q[Q];
+  float2 qz[PSI ? Q : 1];
+  // planes 0 .. R-1 (halo only)
+#pragma unroll
+  for (int lp = 0; lp < R; ++lp) {
+    if (!mbar_wait_bounded(&bar[lp], 0)) timed_out = true;
+    q[lp] = lds2(ring + lp * G::PLANE + own);
+    if (PSI)
+      qz[lp] = __fmul2_rn(__ldg(reinterpret_cast<const float2*>(p.bz + (long long)(pz0 + lp) * p.sxy + col)),
+                          q[lp]);
+  }
+  __syncthreads();   // their slots take planes NSU .. NSU+R-1
+  if (tid == 0) {
+    for (int lp = NSU; lp < NSU + R && lp < nplanes; ++lp) {
+      const int k = lp % NSU;
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&bar[k], G::PLANE_BYTES);
+      tma_load_4d(ring + k * G::PLANE, &umap, &bar[k], tmx, tmy, pz0 + lp, b);
+    }
+  }
+  // planes R .. 2R-1
+#pragma unroll
+  for (int lp = R; lp < 2 * R; ++lp) {
+    if (!mbar_wait_bounded(&bar[lp % NSU], (uint32_t)((lp / NSU) & 1))) timed_out = true;
+    q[lp] = lds2(ring + (lp % NSU) * G::PLANE + own);
+    if (PSI)
+      qz[lp] = __fmul2_rn(__ldg(reinterpret_cast<const float2*>(p.bz + (long long)(pz0 + lp) * p.sxy + col)),
+                          q[lp]);
+  }
+
+  const float ay = p.spy[yg];
+  const float2 axy = make_float2(p.spx[xg] + ay, p.spx[xg + 1] + ay);
+  const bool in_y = yg < p.ny;
+  const bool in0 = in_y && xg < p.nx, in1 = in_y && xg + 1 < p.nx;
+  int e0 = 0, e1 = 0;
+  if (p.inj_off) {
+    const int t = b * p.ntiles + (zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    e0 = p.inj_off[t];
+    e1 = p.inj_off[t + 1];
+  }
+  const int loc0 = ty * G::TXP + 2 * tx;    // entry location of the own pair in plane lz = 0
+
+  struct Ops {
+    float2 uo, kk, hv, bx, by, bz, bzl;
+  };
+  auto ldg2 = [](const float* a) { return __ldg(reinterpret_cast<const float2*>(a)); };
+  auto load_ops = [&](int ii) {
+    const float2 z2 = make_float2(0.f, 0.f);
+    Ops o{z2, z2, z2, z2, z2, z2, z2};
+    const long long id = (long long)(z0 + ii + p.oz) * p.sxy + col;
+    o.uo = *reinterpret_cast<const float2*>(p.up + fo + id);
+    o.kk = ldg2(p.kf + id);
+    if (ADJ && p.image) o.hv = __ldcs(reinterpret_cast<const float2*>(p.hist + fo + id));
+    if (VD && !ADJ) {
+      o.bx = ldg2(p.bx + id);
+      o.by = ldg2(p.by + id);
+      o.bz = ldg2(p.bz + id);
+    }
+    if (PSI) o.bzl = ldg2(p.bz + (long long)(pz0 + ii + 2 * R) * p.sxy + col);
+    return o;
+  };
+  Ops nxt = load_ops(0);
+
+  for (int ib = 0; ib < nz_c; ib += Q) {
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+      const int i = ib + s;
+      if (i < nz_c) {
+        const int z = z0 + i;
+        const long long idx = (long long)(z + p.oz) * p.sxy + col;
+        const Ops cur = nxt;
+        if (i + 1 < nz_c) nxt = load_ops(i + 1);
+        // the lead plane z + R completes the queue
+        const int lead = i + 2 * R;
+        const int sl = lead % NSU;
+        if (!mbar_wait_bounded(&bar[sl], (uint32_t)((lead / NSU) & 1))) timed_out = true;
+        q[(s + 2 * R) % Q] = lds2(ring + sl * G::PLANE + own);
+        if (PSI) qz[(s + 2 * R) % Q] = __fmul2_rn(cur.bzl, q[(s + 2 * R) % Q]);
+        const float* cp = ring + ((i + R) % NSU) * G::PLANE;   // centre plane z
+        const float* bxp = bring + (2 * (i & 1)) * G::PLANE;
+        const float* byp = bxp + G::PLANE;
+        if (PSI && !mbar_wait_bounded(&bbar[i & 1], (uint32_t)((i >> 1) & 1))) timed_out = true;
+
+        // x pairs of the centre row: columns c0 - 2M .. c0 + 2M + 1
+        float2 X[2 * M + 1];
+#pragma unroll
+        for (int k = 0; k <= 2 * M; ++k) X[k] = lds2(cp + (ty + R) * BXW + c0 - 2 * M + 2 * k);
+        auto ux = [&](int d) {   // u at column c0 + d
+          const int e = d + 2 * M;
+          return (e & 1) ? X[e >> 1].y : X[e >> 1].x;
+        };
+        float2 Yp[R + 1], Ym[R + 1];
+#pragma unroll
+        for (int j = 1; j <= R; ++j) {
+          Yp[j] = lds2(cp + (ty + R + j) * BXW + c0);
+          Ym[j] = lds2(cp + (ty + R - j) * BXW + c0);
+        }
+
+        // zero-sum second derivatives, sum_j w_j (u_{+j} + u_{-j} - 2 u_0)
+        const float2 cen = q[(s + R) % Q];
+        const float2 n2 = make_float2(-(cen.x + cen.x), -(cen.y + cen.y));
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 1; j <= R; ++j) {
+          const float2 xp = make_float2(ux(j), ux(j + 1));
+          const float2 xm = make_float2(ux(-j), ux(1 - j));
+          acc = __ffma2_rn(bc2(p.wx.w2[j]), __fadd2_rn(__fadd2_rn(xp, xm), n2), acc);
+          acc = __ffma2_rn(bc2(p.wy.w2[j]), __fadd2_rn(__fadd2_rn(Yp[j], Ym[j]), n2), acc);
+          acc = __ffma2_rn(bc2(p.wz.w2[j]),
+                           __fadd2_rn(__fadd2_rn(q[(s + R + j) % Q], q[(s + R - j) % Q]), n2), acc);
+        }
+        if (VD && !ADJ) {
+          float2 dx = make_float2(0.f, 0.f), dy = dx, dz = dx;
+#pragma unroll
+          for (int j = 1; j <= R; ++j) {
+            const float2 xp = make_float2(ux(j), ux(j + 1));
+            const float2 xm = make_float2(ux(-j), ux(1 - j));
+            dx = __ffma2_rn(bc2(p.wx.w1[j]), __fadd2_rn(xp, neg2(xm)), dx);
+            dy = __ffma2_rn(bc2(p.wy.w1[j]), __fadd2_rn(Yp[j], neg2(Ym[j])), dy);
+            dz = __ffma2_rn(bc2(p.wz.w1[j]),
+                            __fadd2_rn(q[(s + R + j) % Q], neg2(q[(s + R - j) % Q])), dz);
+          }
+          float2 t = __fmul2_rn(cur.bx, dx);
+          t = __ffma2_rn(cur.by, dy, t);
+          t = __ffma2_rn(cur.bz, dz, t);
+          acc = __fadd2_rn(acc, neg2(t));
+        }
+        if (PSI) {
+          // b_x lambda on the centre row, b_y lambda on the centre column
+          float2 PX[2 * M + 1];
+#pragma unroll
+          for (int k = 0; k <= 2 * M; ++k)
+            PX[k] = __fmul2_rn(lds2(bxp + (ty + R) * BXW + c0 - 2 * M + 2 * k), X[k]);
+          auto px = [&](int d) {
+            const int e = d + 2 * M;
+            return (e & 1) ? PX[e >> 1].y : PX[e >> 1].x;
+          };
+#pragma unroll
+          for (int j = 1; j <= R; ++j) {
+            const float2 pp = make_float2(px(j), px(j + 1));
+            const float2 pm = make_float2(px(-j), px(1 - j));
+            acc = __ffma2_rn(bc2(p.wx.w1[j]), __fadd2_rn(pp, neg2(pm)), acc);
+            const float2 yb = __fmul2_rn(lds2(byp + (ty + R + j) * BXW + c0), Yp[j]);
+            const float2 ya = __fmul2_rn(lds2(byp + (ty + R - j) * BXW + c0), Ym[j]);
+            acc = __ffma2_rn(bc2(p.wy.w1[j]), __fadd2_rn(yb, neg2(ya)), acc);
+            acc = __ffma2_rn(bc2(p.wz.w1[j]),
+                             __fadd2_rn(qz[(s + R + j) % Q], neg2(qz[(s + R - j) % Q])), acc);
+          }
+        }
+        if (e1 > e0) {
+          const int l0 = (z - z0) * (TY * G::TXP) + loc0;
+          for (int e = e0; e < e1; ++e) {
+            const int loc = p.inj_loc[e];
+            if (loc == l0) acc.x = fmaf(p.inj_w[e], p.vals[p.inj_vidx[e] + p.step_off], acc.x);
+            else if (loc == l0 + 1)
+              acc.y = fmaf(p.inj_w[e], p.vals[p.inj_vidx[e] + p.step_off], acc.y);
+          }
+        }
+        const float az = p.spz[z];
+        const float2 a = make_float2(axy.x + az, axy.y + az);
+        const float2 h = __fmul2_rn(cur.kk, acc);
+        float2 t = __ffma2_rn(make_float2(-(1.f - a.x), -(1.f - a.y)), cur.uo,
+                              make_float2(2.f * cen.x, 2.f * cen.y));
+        t = __fadd2_rn(t, h);
+        const float2 r = __fmul2_rn(t, make_float2(__frcp_rn(1.f + a.x), __frcp_rn(1.f + a.y)));
+        if (in1) {
+          *reinterpret_cast<float2*>(p.up + fo + idx) = r;
+          if (!ADJ) {
+            if (p.hist) __stcs(reinterpret_cast<float2*>(p.hist + fo + idx), h);
+          } else if (p.image) {
+            float2* gp = reinterpret_cast<float2*>(p.g + fo + idx);
+            *gp = __ffma2_rn(neg2(cen), cur.hv, *gp);
+          }
+        } else if (in0) {
+          p.up[fo + idx] = r.x;
+          if (!ADJ) {
+            if (p.hist) __stcs(p.hist + fo + idx, h.x);
+          } else if (p.image) {
+            float* gp = p.g + fo + idx;
+            *gp = fmaf(-cen.x, cur.hv.x, *gp);
+          }
+        }
+        __syncthreads();   // every thread is done with the centre plane and this b stage
+        if (tid == 0) {
+          const int nx_ = i + R + NSU;   // the centre plane's slot takes plane nx_
+          if (nx_ < nplanes) {
+            const int k = nx_ % NSU;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bar[k], G::PLANE_BYTES);
+            tma_load_4d(ring + k * G::PLANE, &umap, &bar[k], tmx, tmy, pz0 + nx_, b);
+          }
+          if (PSI && i + 2 < nz_c) {
+            const int st = i & 1;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bbar[st], 2 * G::PLANE_BYTES);
+            tma_load_4d(bring + (2 * st) * G::PLANE, &bxmap, &bbar[st], tmx, tmy, z + 2 + p.oz, 0);
+            tma_load_4d(bring + (2 * st + 1) * G::PLANE, &bymap, &bbar[st], tmx, tmy, z + 2 + p.oz,
+                        0);
+          }
+        }
+      }
+    }
+  }
+  if (timed_out && p.flags) atomicOr(p.flags, 2);
+}
+
+template <int R, bool VD, bool ADJ, int BY>
+constexpr size_t smem_bytes_x2() {
+  using G = GeoX2<R, BY>;
+  size_t n = (size_t)G::NSU * G::PLANE;
+  if (VD && ADJ) n += 4 * (size_t)G::PLANE;
+  return n * sizeof(float);
+}
+
+template <int R, bool VD, bool ADJ, int BY>
+cudaError_t launch_t(const StepParams& p, const CUtensorMap& um, const CUtensorMap& bxm,
+                     const CUtensorMap& bym, cudaStream_t st) {
+  constexpr size_t smem = smem_bytes_x2<R, VD, ADJ, BY>();
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_step3d_x2<R, VD, ADJ, BY>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_step3d_x2<R, VD, ADJ, BY>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  dim3 grid((p.nx + 63) / 64, (p.ny + BY - 1) / BY, p.B * p.nzc);
+  k_step3d_x2<R, VD, ADJ, BY><<<grid, dim3(32, BY), smem, st>>>(p, um, bxm, bym);
+  return cudaGetLastError();
+}
+
+template <int R, bool VD, bool ADJ>
+cudaError_t launch_tile(const StepParams& p, const CUtensorMap& um, const CUtensorMap& bxm,
+                        const CUtensorMap& bym, int tile, cudaStream_t st) {
+  return tile3_variant(tile).by == 8 ? launch_t<R, VD, ADJ, 8>(p, um, bxm, bym, st)
+                                     : launch_t<R, VD, ADJ, 16>(p, um, bxm, bym, st);
+}
+
+}  // namespace
+
+cudaError_t launch_step3d_x2(const StepParams& p, const CUtensorMap& um, const CUtensorMap& bxm,
+                             const CUtensorMap& bym, int R, bool vd, bool adj, int tile,
+                             cudaStream_t st) {
+  if (R == 4) {
+    if (vd) return adj ? launch_tile<4, true, true>(p, um, bxm, bym, tile, st)
+                       : launch_tile<4, true, false>(p, um, bxm, bym, tile, st);
+    return adj ? launch_tile<4, false, true>(p, um, bxm, bym, tile, st)
+               : launch_tile<4, false, false>(p, um, bxm, bym, tile, st);
+  }
+  if (vd) return adj ? launch_tile<5, true, true>(p, um, bxm, bym, tile, st)
+                     : launch_tile<5, true, false>(p, um, bxm, bym, tile, st);
+  return adj ? launch_tile<5, false, true>(p, um, bxm, bym, tile, st)
+             : launch_tile<5, false, false>(p, um, bxm, bym, tile, st);
+}
+
+}  // namespace fwi

@@ -127,11 +127,13 @@ def test_gradient_2d_smem_family(vd):
     assert rel_l2(g, g_ref) <= TOL_GRAD
 
 
-@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12])
 @pytest.mark.parametrize("vd", [False, True])
 def test_tile_variants_3d(tile, vd):
-    """3D: shared-memory-staged variants (1-4) and TMA plane-ring variants (5-8)
-    each agree bit for bit within their family and to rounding across."""
+    """3D: shared-memory-staged variants (1-4) agree bit for bit among
+    themselves, TMA plane-ring variants with one (5-8) and two (9-12) x points
+    per thread likewise (one family: the same rounding order), and the two
+    families to rounding."""
     p = small_skull(nt=120)
     fam = 1 if tile <= 4 else 5
     base, _ = gpu_forward(p, tile=fam, variable_density=vd)
@@ -142,7 +144,7 @@ def test_tile_variants_3d(tile, vd):
     assert rel_l2(got, other) < 1e-6
 
 
-@pytest.mark.parametrize("tile", [1, 5])
+@pytest.mark.parametrize("tile", [1, 5, 10])
 def test_gradient_3d_both_families(tile):
     p = small_skull(n=(36, 38, 41), nt=160, order=10)
     obs = observed_from_oracle(p)
@@ -213,3 +215,20 @@ def test_gradient_batching():
     assert np.array_equal(d1, d4) and np.array_equal(d1, d2)
     assert rel_l2(g4, g1) < 1e-6 and rel_l2(g2, g1) < 1e-6
     assert abs(J4 - J1) < 1e-12 * abs(J1)
+
+
+@pytest.mark.parametrize("tile", [5, 8, 9, 12])
+def test_gradient_batching_3d(tile):
+    """3D: four shots in one batch (shots per CTA requested > 1, which the 3D
+    kernels ignore) give the gradient of four one-shot batches and of the
+    oracle."""
+    p = small_skull(n=(36, 38, 41), nt=140, nshots=4)
+    obs = observed_from_oracle(p)
+    J1, g1, d1, _ = gpu_gradient(p, obs, batch=1, tile=tile)
+    J4, g4, d4, plan = gpu_gradient(p, obs, batch=4, tile=tile, shots_per_cta=4)
+    assert plan.stats()["batch"] == 4
+    assert np.array_equal(d1, d4)
+    assert rel_l2(g4, g1) < 1e-6
+    assert abs(J4 - J1) < 1e-12 * abs(J1)
+    _, g_ref, _ = oracle.gradient(oracle_grid(p), p.vp, p.rho, p.src_xyz, p.wavelet, p.rec_xyz, obs)
+    assert rel_l2(g4, g_ref) <= TOL_GRAD
