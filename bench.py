@@ -326,8 +326,7 @@ def serving_stream(nreq=650, warm=50, seed=5, lanes=4, rate=20.0, **kw):
         reqs.append((t, dict(shape=p.shape, spacing=p.spacing, nt=p.nt, dt=p.dt, vp=vp, rho=rho,
                              geometry=binding.Geometry(p.src_xyz, p.rec_xyz), wavelet=f32(p.wavelet),
                              observed=obs, order=p.order, sponge=p.nb, c_ref=p.c_ref)))
-    free, _ = torch.cuda.mem_get_info()
-    budget = int(0.7 * free)
+    budget = int(0.7 * binding.mem_available())
 
     def play(nlanes):
         server = serve.Server(budget_bytes=budget, lanes=nlanes, request_cap=budget // 4)

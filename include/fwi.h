@@ -259,6 +259,13 @@ fwi_status fwi_forward_noalloc(const fwi_grid* grid, int nt, double dt, const fw
 /* Message describing the last error on the calling thread ("" if none). */
 const char* fwi_last_error(void);
 
+/* Device bytes that plan workspaces can still take on the current device:
+ * free device memory plus the part of the default stream-ordered pool that
+ * freed plans left reserved but unused (the default budget of a new plan is
+ * 0.9 of this).  Host utility, no counterpart in the paper.  Errors:
+ * FWI_ERR_INVALID_ARG (NULL), FWI_ERR_CUDA (no device). */
+fwi_status fwi_mem_available(size_t* bytes);
+
 /* Leapfrog stability limit of c*dt/h for this order and dimension:
  * 2/sqrt(ndim * lambda_max), lambda_max = |sum_j (-1)^j w2_j| of the
  * second-derivative stencil.  Returns a negative value for bad input. */

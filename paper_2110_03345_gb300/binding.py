@@ -27,7 +27,8 @@ STATUS = {0: "FWI_OK", 1: "FWI_ERR_INVALID_ARG", 2: "FWI_ERR_UNSTABLE_CFL", 3: "
 EXPORTS = ("fwi_plan_create", "fwi_plan_set_options", "fwi_plan_stats", "fwi_plan_estimate",
            "fwi_plan_destroy", "fwi_forward", "fwi_gradient", "fwi_last_error", "fwi_cfl_limit",
            "fwi_forward_noalloc", "fwi_misfit_forward", "fwi_misfit_backward",
-           "fwi_batch_create", "fwi_batch_run", "fwi_batch_stats_get", "fwi_batch_destroy")
+           "fwi_batch_create", "fwi_batch_run", "fwi_batch_stats_get", "fwi_batch_destroy",
+           "fwi_mem_available")
 
 
 class FwiError(RuntimeError):
@@ -129,6 +130,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.fwi_batch_create.argtypes = [P(vp), ctypes.c_int, P(CProblem), P(COptions),
                                          ctypes.c_size_t, vp, ctypes.c_int]
         lib.fwi_batch_create.restype = ctypes.c_int
+        lib.fwi_mem_available.argtypes = [P(ctypes.c_size_t)]
+        lib.fwi_mem_available.restype = ctypes.c_int
         lib.fwi_batch_run.argtypes = [vp]
         lib.fwi_batch_run.restype = ctypes.c_int
         lib.fwi_batch_stats_get.argtypes = [vp, P(CBatchStats)]
@@ -147,6 +150,14 @@ def _check(status: int):
 
 def cfl_limit(ndim: int, order: int) -> float:
     return float(load().fwi_cfl_limit(ndim, order))
+
+
+def mem_available() -> int:
+    """fwi_mem_available: device bytes plan workspaces can still take (free
+    memory plus the unused reserve of the stream-ordered pool)."""
+    n = ctypes.c_size_t(0)
+    _check(load().fwi_mem_available(ctypes.byref(n)))
+    return int(n.value)
 
 
 def make_grid(shape, spacing, order=8, sponge=20, c_ref=0.0) -> CGrid:

@@ -124,6 +124,40 @@ struct Carve {
 // Plan memory comes from the stream-ordered allocator on the plan's stream:
 // unlike cudaMalloc/cudaFree it never synchronises the device, so plans on
 // different streams (concurrent requests) do not serialise each other.
+// Stream-ordered allocation from the device's default pool.  Freed plan
+// workspaces stay reserved in the pool; when a request does not fit the
+// pool's free pieces and the device, the unused reserve is returned to the
+// device (trim) and the allocation retried once.
+cudaError_t pool_alloc(void** ptr, size_t bytes, cudaStream_t st, int device) {
+  cudaError_t e = cudaMallocAsync(ptr, bytes, st);
+  if (e == cudaSuccess) return e;
+  cudaGetLastError();
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) != cudaSuccess) return e;
+  cudaMemPoolTrimTo(pool, 0);
+  return cudaMallocAsync(ptr, bytes, st);
+}
+
+// Device bytes a new workspace can take: free device memory plus the unused
+// reserve of the default pool.
+size_t device_available(int device) {
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t reserved = 0, used = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess &&
+        reserved > used)
+      fr += (size_t)(reserved - used);
+  }
+  cudaGetLastError();
+  return fr;
+}
+
 fwi_status ensure_arena(fwi_plan* P, size_t bytes) {
   if (bytes <= P->arena_cap) return FWI_OK;
   if (P->fixed_memory)
@@ -133,7 +167,7 @@ fwi_status ensure_arena(fwi_plan* P, size_t bytes) {
     P->arena = nullptr;
     P->arena_cap = 0;
   }
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&P->arena), bytes, P->st);
+  cudaError_t e = pool_alloc(reinterpret_cast<void**>(&P->arena), bytes, P->st, P->device);
   if (e != cudaSuccess) {
     cudaGetLastError();
     P->arena = nullptr;
@@ -153,7 +187,7 @@ fwi_status ensure_tab(fwi_plan* P, size_t bytes) {
     P->tab = nullptr;
   }
   bytes = std::max(bytes, (size_t)1 << 20);
-  CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&P->tab), bytes, P->st));
+  CUDA_TRY(pool_alloc(reinterpret_cast<void**>(&P->tab), bytes, P->st, P->device));
   P->tab_cap = bytes;
   return FWI_OK;
 }
@@ -1176,6 +1210,17 @@ extern "C" {
 
 const char* fwi_last_error(void) { return g_err.c_str(); }
 
+fwi_status fwi_mem_available(size_t* bytes) {
+  if (!bytes) return fail(FWI_ERR_INVALID_ARG, "NULL argument");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(FWI_ERR_CUDA, "no CUDA device");
+  }
+  *bytes = device_available(dev);
+  return FWI_OK;
+}
+
 double fwi_cfl_limit(int ndim, int order) {
   if ((ndim != 2 && ndim != 3) || (order != 8 && order != 10)) return -1.0;
   return cfl_limit(ndim, order);
@@ -1201,6 +1246,7 @@ fwi_status fwi_plan_create(fwi_plan** plan, const fwi_grid* grid, int nt, double
   size_t fr = 0, tot = 0;
   e = cudaMemGetInfo(&fr, &tot);
   if (e != cudaSuccess) return cleanup(fail(FWI_ERR_CUDA, cudaGetErrorString(e)));
+  fr = device_available(P->device);   // free memory plus the pool's unused reserve
   P->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)fr);
   if (cudaDeviceGetAttribute(&P->nsm, cudaDevAttrMultiProcessorCount, P->device) != cudaSuccess) {
     cudaGetLastError();

@@ -37,13 +37,14 @@ def soft_tissue_voxels(p, k=8, seed=3, margin_m=2e-3):
     return out
 
 
-def check_fd(fd, g, tol_l2=1e-2, tol_each=2.5e-2):
+def check_fd(fd, g, tol_l2=1e-2, tol_each=1e-2):
     """FD against a gradient at the voxels.  The FP32 rounding noise of a J
-    difference is absolute (about the same at every voxel), so a voxel with a
-    small gradient sees a larger relative error: the 8 voxels are compared in
-    relative L2 (1e-2), and each one within 2.5e-2."""
+    difference is absolute (about the same at every voxel: 20-40 against
+    gradients of 1e2-1e4 at full size), so a voxel with a small gradient sees
+    a large relative error: the 8 voxels are compared in relative L2 (1e-2),
+    and each one within 1e-2 of the largest gradient among them."""
     assert np.linalg.norm(fd - g) <= tol_l2 * np.linalg.norm(g)
-    assert np.all(np.abs(fd - g) <= tol_each * np.abs(g))
+    assert np.all(np.abs(fd - g) <= tol_each * np.abs(g).max())
 
 
 def fd_check(p, plan, obs, voxels, rho, geo, wav, rel_h=1e-1, points=4):
