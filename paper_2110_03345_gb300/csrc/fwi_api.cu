@@ -279,7 +279,14 @@ struct HostTable {
   std::vector<float> w;
 };
 
-HostTable bucket(const std::vector<Entry>& E, int nbuckets) {
+HostTable bucket(const std::vector<Entry>& E_in, int nbuckets) {
+  // within a bucket, entries in increasing tile-local index (the 3D kernels
+  // walk them plane by plane with one cursor); stable, so the entries of one
+  // node keep their order and its sum the same rounding
+  std::vector<Entry> E(E_in);
+  std::stable_sort(E.begin(), E.end(), [](const Entry& a, const Entry& b) {
+    return a.bucket != b.bucket ? a.bucket < b.bucket : a.loc < b.loc;
+  });
   HostTable H;
   H.off.assign(nbuckets + 1, 0);
   for (const Entry& e : E) H.off[e.bucket + 1]++;
@@ -753,6 +760,11 @@ StepParams base_params(Call& c) {
   p.wx = P->wx;
   p.wy = P->wy;
   p.wz = P->wz;
+  for (int a = 0; a < 3; ++a) {
+    const bool on = a < P->grid.ndim;
+    p.ih2[a] = on ? (float)(1.0 / (P->h[a] * P->h[a])) : 0.f;
+    p.ih1[a] = on ? (float)(1.0 / P->h[a]) : 0.f;
+  }
   p.ntiles = c.T.ntiles();
   p.ncorner = c.ncorner;
   if (P->grid.ndim == 3) {

@@ -61,7 +61,10 @@ struct StepParams {
   int nx, ny, nz;
   int ox, oy, oz;
   AxisW wx, wy, wz;
-  // sparse injection, bucketed by (slot, tile): entries e in [off[s*T+t], off[s*T+t+1])
+  float ih2[3];          // 1 / h_d^2 and 1 / h_d (x, y, z): scales of the unscaled
+  float ih1[3];          // compile-time weights of the 3D TMA kernels
+  // sparse injection, bucketed by (slot, tile): entries e in [off[s*T+t], off[s*T+t+1]),
+  // ordered by inj_loc within a bucket (stable: same-node entries keep their order)
   const int* inj_off;
   const int* inj_loc;    // tile-local linear index (2D: ly*TX+lx; 3D: (lz*TY+ly)*TX+lx)
   const int* inj_vidx;   // index into vals (before step_off)
@@ -123,7 +126,8 @@ __host__ __device__ inline Tile2 tile2_tma_variant(int v) {
     default: return {1, 32};
   }
 }
-// 3D tile variants: thread rows (tile 32 x by) and z chunk
+// 3D tile variants: thread rows (tile 32 x by) and z chunk (at most MAX_ZCHUNK)
+constexpr int MAX_ZCHUNK = 64;
 struct Tile3 { int by, zc; };
 constexpr int NUM_TILE3 = 4;
 __host__ __device__ inline Tile3 tile3_variant(int v) {

@@ -17,6 +17,7 @@
 // Every mbarrier wait is bounded (on time-out the error flag is set and the
 // kernel carries on, so no thread skips a barrier).
 #include "fwi_internal.cuh"
+#include "stencil3d.cuh"
 #include "tma_util.cuh"
 
 #include <cuda.h>
@@ -38,7 +39,7 @@ struct Geo3 {
 };
 
 template <int R, bool VD, bool ADJ, int BY>
-__global__ void __launch_bounds__(32 * BY)
+__global__ void __launch_bounds__(32 * BY, 1024 / (32 * BY))
 k_step3d_tma(const StepParams p, const __grid_constant__ CUtensorMap umap,
              const __grid_constant__ CUtensorMap bxmap, const __grid_constant__ CUtensorMap bymap) {
   using G = Geo3<R, BY>;
@@ -52,6 +53,7 @@ k_step3d_tma(const StepParams p, const __grid_constant__ CUtensorMap umap,
   float* bring = ring + NSU * G::PLANE;      // PSI: [2 stages][b_x, b_y][BYH][BXW]
   __shared__ uint64_t bar[NSU];
   __shared__ uint64_t bbar[2];
+  __shared__ int s_pe[MAX_ZCHUNK + 1];        // first source entry of each plane of the chunk
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * 32 + tx;
@@ -89,6 +91,27 @@ k_step3d_tma(const StepParams p, const __grid_constant__ CUtensorMap umap,
     mbar_init(&bbar[0], 1);
     mbar_init(&bbar[1], 1);
     fence_mbar_init();
+  }
+  // Source entries of the tile are sorted by tile-local index, which grows
+  // with the plane: s_pe[lz] = first entry of plane lz (binary search), so a
+  // plane's entries are s_pe[lz] .. s_pe[lz + 1] - 1.
+  bool has_inj = false;
+  if (p.inj_off) {
+    const int t = b * p.ntiles + (zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const int e0 = p.inj_off[t], e1 = p.inj_off[t + 1];
+    has_inj = e1 > e0;
+    if (has_inj) {
+      for (int k = tid; k <= nz_c; k += NT) {
+        const int lim = k * (TY * TX);
+        int lo = e0, hi = e1;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (__ldg(p.inj_loc + mid) < lim) lo = mid + 1;
+          else hi = mid;
+        }
+        s_pe[k] = lo;
+      }
+    }
   }
   __syncthreads();
   if (tid == 0) {
@@ -128,12 +151,7 @@ k_step3d_tma(const StepParams p, const __grid_constant__ CUtensorMap umap,
 
   const float axy = p.spx[xg] + p.spy[yg];
   const bool in_xy = (xg < p.nx) && (yg < p.ny);
-  int e0 = 0, e1 = 0;
-  if (p.inj_off) {
-    const int t = b * p.ntiles + (zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    e0 = p.inj_off[t];
-    e1 = p.inj_off[t + 1];
-  }
+
   const int r0 = ty + R, c0 = tx + G::XOFF;
 
   // Global operands of a point (u^{n-1}, k, h, b) are loaded one plane ahead
@@ -173,46 +191,53 @@ k_step3d_tma(const StepParams p, const __grid_constant__ CUtensorMap umap,
     const float* byp = bxp + G::PLANE;
     if (PSI && !mbar_wait_bounded(&bbar[i & 1], (uint32_t)((i >> 1) & 1))) timed_out = true;
 
-    // zero-sum second derivatives, sum_j w_j (u_{+j} + u_{-j} - 2 u_0)
+    // zero-sum second derivatives per axis, sum_j w_j (u_{+j} + u_{-j} - 2 u_0),
+    // with the unscaled weights as immediates; 1/h^2 applied per axis
     const float cen = q[R];
-    const float c2 = cen + cen;
-    float acc = 0.f;
+    const float n2 = -(cen + cen);
+    float ax = 0.f, ay = 0.f, az = 0.f;
 #pragma unroll
     for (int j = 1; j <= R; ++j) {
-      acc = fmaf(p.wx.w2[j], (cp[r0 * G::BXW + c0 + j] + cp[r0 * G::BXW + c0 - j]) - c2, acc);
-      acc = fmaf(p.wy.w2[j], (cp[(r0 + j) * G::BXW + c0] + cp[(r0 - j) * G::BXW + c0]) - c2, acc);
-      acc = fmaf(p.wz.w2[j], (q[R + j] + q[R - j]) - c2, acc);
+      ax = fmaf(w2c<R>(j), (cp[r0 * G::BXW + c0 + j] + cp[r0 * G::BXW + c0 - j]) + n2, ax);
+      ay = fmaf(w2c<R>(j), (cp[(r0 + j) * G::BXW + c0] + cp[(r0 - j) * G::BXW + c0]) + n2, ay);
+      az = fmaf(w2c<R>(j), (q[R + j] + q[R - j]) + n2, az);
     }
+    float acc = __fmul_rn(ax, p.ih2[0]);
+    acc = fmaf(ay, p.ih2[1], acc);
+    acc = fmaf(az, p.ih2[2], acc);
     if (VD && !ADJ) {
       float dx = 0.f, dy = 0.f, dz = 0.f;
 #pragma unroll
       for (int j = 1; j <= R; ++j) {
-        dx = fmaf(p.wx.w1[j], cp[r0 * G::BXW + c0 + j] - cp[r0 * G::BXW + c0 - j], dx);
-        dy = fmaf(p.wy.w1[j], cp[(r0 + j) * G::BXW + c0] - cp[(r0 - j) * G::BXW + c0], dy);
-        dz = fmaf(p.wz.w1[j], q[R + j] - q[R - j], dz);
+        dx = fmaf(w1c<R>(j), cp[r0 * G::BXW + c0 + j] + (-cp[r0 * G::BXW + c0 - j]), dx);
+        dy = fmaf(w1c<R>(j), cp[(r0 + j) * G::BXW + c0] + (-cp[(r0 - j) * G::BXW + c0]), dy);
+        dz = fmaf(w1c<R>(j), q[R + j] + (-q[R - j]), dz);
       }
-      float t = __fmul_rn(bxv, dx);
-      t = fmaf(byv, dy, t);
-      t = fmaf(bzv, dz, t);
-      acc = acc - t;
+      float t = __fmul_rn(bxv, __fmul_rn(dx, p.ih1[0]));
+      t = fmaf(byv, __fmul_rn(dy, p.ih1[1]), t);
+      t = fmaf(bzv, __fmul_rn(dz, p.ih1[2]), t);
+      acc = acc + (-t);
     }
     if (PSI) {
+      float sx = 0.f, sy = 0.f, sz = 0.f;
 #pragma unroll
       for (int j = 1; j <= R; ++j) {
         const int xp = r0 * G::BXW + c0 + j, xm = r0 * G::BXW + c0 - j;
         const int yp = (r0 + j) * G::BXW + c0, ym = (r0 - j) * G::BXW + c0;
-        acc = fmaf(p.wx.w1[j], __fmul_rn(bxp[xp], cp[xp]) - __fmul_rn(bxp[xm], cp[xm]), acc);
-        acc = fmaf(p.wy.w1[j], __fmul_rn(byp[yp], cp[yp]) - __fmul_rn(byp[ym], cp[ym]), acc);
-        acc = fmaf(p.wz.w1[j], qz[R + j] - qz[R - j], acc);
+        sx = fmaf(w1c<R>(j), __fmul_rn(bxp[xp], cp[xp]) + (-__fmul_rn(bxp[xm], cp[xm])), sx);
+        sy = fmaf(w1c<R>(j), __fmul_rn(byp[yp], cp[yp]) + (-__fmul_rn(byp[ym], cp[ym])), sy);
+        sz = fmaf(w1c<R>(j), qz[R + j] + (-qz[R - j]), sz);
       }
+      acc = fmaf(sx, p.ih1[0], acc);
+      acc = fmaf(sy, p.ih1[1], acc);
+      acc = fmaf(sz, p.ih1[2], acc);
     }
-    if (e1 > e0) {
+    if (has_inj) {
       const int lz = z - z0;
-      for (int e = e0; e < e1; ++e) {
-        const int loc = p.inj_loc[e];
-        if (loc == (lz * TY + ty) * TX + tx)
-          acc = fmaf(p.inj_w[e], p.vals[p.inj_vidx[e] + p.step_off], acc);
-      }
+      const int me = (lz * TY + ty) * TX + tx;
+      const int pe1 = s_pe[lz + 1];
+      for (int e = s_pe[lz]; e < pe1; ++e)
+        if (__ldg(p.inj_loc + e) == me) acc = fmaf(p.inj_w[e], p.vals[p.inj_vidx[e] + p.step_off], acc);
     }
     const float a = axy + p.spz[z];
     // explicit rounding order (no contraction left to the compiler), shared

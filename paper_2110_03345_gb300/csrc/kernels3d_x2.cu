@@ -19,6 +19,7 @@
 // Every mbarrier wait is bounded: on time-out the error flag is set and the
 // kernel carries on, so no thread skips a barrier.
 #include "fwi_internal.cuh"
+#include "stencil3d.cuh"
 #include "tma_util.cuh"
 
 #include <cuda.h>
@@ -65,6 +66,7 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
   float* bring = ring + NSU * G::PLANE;       // PSI: [2 stages][b_x, b_y][BYH][BXW]
   __shared__ uint64_t bar[NSU];
   __shared__ uint64_t bbar[2];
+  __shared__ int s_pe[MAX_ZCHUNK + 1];        // first source entry of each plane of the chunk
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * 32 + tx;
@@ -103,6 +105,27 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
     mbar_init(&bbar[0], 1);
     mbar_init(&bbar[1], 1);
     fence_mbar_init();
+  }
+  // Source entries of the tile are sorted by tile-local index, which grows
+  // with the plane: s_pe[lz] = first entry of plane lz (binary search), so a
+  // plane's entries are s_pe[lz] .. s_pe[lz + 1] - 1.
+  bool has_inj = false;
+  if (p.inj_off) {
+    const int t = b * p.ntiles + (zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const int e0 = p.inj_off[t], e1 = p.inj_off[t + 1];
+    has_inj = e1 > e0;
+    if (has_inj) {
+      for (int k = tid; k <= nz_c; k += NT) {
+        const int lim = k * (TY * G::TXP);
+        int lo = e0, hi = e1;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (__ldg(p.inj_loc + mid) < lim) lo = mid + 1;
+          else hi = mid;
+        }
+        s_pe[k] = lo;
+      }
+    }
   }
   __syncthreads();
   if (tid == 0) {
@@ -158,12 +181,7 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
   const float2 axy = make_float2(p.spx[xg] + ay, p.spx[xg + 1] + ay);
   const bool in_y = yg < p.ny;
   const bool in0 = in_y && xg < p.nx, in1 = in_y && xg + 1 < p.nx;
-  int e0 = 0, e1 = 0;
-  if (p.inj_off) {
-    const int t = b * p.ntiles + (zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    e0 = p.inj_off[t];
-    e1 = p.inj_off[t + 1];
-  }
+
   const int loc0 = ty * G::TXP + 2 * tx;    // entry location of the own pair in plane lz = 0
 
   struct Ops {
@@ -222,33 +240,38 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
           Ym[j] = lds2(cp + (ty + R - j) * BXW + c0);
         }
 
-        // zero-sum second derivatives, sum_j w_j (u_{+j} + u_{-j} - 2 u_0)
+        // zero-sum second derivatives per axis, sum_j w_j (u_{+j} + u_{-j} - 2 u_0),
+        // with the unscaled weights as immediates; 1/h^2 applied per axis
         const float2 cen = q[(s + R) % Q];
         const float2 n2 = make_float2(-(cen.x + cen.x), -(cen.y + cen.y));
-        float2 acc = make_float2(0.f, 0.f);
+        const float2 z2 = make_float2(0.f, 0.f);
+        float2 ax = z2, ay = z2, az = z2;
 #pragma unroll
         for (int j = 1; j <= R; ++j) {
           const float2 xp = make_float2(ux(j), ux(j + 1));
           const float2 xm = make_float2(ux(-j), ux(1 - j));
-          acc = __ffma2_rn(bc2(p.wx.w2[j]), __fadd2_rn(__fadd2_rn(xp, xm), n2), acc);
-          acc = __ffma2_rn(bc2(p.wy.w2[j]), __fadd2_rn(__fadd2_rn(Yp[j], Ym[j]), n2), acc);
-          acc = __ffma2_rn(bc2(p.wz.w2[j]),
-                           __fadd2_rn(__fadd2_rn(q[(s + R + j) % Q], q[(s + R - j) % Q]), n2), acc);
+          ax = __ffma2_rn(bc2(w2c<R>(j)), __fadd2_rn(__fadd2_rn(xp, xm), n2), ax);
+          ay = __ffma2_rn(bc2(w2c<R>(j)), __fadd2_rn(__fadd2_rn(Yp[j], Ym[j]), n2), ay);
+          az = __ffma2_rn(bc2(w2c<R>(j)),
+                          __fadd2_rn(__fadd2_rn(q[(s + R + j) % Q], q[(s + R - j) % Q]), n2), az);
         }
+        float2 acc = __fmul2_rn(ax, bc2(p.ih2[0]));
+        acc = __ffma2_rn(ay, bc2(p.ih2[1]), acc);
+        acc = __ffma2_rn(az, bc2(p.ih2[2]), acc);
         if (VD && !ADJ) {
-          float2 dx = make_float2(0.f, 0.f), dy = dx, dz = dx;
+          float2 dx = z2, dy = z2, dz = z2;
 #pragma unroll
           for (int j = 1; j <= R; ++j) {
             const float2 xp = make_float2(ux(j), ux(j + 1));
             const float2 xm = make_float2(ux(-j), ux(1 - j));
-            dx = __ffma2_rn(bc2(p.wx.w1[j]), __fadd2_rn(xp, neg2(xm)), dx);
-            dy = __ffma2_rn(bc2(p.wy.w1[j]), __fadd2_rn(Yp[j], neg2(Ym[j])), dy);
-            dz = __ffma2_rn(bc2(p.wz.w1[j]),
+            dx = __ffma2_rn(bc2(w1c<R>(j)), __fadd2_rn(xp, neg2(xm)), dx);
+            dy = __ffma2_rn(bc2(w1c<R>(j)), __fadd2_rn(Yp[j], neg2(Ym[j])), dy);
+            dz = __ffma2_rn(bc2(w1c<R>(j)),
                             __fadd2_rn(q[(s + R + j) % Q], neg2(q[(s + R - j) % Q])), dz);
           }
-          float2 t = __fmul2_rn(cur.bx, dx);
-          t = __ffma2_rn(cur.by, dy, t);
-          t = __ffma2_rn(cur.bz, dz, t);
+          float2 t = __fmul2_rn(cur.bx, __fmul2_rn(dx, bc2(p.ih1[0])));
+          t = __ffma2_rn(cur.by, __fmul2_rn(dy, bc2(p.ih1[1])), t);
+          t = __ffma2_rn(cur.bz, __fmul2_rn(dz, bc2(p.ih1[2])), t);
           acc = __fadd2_rn(acc, neg2(t));
         }
         if (PSI) {
@@ -261,29 +284,35 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
             const int e = d + 2 * M;
             return (e & 1) ? PX[e >> 1].y : PX[e >> 1].x;
           };
+          float2 sx = z2, sy = z2, sz = z2;
 #pragma unroll
           for (int j = 1; j <= R; ++j) {
             const float2 pp = make_float2(px(j), px(j + 1));
             const float2 pm = make_float2(px(-j), px(1 - j));
-            acc = __ffma2_rn(bc2(p.wx.w1[j]), __fadd2_rn(pp, neg2(pm)), acc);
+            sx = __ffma2_rn(bc2(w1c<R>(j)), __fadd2_rn(pp, neg2(pm)), sx);
             const float2 yb = __fmul2_rn(lds2(byp + (ty + R + j) * BXW + c0), Yp[j]);
             const float2 ya = __fmul2_rn(lds2(byp + (ty + R - j) * BXW + c0), Ym[j]);
-            acc = __ffma2_rn(bc2(p.wy.w1[j]), __fadd2_rn(yb, neg2(ya)), acc);
-            acc = __ffma2_rn(bc2(p.wz.w1[j]),
-                             __fadd2_rn(qz[(s + R + j) % Q], neg2(qz[(s + R - j) % Q])), acc);
+            sy = __ffma2_rn(bc2(w1c<R>(j)), __fadd2_rn(yb, neg2(ya)), sy);
+            sz = __ffma2_rn(bc2(w1c<R>(j)),
+                            __fadd2_rn(qz[(s + R + j) % Q], neg2(qz[(s + R - j) % Q])), sz);
           }
+          acc = __ffma2_rn(sx, bc2(p.ih1[0]), acc);
+          acc = __ffma2_rn(sy, bc2(p.ih1[1]), acc);
+          acc = __ffma2_rn(sz, bc2(p.ih1[2]), acc);
         }
-        if (e1 > e0) {
-          const int l0 = (z - z0) * (TY * G::TXP) + loc0;
-          for (int e = e0; e < e1; ++e) {
-            const int loc = p.inj_loc[e];
-            if (loc == l0) acc.x = fmaf(p.inj_w[e], p.vals[p.inj_vidx[e] + p.step_off], acc.x);
-            else if (loc == l0 + 1)
+        if (has_inj) {
+          const int lz = z - z0;
+          const int l0 = lz * (TY * G::TXP) + loc0;
+          const int pe1 = s_pe[lz + 1];
+          for (int e = s_pe[lz]; e < pe1; ++e) {
+            const int l = __ldg(p.inj_loc + e);
+            if (l == l0) acc.x = fmaf(p.inj_w[e], p.vals[p.inj_vidx[e] + p.step_off], acc.x);
+            else if (l == l0 + 1)
               acc.y = fmaf(p.inj_w[e], p.vals[p.inj_vidx[e] + p.step_off], acc.y);
           }
         }
-        const float az = p.spz[z];
-        const float2 a = make_float2(axy.x + az, axy.y + az);
+        const float sz_ = p.spz[z];
+        const float2 a = make_float2(axy.x + sz_, axy.y + sz_);
         const float2 h = __fmul2_rn(cur.kk, acc);
         float2 t = __ffma2_rn(make_float2(-(1.f - a.x), -(1.f - a.y)), cur.uo,
                               make_float2(2.f * cen.x, 2.f * cen.y));
