@@ -153,14 +153,17 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
     const float4* s_u = buf ? s_t1 : s_t0;
     float* const up_s = p.up + (size_t)s * p.fstride;
     float* const h_s = p.hist ? p.hist + (size_t)s * p.fstride : nullptr;
-    // adjoint: this shot's global operands are issued before the tile wait
-    // (the forward loads u^{n-1} where it is used, to stay within 64 registers)
-    float4 uo[ADJ ? RY : 1], hv[ADJ ? RY : 1];
-    if (ADJ) {
+    // this shot's global operands are issued before the tile wait, so their
+    // latency overlaps it: u^{n-1}, and h^k (adjoint) or b_x, b_y (forward)
+    float4 uo[RY], hv[ADJ ? RY : 1];
+    float4 bxf[VD && !ADJ ? RY : 1], byf[VD && !ADJ ? RY : 1];
 #pragma unroll
-      for (int iy = 0; iy < RY; ++iy) {
-        uo[iy] = ld4(up_s + pix[iy]);
-        if (p.image) hv[iy] = __ldcs(reinterpret_cast<const float4*>(h_s + pix[iy]));
+    for (int iy = 0; iy < RY; ++iy) {
+      uo[iy] = ld4(up_s + pix[iy]);
+      if (ADJ && p.image) hv[iy] = __ldcs(reinterpret_cast<const float4*>(h_s + pix[iy]));
+      if (VD && !ADJ) {
+        bxf[iy] = ldg4(p.bx + pix[iy]);
+        byf[iy] = ldg4(p.by + pix[iy]);
       }
     }
     // A wait that times out flags the error and carries on (no early exit, so
@@ -182,7 +185,9 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
       for (int q = 0; q <= 2 * NL; ++q) unpack(s_u[srow * SW + tx + q], v + 4 * q);
 
       // second derivatives in the zero-sum form sum_j w_j (u_{+j} + u_{-j} - 2 u_0)
-      float acc[4], c2[4], d1x[4], d1y[4];
+      // (forward, variable density: the b_x D1x u term is subtracted as soon
+      // as D1x u is known, so the four first derivatives are never live at once)
+      float acc[4], c2[4];
 #pragma unroll
       for (int ix = 0; ix < 4; ++ix) {
         const int c = 4 * NL + ix;
@@ -190,13 +195,13 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
         float t = 0.f;
 #pragma unroll
         for (int j = 1; j <= R; ++j) t = fmaf(wx.w2[j], (v[c + j] + v[c - j]) - c2[ix], t);
-        acc[ix] = t;
-        d1x[ix] = 0.f;
-        d1y[ix] = 0.f;
         if (VD && !ADJ) {
+          float d = 0.f;
 #pragma unroll
-          for (int j = 1; j <= R; ++j) d1x[ix] = fmaf(wx.w1[j], v[c + j] - v[c - j], d1x[ix]);
+          for (int j = 1; j <= R; ++j) d = fmaf(wx.w1[j], v[c + j] - v[c - j], d);
+          t = fmaf(-get(bxf[iy], ix), d, t);
         }
+        acc[ix] = t;
       }
       if (VD && ADJ) {
         // D1x(b_x lambda) from the b_x and lambda windows of this row
@@ -248,15 +253,12 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
             }
           }
         }
+        if (VD && !ADJ) {   // - b_y D1y u
+          const float4 byv = byf[iy];
+          A0 = __ffma2_rn(make_float2(-byv.x, -byv.y), D0, A0);
+          A1 = __ffma2_rn(make_float2(-byv.z, -byv.w), D1, A1);
+        }
         acc[0] = A0.x; acc[1] = A0.y; acc[2] = A1.x; acc[3] = A1.y;
-        d1y[0] = D0.x; d1y[1] = D0.y; d1y[2] = D1.x; d1y[3] = D1.y;
-      }
-      if (VD && !ADJ) {
-        // b_x, b_y are re-read per shot (L1 hits after the first shot)
-        const float4 bxv = ldg4(p.bx + pix[iy]), byv = ldg4(p.by + pix[iy]);
-#pragma unroll
-        for (int ix = 0; ix < 4; ++ix)
-          acc[ix] -= get(bxv, ix) * d1x[ix] + get(byv, ix) * d1y[ix];
       }
       if (e1 > e0) {
         for (int e = e0; e < e1; ++e) {
@@ -271,7 +273,7 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
         }
       }
       float* upp = up_s + pix[iy];
-      const float4 uoi = ADJ ? uo[ADJ ? iy : 0] : ld4(upp);
+      const float4 uoi = uo[iy];
       float res[4], upd[4];
 #pragma unroll
       for (int ix = 0; ix < 4; ++ix) {

@@ -130,9 +130,11 @@ k_step3d_tma(const StepParams p, const __grid_constant__ CUtensorMap umap,
 
   const int own = (ty + R) * G::BXW + tx + G::XOFF;   // own column in a staged plane
   bool timed_out = false;
-  // register queues: q[j] = u at plane z - R + j of this column
-  float q[Q];
-  float qz[PSI ? Q : 1];
+  // register queues, U planes per loop trip: q[j] = u at plane z0 + i0 - R + j
+  // of this column (i0 = first plane of the trip); shifted by U after a trip
+  constexpr int U = 2;
+  float q[Q + U - 1];
+  float qz[PSI ? Q + U - 1 : 1];
 #pragma unroll
   for (int lp = 0; lp < Q - 1; ++lp) {
     if (!mbar_wait_bounded(&bar[lp], 0)) timed_out = true;
@@ -154,17 +156,20 @@ k_step3d_tma(const StepParams p, const __grid_constant__ CUtensorMap umap,
 
   const int r0 = ty + R, c0 = tx + G::XOFF;
 
-  // Global operands of a point (u^{n-1}, k, h, b) are loaded one plane ahead
-  // (software pipelining in registers), so their latency overlaps a plane.
+  // Global operands of a point (u^{n-1}, k, h, g, b) are loaded one plane
+  // ahead (software pipelining in registers), so their latency overlaps a plane.
   struct Ops {
-    float uo, kk, hv, bx, by, bz, bzl;
+    float uo, kk, hv, gv, bx, by, bz, bzl;
   };
   auto load_ops = [&](int ii) {
-    Ops o{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    Ops o{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const long long id = (long long)(z0 + ii + p.oz) * p.sxy + col;
     o.uo = p.up[fo + id];
     o.kk = __ldg(p.kf + id);
-    if (ADJ && p.image) o.hv = __ldcs(p.hist + fo + id);
+    if (ADJ && p.image) {
+      o.hv = __ldcs(p.hist + fo + id);
+      o.gv = p.g[fo + id];
+    }
     if (VD && !ADJ) {
       o.bx = __ldg(p.bx + id);
       o.by = __ldg(p.by + id);
@@ -175,107 +180,115 @@ k_step3d_tma(const StepParams p, const __grid_constant__ CUtensorMap umap,
   };
   Ops nxt = load_ops(0);
 
-  for (int i = 0; i < nz_c; ++i) {
-    const int z = z0 + i;
-    const long long idx = (long long)(z + p.oz) * p.sxy + col;
-    const Ops cur = nxt;
-    if (i + 1 < nz_c) nxt = load_ops(i + 1);
-    const float uo = cur.uo, kk = cur.kk, hv = cur.hv, bxv = cur.bx, byv = cur.by, bzv = cur.bz;
-    // the lead plane z + R completes the queue
-    const int lead = i + 2 * R;
-    if (!mbar_wait_bounded(&bar[lead % NSU], (uint32_t)((lead / NSU) & 1))) timed_out = true;
-    q[Q - 1] = ring[(lead % NSU) * G::PLANE + own];
-    if (PSI) qz[Q - 1] = __fmul_rn(cur.bzl, q[Q - 1]);
-    const float* cp = ring + ((i + R) % NSU) * G::PLANE;   // centre plane z
-    const float* bxp = bring + (2 * (i & 1)) * G::PLANE;
-    const float* byp = bxp + G::PLANE;
-    if (PSI && !mbar_wait_bounded(&bbar[i & 1], (uint32_t)((i >> 1) & 1))) timed_out = true;
+  for (int i0 = 0; i0 < nz_c; i0 += U) {
+#pragma unroll
+    for (int s = 0; s < U; ++s) {
+      const int i = i0 + s;
+      if (i < nz_c) {
+        const int z = z0 + i;
+        const long long idx = (long long)(z + p.oz) * p.sxy + col;
+        const Ops cur = nxt;
+        if (i + 1 < nz_c) nxt = load_ops(i + 1);
+        const float uo = cur.uo, kk = cur.kk, hv = cur.hv, bxv = cur.bx, byv = cur.by,
+                    bzv = cur.bz;
+        // the lead plane z + R completes the queue
+        const int lead = i + 2 * R;
+        if (!mbar_wait_bounded(&bar[lead % NSU], (uint32_t)((lead / NSU) & 1))) timed_out = true;
+        q[s + 2 * R] = ring[(lead % NSU) * G::PLANE + own];
+        if (PSI) qz[s + 2 * R] = __fmul_rn(cur.bzl, q[s + 2 * R]);
+        const float* cp = ring + ((i + R) % NSU) * G::PLANE;   // centre plane z
+        const float* bxp = bring + (2 * (i & 1)) * G::PLANE;
+        const float* byp = bxp + G::PLANE;
+        if (PSI && !mbar_wait_bounded(&bbar[i & 1], (uint32_t)((i >> 1) & 1))) timed_out = true;
 
-    // zero-sum second derivatives per axis, sum_j w_j (u_{+j} + u_{-j} - 2 u_0),
-    // with the unscaled weights as immediates; 1/h^2 applied per axis
-    const float cen = q[R];
-    const float n2 = -(cen + cen);
-    float ax = 0.f, ay = 0.f, az = 0.f;
+        // zero-sum second derivatives per axis, sum_j w_j (u_{+j} + u_{-j} - 2 u_0),
+        // with the unscaled weights as immediates; 1/h^2 applied per axis
+        const float cen = q[s + R];
+        const float n2 = -(cen + cen);
+        float ax = 0.f, ay = 0.f, az = 0.f;
 #pragma unroll
-    for (int j = 1; j <= R; ++j) {
-      ax = fmaf(w2c<R>(j), (cp[r0 * G::BXW + c0 + j] + cp[r0 * G::BXW + c0 - j]) + n2, ax);
-      ay = fmaf(w2c<R>(j), (cp[(r0 + j) * G::BXW + c0] + cp[(r0 - j) * G::BXW + c0]) + n2, ay);
-      az = fmaf(w2c<R>(j), (q[R + j] + q[R - j]) + n2, az);
-    }
-    float acc = __fmul_rn(ax, p.ih2[0]);
-    acc = fmaf(ay, p.ih2[1], acc);
-    acc = fmaf(az, p.ih2[2], acc);
-    if (VD && !ADJ) {
-      float dx = 0.f, dy = 0.f, dz = 0.f;
+        for (int j = 1; j <= R; ++j) {
+          ax = fmaf(w2c<R>(j), (cp[r0 * G::BXW + c0 + j] + cp[r0 * G::BXW + c0 - j]) + n2, ax);
+          ay = fmaf(w2c<R>(j), (cp[(r0 + j) * G::BXW + c0] + cp[(r0 - j) * G::BXW + c0]) + n2, ay);
+          az = fmaf(w2c<R>(j), (q[s + R + j] + q[s + R - j]) + n2, az);
+        }
+        float acc = __fmul_rn(ax, p.ih2[0]);
+        acc = fmaf(ay, p.ih2[1], acc);
+        acc = fmaf(az, p.ih2[2], acc);
+        if (VD && !ADJ) {
+          float dx = 0.f, dy = 0.f, dz = 0.f;
 #pragma unroll
-      for (int j = 1; j <= R; ++j) {
-        dx = fmaf(w1c<R>(j), cp[r0 * G::BXW + c0 + j] + (-cp[r0 * G::BXW + c0 - j]), dx);
-        dy = fmaf(w1c<R>(j), cp[(r0 + j) * G::BXW + c0] + (-cp[(r0 - j) * G::BXW + c0]), dy);
-        dz = fmaf(w1c<R>(j), q[R + j] + (-q[R - j]), dz);
-      }
-      float t = __fmul_rn(bxv, __fmul_rn(dx, p.ih1[0]));
-      t = fmaf(byv, __fmul_rn(dy, p.ih1[1]), t);
-      t = fmaf(bzv, __fmul_rn(dz, p.ih1[2]), t);
-      acc = acc + (-t);
-    }
-    if (PSI) {
-      float sx = 0.f, sy = 0.f, sz = 0.f;
+          for (int j = 1; j <= R; ++j) {
+            dx = fmaf(w1c<R>(j), cp[r0 * G::BXW + c0 + j] + (-cp[r0 * G::BXW + c0 - j]), dx);
+            dy = fmaf(w1c<R>(j), cp[(r0 + j) * G::BXW + c0] + (-cp[(r0 - j) * G::BXW + c0]), dy);
+            dz = fmaf(w1c<R>(j), q[s + R + j] + (-q[s + R - j]), dz);
+          }
+          float t = __fmul_rn(bxv, __fmul_rn(dx, p.ih1[0]));
+          t = fmaf(byv, __fmul_rn(dy, p.ih1[1]), t);
+          t = fmaf(bzv, __fmul_rn(dz, p.ih1[2]), t);
+          acc = acc + (-t);
+        }
+        if (PSI) {
+          float sx = 0.f, sy = 0.f, sz = 0.f;
 #pragma unroll
-      for (int j = 1; j <= R; ++j) {
-        const int xp = r0 * G::BXW + c0 + j, xm = r0 * G::BXW + c0 - j;
-        const int yp = (r0 + j) * G::BXW + c0, ym = (r0 - j) * G::BXW + c0;
-        sx = fmaf(w1c<R>(j), __fmul_rn(bxp[xp], cp[xp]) + (-__fmul_rn(bxp[xm], cp[xm])), sx);
-        sy = fmaf(w1c<R>(j), __fmul_rn(byp[yp], cp[yp]) + (-__fmul_rn(byp[ym], cp[ym])), sy);
-        sz = fmaf(w1c<R>(j), qz[R + j] + (-qz[R - j]), sz);
-      }
-      acc = fmaf(sx, p.ih1[0], acc);
-      acc = fmaf(sy, p.ih1[1], acc);
-      acc = fmaf(sz, p.ih1[2], acc);
-    }
-    if (has_inj) {
-      const int lz = z - z0;
-      const int me = (lz * TY + ty) * TX + tx;
-      const int pe1 = s_pe[lz + 1];
-      for (int e = s_pe[lz]; e < pe1; ++e)
-        if (__ldg(p.inj_loc + e) == me) acc = fmaf(p.inj_w[e], p.vals[p.inj_vidx[e] + p.step_off], acc);
-    }
-    const float a = axy + p.spz[z];
-    // explicit rounding order (no contraction left to the compiler), shared
-    // with the two-point kernels of kernels3d_x2.cu
-    const float h = __fmul_rn(kk, acc);
-    float t = fmaf(-(1.f - a), uo, 2.f * cen);
-    t = __fadd_rn(t, h);
-    const float r = __fmul_rn(t, __frcp_rn(1.f + a));
-    if (in_xy) {
-      p.up[fo + idx] = r;
-      if (!ADJ) {
-        if (p.hist) __stcs(p.hist + fo + idx, h);
-      } else if (p.image) {
-        float* gp = p.g + fo + idx;
-        *gp = fmaf(-cen, hv, *gp);
+          for (int j = 1; j <= R; ++j) {
+            const int xp = r0 * G::BXW + c0 + j, xm = r0 * G::BXW + c0 - j;
+            const int yp = (r0 + j) * G::BXW + c0, ym = (r0 - j) * G::BXW + c0;
+            sx = fmaf(w1c<R>(j), __fmul_rn(bxp[xp], cp[xp]) + (-__fmul_rn(bxp[xm], cp[xm])), sx);
+            sy = fmaf(w1c<R>(j), __fmul_rn(byp[yp], cp[yp]) + (-__fmul_rn(byp[ym], cp[ym])), sy);
+            sz = fmaf(w1c<R>(j), qz[s + R + j] + (-qz[s + R - j]), sz);
+          }
+          acc = fmaf(sx, p.ih1[0], acc);
+          acc = fmaf(sy, p.ih1[1], acc);
+          acc = fmaf(sz, p.ih1[2], acc);
+        }
+        if (has_inj) {
+          const int lz = z - z0;
+          const int me = (lz * TY + ty) * TX + tx;
+          const int pe1 = s_pe[lz + 1];
+          for (int e = s_pe[lz]; e < pe1; ++e)
+            if (__ldg(p.inj_loc + e) == me)
+              acc = fmaf(p.inj_w[e], p.vals[p.inj_vidx[e] + p.step_off], acc);
+        }
+        const float a = axy + p.spz[z];
+        // explicit rounding order (no contraction left to the compiler), shared
+        // with the two-point kernels of kernels3d_x2.cu
+        const float h = __fmul_rn(kk, acc);
+        float t = fmaf(-(1.f - a), uo, 2.f * cen);
+        t = __fadd_rn(t, h);
+        const float r = __fmul_rn(t, __frcp_rn(1.f + a));
+        if (in_xy) {
+          p.up[fo + idx] = r;
+          if (!ADJ) {
+            if (p.hist) __stcs(p.hist + fo + idx, h);
+          } else if (p.image) {
+            p.g[fo + idx] = fmaf(-cen, hv, cur.gv);
+          }
+        }
+        __syncthreads();   // every thread is done with the centre plane and this b stage
+        if (tid == 0) {
+          const int nxp = i + R + NSU;   // the centre plane's buffer takes plane nxp
+          if (nxp < nplanes) {
+            const int k = nxp % NSU;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bar[k], G::PLANE_BYTES);
+            tma_load_4d(ring + k * G::PLANE, &umap, &bar[k], tmx, tmy, pz0 + nxp, b);
+          }
+          if (PSI && i + 2 < nz_c) {
+            const int st = i & 1;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bbar[st], 2 * G::PLANE_BYTES);
+            tma_load_4d(bring + (2 * st) * G::PLANE, &bxmap, &bbar[st], tmx, tmy, z + 2 + p.oz, 0);
+            tma_load_4d(bring + (2 * st + 1) * G::PLANE, &bymap, &bbar[st], tmx, tmy,
+                        z + 2 + p.oz, 0);
+          }
+        }
       }
     }
 #pragma unroll
     for (int j = 0; j < Q - 1; ++j) {
-      q[j] = q[j + 1];
-      if (PSI) qz[j] = qz[j + 1];
-    }
-    __syncthreads();   // every thread is done with the centre plane and this b stage
-    if (tid == 0) {
-      const int nxt = i + R + NSU;   // the centre plane's buffer takes plane nxt
-      if (nxt < nplanes) {
-        const int k = nxt % NSU;
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&bar[k], G::PLANE_BYTES);
-        tma_load_4d(ring + k * G::PLANE, &umap, &bar[k], tmx, tmy, pz0 + nxt, b);
-      }
-      if (PSI && i + 2 < nz_c) {
-        const int st = i & 1;
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&bbar[st], 2 * G::PLANE_BYTES);
-        tma_load_4d(bring + (2 * st) * G::PLANE, &bxmap, &bbar[st], tmx, tmy, z + 2 + p.oz, 0);
-        tma_load_4d(bring + (2 * st + 1) * G::PLANE, &bymap, &bbar[st], tmx, tmy, z + 2 + p.oz, 0);
-      }
+      q[j] = q[j + U];
+      if (PSI) qz[j] = qz[j + U];
     }
   }
   if (timed_out && p.flags) atomicOr(p.flags, 2);

@@ -10,8 +10,8 @@
 //    a 64 x BY column; every shared-memory read is an 8-byte pair and the
 //    arithmetic runs on packed FP32x2 instructions (two lanes, each rounded
 //    as the scalar operation);
-//  * the z loop is unrolled by the queue length 2R+1, so the register queue
-//    of the column rotates by renaming and costs no moves;
+//  * the z loop advances two planes per trip, so the register queue of the
+//    column shifts once per two planes;
 //  * the x-y planes (80 floats wide: x0-8 .. x0+71, 16-byte aligned) arrive by
 //    4D TMA copies into a ring of R+1+PF planes (the centre, the R planes up
 //    to the lead, PF planes in flight); the variable-density adjoint streams
@@ -145,10 +145,11 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
   const int c0 = G::XOFF + 2 * tx;          // own pair's column in a staged row (even)
   const int own = (ty + R) * BXW + c0;
   bool timed_out = false;
-  // register queue: plane z - R + j of iteration i (z = z0 + i) sits in
-  // q[(i + j) % Q]; with the loop unrolled by Q the slots are constants.
-  float2 q[Q];
-  float2 qz[PSI ? Q : 1];
+  // register queues, U planes per loop trip: q[j] = u at plane z0 + i0 - R + j
+  // of this column (i0 = first plane of the trip); shifted by U after a trip
+  constexpr int U = 2;
+  float2 q[Q + U - 1];
+  float2 qz[PSI ? Q + U - 1 : 1];
   // planes 0 .. R-1 (halo only)
 #pragma unroll
   for (int lp = 0; lp < R; ++lp) {
@@ -185,16 +186,19 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
   const int loc0 = ty * G::TXP + 2 * tx;    // entry location of the own pair in plane lz = 0
 
   struct Ops {
-    float2 uo, kk, hv, bx, by, bz, bzl;
+    float2 uo, kk, hv, gv, bx, by, bz, bzl;
   };
   auto ldg2 = [](const float* a) { return __ldg(reinterpret_cast<const float2*>(a)); };
   auto load_ops = [&](int ii) {
     const float2 z2 = make_float2(0.f, 0.f);
-    Ops o{z2, z2, z2, z2, z2, z2, z2};
+    Ops o{z2, z2, z2, z2, z2, z2, z2, z2};
     const long long id = (long long)(z0 + ii + p.oz) * p.sxy + col;
     o.uo = *reinterpret_cast<const float2*>(p.up + fo + id);
     o.kk = ldg2(p.kf + id);
-    if (ADJ && p.image) o.hv = __ldcs(reinterpret_cast<const float2*>(p.hist + fo + id));
+    if (ADJ && p.image) {
+      o.hv = __ldcs(reinterpret_cast<const float2*>(p.hist + fo + id));
+      o.gv = *reinterpret_cast<const float2*>(p.g + fo + id);
+    }
     if (VD && !ADJ) {
       o.bx = ldg2(p.bx + id);
       o.by = ldg2(p.by + id);
@@ -205,10 +209,10 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
   };
   Ops nxt = load_ops(0);
 
-  for (int ib = 0; ib < nz_c; ib += Q) {
+  for (int i0 = 0; i0 < nz_c; i0 += U) {
 #pragma unroll
-    for (int s = 0; s < Q; ++s) {
-      const int i = ib + s;
+    for (int s = 0; s < U; ++s) {
+      const int i = i0 + s;
       if (i < nz_c) {
         const int z = z0 + i;
         const long long idx = (long long)(z + p.oz) * p.sxy + col;
@@ -218,8 +222,8 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
         const int lead = i + 2 * R;
         const int sl = lead % NSU;
         if (!mbar_wait_bounded(&bar[sl], (uint32_t)((lead / NSU) & 1))) timed_out = true;
-        q[(s + 2 * R) % Q] = lds2(ring + sl * G::PLANE + own);
-        if (PSI) qz[(s + 2 * R) % Q] = __fmul2_rn(cur.bzl, q[(s + 2 * R) % Q]);
+        q[s + 2 * R] = lds2(ring + sl * G::PLANE + own);
+        if (PSI) qz[s + 2 * R] = __fmul2_rn(cur.bzl, q[s + 2 * R]);
         const float* cp = ring + ((i + R) % NSU) * G::PLANE;   // centre plane z
         const float* bxp = bring + (2 * (i & 1)) * G::PLANE;
         const float* byp = bxp + G::PLANE;
@@ -242,7 +246,7 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
 
         // zero-sum second derivatives per axis, sum_j w_j (u_{+j} + u_{-j} - 2 u_0),
         // with the unscaled weights as immediates; 1/h^2 applied per axis
-        const float2 cen = q[(s + R) % Q];
+        const float2 cen = q[s + R];
         const float2 n2 = make_float2(-(cen.x + cen.x), -(cen.y + cen.y));
         const float2 z2 = make_float2(0.f, 0.f);
         float2 ax = z2, ay = z2, az = z2;
@@ -253,7 +257,7 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
           ax = __ffma2_rn(bc2(w2c<R>(j)), __fadd2_rn(__fadd2_rn(xp, xm), n2), ax);
           ay = __ffma2_rn(bc2(w2c<R>(j)), __fadd2_rn(__fadd2_rn(Yp[j], Ym[j]), n2), ay);
           az = __ffma2_rn(bc2(w2c<R>(j)),
-                          __fadd2_rn(__fadd2_rn(q[(s + R + j) % Q], q[(s + R - j) % Q]), n2), az);
+                          __fadd2_rn(__fadd2_rn(q[s + R + j], q[s + R - j]), n2), az);
         }
         float2 acc = __fmul2_rn(ax, bc2(p.ih2[0]));
         acc = __ffma2_rn(ay, bc2(p.ih2[1]), acc);
@@ -267,7 +271,7 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
             dx = __ffma2_rn(bc2(w1c<R>(j)), __fadd2_rn(xp, neg2(xm)), dx);
             dy = __ffma2_rn(bc2(w1c<R>(j)), __fadd2_rn(Yp[j], neg2(Ym[j])), dy);
             dz = __ffma2_rn(bc2(w1c<R>(j)),
-                            __fadd2_rn(q[(s + R + j) % Q], neg2(q[(s + R - j) % Q])), dz);
+                            __fadd2_rn(q[s + R + j], neg2(q[s + R - j])), dz);
           }
           float2 t = __fmul2_rn(cur.bx, __fmul2_rn(dx, bc2(p.ih1[0])));
           t = __ffma2_rn(cur.by, __fmul2_rn(dy, bc2(p.ih1[1])), t);
@@ -294,7 +298,7 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
             const float2 ya = __fmul2_rn(lds2(byp + (ty + R - j) * BXW + c0), Ym[j]);
             sy = __ffma2_rn(bc2(w1c<R>(j)), __fadd2_rn(yb, neg2(ya)), sy);
             sz = __ffma2_rn(bc2(w1c<R>(j)),
-                            __fadd2_rn(qz[(s + R + j) % Q], neg2(qz[(s + R - j) % Q])), sz);
+                            __fadd2_rn(qz[s + R + j], neg2(qz[s + R - j])), sz);
           }
           acc = __ffma2_rn(sx, bc2(p.ih1[0]), acc);
           acc = __ffma2_rn(sy, bc2(p.ih1[1]), acc);
@@ -323,16 +327,14 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
           if (!ADJ) {
             if (p.hist) __stcs(reinterpret_cast<float2*>(p.hist + fo + idx), h);
           } else if (p.image) {
-            float2* gp = reinterpret_cast<float2*>(p.g + fo + idx);
-            *gp = __ffma2_rn(neg2(cen), cur.hv, *gp);
+            *reinterpret_cast<float2*>(p.g + fo + idx) = __ffma2_rn(neg2(cen), cur.hv, cur.gv);
           }
         } else if (in0) {
           p.up[fo + idx] = r.x;
           if (!ADJ) {
             if (p.hist) __stcs(p.hist + fo + idx, h.x);
           } else if (p.image) {
-            float* gp = p.g + fo + idx;
-            *gp = fmaf(-cen.x, cur.hv.x, *gp);
+            p.g[fo + idx] = fmaf(-cen.x, cur.hv.x, cur.gv.x);
           }
         }
         __syncthreads();   // every thread is done with the centre plane and this b stage
@@ -354,6 +356,11 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
           }
         }
       }
+    }
+#pragma unroll
+    for (int j = 0; j < Q - 1; ++j) {
+      q[j] = q[j + U];
+      if (PSI) qz[j] = qz[j + U];
     }
   }
   if (timed_out && p.flags) atomicOr(p.flags, 2);
