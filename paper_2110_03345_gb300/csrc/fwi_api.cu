@@ -486,7 +486,7 @@ bool resolve_tile(const fwi_plan* P, int t, int* id, int* shape, bool* tma, bool
     *tma = t > NUM_TILE2;
     *shape = (t - 1) % NUM_TILE2;
   } else {
-    if (t == 0) t = 8;   // TMA-staged plane ring, 32 x 8 columns, 32-plane chunks
+    if (t == 0) t = 12;  // TMA-staged plane ring, two points per thread, 64 x 8 columns, 32-plane chunks
     if (t < 1 || t > 3 * NUM_TILE3) return false;
     *tma = t > NUM_TILE3;
     if (x2) *x2 = t > 2 * NUM_TILE3;

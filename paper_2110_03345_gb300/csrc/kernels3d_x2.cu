@@ -50,7 +50,7 @@ struct GeoX2 {
 };
 
 template <int R, bool VD, bool ADJ, int BY>
-__global__ void __launch_bounds__(32 * BY, 512 / (32 * BY))
+__global__ void __launch_bounds__(32 * BY, ((VD && ADJ) ? 512 : 768) / (32 * BY))
 k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
             const __grid_constant__ CUtensorMap bxmap, const __grid_constant__ CUtensorMap bymap) {
   using G = GeoX2<R, BY>;
