@@ -83,6 +83,13 @@ def make_problem(args):
     return p
 
 
+def kernel_name(ndim, tile):
+    """Stencil kernel of a resolved tile variant."""
+    if ndim == 2:
+        return "k_step2d" if tile <= 4 else "k_step2d_tma"
+    return "k_step3d" if tile <= 4 else ("k_step3d_tma" if tile <= 8 else "k_step3d_x2")
+
+
 def useful_updates(p) -> int:
     """2 propagations x grid points x leapfrog steps x shots."""
     return 2 * p.npoints * (p.nt - 1) * p.nshots
@@ -446,8 +453,8 @@ def run_mine(args):
     tr = traffic_record(f"{p.ndim}d-{kind}", stats["tile"])
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": (tr["dram_bytes_per_point"] * pts_launch) if tr else None,
-            "kernel": ("k_step%dd_tma %s" % (p.ndim, "adjoint+imaging" if kind == "adj"
-                                             else "forward+store")),
+            "kernel": ("%s %s" % (kernel_name(p.ndim, stats["tile"]),
+                                  "adjoint+imaging" if kind == "adj" else "forward+store")),
             "bytes_per_update": bpu, "points_per_launch": int(pts_launch),
             "launch_ms": t_launch * 1e3, "peak_source": peak_src,
             "share_of_step": acc[f"{kind}_ms"] / args.steps / ms}
