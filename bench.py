@@ -311,6 +311,64 @@ def uneven_batch(nprob=64, seed=4, reps=2, **kw):
             "speedup": one_shot["s"] / tb, "speedup_vs_per_problem": per_problem["s"] / tb}
 
 
+def uneven_gradient(nprob=64, seed=4, lanes=4, **kw):
+    """Gradient variant of the uneven set: every problem's gradient (misfit
+    against zero data), (a) submitted at once to the serving loop, which runs
+    them concurrently on `lanes` streams within the HBM budget, one plan per
+    problem with all its shots per launch; (b) one plan per problem, problems
+    one after another; (c) the plain solver with one shot per launch."""
+    import torch
+    from paper_2110_03345_gb300 import binding, inputs, serve
+    ps = inputs.config_uneven_batch(nprob=nprob, seed=seed, **kw)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev)
+    reqs = [dict(shape=p.shape, spacing=p.spacing, nt=p.nt, dt=p.dt, vp=f32(p.vp), rho=f32(p.rho),
+                 geometry=binding.Geometry(p.src_xyz, p.rec_xyz), wavelet=f32(p.wavelet),
+                 observed=torch.zeros((p.nshots, p.rec_xyz.shape[0], p.nt), device=dev),
+                 order=p.order, sponge=p.nb, c_ref=p.c_ref) for p in ps]
+    shots = sum(p.nshots for p in ps)
+    updates = sum(2 * p.nshots * p.npoints * (p.nt - 1) for p in ps)
+    budget = int(0.7 * binding.mem_available())
+
+    def served():
+        server = serve.Server(budget_bytes=budget, lanes=lanes)
+        objs = [serve.Request(**r) for r in reqs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        futs = [server.submit(o) for o in objs]
+        for f in futs:
+            f.result()
+        server.drain()
+        t = time.perf_counter() - t0
+        server.close()
+        return t
+
+    def sequential(per_launch):
+        stream = torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for r in reqs:
+            pl = binding.Plan(r["shape"], r["spacing"], r["nt"], r["dt"], order=r["order"],
+                              sponge=r["sponge"], c_ref=r["c_ref"], stream=stream,
+                              budget=budget)
+            pl.set_options(batch=per_launch)
+            pl.gradient(r["vp"], r["rho"], r["geometry"], r["wavelet"], r["observed"])
+            pl.close()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    served()   # warm-up (allocator pool, kernel attributes)
+    out = {}
+    for name, fn in (("served", served), ("per_problem", lambda: sequential(0)),
+                     ("plain", lambda: sequential(1))):
+        t = fn()
+        out[name] = {"shots_per_s": shots / t, "gpts": updates / t / 1e9, "s": t}
+    out.update({"problems": nprob, "shots": shots, "updates": updates, "lanes": lanes,
+                "speedup": out["plain"]["s"] / out["served"]["s"],
+                "speedup_vs_per_problem": out["per_problem"]["s"] / out["served"]["s"]})
+    return out
+
+
 def serving_stream(nreq=650, warm=50, seed=5, lanes=4, rate=20.0, **kw):
     """Poisson request stream through the serving loop (continuous admission
     onto `lanes` concurrent streams under an HBM budget) and through the plain
@@ -525,10 +583,11 @@ def run_extra_workload(args):
     torch.cuda.set_device(0)
     if args.workload == "uneven":
         r = uneven_batch(nprob=args.nprob or 64)
+        rg = uneven_gradient(nprob=args.nprob or 64)
         line = {"metric": "shots/s (uneven batch, one CUDA graph vs one plan per problem)",
                 "value": r["batched"]["shots_per_s"], "unit": "shots/s", "n_gpus": 1,
                 "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOADS["uneven"]}, "uneven": r}
+                "config": {"workload": WORKLOADS["uneven"]}, "uneven": r, "uneven_gradient": rg}
     else:
         r = serving_stream(nreq=args.nreq or 650)
         line = {"metric": "p99 latency (s) and shots/s, continuous admission vs plain",

@@ -61,10 +61,7 @@ struct Geo {
 // the tensor map of the wavefield buffer p.u (param or global memory);
 // samp_rank is the CTA's rank among its problem's CTAs, gx the problem's tile
 // count along x.
-// ESEARCH: find each thread's source entries by binary search before the
-// stencil (single-problem kernels); otherwise every row scans the tile's
-// entries (the multi-problem kernel, which has fewer registers to spare).
-template <int R, bool VD, bool ADJ, int RY, int BY, bool ESEARCH = true>
+template <int R, bool VD, bool ADJ, int RY, int BY>
 __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW& wx,
                                                 const AxisW& wy, const CUtensorMap* tmap,
                                                 int bxi, int byi, int gx, int grp,
@@ -172,32 +169,10 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
     // A wait that times out flags the error and carries on (no early exit, so
     // no thread can miss a later barrier); the host reports FWI_ERR_TIMEOUT.
     if (!mbar_wait_bounded(&bar[buf], (uint32_t)((k >> 1) & 1)) && p.flags) atomicOr(p.flags, 2);
-    // source entries of this shot's tile are sorted by tile-local index
-    // (ly * TX + lx): per row, a binary search finds the first entry of this
-    // thread's four points and the entries that follow in its range
-    int ebeg[RY], ecnt[RY];
-#pragma unroll
-    for (int iy = 0; iy < RY; ++iy) ecnt[iy] = 0;
     int e0 = 0, e1 = 0;
     if (p.inj_off) {
       e0 = p.inj_off[s * p.ntiles + tile_id];
       e1 = p.inj_off[s * p.ntiles + tile_id + 1];
-      if (ESEARCH && e1 > e0) {
-#pragma unroll
-        for (int iy = 0; iy < RY; ++iy) {
-          const int loc0 = (ty * RY + iy) * TX + 4 * tx;
-          int lo = e0, hi = e1;
-          while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (__ldg(p.inj_loc + mid) < loc0) lo = mid + 1;
-            else hi = mid;
-          }
-          int n = 0;
-          while (lo + n < e1 && __ldg(p.inj_loc + lo + n) < loc0 + 4) ++n;
-          ebeg[iy] = lo;
-          ecnt[iy] = n;
-        }
-      }
     }
 
 #pragma unroll
@@ -285,15 +260,7 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
         }
         acc[0] = A0.x; acc[1] = A0.y; acc[2] = A1.x; acc[3] = A1.y;
       }
-      if (ESEARCH) {
-        for (int k = 0; k < ecnt[iy]; ++k) {
-          const int e = ebeg[iy] + k;
-          const int ix = __ldg(p.inj_loc + e) - (ly * TX + 4 * tx);
-          const float val = p.inj_w[e] * p.vals[p.inj_vidx[e] + p.step_off];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) acc[q] += (q == ix) ? val : 0.f;
-        }
-      } else if (e1 > e0) {
+      if (e1 > e0) {
         for (int e = e0; e < e1; ++e) {
           const int loc = p.inj_loc[e];
           const int ely = loc / TX, elx = loc - ely * TX;
@@ -394,8 +361,8 @@ k_step2d_tma_multi(const MultiDesc* __restrict__ descs, const MultiUnit* __restr
   }
   __syncthreads();
   const CUtensorMap* map = (n & 1) ? &d->map1 : &d->map0;
-  step2d_tma_tile<R, VD, false, RY, BY, false>(sp, UW ? wx : sp.wx, UW ? wy : sp.wy, map, un.tx,
-                                               un.ty, d->gx, un.slot, un.rank, smem, bar);
+  step2d_tma_tile<R, VD, false, RY, BY>(sp, UW ? wx : sp.wx, UW ? wy : sp.wy, map, un.tx, un.ty,
+                                        d->gx, un.slot, un.rank, smem, bar);
 }
 
 template <int R, bool VD, bool ADJ, int RY, int BY>
