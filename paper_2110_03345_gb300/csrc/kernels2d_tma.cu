@@ -83,21 +83,8 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
   const int ns = min(p.S, p.B - s0);
   const int tile_id = byi * gx + bxi;
 
-  if (!ADJ && p.nrec > 0) {
-    // receiver sampling of u^n (not written during this step), one thread per slot x receiver
-    const long long gid = samp_rank * NT + tid;
-    if (gid < (long long)p.B * p.nrec) {
-      const int bb = (int)(gid / p.nrec);
-      const int r = (int)(gid - (long long)bb * p.nrec);
-      const float* ub = p.u + (long long)bb * p.fstride;
-      float acc = 0.f;
-      for (int c = 0; c < p.ncorner; ++c)
-        acc = fmaf(p.smp_w[r * p.ncorner + c], ub[p.smp_node[r * p.ncorner + c]], acc);
-      p.smp_out[p.smp_off + (long long)bb * p.nrec + r] = acc;
-    }
-  }
-  if (ns <= 0) return;
-
+  // Model-only set-up first (barriers, sponge, k, the b_x / b_y tiles): in a
+  // programmatic dependent launch it overlaps the previous step's tail.
   const int tmx = x0 + p.ox - G::XH;   // multiple of 4 floats: 16-byte aligned box start
   const int tmy = y0 + p.oy - R;
   if (tid == 0) {
@@ -105,16 +92,6 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
     mbar_init(&bar[1], 1);
     fence_mbar_init();
   }
-  __syncthreads();
-  if (tid == 0) {
-    mbar_arrive_expect_tx(&bar[0], G::TILE_BYTES);
-    tma_load_3d(s_t0, tmap, &bar[0], tmx, tmy, s0);
-    if (ns > 1) {
-      mbar_arrive_expect_tx(&bar[1], G::TILE_BYTES);
-      tma_load_3d(s_t1, tmap, &bar[1], tmx, tmy, s0 + 1);
-    }
-  }
-
   // Shared model data of the tile, loaded once for the S shots.  Offsets
   // inside one field fit in 32 bits; slot bases are formed once per shot.
   const int xg = x0 + 4 * tx;
@@ -130,7 +107,7 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
     kk[iy] = ldg4(p.kf + pix[iy]);
     ay[iy] = p.spy[yg];
   }
-  if (VD && ADJ) {
+  if (VD && ADJ && ns > 0) {
     for (int i = tid; i < TY * SW; i += NT) {
       const int r = i / SW, c = i - r * SW;
       s_bx[i] = ldg4(p.bx + base + (r + R) * p.sx + 4 * c);
@@ -140,12 +117,36 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
       s_by[i] = ldg4(p.by + base + r * p.sx + 4 * (c + NL));
     }
   }
+  pdl_wait();   // the previous step's wavefields are complete from here on
+
+  if (!ADJ && p.nrec > 0) {
+    // receiver sampling of u^n (not written during this step), one thread per slot x receiver
+    const long long gid = samp_rank * NT + tid;
+    if (gid < (long long)p.B * p.nrec) {
+      const int bb = (int)(gid / p.nrec);
+      const int r = (int)(gid - (long long)bb * p.nrec);
+      const float* ub = p.u + (long long)bb * p.fstride;
+      float acc = 0.f;
+      for (int c = 0; c < p.ncorner; ++c)
+        acc = fmaf(p.smp_w[r * p.ncorner + c], ub[p.smp_node[r * p.ncorner + c]], acc);
+      p.smp_out[p.smp_off + (long long)bb * p.nrec + r] = acc;
+    }
+  }
+  if (ns <= 0) return;
+  __syncthreads();   // barrier initialisation and the b_x / b_y tiles are visible
+  if (tid == 0) {
+    mbar_arrive_expect_tx(&bar[0], G::TILE_BYTES);
+    tma_load_3d(s_t0, tmap, &bar[0], tmx, tmy, s0);
+    if (ns > 1) {
+      mbar_arrive_expect_tx(&bar[1], G::TILE_BYTES);
+      tma_load_3d(s_t1, tmap, &bar[1], tmx, tmy, s0 + 1);
+    }
+  }
   float gs[RY][4];
 #pragma unroll
   for (int iy = 0; iy < RY; ++iy)
 #pragma unroll
     for (int q = 0; q < 4; ++q) gs[iy][q] = 0.f;
-  __syncthreads();   // the b_x / b_y tiles above are read by other threads
 
   for (int k = 0; k < ns; ++k) {
     const int s = s0 + k;
@@ -323,6 +324,7 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
 template <int R, bool VD, bool ADJ, int RY, int BY>
 __global__ void __launch_bounds__(32 * BY, (RY == 1 ? 1024 : 512) / (32 * BY))
 k_step2d_tma(const StepParams p, const __grid_constant__ CUtensorMap tmap) {
+  pdl_trigger();
   extern __shared__ __align__(128) float4 smem[];
   __shared__ uint64_t bar[2];
   const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
@@ -341,6 +343,7 @@ template <int R, bool VD, int RY, int BY, bool UW>
 __global__ void __launch_bounds__(32 * BY, (RY == 1 ? 1024 : 512) / (32 * BY))
 k_step2d_tma_multi(const MultiDesc* __restrict__ descs, const MultiUnit* __restrict__ units, int n,
                    const AxisW wx, const AxisW wy) {
+  pdl_trigger();
   extern __shared__ __align__(128) float4 smem[];
   __shared__ uint64_t bar[2];
   __shared__ StepParams sp;
@@ -390,8 +393,7 @@ cudaError_t launch_t(const StepParams& p, const CUtensorMap& map, cudaStream_t s
   }
   dim3 grid((p.nx + TILE_X - 1) / TILE_X, (p.ny + TY - 1) / TY, (p.B + p.S - 1) / p.S);
   dim3 block(32, BY);
-  k_step2d_tma<R, VD, ADJ, RY, BY><<<grid, block, smem, st>>>(p, map);
-  return cudaGetLastError();
+  return launch_pdl(k_step2d_tma<R, VD, ADJ, RY, BY>, grid, block, smem, st, p, map);
 }
 
 template <int R, bool VD, bool ADJ>
@@ -421,9 +423,8 @@ cudaError_t launch_multi_u(const MultiDesc* descs, const MultiUnit* units, int n
   }
   if (nunits <= 0) return cudaSuccess;
   const AxisW zero{};
-  k_step2d_tma_multi<R, VD, RY, BY, UW><<<nunits, dim3(32, BY), smem, st>>>(
-      descs, units, n, w ? w[0] : zero, w ? w[1] : zero);
-  return cudaGetLastError();
+  return launch_pdl(k_step2d_tma_multi<R, VD, RY, BY, UW>, dim3(nunits), dim3(32, BY), smem, st,
+                    descs, units, n, w ? w[0] : zero, w ? w[1] : zero);
 }
 
 template <int R, bool VD, int RY, int BY>

@@ -53,6 +53,7 @@ template <int R, bool VD, bool ADJ, int BY>
 __global__ void __launch_bounds__(32 * BY, ((VD && ADJ) ? 512 : 768) / (32 * BY))
 k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
             const __grid_constant__ CUtensorMap bxmap, const __grid_constant__ CUtensorMap bymap) {
+  pdl_trigger();
   using G = GeoX2<R, BY>;
   constexpr int TY = BY;
   constexpr int NT = 32 * BY;
@@ -81,21 +82,6 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
   const int xg = x0 + 2 * tx, yg = y0 + ty;
   const long long col = (long long)(yg + p.oy) * p.sx + (xg + p.ox);   // even: 8-byte pairs
 
-  if (!ADJ && p.nrec > 0) {
-    // receiver sampling of u^n (not written during this step), one thread per slot x receiver
-    const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    const long long gid = blk * NT + tid;
-    if (gid < (long long)p.B * p.nrec) {
-      const int bb = (int)(gid / p.nrec);
-      const int r = (int)(gid - (long long)bb * p.nrec);
-      const float* ub = p.u + (long long)bb * p.fstride;
-      float acc = 0.f;
-      for (int c = 0; c < p.ncorner; ++c)
-        acc = fmaf(p.smp_w[r * p.ncorner + c], ub[p.smp_node[r * p.ncorner + c]], acc);
-      p.smp_out[p.smp_off + (long long)bb * p.nrec + r] = acc;
-    }
-  }
-  if (nz_c <= 0) return;
 
   const int tmx = x0 + p.ox - G::XOFF;      // 16-byte aligned box start
   const int tmy = y0 + p.oy - R;
@@ -127,6 +113,22 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
       }
     }
   }
+  pdl_wait();   // the previous step's wavefields are complete from here on
+  if (!ADJ && p.nrec > 0) {
+    // receiver sampling of u^n (not written during this step), one thread per slot x receiver
+    const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const long long gid = blk * NT + tid;
+    if (gid < (long long)p.B * p.nrec) {
+      const int bb = (int)(gid / p.nrec);
+      const int r = (int)(gid - (long long)bb * p.nrec);
+      const float* ub = p.u + (long long)bb * p.fstride;
+      float acc = 0.f;
+      for (int c = 0; c < p.ncorner; ++c)
+        acc = fmaf(p.smp_w[r * p.ncorner + c], ub[p.smp_node[r * p.ncorner + c]], acc);
+      p.smp_out[p.smp_off + (long long)bb * p.nrec + r] = acc;
+    }
+  }
+  if (nz_c <= 0) return;
   __syncthreads();
   if (tid == 0) {
     for (int lp = 0; lp < NSU && lp < nplanes; ++lp) {
@@ -390,8 +392,7 @@ cudaError_t launch_t(const StepParams& p, const CUtensorMap& um, const CUtensorM
     attr_set = true;
   }
   dim3 grid((p.nx + 63) / 64, (p.ny + BY - 1) / BY, p.B * p.nzc);
-  k_step3d_x2<R, VD, ADJ, BY><<<grid, dim3(32, BY), smem, st>>>(p, um, bxm, bym);
-  return cudaGetLastError();
+  return launch_pdl(k_step3d_x2<R, VD, ADJ, BY>, grid, dim3(32, BY), smem, st, p, um, bxm, bym);
 }
 
 template <int R, bool VD, bool ADJ>
