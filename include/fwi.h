@@ -98,7 +98,9 @@ typedef struct {
                            9-12 TMA plane ring with two x points per thread (64);
                            the TMA families give bit-identical results */
     int profile;        /* 1: time every stencil launch with CUDA events */
-    int use_graphs;     /* 1: capture the time loop into CUDA graphs */
+    int use_graphs;     /* reserved, must be 0 (consecutive steps overlap through
+                           programmatic dependent launch; whole runs of uneven
+                           problems are graphs in fwi_batch_*) */
     int shots_per_cta;  /* 2D TMA variants: shots per CTA (0: chosen from the SM count; 3D: 1) */
 } fwi_options;
 
@@ -126,7 +128,9 @@ typedef struct {
 fwi_status fwi_plan_create(fwi_plan** plan, const fwi_grid* grid, int nt, double dt,
                            size_t hbm_budget_bytes, void* stream);
 
-/* Set execution options (see fwi_options).  Takes effect on the next call. */
+/* Set execution options (see fwi_options).  Takes effect on the next call.
+ * Errors: FWI_ERR_INVALID_ARG (NULL, negative batch), FWI_ERR_UNSUPPORTED
+ * (use_graphs != 0); a tile variant out of range is reported by the next call. */
 fwi_status fwi_plan_set_options(fwi_plan* plan, const fwi_options* opt);
 
 /* Counters of the last call. */

@@ -266,14 +266,13 @@ class Plan:
 
     __del__ = close
 
-    def set_options(self, batch=0, ckpt_every=0, tile=0, profile=False, use_graphs=False,
-                    shots_per_cta=0):
+    def set_options(self, batch=0, ckpt_every=0, tile=0, profile=False, shots_per_cta=0):
         """tile: 0 default; 2D 1-4 shared-memory staged (one shot per CTA), 5-8
         TMA-staged with shots looped inside a CTA; 3D 1-4 shared-memory staged,
         5-8 TMA plane ring, 9-12 TMA plane ring with two x points per thread.
         shots_per_cta: 2D TMA variants only."""
         self._opts = COptions(int(batch), int(ckpt_every), int(tile), int(bool(profile)),
-                              int(bool(use_graphs)), int(shots_per_cta))
+                              0, int(shots_per_cta))
         _check(load().fwi_plan_set_options(self._h, ctypes.byref(self._opts)))
 
     def stats(self) -> dict:

@@ -1288,6 +1288,7 @@ fwi_status fwi_plan_create(fwi_plan** plan, const fwi_grid* grid, int nt, double
 fwi_status fwi_plan_set_options(fwi_plan* plan, const fwi_options* opt) {
   if (!plan || !opt) return fail(FWI_ERR_INVALID_ARG, "NULL argument");
   if (opt->batch < 0) return fail(FWI_ERR_INVALID_ARG, "batch must be >= 0");
+  if (opt->use_graphs != 0) return fail(FWI_ERR_UNSUPPORTED, "use_graphs is reserved and must be 0");
   plan->opt = *opt;
   return FWI_OK;
 }
