@@ -61,11 +61,7 @@ struct Geo {
 // the tensor map of the wavefield buffer p.u (param or global memory);
 // samp_rank is the CTA's rank among its problem's CTAs, gx the problem's tile
 // count along x.
-// XPACK: x-direction taps as packed FP32x2 operations on point pairs (the
-// single-problem kernels); the multi-problem kernel, with fewer registers to
-// spare, keeps the scalar form (the same values: each lane rounds as the
-// scalar operation).
-template <int R, bool VD, bool ADJ, int RY, int BY, bool XPACK = true>
+template <int R, bool VD, bool ADJ, int RY, int BY>
 __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW& wx,
                                                 const AxisW& wy, const CUtensorMap* tmap,
                                                 int bxi, int byi, int gx, int grp,
@@ -189,53 +185,24 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
 #pragma unroll
       for (int q = 0; q <= 2 * NL; ++q) unpack(s_u[srow * SW + tx + q], v + 4 * q);
 
-      // second derivatives in the zero-sum form sum_j w_j (u_{+j} + u_{-j} - 2 u_0),
-      // x taps as packed FP32x2 operations on the point pairs (0, 1) and (2, 3)
+      // second derivatives in the zero-sum form sum_j w_j (u_{+j} + u_{-j} - 2 u_0)
       // (forward, variable density: the b_x D1x u term is subtracted as soon
-      // as D1x u is known, so the first derivatives are never live at once)
-      constexpr int C0 = 4 * NL;   // window index of point 0
-      auto pr = [&](int a) { return make_float2(v[a], v[a + 1]); };
+      // as D1x u is known, so the four first derivatives are never live at once)
       float acc[4], c2[4];
 #pragma unroll
-      for (int ix = 0; ix < 4; ++ix) c2[ix] = v[C0 + ix] + v[C0 + ix];
-      if constexpr (!XPACK) {
+      for (int ix = 0; ix < 4; ++ix) {
+        const int c = 4 * NL + ix;
+        c2[ix] = v[c] + v[c];
+        float t = 0.f;
 #pragma unroll
-        for (int ix = 0; ix < 4; ++ix) {
-          const int c = C0 + ix;
-          float t = 0.f;
-#pragma unroll
-          for (int j = 1; j <= R; ++j) t = fmaf(wx.w2[j], (v[c + j] + v[c - j]) - c2[ix], t);
-          if (VD && !ADJ) {
-            float d = 0.f;
-#pragma unroll
-            for (int j = 1; j <= R; ++j) d = fmaf(wx.w1[j], v[c + j] - v[c - j], d);
-            t = fmaf(-get(bxf[iy], ix), d, t);
-          }
-          acc[ix] = t;
-        }
-      } else {
-        const float2 n0 = make_float2(-c2[0], -c2[1]), n1 = make_float2(-c2[2], -c2[3]);
-        float2 T0 = make_float2(0.f, 0.f), T1 = T0;
-#pragma unroll
-        for (int j = 1; j <= R; ++j) {
-          const float2 w2 = make_float2(wx.w2[j], wx.w2[j]);
-          T0 = __ffma2_rn(w2, __fadd2_rn(__fadd2_rn(pr(C0 + j), pr(C0 - j)), n0), T0);
-          T1 = __ffma2_rn(w2, __fadd2_rn(__fadd2_rn(pr(C0 + 2 + j), pr(C0 + 2 - j)), n1), T1);
-        }
+        for (int j = 1; j <= R; ++j) t = fmaf(wx.w2[j], (v[c + j] + v[c - j]) - c2[ix], t);
         if (VD && !ADJ) {
-          float2 E0 = make_float2(0.f, 0.f), E1 = E0;
+          float d = 0.f;
 #pragma unroll
-          for (int j = 1; j <= R; ++j) {
-            const float2 w1 = make_float2(wx.w1[j], wx.w1[j]);
-            const float2 m0 = pr(C0 - j), m1 = pr(C0 + 2 - j);
-            E0 = __ffma2_rn(w1, __fadd2_rn(pr(C0 + j), make_float2(-m0.x, -m0.y)), E0);
-            E1 = __ffma2_rn(w1, __fadd2_rn(pr(C0 + 2 + j), make_float2(-m1.x, -m1.y)), E1);
-          }
-          const float4 bxv = bxf[iy];
-          T0 = __ffma2_rn(make_float2(-bxv.x, -bxv.y), E0, T0);
-          T1 = __ffma2_rn(make_float2(-bxv.z, -bxv.w), E1, T1);
+          for (int j = 1; j <= R; ++j) d = fmaf(wx.w1[j], v[c + j] - v[c - j], d);
+          t = fmaf(-get(bxf[iy], ix), d, t);
         }
-        acc[0] = T0.x; acc[1] = T0.y; acc[2] = T1.x; acc[3] = T1.y;
+        acc[ix] = t;
       }
       if (VD && ADJ) {
         // D1x(b_x lambda) from the b_x and lambda windows of this row
@@ -244,7 +211,7 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
         for (int q = 0; q <= 2 * NL; ++q) unpack(s_bx[ly * SW + tx + q], bw + 4 * q);
 #pragma unroll
         for (int ix = 0; ix < 4; ++ix) {
-          const int c = C0 + ix;
+          const int c = 4 * NL + ix;
           float d = 0.f;
 #pragma unroll
           for (int j = 1; j <= R; ++j)
@@ -397,8 +364,8 @@ k_step2d_tma_multi(const MultiDesc* __restrict__ descs, const MultiUnit* __restr
   }
   __syncthreads();
   const CUtensorMap* map = (n & 1) ? &d->map1 : &d->map0;
-  step2d_tma_tile<R, VD, false, RY, BY, false>(sp, UW ? wx : sp.wx, UW ? wy : sp.wy, map, un.tx,
-                                               un.ty, d->gx, un.slot, un.rank, smem, bar);
+  step2d_tma_tile<R, VD, false, RY, BY>(sp, UW ? wx : sp.wx, UW ? wy : sp.wy, map, un.tx, un.ty,
+                                        d->gx, un.slot, un.rank, smem, bar);
 }
 
 template <int R, bool VD, bool ADJ, int RY, int BY>

@@ -79,3 +79,32 @@ def test_estimate_and_stats():
     s = plan.stats()
     assert s["fwd_launches"] == p.nt - 1 and s["batch"] == 2
     assert s["updates"] == 2 * 64 * 80 * (p.nt - 1)
+
+
+def test_reserved_option_and_tile_range():
+    p = _problem()
+    plan = binding.Plan(p.shape, p.spacing, p.nt, p.dt, sponge=p.nb, c_ref=1500.0)
+    lib = binding.load()
+    import ctypes
+    opts = binding.COptions(0, 0, 0, 0, 1, 0)   # use_graphs = 1
+    assert lib.fwi_plan_set_options(plan._h, ctypes.byref(opts)) == 7   # FWI_ERR_UNSUPPORTED
+    plan.set_options(tile=13)   # out of range: reported by the next call
+    _expect(1, lambda: plan.forward(to_dev(p.vp), None, binding.Geometry(p.src_xyz, p.rec_xyz),
+                                    to_dev(p.wavelet)))
+
+
+def test_mem_available_counts_the_pool_reserve():
+    """A destroyed plan's workspace stays reserved in the stream-ordered pool;
+    fwi_mem_available still counts it, so a new plan's default budget does."""
+    import torch
+    free0, _ = torch.cuda.mem_get_info()
+    a0 = binding.mem_available()
+    assert a0 >= free0 * 0.99
+    p = inputs.breast_problem((512, 512), 0.1e-3, 400, nelem=32, shots=list(range(8)), nb=20,
+                              radius=0.4 * 512 * 0.1e-3)
+    plan = binding.Plan(p.shape, p.spacing, p.nt, p.dt, sponge=p.nb, c_ref=1600.0)
+    plan.forward(to_dev(p.vp), None, binding.Geometry(p.src_xyz, p.rec_xyz), to_dev(p.wavelet))
+    held = plan.stats()["workspace_bytes"]
+    plan.close()
+    torch.cuda.synchronize()
+    assert binding.mem_available() >= a0 - 0.05 * held - (64 << 20)
