@@ -13,10 +13,12 @@
 //    (16 bytes) plus the shared fields divided by S.
 //  * Each shot's wavefield tile plus halo (radius R in y, 4 or 8 floats in x)
 //    is fetched by one thread with a 3D TMA copy (cp.async.bulk.tensor) into
-//    one of two shared-memory buffers, completion tracked by an mbarrier;
-//    the copy for shot k+2 is issued as soon as every thread is done with
-//    shot k, so loads overlap the stencil of the next shot.  Every mbarrier
-//    wait is bounded: on time-out the CTA sets an error flag and returns.
+//    one of two shared-memory buffers, completion tracked by a "full"
+//    mbarrier; each warp signals an "empty" mbarrier when it is done with a
+//    buffer, and one thread issues the copy for shot k+2 once every warp is
+//    done with shot k, while the other warps go on with shot k+1 (no
+//    CTA-wide barrier between shots).  Every mbarrier wait is bounded: on
+//    time-out the CTA sets an error flag and carries on.
 #include "fwi_internal.cuh"
 #include "tma_util.cuh"
 
@@ -88,8 +90,10 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
   const int tmx = x0 + p.ox - G::XH;   // multiple of 4 floats: 16-byte aligned box start
   const int tmy = y0 + p.oy - R;
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
+    mbar_init(&bar[0], 1);    // full: the TMA copy of a shot's tile landed in buffer 0 / 1
     mbar_init(&bar[1], 1);
+    mbar_init(&bar[2], BY);   // empty: every warp is done with buffer 0 / 1
+    mbar_init(&bar[3], BY);
     fence_mbar_init();
   }
   // Shared model data of the tile, loaded once for the S shots.  Offsets
@@ -298,8 +302,14 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
         gs[iy][3] = fmaf(v[4 * NL + 3], hv[iy].w, gs[iy][3]);
       }
     }
-    __syncthreads();   // every thread is done with this buffer
+    // This warp is done with the buffer.  Thread 0 refills it for shot k + 2
+    // once every warp has arrived; the other warps go on to shot k + 1 (its
+    // tile is already loading), so no CTA-wide barrier separates the shots.
+    __syncwarp();
+    if ((tid & 31) == 0) mbar_arrive(&bar[2 + buf]);
     if (tid == 0 && k + 2 < ns) {
+      if (!mbar_wait_bounded(&bar[2 + buf], (uint32_t)((k >> 1) & 1)) && p.flags)
+        atomicOr(p.flags, 2);
       fence_proxy_async_smem();
       mbar_arrive_expect_tx(&bar[buf], G::TILE_BYTES);
       tma_load_3d(buf ? s_t1 : s_t0, tmap, &bar[buf], tmx, tmy, s + 2);
@@ -326,7 +336,7 @@ __global__ void __launch_bounds__(32 * BY, (RY == 1 ? 1024 : 512) / (32 * BY))
 k_step2d_tma(const StepParams p, const __grid_constant__ CUtensorMap tmap) {
   pdl_trigger();
   extern __shared__ __align__(128) float4 smem[];
-  __shared__ uint64_t bar[2];
+  __shared__ uint64_t bar[4];
   const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   step2d_tma_tile<R, VD, ADJ, RY, BY>(p, p.wx, p.wy, &tmap, blockIdx.x, blockIdx.y, gridDim.x,
                                       blockIdx.z, blk, smem, bar);
@@ -345,7 +355,7 @@ k_step2d_tma_multi(const MultiDesc* __restrict__ descs, const MultiUnit* __restr
                    const AxisW wx, const AxisW wy) {
   pdl_trigger();
   extern __shared__ __align__(128) float4 smem[];
-  __shared__ uint64_t bar[2];
+  __shared__ uint64_t bar[4];
   __shared__ StepParams sp;
   const MultiUnit un = units[blockIdx.x];
   const MultiDesc* d = descs + un.prob;

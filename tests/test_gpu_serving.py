@@ -12,7 +12,7 @@ from _helpers import to_dev
 pytestmark = pytest.mark.gpu
 
 
-def make_requests(n=10, seed=11):
+def make_requests(n=20, seed=11):
     stream = inputs.config_serving(nreq=n, seed=seed, rate=200.0, side2d=(96, 160),
                                    side3d=(36, 48), nt=(120, 260))
     reqs = []
