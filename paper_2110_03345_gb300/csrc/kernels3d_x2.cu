@@ -65,10 +65,8 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
   extern __shared__ __align__(128) float smem3x[];
   float* ring = smem3x;                       // [NSU][BYH][BXW]
   float* bring = ring + NSU * G::PLANE;       // PSI: [2 stages][b_x, b_y][BYH][BXW]
-  __shared__ uint64_t bar[NSU];     // full: a plane landed in a ring slot
-  __shared__ uint64_t bbar[2];      // full: the b_x / b_y planes of a stage landed
-  __shared__ uint64_t ebar[NSU];    // empty: every warp is done with a ring slot
-  __shared__ uint64_t ebbar[2];     // empty: every warp is done with a b stage
+  __shared__ uint64_t bar[NSU];
+  __shared__ uint64_t bbar[2];
   __shared__ int s_pe[MAX_ZCHUNK + 1];        // first source entry of each plane of the chunk
 
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -89,14 +87,9 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
   const int tmy = y0 + p.oy - R;
   const int pz0 = z0 - R + p.oz;            // padded z of staged plane 0
   if (tid == 0) {
-    for (int k = 0; k < NSU; ++k) {
-      mbar_init(&bar[k], 1);
-      mbar_init(&ebar[k], BY);
-    }
-    for (int k = 0; k < 2; ++k) {
-      mbar_init(&bbar[k], 1);
-      mbar_init(&ebbar[k], BY);
-    }
+    for (int k = 0; k < NSU; ++k) mbar_init(&bar[k], 1);
+    mbar_init(&bbar[0], 1);
+    mbar_init(&bbar[1], 1);
     fence_mbar_init();
   }
   // Source entries of the tile are sorted by tile-local index, which grows
@@ -168,16 +161,10 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
       qz[lp] = __fmul2_rn(__ldg(reinterpret_cast<const float2*>(p.bz + (long long)(pz0 + lp) * p.sxy + col)),
                           q[lp]);
   }
-  // planes 0 .. R-1 are halo only: once every warp has them, their slots
-  // take planes NSU .. NSU+R-1 (the release of plane lp is phase lp / NSU of
-  // its slot's empty barrier)
-  __syncwarp();
-  if ((tid & 31) == 0)
-    for (int lp = 0; lp < R; ++lp) mbar_arrive(&ebar[lp]);
+  __syncthreads();   // their slots take planes NSU .. NSU+R-1
   if (tid == 0) {
     for (int lp = NSU; lp < NSU + R && lp < nplanes; ++lp) {
       const int k = lp % NSU;
-      if (!mbar_wait_bounded(&ebar[k], (uint32_t)(((lp - NSU) / NSU) & 1))) timed_out = true;
       fence_proxy_async_smem();
       mbar_arrive_expect_tx(&bar[k], G::PLANE_BYTES);
       tma_load_4d(ring + k * G::PLANE, &umap, &bar[k], tmx, tmy, pz0 + lp, b);
@@ -352,26 +339,17 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
             p.g[fo + idx] = fmaf(-cen.x, cur.hv.x, cur.gv.x);
           }
         }
-        // this warp is done with the centre plane (and this b stage); thread 0
-        // refills a slot once every warp has released it, while the other warps
-        // go on (no CTA-wide barrier per plane)
-        __syncwarp();
-        if ((tid & 31) == 0) {
-          mbar_arrive(&ebar[(i + R) % NSU]);
-          if (PSI) mbar_arrive(&ebbar[i & 1]);
-        }
+        __syncthreads();   // every thread is done with the centre plane and this b stage
         if (tid == 0) {
           const int nx_ = i + R + NSU;   // the centre plane's slot takes plane nx_
           if (nx_ < nplanes) {
-            const int k = nx_ % NSU;   // the slot of plane i + R
-            if (!mbar_wait_bounded(&ebar[k], (uint32_t)(((i + R) / NSU) & 1))) timed_out = true;
+            const int k = nx_ % NSU;
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&bar[k], G::PLANE_BYTES);
             tma_load_4d(ring + k * G::PLANE, &umap, &bar[k], tmx, tmy, pz0 + nx_, b);
           }
           if (PSI && i + 2 < nz_c) {
             const int st = i & 1;
-            if (!mbar_wait_bounded(&ebbar[st], (uint32_t)((i >> 1) & 1))) timed_out = true;
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&bbar[st], 2 * G::PLANE_BYTES);
             tma_load_4d(bring + (2 * st) * G::PLANE, &bxmap, &bbar[st], tmx, tmy, z + 2 + p.oz, 0);
