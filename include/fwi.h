@@ -45,7 +45,7 @@ typedef enum {
     FWI_ERR_CUDA = 4,         /* a CUDA runtime call failed */
     FWI_ERR_NONFINITE = 5,    /* the model or the result holds Inf/NaN */
     FWI_ERR_TIMEOUT = 6,      /* a bounded device wait gave up */
-    FWI_ERR_UNSUPPORTED = 7   /* valid request this build does not implement */
+    FWI_ERR_UNSUPPORTED = 7   /* valid request the library does not implement */
 } fwi_status;
 
 /* Regular grid and spatial discretisation (Sec. 2.3 Listing 5, Sec. 2.4). */
