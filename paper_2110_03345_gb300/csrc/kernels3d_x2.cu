@@ -64,9 +64,10 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
   constexpr bool PSI = VD && ADJ;
   extern __shared__ __align__(128) float smem3x[];
   float* ring = smem3x;                       // [NSU][BYH][BXW]
-  float* bring = ring + NSU * G::PLANE;       // PSI: [2 stages][b_x, b_y][BYH][BXW]
+  constexpr int NBS = 4;                      // b stages: two loop trips of two planes
+  float* bring = ring + NSU * G::PLANE;       // PSI: [NBS stages][b_x, b_y][BYH][BXW]
   __shared__ uint64_t bar[NSU];
-  __shared__ uint64_t bbar[2];
+  __shared__ uint64_t bbar[NBS];
   __shared__ int s_pe[MAX_ZCHUNK + 1];        // first source entry of each plane of the chunk
 
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -88,8 +89,7 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
   const int pz0 = z0 - R + p.oz;            // padded z of staged plane 0
   if (tid == 0) {
     for (int k = 0; k < NSU; ++k) mbar_init(&bar[k], 1);
-    mbar_init(&bbar[0], 1);
-    mbar_init(&bbar[1], 1);
+    for (int k = 0; k < NBS; ++k) mbar_init(&bbar[k], 1);
     fence_mbar_init();
   }
   // Source entries of the tile are sorted by tile-local index, which grows
@@ -136,7 +136,7 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
       tma_load_4d(ring + lp * G::PLANE, &umap, &bar[lp], tmx, tmy, pz0 + lp, b);
     }
     if (PSI) {
-      for (int i = 0; i < 2 && i < nz_c; ++i) {
+      for (int i = 0; i < NBS && i < nz_c; ++i) {
         mbar_arrive_expect_tx(&bbar[i], 2 * G::PLANE_BYTES);
         tma_load_4d(bring + (2 * i) * G::PLANE, &bxmap, &bbar[i], tmx, tmy, z0 + i + p.oz, 0);
         tma_load_4d(bring + (2 * i + 1) * G::PLANE, &bymap, &bbar[i], tmx, tmy, z0 + i + p.oz, 0);
@@ -227,9 +227,9 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
         q[s + 2 * R] = lds2(ring + sl * G::PLANE + own);
         if (PSI) qz[s + 2 * R] = __fmul2_rn(cur.bzl, q[s + 2 * R]);
         const float* cp = ring + ((i + R) % NSU) * G::PLANE;   // centre plane z
-        const float* bxp = bring + (2 * (i & 1)) * G::PLANE;
+        const float* bxp = bring + (2 * (i % NBS)) * G::PLANE;
         const float* byp = bxp + G::PLANE;
-        if (PSI && !mbar_wait_bounded(&bbar[i & 1], (uint32_t)((i >> 1) & 1))) timed_out = true;
+        if (PSI && !mbar_wait_bounded(&bbar[i % NBS], (uint32_t)((i / NBS) & 1))) timed_out = true;
 
         // x pairs of the centre row: columns c0 - 2M .. c0 + 2M + 1
         float2 X[2 * M + 1];
@@ -339,8 +339,16 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
             p.g[fo + idx] = fmaf(-cen.x, cur.hv.x, cur.gv.x);
           }
         }
-        __syncthreads();   // every thread is done with the centre plane and this b stage
-        if (tid == 0) {
+      }
+    }
+    // one barrier per loop trip: every thread is done with the trip's centre
+    // planes and b stages, whose slots take the planes R + NSU and NBS ahead
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+      for (int s = 0; s < U; ++s) {
+        const int i = i0 + s;
+        if (i < nz_c) {
           const int nx_ = i + R + NSU;   // the centre plane's slot takes plane nx_
           if (nx_ < nplanes) {
             const int k = nx_ % NSU;
@@ -348,13 +356,13 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
             mbar_arrive_expect_tx(&bar[k], G::PLANE_BYTES);
             tma_load_4d(ring + k * G::PLANE, &umap, &bar[k], tmx, tmy, pz0 + nx_, b);
           }
-          if (PSI && i + 2 < nz_c) {
-            const int st = i & 1;
+          if (PSI && i + NBS < nz_c) {
+            const int st = i % NBS;
+            const int zb = z0 + i + NBS + p.oz;
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&bbar[st], 2 * G::PLANE_BYTES);
-            tma_load_4d(bring + (2 * st) * G::PLANE, &bxmap, &bbar[st], tmx, tmy, z + 2 + p.oz, 0);
-            tma_load_4d(bring + (2 * st + 1) * G::PLANE, &bymap, &bbar[st], tmx, tmy, z + 2 + p.oz,
-                        0);
+            tma_load_4d(bring + (2 * st) * G::PLANE, &bxmap, &bbar[st], tmx, tmy, zb, 0);
+            tma_load_4d(bring + (2 * st + 1) * G::PLANE, &bymap, &bbar[st], tmx, tmy, zb, 0);
           }
         }
       }
@@ -372,7 +380,7 @@ template <int R, bool VD, bool ADJ, int BY>
 constexpr size_t smem_bytes_x2() {
   using G = GeoX2<R, BY>;
   size_t n = (size_t)G::NSU * G::PLANE;
-  if (VD && ADJ) n += 4 * (size_t)G::PLANE;
+  if (VD && ADJ) n += 2 * 4 * (size_t)G::PLANE;   // NBS = 4 stages of b_x, b_y
   return n * sizeof(float);
 }
 
