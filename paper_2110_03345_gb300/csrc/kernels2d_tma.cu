@@ -104,14 +104,12 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
   int pix[RY];
   float4 kk[RY];
   float ay[RY];
-  bool in_sponge[RY];   // some point of the row has a nonzero damping a
 #pragma unroll
   for (int iy = 0; iy < RY; ++iy) {
     const int yg = y0 + ty * RY + iy;
     pix[iy] = (yg + p.oy) * p.sx + (xg + p.ox);
     kk[iy] = ldg4(p.kf + pix[iy]);
     ay[iy] = p.spy[yg];
-    in_sponge[iy] = ay[iy] != 0.f || ax4.x != 0.f || ax4.y != 0.f || ax4.z != 0.f || ax4.w != 0.f;
   }
   if (VD && ADJ && ns > 0) {
     for (int i = tid; i < TY * SW; i += NT) {
@@ -281,28 +279,16 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
       }
       float* upp = up_s + pix[iy];
       const float4 uoi = uo[iy];
-      // u^{n+1} = (2 u^n - (1 - a) u^{n-1} + h) / (1 + a), in one explicit
-      // rounding order; outside the sponge (a = 0) the division is skipped,
-      // which gives the same bits (x 1/(1 + 0) is exact)
       float res[4], upd[4];
 #pragma unroll
       for (int ix = 0; ix < 4; ++ix) {
         const float a = get(ax4, ix) + ay[iy];
-        const float h = __fmul_rn(get(kk[iy], ix), acc[ix]);
+        const float h = get(kk[iy], ix) * acc[ix];
         const float cen = v[4 * NL + ix];
-        res[ix] = __fadd_rn(fmaf(-(1.f - a), get(uoi, ix), 2.f * cen), h);
-        upd[ix] = h;
-      }
-      if (in_sponge[iy]) {
-#pragma unroll
-        for (int ix = 0; ix < 4; ++ix)
-          res[ix] = __fmul_rn(res[ix], __frcp_rn(1.f + (get(ax4, ix) + ay[iy])));
-      }
-#pragma unroll
-      for (int ix = 0; ix < 4; ++ix) {
+        const float r = (2.f * cen - (1.f - a) * get(uoi, ix) + h) * __frcp_rn(1.f + a);
         const bool in = (yg < p.ny) && (xg + ix < p.nx);
-        res[ix] = in ? res[ix] : 0.f;
-        upd[ix] = in ? upd[ix] : 0.f;
+        res[ix] = in ? r : 0.f;
+        upd[ix] = in ? h : 0.f;
       }
       st4(upp, make_float4(res[0], res[1], res[2], res[3]));
       if (!ADJ) {

@@ -259,9 +259,7 @@ k_step3d_tma(const StepParams p, const __grid_constant__ CUtensorMap umap,
         const float h = __fmul_rn(kk, acc);
         float t = fmaf(-(1.f - a), uo, 2.f * cen);
         t = __fadd_rn(t, h);
-        // outside the sponge (a = 0) the division is skipped: same bits
-        float r = t;
-        if (a != 0.f) r = __fmul_rn(t, __frcp_rn(1.f + a));
+        const float r = __fmul_rn(t, __frcp_rn(1.f + a));
         if (in_xy) {
           p.up[fo + idx] = r;
           if (!ADJ) {

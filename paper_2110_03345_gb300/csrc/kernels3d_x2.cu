@@ -323,10 +323,7 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
         float2 t = __ffma2_rn(make_float2(-(1.f - a.x), -(1.f - a.y)), cur.uo,
                               make_float2(2.f * cen.x, 2.f * cen.y));
         t = __fadd2_rn(t, h);
-        // outside the sponge (a = 0) the division is skipped: same bits
-        float2 r = t;
-        if (a.x != 0.f || a.y != 0.f)
-          r = __fmul2_rn(t, make_float2(__frcp_rn(1.f + a.x), __frcp_rn(1.f + a.y)));
+        const float2 r = __fmul2_rn(t, make_float2(__frcp_rn(1.f + a.x), __frcp_rn(1.f + a.y)));
         if (in1) {
           *reinterpret_cast<float2*>(p.up + fo + idx) = r;
           if (!ADJ) {
