@@ -65,18 +65,22 @@ def parse():
     return ap.parse_args()
 
 
-def make_problem(args):
+def make_problem(args, rank=0):
+    """The workload; rank r > 0 fires its own sources (the transducer set
+    rotated by r), so the ranks of a multi-GPU run process distinct shots."""
     from paper_2110_03345_gb300 import inputs
     if args.workload == "breast2d":
         n = args.n or 1024
         nt = args.nt or 4000
         dx = 0.1e-3 * 1024 / n
-        p = inputs.config_breast_2d(n=n, dx=dx, nt=nt)
+        shots = None if rank == 0 else [(2 * i + rank) % 256 for i in range(128)]
+        p = inputs.config_breast_2d(n=n, dx=dx, nt=nt, shots=shots)
     else:
         n = args.n or 256
         nt = args.nt or 2000
         dx = 0.25e-3 * 256 / n
-        p = inputs.config_skull_3d(n=n, dx=dx, nt=nt)
+        shots = None if rank == 0 else [(16 * i + rank) % 512 for i in range(32)]
+        p = inputs.config_skull_3d(n=n, dx=dx, nt=nt, shots=shots)
     if args.shots:
         p.src_xyz = p.src_xyz[:args.shots]
         p.wavelet = p.wavelet[:args.shots]
@@ -440,7 +444,7 @@ def run_mine(args):
         if dist is not None:
             dist.barrier()
 
-    p = make_problem(args)
+    p = make_problem(args, rank)
     vd = p.rho is not None
     f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
     vp_h = torch.from_numpy(f32(p.vp)).pin_memory()
@@ -477,25 +481,25 @@ def run_mine(args):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    from paper_2110_03345_gb300 import distributed as fwi_dist
     J = None
     for _ in range(args.steps):
         J, _, _ = plan.gradient(vp, rho, geo, wav, obs, grad=grad)
         s = plan.stats()
         for k in acc:
             acc[k] += s[k]
+        # the exchange step of a multi-GPU run: the gradient and misfit of all
+        # ranks' shots are summed (the paper's sum over shots); no-op on one GPU
+        J = fwi_dist.sum_over_ranks(grad, J)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
     clk = clocks.stop()
     if dist is not None:
-        from paper_2110_03345_gb300 import distributed as fwi_dist
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-        # data-parallel gradient combination across ranks (the paper's sum over shots);
-        # outside the timed region: each rank solves its own replica of the workload
-        J = fwi_dist.sum_over_ranks(grad, J)
     stats = plan.stats()
 
     upd = useful_updates(p)
