@@ -573,6 +573,9 @@ fwi_status choose_plan(const fwi_plan* P, const fwi_geometry* g, bool vd, bool g
                                              std::to_string(budget) + " bytes)");
   if (P->opt.batch > 0) B = std::min(B, P->opt.batch);
   B = std::min(B, ns);
+  // equal batches: the same number of batches, none left nearly empty
+  // (16 shots at 15 per batch run as 8 + 8, not 15 + 1)
+  B = (ns + (ns + B - 1) / B - 1) / ((ns + B - 1) / B);
   out.B = B;
   out.K = K;
   out.nck = K ? (P->nt - 2) / K + 1 : 0;
