@@ -101,7 +101,8 @@ def tune(shape, spacing, dt, order, sponge, c_ref, vp, rho, geometry, wavelet, o
     return dict(best[1])
 
 
-BATCH_CANDIDATES = [dict(tile=t, shots_per_cta=s) for t in (5, 6, 7, 8) for s in (0, 2, 4, 6)]
+BATCH_CANDIDATES = [dict(tile=t, shots_per_cta=s) for t in (5, 6, 7, 8) for s in (0, 2, 4, 6)] + \
+                   [dict(tile=t, shots_per_cta=s) for t in (6, 8) for s in (8, 12, 16)]
 
 
 def batch_key(problems):
