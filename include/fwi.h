@@ -97,7 +97,8 @@ typedef struct {
                            staged, 5-8 TMA plane ring (32 x points per CTA row),
                            9-12 TMA plane ring with two x points per thread (64);
                            the TMA families give bit-identical results */
-    int profile;        /* 1: time every stencil launch with CUDA events */
+    int profile;        /* n > 0: time every n-th stencil launch with CUDA events
+                           (1: every launch); 0: no events */
     int use_graphs;     /* reserved, must be 0 (consecutive steps overlap through
                            programmatic dependent launch; whole runs of uneven
                            problems are graphs in fwi_batch_*) */
@@ -114,10 +115,12 @@ typedef struct {
     int64_t updates;            /* grid-point updates in the last call (all kernels) */
     int64_t fwd_launches;       /* forward stencil launches (incl. recompute) */
     int64_t adj_launches;       /* adjoint stencil launches */
-    double fwd_ms;              /* summed CUDA-event time of forward stencil launches (profile=1) */
+    double fwd_ms;              /* summed CUDA-event time of the timed forward stencil launches */
     double adj_ms;              /* same for adjoint stencil launches */
-    int64_t fwd_points;         /* grid points (incl. padding-free interior) per forward launch, summed */
+    int64_t fwd_points;         /* grid points (interior) x shots of every forward launch, summed */
     int64_t adj_points;
+    int64_t fwd_timed;          /* forward launches that carried events (profile option) */
+    int64_t adj_timed;
 } fwi_stats;
 
 /* Create a plan for one grid and time axis (nt samples of step dt seconds).

@@ -80,7 +80,8 @@ class CStats(ctypes.Structure):
                 ("updates", ctypes.c_int64), ("fwd_launches", ctypes.c_int64),
                 ("adj_launches", ctypes.c_int64), ("fwd_ms", ctypes.c_double),
                 ("adj_ms", ctypes.c_double), ("fwd_points", ctypes.c_int64),
-                ("adj_points", ctypes.c_int64)]
+                ("adj_points", ctypes.c_int64), ("fwd_timed", ctypes.c_int64),
+                ("adj_timed", ctypes.c_int64)]
 
 
 def lib_path() -> str:
@@ -271,7 +272,8 @@ class Plan:
         TMA-staged with shots looped inside a CTA; 3D 1-4 shared-memory staged,
         5-8 TMA plane ring, 9-12 TMA plane ring with two x points per thread.
         shots_per_cta: 2D TMA variants only."""
-        self._opts = COptions(int(batch), int(ckpt_every), int(tile), int(bool(profile)),
+        # profile: True / 1 times every stencil launch, n > 1 every n-th
+        self._opts = COptions(int(batch), int(ckpt_every), int(tile), int(profile),
                               0, int(shots_per_cta))
         _check(load().fwi_plan_set_options(self._h, ctypes.byref(self._opts)))
 

@@ -726,6 +726,7 @@ struct Call {
   int64_t launches = 0;
   int64_t fwd_launches = 0, adj_launches = 0;
   int64_t fwd_points = 0, adj_points = 0;
+  int64_t fwd_timed = 0, adj_timed = 0;   // launches that carried events
 };
 
 fwi_status record_event(fwi_plan* P, int kind) {
@@ -803,7 +804,8 @@ fwi_status launch_step(Call& c, const StepParams& p_in, bool adj) {
     c.launches++;
     p.nrec = 0;
   }
-  const bool prof = P->opt.profile != 0;
+  const bool prof = P->opt.profile > 0 &&
+                    (c.fwd_launches + c.adj_launches) % P->opt.profile == 0;
   p.flags = P->d_flags + 1;
   p.S = c.pl.S;
   const CUtensorMap* map = nullptr;
@@ -823,7 +825,11 @@ fwi_status launch_step(Call& c, const StepParams& p_in, bool adj) {
   else if (c.pl.tma) e = launch_step2d_tma(p, *map, P->R, c.vd, adj, c.pl.shape, P->st);
   else e = launch_step2d(p, P->R, c.vd, adj, c.pl.shape, P->st);
   if (e != cudaSuccess) return fail(FWI_ERR_CUDA, std::string("stencil launch: ") + cudaGetErrorString(e));
-  if (prof) FWI_TRY(record_event(P, adj ? 1 : 0));
+  if (prof) {
+    FWI_TRY(record_event(P, adj ? 1 : 0));
+    if (adj) c.adj_timed++;
+    else c.fwd_timed++;
+  }
   c.launches++;
   const int64_t pts = (int64_t)p.B * P->L.nx * P->L.ny * P->L.nz;
   if (adj) { c.adj_launches++; c.adj_points += pts; }
@@ -1066,6 +1072,8 @@ fwi_status finish_call(Call& c) {
   s.adj_launches = c.adj_launches;
   s.fwd_points = c.fwd_points;
   s.adj_points = c.adj_points;
+  s.fwd_timed = c.fwd_timed;
+  s.adj_timed = c.adj_timed;
   s.updates = c.fwd_points + c.adj_points;
   s.fwd_ms = s.adj_ms = 0.0;
   for (size_t i = 0; i + 1 < P->ev_used; i += 2) {
@@ -1291,6 +1299,7 @@ fwi_status fwi_plan_create(fwi_plan** plan, const fwi_grid* grid, int nt, double
 fwi_status fwi_plan_set_options(fwi_plan* plan, const fwi_options* opt) {
   if (!plan || !opt) return fail(FWI_ERR_INVALID_ARG, "NULL argument");
   if (opt->batch < 0) return fail(FWI_ERR_INVALID_ARG, "batch must be >= 0");
+  if (opt->profile < 0) return fail(FWI_ERR_INVALID_ARG, "profile must be >= 0");
   if (opt->use_graphs != 0) return fail(FWI_ERR_UNSUPPORTED, "use_graphs is reserved and must be 0");
   plan->opt = *opt;
   return FWI_OK;
