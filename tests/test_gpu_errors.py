@@ -108,3 +108,19 @@ def test_mem_available_counts_the_pool_reserve():
     plan.close()
     torch.cuda.synchronize()
     assert binding.mem_available() >= a0 - 0.05 * held - (64 << 20)
+
+
+def test_sampled_launch_timing():
+    """profile = n puts CUDA events around every n-th stencil launch."""
+    p = _problem()
+    plan = binding.Plan(p.shape, p.spacing, p.nt, p.dt, sponge=p.nb, c_ref=1500.0)
+    geo = binding.Geometry(p.src_xyz, p.rec_xyz)
+    for every, want in ((1, p.nt - 1), (4, (p.nt - 1 + 3) // 4), (0, 0)):
+        plan.set_options(profile=every)
+        plan.forward(to_dev(p.vp), None, geo, to_dev(p.wavelet))
+        s = plan.stats()
+        assert s["fwd_launches"] == p.nt - 1
+        assert s["fwd_timed"] == want
+        assert (s["fwd_ms"] > 0) == (want > 0)
+    with pytest.raises(binding.FwiError):
+        plan.set_options(profile=-1)
