@@ -87,7 +87,7 @@ def make_problem(args, rank=0):
     return p
 
 
-PROFILE_EVERY = 8   # stencil launches per CUDA-event-timed launch in the timed region
+PROFILE_EVERY = 32   # stencil launches per CUDA-event-timed launch in the timed region
 
 
 def kernel_name(ndim, tile):
