@@ -124,3 +124,14 @@ def test_sampled_launch_timing():
         assert (s["fwd_ms"] > 0) == (want > 0)
     with pytest.raises(binding.FwiError):
         plan.set_options(profile=-1)
+
+
+def test_equal_batches():
+    """16 shots with at most 15 per launch run as two batches of 8."""
+    p = inputs.breast_problem((64, 80), 0.5e-3, 40, nelem=32, shots=list(range(0, 32, 2)), nb=8,
+                              radius=0.3 * 64 * 0.5e-3)
+    plan = binding.Plan(p.shape, p.spacing, p.nt, p.dt, sponge=p.nb, c_ref=1500.0)
+    plan.set_options(batch=15)
+    plan.forward(to_dev(p.vp), None, binding.Geometry(p.src_xyz, p.rec_xyz), to_dev(p.wavelet))
+    s = plan.stats()
+    assert s["batch"] == 8 and s["fwd_launches"] == 2 * (p.nt - 1)
