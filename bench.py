@@ -321,9 +321,10 @@ def uneven_batch(nprob=64, seed=4, reps=2, **kw):
 def uneven_gradient(nprob=64, seed=4, lanes=4, **kw):
     """Gradient variant of the uneven set: every problem's gradient (misfit
     against zero data), (a) submitted at once to the serving loop, which runs
-    them concurrently on `lanes` streams within the HBM budget, one plan per
-    problem with all its shots per launch; (b) one plan per problem, problems
-    one after another; (c) the plain solver with one shot per launch."""
+    them concurrently on `lanes` streams within the HBM budget and while their
+    GPU-fill weights sum to at most one, one plan per problem with all its
+    shots per launch; (b) one plan per problem, problems one after another;
+    (c) the plain solver with one shot per launch."""
     import torch
     from paper_2110_03345_gb300 import binding, inputs, serve
     ps = inputs.config_uneven_batch(nprob=nprob, seed=seed, **kw)
@@ -338,7 +339,8 @@ def uneven_gradient(nprob=64, seed=4, lanes=4, **kw):
     budget = int(0.7 * binding.mem_available())
 
     def served():
-        server = serve.Server(budget_bytes=budget, lanes=lanes)
+        # requests that each fill the GPU (>= 8 M points x shots) run one at a time
+        server = serve.Server(budget_bytes=budget, lanes=lanes, fill_points=8 << 20)
         objs = [serve.Request(**r) for r in reqs]
         torch.cuda.synchronize()
         t0 = time.perf_counter()

@@ -96,11 +96,19 @@ def run_request(req: Request, stream, budget=0):
 
 class Server:
     """Continuous admission of requests onto `lanes` concurrent CUDA streams
-    within `budget_bytes` of device memory."""
+    within `budget_bytes` of device memory.
 
-    def __init__(self, budget_bytes: int, lanes: int = 4, device=None, request_cap: int = 0):
+    fill_points (optional): grid points x shots that fill the GPU.  A request
+    then weighs min(1, its points x shots / fill_points) and requests run
+    together only while their weights sum to at most 1 (one always runs), so
+    requests that each fill the GPU do not contend for it."""
+
+    def __init__(self, budget_bytes: int, lanes: int = 4, device=None, request_cap: int = 0,
+                 fill_points: int = 0):
         self.budget = int(budget_bytes)
         self.lanes = lanes
+        self.fill_points = int(fill_points)
+        self._load = 0.0
         # one request may hold at most this much (default: an equal share per lane)
         self.request_cap = int(request_cap) or self.budget // lanes
         self.device = device if device is not None else torch.cuda.current_device()
@@ -156,14 +164,27 @@ class Server:
                 req, fut = self._queue.popleft()   # FIFO: the head goes first
                 lane = self._free_lanes.pop()
                 self._used += req.bytes
+                self._load += self._weight(req)
                 self._running += 1
                 self.peak_bytes = max(self.peak_bytes, self._used)
                 self.peak_running = max(self.peak_running, self._running)
             threading.Thread(target=self._work, args=(req, fut, lane), daemon=True).start()
 
+    def _weight(self, req: Request) -> float:
+        if not self.fill_points:
+            return 0.0
+        pts = 1
+        for n in req.shape:
+            pts *= int(n)
+        return min(1.0, pts * req.shots / self.fill_points)
+
     def _admissible(self):
-        return bool(self._queue) and bool(self._free_lanes) and \
-            self._used + self._queue[0][0].bytes <= self.budget
+        if not (self._queue and self._free_lanes):
+            return False
+        head = self._queue[0][0]
+        if self._used + head.bytes > self.budget:
+            return False
+        return self._running == 0 or self._load + self._weight(head) <= 1.0 + 1e-9
 
     def _work(self, req: Request, fut: Future, lane: int):
         torch.cuda.set_device(self.device)
@@ -179,6 +200,7 @@ class Server:
         finally:
             with self._cv:
                 self._used -= req.bytes
+                self._load -= self._weight(req)
                 self._running -= 1
                 self._free_lanes.append(lane)
                 self.completed.append(req)

@@ -78,3 +78,20 @@ def test_oversized_request_is_refused():
         fut.result(timeout=60)
     assert ei.value.status == 3
     server.close()
+
+
+def test_fill_weights_serialise_large_requests():
+    """With fill_points below every request's size each request weighs 1, so
+    requests run one at a time; results are those of the requests alone."""
+    reqs = make_requests(n=6, seed=14)
+    server = serve.Server(budget_bytes=24 << 30, lanes=4, fill_points=1)
+    futs = [server.submit(r) for _, r in reqs]
+    done = [f.result(timeout=300) for f in futs]
+    server.drain()
+    server.close()
+    assert server.peak_running == 1
+    alone = torch.cuda.Stream()
+    for r in done:
+        ref = serve.run_request(r, alone)
+        torch.cuda.synchronize()
+        assert results_equal(r.result, ref)
