@@ -339,8 +339,11 @@ def uneven_gradient(nprob=64, seed=4, lanes=4, **kw):
     budget = int(0.7 * binding.mem_available())
 
     def served():
-        # requests that each fill the GPU (>= 8 M points x shots) run one at a time
-        server = serve.Server(budget_bytes=budget, lanes=lanes, fill_points=8 << 20)
+        # requests that each fill the GPU (>= 8 M points x shots) run one at a
+        # time, and a request may take the whole budget (as in the sequential
+        # arms), so no plan is pushed into checkpointing by a per-request cap
+        server = serve.Server(budget_bytes=budget, lanes=lanes, fill_points=8 << 20,
+                              request_cap=budget)
         objs = [serve.Request(**r) for r in reqs]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
