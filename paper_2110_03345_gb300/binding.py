@@ -214,7 +214,8 @@ class Geometry:
         self.rec = np.ascontiguousarray(rec_xyz, dtype=np.float64)
         if self.src.ndim == 2:
             self.src = self.src[None]
-        assert self.src.ndim == 3 and self.rec.ndim == 2
+        if self.src.ndim != 3 or self.rec.ndim != 2 or self.src.shape[2] != self.rec.shape[1]:
+            raise ValueError("src_xyz must be [nshots][nsrc][ndim] and rec_xyz [nrec][ndim]")
         dp = ctypes.POINTER(ctypes.c_double)
         self.c = CGeometry(self.src.shape[0], self.src.shape[1], self.rec.shape[0],
                            self.src.ctypes.data_as(dp), self.rec.ctypes.data_as(dp))
