@@ -1,0 +1,77 @@
+"""Host-side logic that needs no GPU: the seeded workload generators (sizes,
+determinism, the time step at CFL 0.4), the serving latency statistics and
+the autotuner's problem classes."""
+import types
+
+import numpy as np
+import pytest
+
+from paper_2110_03345_gb300 import autotune, inputs, serve
+
+
+def test_breast_workload_matches_its_description():
+    p = inputs.config_breast_2d(n=128, dx=0.8e-3, nt=40)   # same recipe, scaled down
+    assert p.shape == (128, 128) and p.nshots == 128 and p.rec_xyz.shape == (256, 2)
+    # sources are the even ring elements, every element receives
+    np.testing.assert_allclose(p.src_xyz[:, 0, :], p.rec_xyz[::2])
+    assert 1400.0 <= p.vp.min() and p.vp.max() <= 1600.0
+    assert 950.0 <= p.rho.min() and p.rho.max() <= 1100.0
+    assert p.dt == pytest.approx(0.4 * 0.8e-3 / 1600.0)
+    assert not np.array_equal(p.vp, p.vp_true)             # observed data from a perturbed model
+
+
+def test_full_size_breast_time_step():
+    """The 1024^2 benchmark workload: 0.1 mm, CFL 0.4 at c_max = 1600 m/s gives 25 ns."""
+    assert inputs.cfl_dt(0.1e-3, 1600.0, 0.4) == pytest.approx(25e-9)
+
+
+def test_generators_are_seeded():
+    a = inputs.config_breast_2d(n=96, dx=1e-3, nt=20)
+    b = inputs.config_breast_2d(n=96, dx=1e-3, nt=20)
+    assert np.array_equal(a.vp, b.vp) and np.array_equal(a.rho, b.rho)
+    assert np.array_equal(a.wavelet, b.wavelet)
+    s1 = inputs.config_skull_3d(n=40, dx=1.6e-3, nt=20)
+    s2 = inputs.config_skull_3d(n=40, dx=1.6e-3, nt=20)
+    assert np.array_equal(s1.vp, s2.vp) and np.array_equal(s1.rec_xyz, s2.rec_xyz)
+    assert s1.nshots == 32 and s1.rec_xyz.shape == (512, 3)
+    assert set(np.unique(s1.vp)) >= {1500.0, 2800.0}
+
+
+def test_uneven_batch_recipe():
+    ps = inputs.config_uneven_batch(nprob=12, seed=4, side=(64, 128), nt=(50, 80), shots=(1, 16))
+    assert len(ps) == 12
+    for p in ps:
+        assert p.shape[0] == p.shape[1] and p.shape[0] % 4 == 0 and 64 <= p.shape[0] <= 128
+        assert 50 <= p.nt <= 80 and 1 <= p.nshots <= 16
+    ps2 = inputs.config_uneven_batch(nprob=12, seed=4, side=(64, 128), nt=(50, 80), shots=(1, 16))
+    assert [p.shape for p in ps] == [p.shape for p in ps2]
+
+
+def test_serving_stream_recipe():
+    st = inputs.config_serving(nreq=200, seed=5, rate=20.0, side2d=(64, 96), side3d=(24, 32),
+                               nt=(30, 40))
+    t = np.array([a for a, _, _ in st])
+    assert np.all(np.diff(t) > 0)
+    assert 200 / t[-1] == pytest.approx(20.0, rel=0.25)     # Poisson at 20 per second
+    frac2d = np.mean([len(p.shape) == 2 for _, _, p in st])
+    fracfwd = np.mean([k == "forward" for _, k, _ in st])
+    assert 0.65 < frac2d < 0.85 and 0.4 < fracfwd < 0.6
+    assert all(p.nshots == 1 for _, _, p in st)
+
+
+def test_latency_statistics():
+    reqs = [types.SimpleNamespace(t_submit=float(i), t_done=float(i) + 1.0 + (i == 99) * 9.0,
+                                  shots=1) for i in range(100)]
+    st = serve.latency_stats(reqs)
+    assert st["p50_s"] == pytest.approx(1.0)
+    assert st["p99_s"] > 1.0 and st["requests"] == 100
+    assert st["shots_per_s"] == pytest.approx(100 / (109.0 - 0.0))
+
+
+def test_autotune_problem_classes():
+    k1 = autotune.problem_key((1024, 1024), 8, True, True, 15)
+    k2 = autotune.problem_key((1000, 1020), 8, True, True, 15)   # same tile-rounded class
+    k3 = autotune.problem_key((1024, 1024), 8, True, True, 8)
+    assert k1 == k2 and k1 != k3
+    assert autotune.problem_key((256, 256, 256), 10, True, True, 1).startswith("3d-o10-vd-grad")
+    assert all(5 <= c["tile"] <= 12 for c in autotune.CANDIDATES_3D)   # TMA-staged 3D variants
