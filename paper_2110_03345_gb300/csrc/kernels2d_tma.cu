@@ -77,7 +77,6 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
   float4* s_t1 = smem + SH * SW;       // buffer 1
   float4* s_bx = smem + 2 * SH * SW;   // adjoint vd: b_x on tile rows with x halo [TY][SW]
   float4* s_by = s_bx + TY * SW;       // adjoint vd: b_y on tile columns with y halo [SH][QW]
-  float4* s_bf = s_bx;                 // forward vd: b_x, b_y of the tile [2][TY][QW]
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * 32 + tx;
@@ -111,15 +110,6 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
     pix[iy] = (yg + p.oy) * p.sx + (xg + p.ox);
     kk[iy] = ldg4(p.kf + pix[iy]);
     ay[iy] = p.spy[yg];
-  }
-  if (VD && !ADJ && ns > 0) {
-    // b_x, b_y of the tile's own points, shared by the S shots
-    for (int i = tid; i < TY * QW; i += NT) {
-      const int r = i / QW, c = i - r * QW;
-      const int off = (y0 + r + p.oy) * p.sx + (x0 + p.ox) + 4 * c;
-      s_bf[i] = ldg4(p.bx + off);
-      s_bf[TY * QW + i] = ldg4(p.by + off);
-    }
   }
   if (VD && ADJ && ns > 0) {
     for (int i = tid; i < TY * SW; i += NT) {
@@ -169,12 +159,17 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
     float* const up_s = p.up + (size_t)s * p.fstride;
     float* const h_s = p.hist ? p.hist + (size_t)s * p.fstride : nullptr;
     // this shot's global operands are issued before the tile wait, so their
-    // latency overlaps it: u^{n-1}, and h^k (adjoint)
+    // latency overlaps it: u^{n-1}, and h^k (adjoint) or b_x, b_y (forward)
     float4 uo[RY], hv[ADJ ? RY : 1];
+    float4 bxf[VD && !ADJ ? RY : 1], byf[VD && !ADJ ? RY : 1];
 #pragma unroll
     for (int iy = 0; iy < RY; ++iy) {
       uo[iy] = ld4(up_s + pix[iy]);
       if (ADJ && p.image) hv[iy] = __ldcs(reinterpret_cast<const float4*>(h_s + pix[iy]));
+      if (VD && !ADJ) {
+        bxf[iy] = ldg4(p.bx + pix[iy]);
+        byf[iy] = ldg4(p.by + pix[iy]);
+      }
     }
     // A wait that times out flags the error and carries on (no early exit, so
     // no thread can miss a later barrier); the host reports FWI_ERR_TIMEOUT.
@@ -209,7 +204,7 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
           float d = 0.f;
 #pragma unroll
           for (int j = 1; j <= R; ++j) d = fmaf(wx.w1[j], v[c + j] - v[c - j], d);
-          t = fmaf(-get(s_bf[(ty * RY + iy) * QW + tx], ix), d, t);
+          t = fmaf(-get(bxf[iy], ix), d, t);
         }
         acc[ix] = t;
       }
@@ -264,7 +259,7 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
           }
         }
         if (VD && !ADJ) {   // - b_y D1y u
-          const float4 byv = s_bf[TY * QW + (ty * RY + iy) * QW + tx];
+          const float4 byv = byf[iy];
           A0 = __ffma2_rn(make_float2(-byv.x, -byv.y), D0, A0);
           A1 = __ffma2_rn(make_float2(-byv.z, -byv.w), D1, A1);
         }
@@ -388,7 +383,6 @@ constexpr size_t smem_bytes() {
   using G = Geo<R, RY, BY>;
   size_t n = 2 * (size_t)G::SH * G::SW;
   if (VD && ADJ) n += (size_t)G::TY * G::SW + (size_t)G::SH * G::QW;
-  if (VD && !ADJ) n += 2 * (size_t)G::TY * G::QW;
   return n * sizeof(float4);
 }
 
