@@ -135,7 +135,7 @@ __host__ __device__ inline Tile3 tile3_variant(int v) {
     case 1: return {8, 64};
     case 2: return {16, 32};
     case 3: return {8, 32};
-    default: return {16, 64};
+    default: return {8, 16};   // short chunks: more CTAs per shot against the wave tail
   }
 }
 
