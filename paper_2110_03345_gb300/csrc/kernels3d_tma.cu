@@ -163,9 +163,11 @@ k_step3d_tma(const StepParams p, const __grid_constant__ CUtensorMap umap,
   // ahead (software pipelining in registers), so their latency overlaps a plane.
   struct Ops {
     float uo, kk, hv, gv, bx, by, bz, bzl;
+    float sz;   // sponge damping of the plane (z part)
   };
   auto load_ops = [&](int ii) {
-    Ops o{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    Ops o{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    o.sz = __ldg(p.spz + z0 + ii);
     const long long id = (long long)(z0 + ii + p.oz) * p.sxy + col;
     o.uo = p.up[fo + id];
     o.kk = __ldg(p.kf + id);
@@ -253,7 +255,7 @@ k_step3d_tma(const StepParams p, const __grid_constant__ CUtensorMap umap,
             if (__ldg(p.inj_loc + e) == me)
               acc = fmaf(p.inj_w[e], p.vals[p.inj_vidx[e] + p.step_off], acc);
         }
-        const float a = axy + p.spz[z];
+        const float a = axy + cur.sz;
         // explicit rounding order (no contraction left to the compiler), shared
         // with the two-point kernels of kernels3d_x2.cu
         const float h = __fmul_rn(kk, acc);

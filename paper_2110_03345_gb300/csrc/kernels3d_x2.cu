@@ -189,11 +189,13 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
 
   struct Ops {
     float2 uo, kk, hv, gv, bx, by, bz, bzl;
+    float sz;   // sponge damping of the plane (z part)
   };
   auto ldg2 = [](const float* a) { return __ldg(reinterpret_cast<const float2*>(a)); };
   auto load_ops = [&](int ii) {
     const float2 z2 = make_float2(0.f, 0.f);
-    Ops o{z2, z2, z2, z2, z2, z2, z2, z2};
+    Ops o{z2, z2, z2, z2, z2, z2, z2, z2, 0.f};
+    o.sz = __ldg(p.spz + z0 + ii);
     const long long id = (long long)(z0 + ii + p.oz) * p.sxy + col;
     o.uo = *reinterpret_cast<const float2*>(p.up + fo + id);
     o.kk = ldg2(p.kf + id);
@@ -317,7 +319,7 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
               acc.y = fmaf(p.inj_w[e], p.vals[p.inj_vidx[e] + p.step_off], acc.y);
           }
         }
-        const float sz_ = p.spz[z];
+        const float sz_ = cur.sz;
         const float2 a = make_float2(axy.x + sz_, axy.y + sz_);
         const float2 h = __fmul2_rn(cur.kk, acc);
         float2 t = __ffma2_rn(make_float2(-(1.f - a.x), -(1.f - a.y)), cur.uo,
