@@ -61,3 +61,16 @@ def test_paper_homogeneous_setup_is_within_the_limit():
         for d in (2, 3):
             for order in (8, 10):
                 assert cfl < binding.cfl_limit(d, order)
+
+
+@pytest.mark.skipif(__import__("torch").cuda.is_available(), reason="checks the no-GPU path")
+def test_no_cpu_fallback_without_a_gpu():
+    """Without a GPU the solver calls raise: there is no CPU path to fall back to."""
+    with pytest.raises(Exception):
+        binding.Plan((64, 64), 1e-3, 20, 1e-7)
+    lib = binding.load()
+    plan = ctypes.c_void_p()
+    g = binding.make_grid((64, 64), 1e-3, 8, 8, 1500.0)
+    status = lib.fwi_plan_create(ctypes.byref(plan), ctypes.byref(g), 20, 1e-7, 0, None)
+    assert status == 4   # FWI_ERR_CUDA: no device
+    assert len(lib.fwi_last_error()) > 0
