@@ -1,9 +1,11 @@
 // 3D leapfrog step kernels, TMA-staged (2.5D blocking with a plane ring).
 //
-// Same arithmetic as kernels3d.cu (Eq. 10 of Sec. 2.4 without attenuation,
+// Same scheme as kernels3d.cu (Eq. 10 of Sec. 2.4 without attenuation,
 // damped leapfrog, exact discrete adjoint, imaging condition of Sec. 2.2
-// Eq. 8 fused into the adjoint).  A CTA of 32 x BY threads owns a 32 x BY
-// column of one shot and streams along z over a chunk of planes:
+// Eq. 8 fused into the adjoint), in the explicit rounding order shared with
+// the two-point kernels of kernels3d_x2.cu (bit-identical results).  A CTA
+// of 32 x BY threads owns a 32 x BY column of one shot and streams along z
+// over a chunk of planes:
 //
 //  * each x-y plane of the column, with its halo, arrives by a 4D TMA copy
 //    (x, y, z, shot) into a ring of 2R+2 shared-memory planes, so the copies

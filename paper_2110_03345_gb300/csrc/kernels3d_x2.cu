@@ -11,11 +11,12 @@
 //    arithmetic runs on packed FP32x2 instructions (two lanes, each rounded
 //    as the scalar operation);
 //  * the z loop advances two planes per trip, so the register queue of the
-//    column shifts once per two planes;
+//    column shifts once per two planes, and one barrier plus one round of
+//    TMA refills closes each trip;
 //  * the x-y planes (80 floats wide: x0-8 .. x0+71, 16-byte aligned) arrive by
 //    4D TMA copies into a ring of R+1+PF planes (the centre, the R planes up
 //    to the lead, PF planes in flight); the variable-density adjoint streams
-//    b_x, b_y planes through a second two-stage ring as before.
+//    b_x, b_y planes through a second, four-stage ring (two trips).
 // Every mbarrier wait is bounded: on time-out the error flag is set and the
 // kernel carries on, so no thread skips a barrier.
 #include "fwi_internal.cuh"
