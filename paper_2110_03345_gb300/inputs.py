@@ -341,3 +341,76 @@ def random_points(n, shape, dx, seed, margin):
     lo = margin * dx
     hi = (np.array(shape) - 1 - margin) * dx
     return rng.uniform(lo, hi, (n, len(shape)))
+
+
+# ---------------------------------------------------------------------------
+# Inversion workload (the 2D imaging experiment of Sec. 3.2)
+# ---------------------------------------------------------------------------
+
+def tone_burst(f0: float, dt: float, nt: int, cycles: int = 3, t0: float = 0.0,
+               amp: float = 1.0):
+    """`cycles`-cycle tone burst centred at f0 starting at t0: a sine of
+    frequency f0 under a Hann envelope that spans the burst, zero elsewhere."""
+    tau = np.arange(nt) * dt - t0
+    T = cycles / f0
+    on = (tau >= 0.0) & (tau <= T)
+    env = 0.5 * (1.0 - np.cos(2.0 * np.pi * tau / T))
+    return np.where(on, amp * np.sin(2.0 * np.pi * f0 * tau) * env, 0.0)
+
+
+def shot_schedule(nshots: int, per_iter: int, nblocks: int, seed: int):
+    """Random shot subsets without replacement (Sec. 3.2): for each block a
+    fresh permutation of the shots, cut into iterations of `per_iter` shots
+    (the last one shorter when per_iter does not divide nshots), so every
+    shot is used once per block.  Returns [block][iteration] -> int64 ids."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(nblocks):
+        perm = rng.permutation(nshots).astype(np.int64)
+        out.append([perm[i:i + per_iter] for i in range(0, nshots, per_iter)])
+    return out
+
+
+def disk_mask(shape, dx, centre, radius):
+    """1 inside the disk (or ball) of the given centre and radius, 0 outside."""
+    axes = [np.arange(s) * dx for s in shape]
+    grids = np.meshgrid(*axes, indexing="ij")
+    r2 = sum((g - c) ** 2 for g, c in zip(grids, centre))
+    return (r2 <= radius * radius).astype(np.float64)
+
+
+def config_inversion_2d(scale: float = 1.0, shape=(456, 485), dx=0.5e-3, dt=0.08e-6, nt=2500,
+                        nelem=128, f0=500e3, freqs=(300e3, 400e3, 500e3, 600e3), per_iter=16,
+                        c_start=1500.0, order=8, nb=20, seed=2, schedule_seed=7,
+                        filter_cycles=3.0):
+    """The 2D breast imaging experiment of Sec. 3.2 with a synthetic phantom:
+    456 x 485 grid at 0.5 mm, 128 ring transducers that all fire and receive,
+    a 3-cycle tone burst at 500 kHz, 2500 steps of 0.08 us, constant density,
+    a starting model of 1500 m/s, frequency blocks from 300 to 600 kHz with 16
+    shots per iteration drawn without replacement (8 iterations per block).
+
+    ``scale`` > 1 gives the same experiment in scaled units (grid / scale,
+    spacing, step and period x scale): dimensionless, the same physics on a
+    smaller grid.  The tone burst starts after filter_cycles periods of the
+    lowest block frequency, so a zero-phase low-pass of that length sees the
+    whole burst.  ``extra`` holds freqs, schedule, mask (update region: the
+    disk 5 points inside the ring) and filter_cycles."""
+    s = float(scale)
+    shp = tuple(int(round(n / s)) for n in shape)
+    dx, dt, f0 = dx * s, dt * s, f0 / s
+    freqs = tuple(f / s for f in freqs)
+    nt = int(round(nt / s))
+    base = breast_problem(shp, dx, nt, nelem=nelem, shots=np.arange(nelem), order=order, nb=nb,
+                          seed=seed, f0=f0, c_max=1600.0)
+    t0 = filter_cycles / min(freqs)
+    w = tone_burst(f0, dt, nt, t0=t0)
+    wav = np.broadcast_to(w, (nelem, 1, nt)).copy()
+    ny, nx = shp
+    ctr = ((ny / 2) * dx, (nx / 2) * dx)
+    ring_r = float(np.hypot(*(base.rec_xyz[0] - np.array(ctr))))
+    mask = disk_mask(shp, dx, ctr, ring_r - 5 * dx)
+    sched = shot_schedule(nelem, per_iter, len(freqs), schedule_seed)
+    return Problem("inversion_2d", shp, dx, dt, nt, order, nb, np.full(shp, float(c_start)),
+                   None, base.src_xyz, base.rec_xyz, wav, c_ref=1600.0, vp_true=base.vp,
+                   extra={"freqs": freqs, "schedule": sched, "mask": mask,
+                          "filter_cycles": float(filter_cycles)})

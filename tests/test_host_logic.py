@@ -75,3 +75,33 @@ def test_autotune_problem_classes():
     assert k1 == k2 and k1 != k3
     assert autotune.problem_key((256, 256, 256), 10, True, True, 1).startswith("3d-o10-vd-grad")
     assert all(5 <= c["tile"] <= 12 for c in autotune.CANDIDATES_3D)   # TMA-staged 3D variants
+
+
+def test_shot_schedule_uses_every_shot_once_per_block():
+    s = inputs.shot_schedule(128, 16, 4, seed=7)
+    assert len(s) == 4 and all(len(b) == 8 for b in s)
+    for b in s:
+        ids = np.concatenate(b)
+        assert sorted(ids.tolist()) == list(range(128))
+    assert not np.array_equal(np.concatenate(s[0]), np.concatenate(s[1]))
+    again = inputs.shot_schedule(128, 16, 4, seed=7)
+    assert all(np.array_equal(x, y) for bx, by in zip(s, again) for x, y in zip(bx, by))
+    ragged = inputs.shot_schedule(10, 4, 1, seed=1)[0]
+    assert [len(x) for x in ragged] == [4, 4, 2]
+
+
+def test_inversion_workload_matches_the_paper_setup():
+    p = inputs.config_inversion_2d()
+    assert p.shape == (456, 485) and p.spacing == 0.5e-3 and p.nt == 2500
+    assert p.dt == pytest.approx(0.08e-6) and p.rho is None
+    assert p.nshots == 128 and p.rec_xyz.shape == (128, 2)
+    assert np.all(p.vp == 1500.0) and p.vp_true.min() >= 1400.0
+    assert 0.25 < 1600.0 * p.dt / p.spacing < 0.27                   # CFL 0.26 of Sec. 3.2
+    assert p.extra["freqs"] == (300e3, 400e3, 500e3, 600e3)
+    w = p.wavelet[0, 0]
+    on = np.nonzero(w)[0]
+    assert on[0] * p.dt >= 3.0 / 300e3 - p.dt                        # burst after the filter reach
+    assert (on[-1] - on[0]) * p.dt == pytest.approx(3 / 500e3, abs=3 * p.dt)   # 3 cycles
+    small = inputs.config_inversion_2d(scale=4)
+    assert small.shape == (114, 121) and small.dt == pytest.approx(0.32e-6)
+    assert small.extra["mask"].max() == 1.0 and small.extra["mask"][0, 0] == 0.0
