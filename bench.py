@@ -39,6 +39,8 @@ WORKLOADS = {
     "skull3d": "3D skull phantom 256^3, dx=0.25 mm, vd, o10, 32 shots x 2000 steps, 512 receivers",
     "uneven": "64 independent 2D problems, side U{256..1024}, 500-4000 steps, 1-16 shots, vd, o8 (forward)",
     "serving": "Poisson stream (20 req/s) of forward/gradient requests, 75% 2D 512^2-1024^2, 25% 3D 128^3-192^3, 1000-3000 steps",
+    "invert": "Sec. 3.2 2D breast imaging: 456x485 at 0.5 mm, 128 ring transducers, 3-cycle 500 kHz tone burst, "
+              "2500 steps of 0.08 us, cd, o8; 4 frequency blocks 300-600 kHz x 8 iterations x 16 random shots",
 }
 
 
@@ -62,6 +64,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving samples")
     ap.add_argument("--nprob", type=int, default=0, help="uneven: problems (default 64)")
     ap.add_argument("--nreq", type=int, default=0, help="serving: requests (default 650)")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="invert: the experiment in scaled units (grid / scale)")
     return ap.parse_args()
 
 
@@ -594,10 +598,101 @@ def run_mine(args):
     return 0
 
 
+# ---------------------------------------------------------------- inversion loop
+
+def inversion_run(scale=1.0, step=10.0, blocks=None):
+    """The imaging experiment of Sec. 3.2 through invert.Inversion: frequency
+    blocks, 16 random shots per iteration (each shot once per block), one
+    normalised gradient-descent step per iteration.  Observed data come from
+    the same solver on the true phantom.  Reports the loop's wall time (every
+    iteration: two low-pass launches, the gradient of 16 shots, the update),
+    its throughput and the error to the true model (epsilon of Sec. 3.2)."""
+    import torch
+    from paper_2110_03345_gb300 import binding, inputs, invert
+    p = inputs.config_inversion_2d(scale=scale)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def f32(a):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+
+    plan = binding.Plan(p.shape, p.spacing, p.nt, p.dt, order=p.order, sponge=p.nb, c_ref=p.c_ref)
+    geo = binding.Geometry(p.src_xyz, p.rec_xyz)
+    wav = f32(p.wavelet)
+    obs = plan.forward(f32(p.vp_true), None, geo, wav)
+    freqs = tuple(p.extra["freqs"]) if blocks is None else tuple(p.extra["freqs"][:blocks])
+    sched = p.extra["schedule"][:len(freqs)]
+    per_iter = max(len(ids) for b in sched for ids in b)
+    run = invert.Inversion(plan, p.src_xyz, p.rec_xyz, wav, obs, mask=f32(p.extra["mask"]),
+                           bounds=(1400.0, 1600.0), filter_cycles=p.extra["filter_cycles"],
+                           max_shots=per_iter)
+    run.iterate(f32(p.vp), sched[0][0], freqs[0], step)          # warm-up on a copy
+    per_call = []                                                  # kernels of each gradient call
+    vp = f32(p.vp)
+    rec = run.run(vp, freqs, sched, step,
+                  callback=lambda b, i, J: per_call.append(plan.stats()["launches"]))
+    iters = sum(len(b) for b in sched)
+    launches = sum(per_call) + 4 * iters                           # + 2 low-pass, 2 update kernels
+    vp_h = vp.cpu().numpy().astype(np.float64)
+    region = p.extra["mask"] > 0
+
+    def eps(v, where=None):
+        d = np.abs(v - p.vp_true)
+        return float(d[where].mean() if where is not None else d.mean())
+
+    # device time of the loop's own kernels, for one iteration of the first block
+    st = plan.stream
+    M = invert.half_width(freqs[0], p.dt, p.extra["filter_cycles"])
+    ids = sched[0][0]
+    out = torch.empty((len(ids),) + tuple(obs.shape[1:]), device=dev, dtype=torch.float32)
+    vp_t = f32(p.vp)
+    work = torch.empty(1, device=dev, dtype=torch.float32)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    with torch.cuda.stream(st):
+        e[0].record(st)
+        for _ in range(5):
+            binding.lowpass(obs, ids, p.dt, freqs[0], M, out=out, stream=st)
+        e[1].record(st)
+        for _ in range(5):
+            binding.vp_update(vp_t, run.grad, step, 1400.0, 1600.0, work=work, stream=st)
+        e[2].record(st)
+    st.synchronize()
+    lp_ms, up_ms = e[0].elapsed_time(e[1]) / 5, e[1].elapsed_time(e[2]) / 5
+    lp_bytes = 2 * 4 * out.numel()
+    plan.close()
+    return {"grid": list(p.shape), "nt": p.nt, "shots": p.nshots, "blocks_khz": [f / 1e3 for f in freqs],
+            "iterations": iters, "shots_per_iteration": per_iter, "step_m_per_s": step,
+            "seconds": rec.seconds, "shot_gradients": rec.shot_gradients,
+            "shot_gradients_per_s": rec.shot_gradients / rec.seconds,
+            "gpts": rec.point_updates / rec.seconds / 1e9,
+            "s_per_iteration": rec.seconds / iters,
+            "epsilon_start": eps(p.vp), "epsilon_final": eps(vp_h),
+            "epsilon_start_in_ring": eps(p.vp, region), "epsilon_final_in_ring": eps(vp_h, region),
+            "misfit_first_iteration_per_block": [Jb[0] for Jb in rec.misfits],
+            "misfit_last_iteration_per_block": [Jb[-1] for Jb in rec.misfits],
+            "lowpass_ms": lp_ms, "lowpass_gbs": lp_bytes / (lp_ms * 1e-3) / 1e9,
+            "update_ms": up_ms, "gpu_launches": int(launches), "scale": scale}
+
+
 def run_extra_workload(args):
     """--workload uneven | serving: one JSON line for that workload alone."""
     import torch
     torch.cuda.set_device(0)
+    if args.workload == "invert":
+        from paper_2110_03345_gb300 import inputs
+        r = inversion_run(scale=args.scale)
+        cpu = None
+        if not args.no_cpu_baseline:
+            p = inputs.config_inversion_2d(scale=args.scale)
+            c = cpu_baseline(p, args.cpu_seconds)
+            per_grad = 2 * p.npoints * (p.nt - 1)
+            cpu = dict(c, value=c["value"] * 1e9 / per_grad, unit="shot gradients/s")
+        line = {"metric": "shot gradients/s in the inversion loop (low-pass, gradient, update)",
+                "value": r["shot_gradients_per_s"], "unit": "shot gradients/s", "n_gpus": 1,
+                "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOADS["invert"], "scale": args.scale},
+                "gpu_launches": r["gpu_launches"], "cpu_baseline": cpu, "inversion": r}
+        print(json.dumps(line))
+        return 0
     if args.workload == "uneven":
         r = uneven_batch(nprob=args.nprob or 64)
         rg = uneven_gradient(nprob=args.nprob or 64)
@@ -619,7 +714,7 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload in ("uneven", "serving"):
+    if args.workload in ("uneven", "serving", "invert"):
         return run_extra_workload(args)
     return run_mine(args)
 

@@ -273,6 +273,54 @@ const char* fwi_last_error(void);
  * FWI_ERR_INVALID_ARG (NULL), FWI_ERR_CUDA (no device). */
 fwi_status fwi_mem_available(size_t* bytes);
 
+/* ------------------------------------------------------------------------
+ * The inversion loop around the gradient (Sec. 2.3: a gradient-descent
+ * optimiser steps the model after each gradient; Sec. 3.2: blocks of
+ * increasing frequency, each iteration on a random subset of the shots, the
+ * wavelets and traces processed for the block's upper frequency).  The loop
+ * itself is host code; these are its two device steps besides fwi_gradient.
+ * ------------------------------------------------------------------------ */
+
+#define FWI_LOWPASS_MAX_HALF_WIDTH 2048
+
+/* Zero-phase low-pass of rows of samples, gathered by shot: the processing
+ * of wavelets and observed traces for a frequency block with upper
+ * frequency f_max.
+ *   out[i][r][n] = sum_{j=-M}^{M} h_j in[ids[i]][r][n - j], in = 0 outside
+ *   0 <= n < nt, with h_j proportional to sinc(2 f_max dt j) times the Hann
+ *   window 0.5 (1 + cos(pi j / (M + 1))), scaled so that sum_j h_j = 1
+ *   (gain 1 at zero frequency, 1/2 at f_max; M >= 3 / (f_max dt) keeps the
+ *   pass band below 0.7 f_max within 1% and the stop band above 1.5 f_max
+ *   below 0.25%).
+ *   in:  device [n_in][rows][nt] (wavelets: rows = nsrc; traces: rows = nrec).
+ *   ids: host [n_ids], each in [0, n_in); repeats allowed.
+ *   out: device [n_ids][rows][nt], must not overlap in.
+ *   half_width M in [0, FWI_LOWPASS_MAX_HALF_WIDTH] (0 copies the rows).
+ * Enqueued on `stream` (a cudaStream_t, NULL = legacy default stream); no
+ * synchronisation.  The taps are evaluated in FP32 on the device and the
+ * sums accumulate in FP32 in the order j = -M..M.  Errors:
+ * FWI_ERR_INVALID_ARG (sizes, NULL arrays, ids, half_width, dt or f_max not
+ * positive, overlap, rows > 65535), FWI_ERR_CUDA. */
+fwi_status fwi_lowpass(const float* in, int n_in, int rows, int nt, const int* ids, int n_ids,
+                       double dt, double f_max, int half_width, float* out, void* stream);
+
+/* One gradient-descent step on the sound speed (Sec. 2.3), normalised so
+ * that the largest change of any point is `step`:
+ *   d_i = mask_i * (-2 grad_m_i / vp_i^3)     (dJ/dvp from dJ/dm, m = 1/vp^2)
+ *   s = max_i |d_i|
+ *   vp_i <- min(max(vp_i - step * d_i / s, vp_min), vp_max)
+ * vp is left unchanged when s = 0; when any d_i is Inf or NaN every vp_i
+ * becomes NaN (the next propagation then reports FWI_ERR_NONFINITE).
+ *   vp:     device [n] in/out, positive.
+ *   grad_m: device [n], dJ/dm as written by fwi_gradient.
+ *   mask:   device [n] weights (0 freezes a point) or NULL for all ones.
+ *   work:   device scratch of at least 4 bytes (overwritten).
+ * Enqueued on `stream`; no synchronisation.  FP32; the maximum is exact and
+ * independent of scheduling.  Errors: FWI_ERR_INVALID_ARG (n < 0, NULL
+ * arrays, step < 0 or not finite, vp_min > vp_max), FWI_ERR_CUDA. */
+fwi_status fwi_vp_update(float* vp, const float* grad_m, const float* mask, long long n,
+                         float step, float vp_min, float vp_max, float* work, void* stream);
+
 /* Leapfrog stability limit of c*dt/h for this order and dimension:
  * 2/sqrt(ndim * lambda_max), lambda_max = |sum_j (-1)^j w2_j| of the
  * second-derivative stencil.  Returns a negative value for bad input. */

@@ -8,5 +8,6 @@ Submodules:
   serve        serving loop: requests admitted onto concurrent streams by HBM budget
   autotune     kernel variant and shots-per-CTA tuner (single problems and batches)
   distributed  shot sharding and the gradient sum over ranks
+  invert       the inversion loop: frequency blocks, shot subsets, gradient descent
 """
-__all__ = ["inputs", "binding", "build", "autograd", "serve", "autotune", "distributed"]
+__all__ = ["inputs", "binding", "build", "autograd", "serve", "autotune", "distributed", "invert"]

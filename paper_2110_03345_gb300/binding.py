@@ -28,7 +28,7 @@ EXPORTS = ("fwi_plan_create", "fwi_plan_set_options", "fwi_plan_stats", "fwi_pla
            "fwi_plan_destroy", "fwi_forward", "fwi_gradient", "fwi_last_error", "fwi_cfl_limit",
            "fwi_forward_noalloc", "fwi_misfit_forward", "fwi_misfit_backward",
            "fwi_batch_create", "fwi_batch_run", "fwi_batch_stats_get", "fwi_batch_destroy",
-           "fwi_mem_available")
+           "fwi_mem_available", "fwi_lowpass", "fwi_vp_update")
 
 
 class FwiError(RuntimeError):
@@ -133,6 +133,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.fwi_batch_create.restype = ctypes.c_int
         lib.fwi_mem_available.argtypes = [P(ctypes.c_size_t)]
         lib.fwi_mem_available.restype = ctypes.c_int
+        lib.fwi_lowpass.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_int),
+                                    ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                    vp, vp]
+        lib.fwi_lowpass.restype = ctypes.c_int
+        lib.fwi_vp_update.argtypes = [vp, vp, vp, ctypes.c_longlong, ctypes.c_float,
+                                      ctypes.c_float, ctypes.c_float, vp, vp]
+        lib.fwi_vp_update.restype = ctypes.c_int
         lib.fwi_batch_run.argtypes = [vp]
         lib.fwi_batch_run.restype = ctypes.c_int
         lib.fwi_batch_stats_get.argtypes = [vp, P(CBatchStats)]
@@ -192,6 +199,48 @@ def forward_noalloc(shape, spacing, nt, dt, vp, rho, geometry, wavelet, traces=N
                                       ctypes.byref(geometry.c), _ptr(wavelet), _ptr(traces),
                                       ctypes.c_void_p(stream.cuda_stream)))
     return traces
+
+
+LOWPASS_MAX_HALF_WIDTH = 2048
+
+
+def lowpass(x, ids, dt, f_max, half_width, out=None, stream=None):
+    """fwi_lowpass: out[i] = zero-phase low-pass (cut-off f_max, half-width
+    `half_width` samples) of x[ids[i]] along the last axis.  x: CUDA float32
+    [n][rows][nt]; ids: host integers; out: [len(ids)][rows][nt] or None."""
+    import torch
+    if x.dim() != 3:
+        raise ValueError("x must be [n][rows][nt]")
+    ids = np.ascontiguousarray(np.asarray(ids, dtype=np.int64).reshape(-1)).astype(np.int32)
+    n, rows, nt = (int(v) for v in x.shape)
+    if out is None:
+        out = torch.empty((len(ids), rows, nt), device=x.device, dtype=torch.float32)
+    if tuple(out.shape) != (len(ids), rows, nt):
+        raise ValueError("out must be [len(ids)][rows][nt]")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(load().fwi_lowpass(_ptr(x), n, rows, nt,
+                              ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(ids),
+                              float(dt), float(f_max), int(half_width), _ptr(out),
+                              ctypes.c_void_p(stream.cuda_stream)))
+    return out
+
+
+def vp_update(vp, grad_m, step, vp_min, vp_max, mask=None, work=None, stream=None):
+    """fwi_vp_update: one normalised gradient-descent step on vp (in place):
+    the largest change is `step`, restricted to `mask`, clipped to
+    [vp_min, vp_max].  work: a CUDA float32 tensor of >= 1 element or None."""
+    import torch
+    if grad_m.numel() != vp.numel() or (mask is not None and mask.numel() != vp.numel()):
+        raise ValueError("vp, grad_m and mask must have the same size")
+    if work is None:
+        work = torch.empty(1, device=vp.device, dtype=torch.float32)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(load().fwi_vp_update(_ptr(vp), _ptr(grad_m), _ptr(mask), int(vp.numel()),
+                                float(step), float(vp_min), float(vp_max), _ptr(work),
+                                ctypes.c_void_p(stream.cuda_stream)))
+    return vp
 
 
 def _ptr(t):
