@@ -129,11 +129,13 @@ def _smooth(a, sigma_pts):
     return gaussian_filter(a, sigma_pts, mode="nearest")
 
 
-def breast_model_2d(n: int, dx: float, seed: int, scale: float = 1.0):
+def breast_model_2d(n: int, dx: float, seed: int, scale: float = 1.0, fat_vp=(1430.0, 1470.0),
+                    incl_vp=(1400.0, 1600.0)):
     """Breast-like 2D slice: water (1500 m/s, 1000 kg/m^3); an ellipse of fatty
-    tissue (semi-axes ~35-40 mm x scale) holding 20-40 random inclusions with
-    c ~ U[1400, 1600], rho ~ U[950, 1100]; smoothed noise of std 5 m/s;
-    clipped to [1400, 1600] / [950, 1100].  Returns (vp, rho)."""
+    tissue (semi-axes ~35-40 mm x scale, c ~ U[fat_vp]) holding 20-40 random
+    inclusions with c ~ U[incl_vp] (default [1400, 1600]), rho ~ U[950, 1100];
+    smoothed noise of std 5 m/s; clipped to [1400, 1600] / [950, 1100].
+    Returns (vp, rho)."""
     rng = np.random.default_rng(seed)
     y = (np.arange(n) + 0.5 - n / 2) * dx
     Y, X = np.meshgrid(y, y, indexing="ij")
@@ -141,7 +143,7 @@ def breast_model_2d(n: int, dx: float, seed: int, scale: float = 1.0):
     rho = np.full((n, n), 1000.0)
     ay, ax = rng.uniform(35e-3, 40e-3, 2) * scale
     breast = _ellipse_mask(Y, X, 0.0, 0.0, ay, ax, rng.uniform(0, np.pi))
-    vp[breast] = rng.uniform(1430, 1470)
+    vp[breast] = rng.uniform(*fat_vp)
     rho[breast] = rng.uniform(950, 980)
     for _ in range(int(rng.integers(20, 41))):
         r = math.sqrt(rng.uniform(0.0, 1.0)) * 0.8
@@ -149,7 +151,7 @@ def breast_model_2d(n: int, dx: float, seed: int, scale: float = 1.0):
         cy, cx = r * ay * math.sin(ang), r * ax * math.cos(ang)
         sy, sx = rng.uniform(2e-3, 15e-3, 2) * scale
         m = _ellipse_mask(Y, X, cy, cx, sy, sx, rng.uniform(0, np.pi)) & breast
-        vp[m] = rng.uniform(1400, 1600)
+        vp[m] = rng.uniform(*incl_vp)
         rho[m] = rng.uniform(950, 1100)
     noise = _smooth(rng.standard_normal((n, n)), 0.5e-3 / dx)
     noise *= 5.0 / max(noise.std(), 1e-12)
@@ -176,7 +178,8 @@ def gaussian_blobs(shape, dx, seed, n=3, amp=20.0, sigma=3e-3, extent=0.3):
 
 
 def breast_problem(shape, dx, nt, nelem=256, shots=None, order=8, nb=20, seed=2, f0=500e3,
-                   c_max=1600.0, radius=None, perturb_seed=20):
+                   c_max=1600.0, radius=None, perturb_seed=20, fat_vp=(1430.0, 1470.0),
+                   incl_vp=(1400.0, 1600.0)):
     """Breast-like 2D problem on a (possibly non-square) grid: the phantom of
     ``breast_model_2d`` scaled to the smaller side and centre-cropped, a ring of
     ``nelem`` elements about the centre (default radius: 0.4395 x the smaller
@@ -186,7 +189,7 @@ def breast_problem(shape, dx, nt, nelem=256, shots=None, order=8, nb=20, seed=2,
     ny, nx = (int(s) for s in shape)
     m, full = min(ny, nx), max(ny, nx)
     scale = m * dx / (1024 * 0.1e-3)
-    vpf, rhof = breast_model_2d(full, dx, seed, scale=scale)
+    vpf, rhof = breast_model_2d(full, dx, seed, scale=scale, fat_vp=fat_vp, incl_vp=incl_vp)
     oy, ox = (full - ny) // 2, (full - nx) // 2
     vp = vpf[oy:oy + ny, ox:ox + nx].copy()
     rho = rhof[oy:oy + ny, ox:ox + nx].copy()
@@ -382,26 +385,34 @@ def disk_mask(shape, dx, centre, radius):
 def config_inversion_2d(scale: float = 1.0, shape=(456, 485), dx=0.5e-3, dt=0.08e-6, nt=2500,
                         nelem=128, f0=500e3, freqs=(300e3, 400e3, 500e3, 600e3), per_iter=16,
                         c_start=1500.0, order=8, nb=20, seed=2, schedule_seed=7,
-                        filter_cycles=3.0):
+                        filter_cycles=3.0, fat_vp=(1480.0, 1495.0), incl_vp=(1440.0, 1560.0)):
     """The 2D breast imaging experiment of Sec. 3.2 with a synthetic phantom:
     456 x 485 grid at 0.5 mm, 128 ring transducers that all fire and receive,
     a 3-cycle tone burst at 500 kHz, 2500 steps of 0.08 us, constant density,
     a starting model of 1500 m/s, frequency blocks from 300 to 600 kHz with 16
     shots per iteration drawn without replacement (8 iterations per block).
 
-    ``scale`` > 1 gives the same experiment in scaled units (grid / scale,
-    spacing, step and period x scale): dimensionless, the same physics on a
-    smaller grid.  The tone burst starts after filter_cycles periods of the
-    lowest block frequency, so a zero-phase low-pass of that length sees the
-    whole burst.  ``extra`` holds freqs, schedule, mask (update region: the
-    disk 5 points inside the ring) and filter_cycles."""
+    The phantom is ``breast_problem``'s with fatty tissue at U[fat_vp] =
+    U[1480, 1495] m/s and inclusions at U[incl_vp] = U[1440, 1560] m/s, so
+    that travel times through the breast from the 1500 m/s start stay within
+    about half a period of the first (300 kHz) block, as the paper's start
+    must have been for its first block to converge.
+
+    ``scale`` > 1 keeps the domain and the phantom and divides the grid and
+    the frequencies by `scale` (spacing, step and period x scale): the same
+    points per wavelength and CFL number on a smaller grid, with the phantom
+    `scale` times fewer wavelengths across (an easier, cheaper inversion).
+    The tone burst starts after filter_cycles periods of the lowest block
+    frequency, so a zero-phase low-pass of that length sees the whole burst.
+    ``extra`` holds freqs, schedule, mask (update region: the disk 5 points
+    inside the ring) and filter_cycles."""
     s = float(scale)
     shp = tuple(int(round(n / s)) for n in shape)
     dx, dt, f0 = dx * s, dt * s, f0 / s
     freqs = tuple(f / s for f in freqs)
     nt = int(round(nt / s))
     base = breast_problem(shp, dx, nt, nelem=nelem, shots=np.arange(nelem), order=order, nb=nb,
-                          seed=seed, f0=f0, c_max=1600.0)
+                          seed=seed, f0=f0, c_max=1600.0, fat_vp=fat_vp, incl_vp=incl_vp)
     t0 = filter_cycles / min(freqs)
     w = tone_burst(f0, dt, nt, t0=t0)
     wav = np.broadcast_to(w, (nelem, 1, nt)).copy()
