@@ -74,3 +74,29 @@ def test_no_cpu_fallback_without_a_gpu():
     status = lib.fwi_plan_create(ctypes.byref(plan), ctypes.byref(g), 20, 1e-7, 0, None)
     assert status == 4   # FWI_ERR_CUDA: no device
     assert len(lib.fwi_last_error()) > 0
+
+
+def test_inversion_entry_points_validate_on_the_host():
+    """fwi_lowpass and fwi_vp_update reject bad arguments before any device
+    work (so these calls need no GPU), and an empty request is a no-op."""
+    lib = binding.load()
+    P = ctypes.POINTER(ctypes.c_int)
+    ids = (ctypes.c_int * 2)(0, 3)
+    fake_in, fake_out = ctypes.c_void_p(0x10000), ctypes.c_void_p(0x90000)
+    lp = lib.fwi_lowpass
+    assert lp(fake_in, 2, 1, 100, ids, 0, 1e-7, 1e6, 8, fake_out, None) == 0      # no ids
+    assert lp(fake_in, 2, 1, 100, ids, -1, 1e-7, 1e6, 8, fake_out, None) == 1
+    assert lp(None, 2, 1, 100, ids, 1, 1e-7, 1e6, 8, fake_out, None) == 1
+    assert lp(fake_in, 2, 1, 100, ids, 2, 1e-7, 1e6, 8, fake_out, None) == 1       # id 3 >= n_in
+    assert b"outside" in lib.fwi_last_error()
+    assert lp(fake_in, 4, 1, 100, ids, 2, 1e-7, 1e6, 2049, fake_out, None) == 1    # half-width
+    assert lp(fake_in, 4, 1, 100, ids, 2, 0.0, 1e6, 8, fake_out, None) == 1        # dt
+    assert lp(fake_in, 4, 1, 100, ids, 2, 1e-7, 1e6, 8, fake_in, None) == 1        # overlap
+    assert lp(fake_in, 4, 70000, 100, ids, 2, 1e-7, 1e6, 8, fake_out, None) == 1   # rows
+    up = lib.fwi_vp_update
+    assert up(fake_in, fake_in, None, 0, 1.0, 1.0, 2.0, fake_out, None) == 0       # n = 0
+    assert up(fake_in, fake_in, None, -5, 1.0, 1.0, 2.0, fake_out, None) == 1
+    assert up(None, fake_in, None, 5, 1.0, 1.0, 2.0, fake_out, None) == 1
+    assert up(fake_in, fake_in, None, 5, -1.0, 1.0, 2.0, fake_out, None) == 1      # step < 0
+    assert up(fake_in, fake_in, None, 5, 1.0, 2.0, 1.0, fake_out, None) == 1       # bounds
+    assert up(fake_in, fake_in, None, 5, float("nan"), 1.0, 2.0, fake_out, None) == 1

@@ -90,18 +90,46 @@ def test_shot_schedule_uses_every_shot_once_per_block():
     assert [len(x) for x in ragged] == [4, 4, 2]
 
 
+def _golden(name):
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    return {r[0]: [float(v) for v in r[1:]] for r in rows}
+
+
 def test_inversion_workload_matches_the_paper_setup():
+    """The Sec. 3.2 values in tests/golden/paper_sec32_setup.txt."""
+    ref = _golden("paper_sec32_setup.txt")
     p = inputs.config_inversion_2d()
-    assert p.shape == (456, 485) and p.spacing == 0.5e-3 and p.nt == 2500
-    assert p.dt == pytest.approx(0.08e-6) and p.rho is None
-    assert p.nshots == 128 and p.rec_xyz.shape == (128, 2)
-    assert np.all(p.vp == 1500.0) and p.vp_true.min() >= 1400.0
-    assert 0.25 < 1600.0 * p.dt / p.spacing < 0.27                   # CFL 0.26 of Sec. 3.2
-    assert p.extra["freqs"] == (300e3, 400e3, 500e3, 600e3)
+    assert list(p.shape) == [int(v) for v in ref["grid"]] and p.spacing == ref["dx_m"][0]
+    assert p.dt == pytest.approx(ref["dt_s"][0]) and p.rho is None
+    assert p.nt * p.dt == pytest.approx(ref["duration_s"][0])
+    assert p.nshots == ref["transducers"][0] and p.rec_xyz.shape == (ref["transducers"][0], 2)
+    np.testing.assert_allclose(p.src_xyz[:, 0, :], p.rec_xyz)        # every transducer fires
+    assert np.all(p.vp == ref["start_vp"][0]) and p.vp_true.min() >= 1400.0
+    cfl = p.vp_true.max() * p.dt / p.spacing
+    assert cfl <= ref["cfl_max"][0] + 5e-3 and cfl > ref["cfl_max"][0] - 0.02
+    f = p.extra["freqs"]
+    assert f[0] == ref["f_first_hz"][0] and f[-1] == ref["f_last_hz"][0]
+    assert all(len(b) == ref["iterations"][0] for b in p.extra["schedule"])
+    assert all(len(i) == ref["shots_per_iter"][0] for b in p.extra["schedule"] for i in b)
     w = p.wavelet[0, 0]
     on = np.nonzero(w)[0]
-    assert on[0] * p.dt >= 3.0 / 300e3 - p.dt                        # burst after the filter reach
-    assert (on[-1] - on[0]) * p.dt == pytest.approx(3 / 500e3, abs=3 * p.dt)   # 3 cycles
+    assert on[0] * p.dt >= 3.0 / f[0] - p.dt                          # burst after the filter reach
+    T = ref["burst_cycles"][0] / ref["burst_hz"][0]
+    assert (on[-1] - on[0]) * p.dt == pytest.approx(T, abs=3 * p.dt)
+    spec = np.abs(np.fft.rfft(w, 1 << 16))
+    fr = np.fft.rfftfreq(1 << 16, p.dt)
+    assert fr[np.argmax(spec)] == pytest.approx(ref["burst_hz"][0], rel=0.05)   # centred at 500 kHz
     small = inputs.config_inversion_2d(scale=4)
     assert small.shape == (114, 121) and small.dt == pytest.approx(0.32e-6)
     assert small.extra["mask"].max() == 1.0 and small.extra["mask"][0, 0] == 0.0
+
+
+def test_inversion_filter_half_width():
+    from paper_2110_03345_gb300 import invert
+    assert invert.half_width(300e3, 0.08e-6) == 125                 # 3 periods of 300 kHz
+    assert invert.half_width(600e3, 0.08e-6) == 63
+    assert invert.half_width(300e3, 0.08e-6, cycles=1.0) == 42
+    with pytest.raises(ValueError):
+        invert.half_width(1e3, 0.08e-6)                            # beyond the kernel's 2048
