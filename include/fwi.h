@@ -127,7 +127,9 @@ typedef struct {
  * The plan holds the device workspace, allocated on first use and kept
  * within hbm_budget_bytes (0: 90% of the free device memory at creation).
  * stream: a cudaStream_t (NULL = legacy default stream) the plan enqueues on.
- * Errors: FWI_ERR_INVALID_ARG for a bad grid, nt < 1 or dt <= 0. */
+ * Errors: FWI_ERR_INVALID_ARG for a bad grid (including one whose padded
+ * field would hold 2^31 floats or more: in-field offsets are 32-bit), nt < 1
+ * or dt <= 0. */
 fwi_status fwi_plan_create(fwi_plan** plan, const fwi_grid* grid, int nt, double dt,
                            size_t hbm_budget_bytes, void* stream);
 

@@ -344,6 +344,18 @@ double cfl_limit(int ndim, int order) {
   return 2.0 / std::sqrt(ndim * lam);
 }
 
+// Floats per padded field of a grid: the layout build_layout gives it (x
+// padded by OX and rounded to TILE_X plus 8, y by R each side and rounded to
+// ROUND_Y, z by R each side, the field rounded to 64 floats).
+long long padded_field_floats(const fwi_grid* g) {
+  const long long R = g->order / 2;
+  const long long nx = g->shape[g->ndim - 1], ny = g->shape[g->ndim - 2];
+  const long long sx = OX + (nx + TILE_X - 1) / TILE_X * TILE_X + 8;
+  const long long rows = R + (ny + ROUND_Y - 1) / ROUND_Y * ROUND_Y + R;
+  const long long planes = g->ndim == 3 ? g->shape[0] + 2 * R : 1;
+  return (sx * rows * planes + 63) / 64 * 64;
+}
+
 fwi_status validate_grid(const fwi_grid* g) {
   if (!g) return fail(FWI_ERR_INVALID_ARG, "grid is NULL");
   if (g->ndim != 2 && g->ndim != 3) return fail(FWI_ERR_INVALID_ARG, "ndim must be 2 or 3");
@@ -356,9 +368,10 @@ fwi_status validate_grid(const fwi_grid* g) {
     if (g->sponge < 0 || 2 * (int64_t)g->sponge >= g->shape[d])
       return fail(FWI_ERR_INVALID_ARG, "sponge must be >= 0 and < shape/2");
   }
-  long long N = 1;
-  for (int d = 0; d < g->ndim; ++d) N *= g->shape[d];
-  if (N > (1LL << 34)) return fail(FWI_ERR_INVALID_ARG, "grid too large");
+  // In-field offsets (receiver sampling tables, tile-local arithmetic) are
+  // 32-bit: a padded field must hold fewer than 2^31 floats.
+  if (padded_field_floats(g) > 0x7fffffffLL)
+    return fail(FWI_ERR_INVALID_ARG, "grid too large: a padded field exceeds 2^31 - 1 floats");
   return FWI_OK;
 }
 
@@ -396,7 +409,7 @@ void build_layout(fwi_plan* P) {
   L.oz = (g.ndim == 3) ? P->R : 0;
   L.planes = (g.ndim == 3) ? L.oz + L.nz + P->R : 1;
   L.sxy = (long long)L.sx * L.rows;
-  L.fstride = (long long)align_up((size_t)(L.sxy * L.planes), 64);
+  L.fstride = (long long)align_up((size_t)(L.sxy * L.planes), 64);   // = padded_field_floats
   double w2[6], w1[6];
   fd_weights(g.order, w2, w1);
   AxisW* W[3] = {&P->wx, &P->wy, &P->wz};

@@ -100,3 +100,21 @@ def test_inversion_entry_points_validate_on_the_host():
     assert up(fake_in, fake_in, None, 5, -1.0, 1.0, 2.0, fake_out, None) == 1      # step < 0
     assert up(fake_in, fake_in, None, 5, 1.0, 2.0, 1.0, fake_out, None) == 1       # bounds
     assert up(fake_in, fake_in, None, 5, float("nan"), 1.0, 2.0, fake_out, None) == 1
+
+
+def test_grids_beyond_32_bit_field_offsets_are_rejected_on_the_host():
+    """A padded field must hold fewer than 2^31 floats (in-field offsets are
+    32-bit); larger grids fail with FWI_ERR_INVALID_ARG before any device call."""
+    lib = binding.load()
+    for shape in [(1300, 1300, 1300), (1 << 20, 4096), (40000, 60000)]:
+        plan = ctypes.c_void_p()
+        g = binding.make_grid(shape, 1e-3, 8, 8, 1500.0)
+        assert lib.fwi_plan_create(ctypes.byref(plan), ctypes.byref(g), 20, 1e-7, 0, None) == 1
+        assert b"2^31" in lib.fwi_last_error()
+    for shape in [(1200, 1200, 1200), (20000, 20000)]:              # below the limit
+        plan = ctypes.c_void_p()
+        g = binding.make_grid(shape, 1e-3, 8, 8, 1500.0)
+        st = lib.fwi_plan_create(ctypes.byref(plan), ctypes.byref(g), 20, 1e-7, 0, None)
+        assert st != 1, lib.fwi_last_error()
+        if st == 0:
+            lib.fwi_plan_destroy(plan)
