@@ -73,7 +73,9 @@ typedef struct {
 
 /* Acquisition geometry (Sec. 2.3 Listings 7-8): nshots shots, each with nsrc
  * point sources; nrec receivers shared by every shot.  Points must lie inside
- * the grid: 0 <= x_d <= (shape[d]-1)*spacing[d]. */
+ * the grid: 0 <= x_d <= (shape[d]-1)*spacing[d].  The wavelet and trace
+ * arrays of one call must each hold fewer than 2^31 samples
+ * (nshots*nsrc*nt, nshots*nrec*nt); larger requests are split over calls. */
 typedef struct {
     int nshots;               /* >= 1 */
     int nsrc;                 /* sources per shot, >= 1 */

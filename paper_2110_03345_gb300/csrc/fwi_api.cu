@@ -456,6 +456,11 @@ fwi_status validate_geometry(const fwi_plan* P, const fwi_geometry* g) {
   if (!g->src_xyz || !g->rec_xyz) return fail(FWI_ERR_INVALID_ARG, "coordinates are NULL");
   if ((long long)g->nshots * g->nsrc > (1LL << 24) || g->nrec > (1 << 24))
     return fail(FWI_ERR_INVALID_ARG, "too many sources or receivers");
+  // wavelet and trace samples are addressed with 32-bit indices
+  if ((long long)g->nshots * g->nsrc * P->nt > 0x7fffffffLL ||
+      (long long)g->nshots * g->nrec * P->nt > 0x7fffffffLL)
+    return fail(FWI_ERR_INVALID_ARG,
+                "the wavelet or trace array would hold 2^31 samples or more: split the shots over calls");
   const int nd = P->grid.ndim;
   auto check = [&](const double* p) {
     for (int d = 0; d < nd; ++d) {
