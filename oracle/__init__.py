@@ -19,6 +19,10 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
   apply_L/LT     pinned: smooth analytic fields, operator dot-product test.
   sponge         pinned only by invariants (energy decay, small reflection);
                  the profile itself is a reading of a citation-only passage.
+
+Submodules: ``inversion`` (the inversion loop of Sec. 2.3 / 3.2) and
+``time4`` (a fourth-order-in-time scheme and its gradient), each with its
+own parity status in its header.
 """
 from __future__ import annotations
 
