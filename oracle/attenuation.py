@@ -69,15 +69,16 @@ def _coefficients(grid: Grid, vp, alpha0, y):
     return vp, al, k, a, beta
 
 
-def forward(grid: Grid, vp, rho, alpha0, y, src_xyz, wavelet, rec_xyz, keep=False):
+def forward(grid: Grid, vp, rho, alpha0, y, src_xyz, wavelet, rec_xyz, keep=False, interp=None):
     """Traces [nrec][nt] of one shot (src_xyz [nsrc][ndim], wavelet
     [nsrc][nt]); alpha0 is a scalar or a field (nepers per metre, at unit
-    angular frequency for y = 2).  keep=True also returns u^n, [nt][N]."""
+    angular frequency for y = 2).  keep=True also returns u^n, [nt][N].
+    interp: point weights (None: bi-/tri-linear; see oracle.sinc)."""
     N = grid.npoints
     _, _, k, a, beta = _coefficients(grid, vp, alpha0, y)
     L, _, lap = _ops(grid, rho)
-    S = _source_fields(grid, src_xyz, wavelet)
-    recs = _points(grid, rec_xyz)
+    S = _source_fields(grid, src_xyz, wavelet, interp)
+    recs = _points(grid, rec_xyz, interp)
     traces = np.zeros((len(recs), grid.nt))
     U = np.zeros((grid.nt, N)) if keep else None
     u_prev = np.zeros(N)
@@ -100,7 +101,7 @@ def forward(grid: Grid, vp, rho, alpha0, y, src_xyz, wavelet, rec_xyz, keep=Fals
     return (traces, U) if keep else traces
 
 
-def gradient(grid: Grid, vp, rho, alpha0, y, src_xyz, wavelet, rec_xyz, observed):
+def gradient(grid: Grid, vp, rho, alpha0, y, src_xyz, wavelet, rec_xyz, observed, interp=None):
     """(J, dJ/dm, traces) of one shot by the reverse sweep of the recursion:
     with c = ubar^{n+1} / (1 + a),
         ubar^n     += 2c + L^T(k c) + lap(beta k c) / dt,
@@ -114,9 +115,9 @@ def gradient(grid: Grid, vp, rho, alpha0, y, src_xyz, wavelet, rec_xyz, observed
     dt = grid.dt
     vpf, al, k, a, beta = _coefficients(grid, vp, alpha0, y)
     L, LT, lap = _ops(grid, rho)
-    S = _source_fields(grid, src_xyz, wavelet)
-    recs = _points(grid, rec_xyz)
-    d, U = forward(grid, vp, rho, alpha0, y, src_xyz, wavelet, rec_xyz, keep=True)
+    S = _source_fields(grid, src_xyz, wavelet, interp)
+    recs = _points(grid, rec_xyz, interp)
+    d, U = forward(grid, vp, rho, alpha0, y, src_xyz, wavelet, rec_xyz, keep=True, interp=interp)
     r = d - np.asarray(observed, dtype=np.float64).reshape(d.shape)
     J = 0.5 * float(np.sum(r * r))
 

@@ -1,0 +1,109 @@
+"""Pins for the sinc-interpolation oracle (oracle/sinc.py).
+
+  window         b = 6.31 minimises the largest interpolation error of
+                 cos(k x + phi), k <= pi/2, at r = 4; that error is 1.3e-3
+  2D / 3D        tensor-product weights interpolate band-limited plane waves
+  on-node        an on-node source and receiver give the bilinear result
+  off-grid       a sinc-interpolated off-grid source reproduces, at the
+                 receivers, the same source split over on-node sources with
+                 the same weights (superposition)
+  gradient       exact through the reverse sweep: central differences
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import attenuation as att
+from oracle import sinc
+from paper_2110_03345_gb300 import inputs
+
+
+def max_error(b, r=4, kmax=np.pi / 2):
+    err = 0.0
+    for x in np.linspace(10.0, 11.0, 41):
+        idx, w = sinc.weights_1d(x, r, b)
+        for k in np.linspace(0.0, kmax, 40):
+            for ph in (0.0, 0.7, 1.9):
+                err = max(err, abs(w @ np.cos(k * idx + ph) - np.cos(k * x + ph)))
+    return err
+
+
+def test_window_parameter_is_the_error_minimiser():
+    e = max_error(6.31)
+    assert e < 1.4e-3
+    for b in (5.8, 6.0, 6.6, 6.8):
+        assert max_error(b) > e
+    assert max_error(4.14) > 3 * e                 # a wider band's window is worse here
+
+
+def test_on_node_weights_are_a_single_node():
+    idx, w = sinc.weights_1d(7.0)
+    assert w[idx == 7][0] == pytest.approx(1.0, abs=1e-15)
+    assert np.max(np.abs(w[idx != 7])) < 1e-15
+
+
+@pytest.mark.parametrize("shape,spacing", [((40, 44), (0.5e-3, 0.4e-3)),
+                                           ((20, 22, 24), (0.5e-3, 0.5e-3, 0.45e-3))])
+def test_band_limited_plane_waves_are_interpolated(shape, spacing):
+    g = oracle.Grid(shape, spacing, dt=1e-7, nt=2)
+    rng = np.random.default_rng(2)
+    interp = sinc.hicks()
+    axes = np.meshgrid(*[np.arange(n) * h for n, h in zip(shape, spacing)], indexing="ij")
+    for _ in range(10):
+        kvec = rng.uniform(-np.pi / 2, np.pi / 2, len(shape)) / np.array(spacing)
+        ph = rng.uniform(0, 2 * np.pi)
+        f = np.cos(sum(k * a for k, a in zip(kvec, axes)) + ph)
+        p = np.array([rng.uniform(5, n - 6) * h for n, h in zip(shape, spacing)])
+        idx, w = interp(g, p)
+        assert len(idx) == 8 ** len(shape)
+        assert abs(w @ f.ravel()[idx] - np.cos(kvec @ p + ph)) < 3e-3 * len(shape)
+    with pytest.raises(ValueError):
+        interp(g, np.array([1.0 * spacing[0]] + [10 * h for h in spacing[1:]]))
+
+
+def _problem(seed=0):
+    shape, dx = (40, 44), 0.5e-3
+    vp, rho = inputs.random_smooth_model(shape, dx, seed)
+    dt = 0.4 * dx / vp.max()
+    g = oracle.Grid(shape, dx, dt=dt, nt=120, order=8, nb=6, c_ref=1500.0)
+    w = inputs.ricker(5e5, dt, g.nt)[None, :]
+    return g, vp, rho, w
+
+
+def test_on_node_points_reduce_to_bilinear():
+    g, vp, rho, w = _problem()
+    src = np.array([[20 * 0.5e-3, 17 * 0.5e-3]])
+    rec = np.array([[12 * 0.5e-3, 30 * 0.5e-3], [28 * 0.5e-3, 9 * 0.5e-3]])
+    d_lin = att.forward(g, vp, rho, 0.0, 0, src, w, rec)
+    d_sinc = att.forward(g, vp, rho, 0.0, 0, src, w, rec, interp=sinc.hicks())
+    np.testing.assert_allclose(d_sinc, d_lin, rtol=0, atol=1e-12 * np.abs(d_lin).max())
+
+
+def test_off_grid_source_is_the_weighted_sum_of_on_node_sources():
+    g, vp, rho, w = _problem()
+    interp = sinc.hicks()
+    src = np.array([[20.37 * 0.5e-3, 17.61 * 0.5e-3]])
+    rec = np.array([[12 * 0.5e-3, 30 * 0.5e-3], [28 * 0.5e-3, 9 * 0.5e-3]])
+    d = att.forward(g, vp, rho, 0.0, 0, src, w, rec, interp=interp)
+    idx, wt = interp(g, src[0])
+    nodes = np.array(np.unravel_index(idx, g.shape)).T * 0.5e-3
+    d_sum = att.forward(g, vp, rho, 0.0, 0, nodes, wt[:, None] * w, rec)   # on-node, bilinear
+    np.testing.assert_allclose(d, d_sum, rtol=0, atol=1e-12 * np.abs(d).max())
+
+
+def test_gradient_with_sinc_points_matches_central_differences():
+    g, vp, rho, w = _problem(seed=3)
+    interp = sinc.hicks()
+    src = np.array([[20.37 * 0.5e-3, 17.61 * 0.5e-3]])
+    rec = inputs.random_points(4, g.shape, 0.5e-3, 9, margin=8)
+    obs = att.forward(g, vp * 1.03, rho, 0.0, 0, src, w, rec, interp=interp)
+    J0, grad, _ = att.gradient(g, vp, rho, 0.0, 0, src, w, rec, obs, interp=interp)
+    m = 1.0 / vp ** 2
+    for p in [(20, 18), (12, 27)]:
+        h = 1e-4 * m[p]
+        mp, mm = m.copy(), m.copy()
+        mp[p] += h
+        mm[p] -= h
+        Jp = 0.5 * np.sum((att.forward(g, 1 / np.sqrt(mp), rho, 0.0, 0, src, w, rec, interp=interp) - obs) ** 2)
+        Jm = 0.5 * np.sum((att.forward(g, 1 / np.sqrt(mm), rho, 0.0, 0, src, w, rec, interp=interp) - obs) ** 2)
+        assert (Jp - Jm) / (2 * h) == pytest.approx(grad[p], rel=1e-6, abs=1e-9 * np.abs(grad).max())
