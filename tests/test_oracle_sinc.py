@@ -8,6 +8,9 @@
                  receivers, the same source split over on-node sources with
                  the same weights (superposition)
   gradient       exact through the reverse sweep: central differences
+  physics        an off-grid source and receivers follow the closed-form 2D
+                 Green's function at 4 points per wavelength (sinc 0.3%,
+                 bilinear 9%)
 """
 import numpy as np
 import pytest
@@ -107,3 +110,33 @@ def test_gradient_with_sinc_points_matches_central_differences():
         Jp = 0.5 * np.sum((att.forward(g, 1 / np.sqrt(mp), rho, 0.0, 0, src, w, rec, interp=interp) - obs) ** 2)
         Jm = 0.5 * np.sum((att.forward(g, 1 / np.sqrt(mm), rho, 0.0, 0, src, w, rec, interp=interp) - obs) ** 2)
         assert (Jp - Jm) / (2 * h) == pytest.approx(grad[p], rel=1e-6, abs=1e-9 * np.abs(grad).max())
+
+
+def test_off_grid_accuracy_against_the_analytic_solution():
+    """Homogeneous 2D medium, source and 8 receivers off the grid (9 mm ring),
+    4 points per wavelength at 2.5 x the Ricker's peak frequency, CFL 0.1 (small
+    time error), record ending before boundary echoes: the sinc weights follow
+    the closed-form Green's function (Sec. 3.1) within 0.5%, the bilinear
+    ones are off by ~9%."""
+    c, f0 = 1500.0, 3e5
+    dx = c / (2.5 * f0) / 4
+    n = int(60e-3 / dx)
+    dt = 0.1 * dx / c
+    nt = int(20e-6 / dt)
+    g = oracle.Grid((n, n), dx, dt=dt, nt=nt, order=10, nb=10, c_ref=c)
+    q = inputs.ricker_fn(f0, t0=1.5 / f0)
+    w = q(np.arange(nt) * dt)[None, :]
+    ctr = (n // 2 + 0.5) * dx
+    src = np.array([[ctr, ctr - 0.3 * dx]])
+    R = 9e-3
+    ang = np.linspace(0, 2 * np.pi, 8, endpoint=False)
+    rec = np.stack([ctr + R * np.sin(ang), ctr - 0.3 * dx + R * np.cos(ang)], 1)
+    ana = oracle.analytic_2d(q, R, np.arange(nt) * dt, c)
+    vp = np.full((n, n), c)
+
+    def nrmse(d):
+        return np.sqrt(np.mean((d - ana[None]) ** 2)) / np.sqrt(np.mean(ana ** 2))
+
+    e_lin = nrmse(att.forward(g, vp, None, 0.0, 0, src, w, rec))
+    e_sinc = nrmse(att.forward(g, vp, None, 0.0, 0, src, w, rec, interp=sinc.hicks()))
+    assert e_sinc < 5e-3 and e_lin > 5e-2, (e_sinc, e_lin)     # measured 0.0032, 0.090
