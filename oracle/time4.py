@@ -82,15 +82,17 @@ def _LT(grid, f, rho):
     return apply_LT(grid, f.reshape(grid.shape), rho).reshape(-1)
 
 
-def forward(grid: Grid, vp, rho, src_xyz, wavelet, rec_xyz, correction=True, keep=False):
+def forward(grid: Grid, vp, rho, src_xyz, wavelet, rec_xyz, correction=True, keep=False,
+            interp=None):
     """Traces [nrec][nt] of one shot (src_xyz [nsrc][ndim], wavelet
     [nsrc][nt]); u^0 = u^{-1} = 0, d^n = P u^n.  correction=False drops the
     fourth-order terms (the leapfrog of the C oracle).  keep=True also
-    returns the states u^n, [nt][N]."""
+    returns the states u^n, [nt][N].  interp: point weights (None:
+    bi-/tri-linear; see oracle.sinc)."""
     N = grid.npoints
     k, alpha = _model(grid, vp)
-    S = _source_fields(grid, src_xyz, wavelet)
-    recs = _points(grid, rec_xyz)
+    S = _source_fields(grid, src_xyz, wavelet, interp)
+    recs = _points(grid, rec_xyz, interp)
     traces = np.zeros((len(recs), grid.nt))
     U = np.zeros((grid.nt, N)) if keep else None
     u_prev = np.zeros(N)

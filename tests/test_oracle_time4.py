@@ -9,6 +9,8 @@
   adjoint          dot-product test of the step operator G and its transpose
   gradient         Taylor remainder O(h^2); central differences, in the
                    interior and in the sponge, constant and variable density
+  physics          at twice the leapfrog's step it follows the closed-form 2D
+                   Green's function 20x more closely (0.12% against 2.3%)
 """
 import numpy as np
 import pytest
@@ -160,3 +162,32 @@ def test_gradient_3d_central_differences():
     fd = (_misfit(g, 1 / np.sqrt(mp), rho, src, w, rec, obs)
           - _misfit(g, 1 / np.sqrt(mm), rho, src, w, rec, obs)) / (2 * h)
     assert fd == pytest.approx(grad[p], rel=1e-6)
+
+
+def test_accuracy_against_the_analytic_solution_at_twice_the_step():
+    """Homogeneous 2D medium, order 10, 6 points per wavelength at 2.5 x the
+    Ricker peak, off-grid source and receivers with sinc weights (small
+    interpolation error), record ending before boundary echoes: at CFL 0.8
+    (half the steps) the fourth-order scheme follows the closed-form Green's
+    function (Sec. 3.1) far more closely than the leapfrog at CFL 0.4."""
+    from oracle import sinc
+    c, f0 = 1500.0, 3e5
+    dx = c / (2.5 * f0) / 6
+    n = int(60e-3 / dx)
+    q = inputs.ricker_fn(f0, t0=1.5 / f0)
+    ctr = (n // 2 + 0.5) * dx
+    src = np.array([[ctr, ctr - 0.3 * dx]])
+    R = 9e-3
+    ang = np.linspace(0, 2 * np.pi, 8, endpoint=False)
+    rec = np.stack([ctr + R * np.sin(ang), ctr - 0.3 * dx + R * np.cos(ang)], 1)
+    vp = np.full((n, n), c)
+    err = {}
+    for corr, cfl in ((False, 0.4), (True, 0.8)):
+        dt = cfl * dx / c
+        nt = int(20e-6 / dt)
+        g = oracle.Grid((n, n), dx, dt=dt, nt=nt, order=10, nb=10, c_ref=c)
+        w = q(np.arange(nt) * dt)[None, :]
+        ana = oracle.analytic_2d(q, R, np.arange(nt) * dt, c)
+        d = time4.forward(g, vp, None, src, w, rec, correction=corr, interp=sinc.hicks())
+        err[corr] = np.sqrt(np.mean((d - ana[None]) ** 2)) / np.sqrt(np.mean(ana ** 2))
+    assert err[True] < 3e-3 and err[True] < err[False] / 5, err   # measured 0.0012, 0.023
