@@ -10,7 +10,10 @@
  * (forward modelling, Sec. 3.1) and the L2 trace misfit with its gradient
  * with respect to the squared slowness m = 1/vp^2, computed by the
  * adjoint-state method of Sec. 2.2, Eqs. 5-9 on the discrete scheme (one
- * forward and one adjoint propagation per shot, Sec. 3.2).
+ * forward and one adjoint propagation per shot, Sec. 3.2).  For the
+ * inversion loop around the gradient (Sec. 2.3, Sec. 3.2) it also provides
+ * the per-block low-pass of wavelets and traces (fwi_lowpass) and the
+ * gradient-descent update of vp (fwi_vp_update).
  *
  * Conventions shared by every call:
  *  - Arrays are C order, the LAST axis fastest: 2D fields are [ny][nx],
