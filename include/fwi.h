@@ -328,6 +328,33 @@ fwi_status fwi_lowpass(const float* in, int n_in, int rows, int nt, const int* i
 fwi_status fwi_vp_update(float* vp, const float* grad_m, const float* mask, long long n,
                          float step, float vp_min, float vp_max, float* work, void* stream);
 
+/* Interpolation weights of one off-grid point (Sec. 2.4: bi-/tri-linear or
+ * high-order sinc interpolation of sources and receivers).  Host utility, no
+ * device work.
+ *   FWI_INTERP_LINEAR: the 2^ndim bi-/tri-linear corners the solver uses
+ *     (sources spread w / cell volume, receivers sample with w).
+ *   FWI_INTERP_SINC: Kaiser-windowed sinc, per axis the 2r nodes
+ *     floor(x)-r+1 .. floor(x)+r (x in grid units) weighted by
+ *     I0(b sqrt(1 - (d/r)^2)) / I0(b) * sin(pi d) / (pi d), d = node - x,
+ *     r = FWI_SINC_RADIUS, b = FWI_SINC_KAISER_B (the window that minimises
+ *     the largest error of interpolating cosines down to 4 points per
+ *     wavelength, 1.3e-3); the point's weights are the products over the
+ *     axes, (2r)^ndim nodes, the slowest axis varying slowest.  The solver
+ *     does not use these weights yet.
+ *   xyz:     host [ndim] metres, slowest axis first, inside the grid (sinc:
+ *            at least r - 1 nodes inside every face).
+ *   nodes:   host out [cap][ndim] grid indices, slowest axis first.
+ *   weights: host out [cap].
+ *   count:   out, the number of nodes (set even when cap is too small).
+ * Errors: FWI_ERR_INVALID_ARG (grid, NULL, interp, point outside or too close
+ * to a face, cap below count). */
+#define FWI_INTERP_LINEAR 0
+#define FWI_INTERP_SINC 1
+#define FWI_SINC_RADIUS 4
+#define FWI_SINC_KAISER_B 6.31
+fwi_status fwi_point_weights(const fwi_grid* grid, const double* xyz, int interp,
+                             int64_t* nodes, double* weights, int cap, int* count);
+
 /* Leapfrog stability limit of c*dt/h for this order and dimension:
  * 2/sqrt(ndim * lambda_max), lambda_max = |sum_j (-1)^j w2_j| of the
  * second-derivative stencil.  Returns a negative value for bad input. */

@@ -28,7 +28,7 @@ EXPORTS = ("fwi_plan_create", "fwi_plan_set_options", "fwi_plan_stats", "fwi_pla
            "fwi_plan_destroy", "fwi_forward", "fwi_gradient", "fwi_last_error", "fwi_cfl_limit",
            "fwi_forward_noalloc", "fwi_misfit_forward", "fwi_misfit_backward",
            "fwi_batch_create", "fwi_batch_run", "fwi_batch_stats_get", "fwi_batch_destroy",
-           "fwi_mem_available", "fwi_lowpass", "fwi_vp_update")
+           "fwi_mem_available", "fwi_lowpass", "fwi_vp_update", "fwi_point_weights")
 
 
 class FwiError(RuntimeError):
@@ -140,6 +140,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.fwi_vp_update.argtypes = [vp, vp, vp, ctypes.c_longlong, ctypes.c_float,
                                       ctypes.c_float, ctypes.c_float, vp, vp]
         lib.fwi_vp_update.restype = ctypes.c_int
+        lib.fwi_point_weights.argtypes = [P(CGrid), P(ctypes.c_double), ctypes.c_int,
+                                          P(ctypes.c_int64), P(ctypes.c_double), ctypes.c_int,
+                                          P(ctypes.c_int)]
+        lib.fwi_point_weights.restype = ctypes.c_int
         lib.fwi_batch_run.argtypes = [vp]
         lib.fwi_batch_run.restype = ctypes.c_int
         lib.fwi_batch_stats_get.argtypes = [vp, P(CBatchStats)]
@@ -202,6 +206,28 @@ def forward_noalloc(shape, spacing, nt, dt, vp, rho, geometry, wavelet, traces=N
 
 
 LOWPASS_MAX_HALF_WIDTH = 2048
+INTERP_LINEAR, INTERP_SINC = 0, 1
+
+
+def point_weights(shape, spacing, xyz, interp=INTERP_LINEAR, order=8, sponge=0):
+    """fwi_point_weights (host only): (nodes [count][ndim], weights [count])
+    of one off-grid point, bi-/tri-linear or Kaiser-windowed sinc."""
+    g = make_grid(shape, spacing, order, sponge, 0.0)
+    nd = len(tuple(shape))
+    x = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64).reshape(nd))
+    cnt = ctypes.c_int(0)
+    lib = load()
+    dp = ctypes.POINTER(ctypes.c_double)
+    st = lib.fwi_point_weights(ctypes.byref(g), x.ctypes.data_as(dp), int(interp), None, None, 0,
+                               ctypes.byref(cnt))
+    if cnt.value == 0:
+        _check(st)
+    nodes = np.zeros((cnt.value, nd), dtype=np.int64)
+    w = np.zeros(cnt.value)
+    _check(lib.fwi_point_weights(ctypes.byref(g), x.ctypes.data_as(dp), int(interp),
+                                 nodes.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                 w.ctypes.data_as(dp), cnt.value, ctypes.byref(cnt)))
+    return nodes, w
 
 
 def lowpass(x, ids, dt, f_max, half_width, out=None, stream=None):

@@ -59,6 +59,8 @@ void fd_weights(int order, double* w2, double* w1) {
   }
 }
 
+constexpr double kPiD = 3.14159265358979323846;
+
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 int round_up(int v, int a) { return (v + a - 1) / a * a; }
 
@@ -1259,6 +1261,83 @@ fwi_status fwi_mem_available(size_t* bytes) {
     return fail(FWI_ERR_CUDA, "no CUDA device");
   }
   *bytes = device_available(dev);
+  return FWI_OK;
+}
+
+fwi_status fwi_point_weights(const fwi_grid* grid, const double* xyz, int interp,
+                             int64_t* nodes, double* weights, int cap, int* count) {
+  if (count) *count = 0;
+  FWI_TRY(validate_grid(grid));
+  if (!xyz || !count) return fail(FWI_ERR_INVALID_ARG, "fwi_point_weights: NULL argument");
+  if (interp != FWI_INTERP_LINEAR && interp != FWI_INTERP_SINC)
+    return fail(FWI_ERR_INVALID_ARG, "fwi_point_weights: interp must be FWI_INTERP_LINEAR or FWI_INTERP_SINC");
+  const int nd = grid->ndim;
+  for (int d = 0; d < nd; ++d) {
+    const double hi = (double)(grid->shape[d] - 1) * grid->spacing[d];
+    const double tol = 1e-9 * grid->spacing[d];
+    if (!std::isfinite(xyz[d]) || xyz[d] < -tol || xyz[d] > hi + tol)
+      return fail(FWI_ERR_INVALID_ARG, "fwi_point_weights: point outside the grid");
+  }
+  if (interp == FWI_INTERP_LINEAR) {
+    fwi_plan P;   // only the layout fields are used (no device work)
+    P.grid = *grid;
+    build_layout(&P);
+    const Corners C = point_corners(&P, xyz);
+    *count = C.n;
+    if (cap < C.n || !nodes || !weights)
+      return fail(FWI_ERR_INVALID_ARG, "fwi_point_weights: cap below count (count is set)");
+    for (int c = 0; c < C.n; ++c) {
+      for (int d = 0; d < nd; ++d) nodes[(size_t)c * nd + d] = C.node[c][nd - 1 - d];
+      weights[c] = C.w[c];
+    }
+    return FWI_OK;
+  }
+  // Kaiser-windowed sinc: per axis the 2r nodes floor(x)-r+1 .. floor(x)+r
+  // with w = I0(b sqrt(1 - (d/r)^2)) / I0(b) * sin(pi d) / (pi d), d = i - x;
+  // the point weights are the products over the axes.
+  constexpr int r = FWI_SINC_RADIUS;
+  constexpr double b = FWI_SINC_KAISER_B;
+  auto bessel_i0 = [](double x) {          // power series sum_k ((x/2)^k / k!)^2
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 200 && term > 1e-18 * sum; ++k) {
+      term *= (x / (2.0 * k)) * (x / (2.0 * k));
+      sum += term;
+    }
+    return sum;
+  };
+  const double i0b = bessel_i0(b);
+  int first[3] = {0, 0, 0};
+  double w1[3][2 * FWI_SINC_RADIUS];
+  int total = 1;
+  for (int d = 0; d < nd; ++d) {
+    const double x = xyz[d] / grid->spacing[d];
+    const long long f = (long long)std::floor(x);
+    if (f - r + 1 < 0 || f + r > grid->shape[d] - 1)
+      return fail(FWI_ERR_INVALID_ARG, "fwi_point_weights: a sinc point must lie r - 1 nodes inside every face");
+    first[d] = (int)(f - r + 1);
+    for (int j = 0; j < 2 * r; ++j) {
+      const double dd = (double)(first[d] + j) - x;
+      const double q = 1.0 - (dd / r) * (dd / r);
+      const double win = std::fabs(dd) <= r ? bessel_i0(b * std::sqrt(q > 0.0 ? q : 0.0)) / i0b : 0.0;
+      const double sn = dd == 0.0 ? 1.0 : std::sin(kPiD * dd) / (kPiD * dd);
+      w1[d][j] = win * sn;
+    }
+    total *= 2 * r;
+  }
+  *count = total;
+  if (cap < total || !nodes || !weights)
+    return fail(FWI_ERR_INVALID_ARG, "fwi_point_weights: cap below count (count is set)");
+  for (int c = 0; c < total; ++c) {         // the slowest axis varies slowest
+    int rem = c;
+    double w = 1.0;
+    for (int d = nd - 1; d >= 0; --d) {
+      const int j = rem % (2 * r);
+      rem /= 2 * r;
+      nodes[(size_t)c * nd + d] = first[d] + j;
+      w *= w1[d][j];
+    }
+    weights[c] = w;
+  }
   return FWI_OK;
 }
 

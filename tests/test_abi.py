@@ -118,3 +118,33 @@ def test_grids_beyond_32_bit_field_offsets_are_rejected_on_the_host():
         assert st != 1, lib.fwi_last_error()
         if st == 0:
             lib.fwi_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("shape,spacing", [((40, 44), (0.5e-3, 0.4e-3)),
+                                           ((20, 22, 24), (0.5e-3, 0.5e-3, 0.45e-3))])
+def test_point_weights_match_the_oracle(shape, spacing):
+    """fwi_point_weights (host only): the solver's bi-/tri-linear corners and
+    the Kaiser-windowed sinc weights equal the oracle's (oracle.point_weights,
+    oracle.sinc, each pinned), node for node."""
+    import oracle
+    from oracle import sinc
+    g = oracle.Grid(shape, spacing, dt=1e-7, nt=2)
+    rng = np.random.default_rng(5)
+    for _ in range(6):
+        p = np.array([rng.uniform(4, n - 5) * h for n, h in zip(shape, spacing)])
+        for interp, ref in ((binding.INTERP_LINEAR, oracle.point_weights),
+                            (binding.INTERP_SINC, sinc.hicks())):
+            nodes, w = binding.point_weights(shape, spacing, p, interp)
+            idx_ref, w_ref = ref(g, p)
+            flat = np.ravel_multi_index(nodes.T, shape)
+            order, order_ref = np.argsort(flat), np.argsort(idx_ref)
+            np.testing.assert_array_equal(flat[order], np.asarray(idx_ref)[order_ref])
+            np.testing.assert_allclose(w[order], np.asarray(w_ref)[order_ref], rtol=0, atol=1e-13)
+    lib = binding.load()
+    gc = binding.make_grid(shape, spacing, 8, 0, 0.0)
+    cnt = ctypes.c_int(0)
+    edge = (ctypes.c_double * len(shape))(*([1.5 * spacing[0]] + [10 * h for h in spacing[1:]]))
+    assert lib.fwi_point_weights(ctypes.byref(gc), edge, binding.INTERP_SINC, None, None, 0,
+                                 ctypes.byref(cnt)) == 1            # too close to a face
+    nodes, w = binding.point_weights(shape, spacing, [1.5 * spacing[0]] + [10 * h for h in spacing[1:]])
+    assert len(w) == 2 ** len(shape) and abs(w.sum() - 1.0) < 1e-14   # bilinear works there
