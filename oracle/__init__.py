@@ -23,8 +23,8 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
 Submodules: ``inversion`` (the inversion loop of Sec. 2.3 / 3.2), ``time4``
 (a fourth-order-in-time scheme and its gradient), ``attenuation`` (the
 power-law attenuation term of Eq. 10 and its gradient), ``sinc``
-(Kaiser-windowed sinc interpolation of off-grid points) and ``pml`` (a 2D
-perfectly matched layer and its gradient), each with its own parity status
+(Kaiser-windowed sinc interpolation of off-grid points) and ``pml`` (a
+perfectly matched layer in 2D and 3D and its gradient), each with its own parity status
 in its header.
 """
 from __future__ import annotations
