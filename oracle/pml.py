@@ -1,7 +1,6 @@
 """FP64 oracle of a perfectly matched layer (PML) for the acoustic equation
-with constant density in 2D and 3D (Sec. 2.4 offers a PML next to the
-sponge, citing an unsplit formulation), and of its exact discrete gradient
-with respect to m = 1/vp^2.
+in 2D and 3D (Sec. 2.4 offers a PML next to the sponge, citing an unsplit
+formulation), and of its exact discrete gradient with respect to m = 1/vp^2.
 
 TEST INFRASTRUCTURE ONLY, like the rest of this package: the tests,
 ``__graft_entry__.smoke()`` and the CPU legs of ``bench.py`` may use it; the
@@ -29,20 +28,22 @@ phi by the trapezoidal rule driven by the new u and q:
 
 a = (sum z) dt / 2, e = (sum_{j<l} z_j z_l) dt^2, f = (prod z) dt^2,
 k = (vp dt)^2.  Outside the layer every z is zero, phi and the q term
-vanish, and the step is the solver's leapfrog.  Variable density is not
-covered.
+vanish, and the step is the solver's leapfrog.  With variable density, lap
+becomes the solver's rho div(rho^-1 grad): the density must be constant
+over the layer and the stencil reach next to it (checked), where the two
+operators coincide.
 
-Parity status: forward pinned (no layer: the C leapfrog in 2D and 3D;
-first-derivative stencil antisymmetric; reflection far below the sponge's
-of the same width in 2D and 3D; no late-time growth); gradient pinned
-(Taylor remainder; central differences inside and outside the layer, 2D and
-3D).
+Parity status: forward pinned (no layer: the C leapfrog in 2D and 3D, with
+and without density; first-derivative stencil antisymmetric; reflection far
+below the sponge's of the same width in 2D and 3D; no late-time growth);
+gradient pinned (Taylor remainder; central differences inside and outside
+the layer, 2D and 3D, with and without density).
 """
 from __future__ import annotations
 
 import numpy as np
 
-from . import Grid, apply_L, fd_weights
+from . import Grid, apply_L, apply_LT, fd_weights
 from .time4 import _points, _source_fields
 
 
@@ -104,16 +105,31 @@ def _coefficients(grid: Grid, vp):
     return k, a, e, f, axes
 
 
-def _rhs(grid, u, phi, s):
-    E = apply_L(grid, u, None) + s
+def _check_density(grid: Grid, rho):
+    """rho must be constant where any z is nonzero or within the stencil reach."""
+    if rho is None or grid.nb == 0:
+        return
+    rho = np.asarray(rho, dtype=np.float64).reshape(grid.shape)
+    reach = grid.nb + grid.order // 2
+    inner = tuple(slice(reach, n - reach) for n in grid.shape)
+    band = np.ones(grid.shape, dtype=bool)
+    band[inner] = False
+    vals = rho[band]
+    if vals.size and np.ptp(vals) > 1e-12 * np.abs(vals).max():
+        raise ValueError("the density must be constant over the PML and the stencil reach")
+
+
+def _rhs(grid, u, phi, s, rho=None):
+    E = apply_L(grid, u, rho) + s
     for j, ph in enumerate(phi):
         E = E + d1(grid, ph, j)
     return E
 
 
-def forward(grid: Grid, vp, src_xyz, wavelet, rec_xyz, keep=False):
-    """Traces [nrec][nt] of one shot (constant density).  keep=True also
-    returns the states (u, q, phi) of every step."""
+def forward(grid: Grid, vp, src_xyz, wavelet, rec_xyz, keep=False, rho=None):
+    """Traces [nrec][nt] of one shot (rho None: constant density).  keep=True
+    also returns the states (u, q, phi) of every step."""
+    _check_density(grid, rho)
     k, a, e, f, axes = _coefficients(grid, vp)
     S = _source_fields(grid, src_xyz, wavelet)
     recs = _points(grid, rec_xyz)
@@ -132,7 +148,7 @@ def forward(grid: Grid, vp, src_xyz, wavelet, rec_xyz, keep=False):
             hist.append((u, q, phi))
         if n == nt - 1:
             break
-        E = _rhs(grid, u, phi, S[n + 1].reshape(grid.shape))
+        E = _rhs(grid, u, phi, S[n + 1].reshape(grid.shape), rho)
         u_new = (2.0 * u - (1.0 - a) * u_prev - e * u - f * q + k * E) / (1.0 + a)
         q_new = q + grid.dt * u_new
         phi = [p * ph + b * d1(grid, u_new, j) + gq * d1(grid, q_new, j)
@@ -141,17 +157,18 @@ def forward(grid: Grid, vp, src_xyz, wavelet, rec_xyz, keep=False):
     return (traces, hist) if keep else traces
 
 
-def gradient(grid: Grid, vp, src_xyz, wavelet, rec_xyz, observed):
+def gradient(grid: Grid, vp, src_xyz, wavelet, rec_xyz, observed, rho=None):
     """(J, dJ/dm, traces) of one shot by the reverse sweep.  For step n:
     undo phi^{n+1} (into ubar^{n+1}, qbar^{n+1}, phibar^n), then
     q^{n+1} = q^n + dt u^{n+1}, then the u update with c = ubar^{n+1}/(1 + a)
-    (d_j^T = -d_j; the second-derivative stencil is symmetric)."""
+    (d_j^T = -d_j; the transpose of the solver's operator is the C oracle's
+    L^T)."""
     k, a, e, f, axes = _coefficients(grid, vp)
     S = _source_fields(grid, src_xyz, wavelet)
     recs = _points(grid, rec_xyz)
     nt = grid.nt
     dt = grid.dt
-    d, hist = forward(grid, vp, src_xyz, wavelet, rec_xyz, keep=True)
+    d, hist = forward(grid, vp, src_xyz, wavelet, rec_xyz, keep=True, rho=rho)
     r = d - np.asarray(observed, dtype=np.float64).reshape(d.shape)
     J = 0.5 * float(np.sum(r * r))
 
@@ -179,9 +196,9 @@ def gradient(grid: Grid, vp, src_xyz, wavelet, rec_xyz, observed):
         qbar = qbar_next                             # becomes qbar^n below
         # u^{n+1} = [2u^n - (1-a) u^{n-1} - e u^n - f q^n + k E^n] / (1 + a)
         c = ubar_next / (1.0 + a)
-        kbar += c * _rhs(grid, u_n, phi_n, S[n + 1].reshape(grid.shape))
+        kbar += c * _rhs(grid, u_n, phi_n, S[n + 1].reshape(grid.shape), rho)
         kc = k * c
-        ubar = ubar + (2.0 - e) * c + apply_L(grid, kc, None)
+        ubar = ubar + (2.0 - e) * c + apply_LT(grid, kc, rho)
         qbar = qbar - f * c
         phibar = [pb - d1(grid, kc, j) for j, pb in enumerate(phibar)]
         ubar_prev = receiver_adjoint(n - 1) - (1.0 - a) * c if n >= 1 else None

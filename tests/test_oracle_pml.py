@@ -186,3 +186,45 @@ def test_3d_gradient_central_differences():
         fd = (_misfit(g, 1 / np.sqrt(mp), src, w, rec, obs)
               - _misfit(g, 1 / np.sqrt(mm), src, w, rec, obs)) / (2 * h)
         assert fd == pytest.approx(grad[p], rel=1e-6, abs=1e-9 * np.abs(grad).max())
+
+
+def _density_with_constant_rim(shape, dx, reach, seed=6):
+    """Smooth random density in the interior, 1000 kg/m^3 over the outer
+    `reach` points (the layer and the stencil reach next to it)."""
+    _, rho = inputs.random_smooth_model(shape, dx, seed)
+    idx = np.indices(shape)
+    dist = np.min([np.minimum(i, n - 1 - i) for i, n in zip(idx, shape)], axis=0)
+    ramp = np.clip((dist - reach) / 4.0, 0.0, 1.0)
+    return 1000.0 + ramp * (rho - 1000.0)
+
+
+def test_variable_density_without_a_layer_is_the_leapfrog_and_is_checked():
+    shape, dx = (40, 44), 0.5e-3
+    vp, rho = inputs.random_smooth_model(shape, dx, 1)
+    dt = 0.4 * dx / vp.max()
+    g = oracle.Grid(shape, dx, dt=dt, nt=150, order=8, nb=0, c_ref=1500.0)
+    src = inputs.random_points(1, shape, dx, 2, margin=8)
+    rec = inputs.random_points(4, shape, dx, 3, margin=8)
+    w = inputs.ricker(5e5, dt, g.nt)[None, :]
+    ref = oracle.forward(g, vp, rho, src[None], w[None], rec)[0]
+    np.testing.assert_allclose(pml.forward(g, vp, src, w, rec, rho=rho), ref, rtol=0,
+                               atol=1e-12 * np.abs(ref).max())
+    g8 = oracle.Grid(shape, dx, dt=dt, nt=10, order=8, nb=8, c_ref=1500.0)
+    with pytest.raises(ValueError):
+        pml.forward(g8, vp, src, w[:, :10], rec, rho=rho)         # density varies in the layer
+
+
+def test_variable_density_gradient_central_differences():
+    g, vp, src, w, rec, _ = _gsetup()
+    rho = _density_with_constant_rim(g.shape, 0.5e-3, g.nb + 4)
+    obs = pml.forward(g, vp * 1.02, src, w, rec, rho=rho)
+    J0, grad, _ = pml.gradient(g, vp, src, w, rec, obs, rho=rho)
+    m = 1.0 / vp ** 2
+    for p in [(20, 22), (14, 30), (3, 20)]:
+        h = 1e-4 * m[p]
+        mp, mm = m.copy(), m.copy()
+        mp[p] += h
+        mm[p] -= h
+        Jp = 0.5 * np.sum((pml.forward(g, 1 / np.sqrt(mp), src, w, rec, rho=rho) - obs) ** 2)
+        Jm = 0.5 * np.sum((pml.forward(g, 1 / np.sqrt(mm), src, w, rec, rho=rho) - obs) ** 2)
+        assert (Jp - Jm) / (2 * h) == pytest.approx(grad[p], rel=1e-6, abs=1e-9 * np.abs(grad).max())
