@@ -38,7 +38,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import Grid, apply_L, apply_LT, sponge
-from .time4 import _points, _source_fields
+from .points import point_list as _points, source_fields as _source_fields
 
 
 def _ops(grid: Grid, rho):

@@ -43,28 +43,8 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import Grid, apply_L, apply_LT, point_weights, sponge
-
-
-def _points(grid: Grid, xyz, interp=None):
-    """Per point: flat node indices and interpolation weights (bi-/tri-linear
-    from the C oracle, or interp(grid, point) -> (indices, weights))."""
-    xyz = np.asarray(xyz, dtype=np.float64).reshape(-1, grid.ndim)
-    f = point_weights if interp is None else interp
-    return [f(grid, p) for p in xyz]
-
-
-def _source_fields(grid: Grid, src_xyz, wavelet, interp=None):
-    """s^n for n = -1 .. nt (zero outside the record), [nt + 2][N]: the
-    wavelet samples spread onto the nodes with weight / cell volume."""
-    N = grid.npoints
-    dV = float(np.prod(grid.spacing))
-    wav = np.asarray(wavelet, dtype=np.float64).reshape(-1, grid.nt)
-    S = np.zeros((grid.nt + 2, N))
-    for (idx, w), q in zip(_points(grid, src_xyz, interp), wav):
-        for i, wi in zip(idx, w):
-            S[1:grid.nt + 1, i] += (wi / dV) * q
-    return S                                # S[n + 1] = s^n
+from . import Grid, apply_L, apply_LT, sponge
+from .points import point_list as _points, source_fields as _source_fields
 
 
 def _model(grid: Grid, vp):
