@@ -6,7 +6,8 @@
   dJ/dvp              central finite differences of the misfit in vp
   gradient descent    descent, step normalisation, clipping, mask, zero gradient
   inversion loop      zero step keeps the model and gives the per-shot-subset
-                      misfits; the error to the true model falls
+                      misfits; the error to the true model falls; the
+                      filtered data agree at the true model
 """
 import numpy as np
 import pytest
@@ -167,13 +168,37 @@ def test_invert_with_zero_step_reports_the_subset_misfits():
 
 
 def test_invert_reduces_the_model_error():
-    """One 8-iteration block of the Sec. 3.2 experiment at 1/8 scale."""
-    p, g, obs, M = tiny_inversion()
+    """The first four iterations (64 shots) of the Sec. 3.2 experiment at 1/4
+    scale (at 1/8 scale the filter's record-end edge dominates the misfit)."""
+    p = inputs.config_inversion_2d(scale=4.0)
+    g = oracle.Grid(p.shape, p.spacing, p.dt, p.nt, p.order, p.nb, p.c_ref)
+    sched = [p.extra["schedule"][0][:4]]
+    used = np.concatenate(sched[0])
+    obs = np.zeros((p.nshots, p.rec_xyz.shape[0], p.nt))
+    obs[used] = oracle.forward(g, p.vp_true, None, p.src_xyz[used], p.wavelet[used], p.rec_xyz)
+    M = [int(np.ceil(p.extra["filter_cycles"] / (p.extra["freqs"][0] * p.dt)))]
     mask = p.extra["mask"]
     vp, Js = inv.invert(g, p.vp, None, p.src_xyz, p.wavelet, p.rec_xyz, obs,
-                        p.extra["freqs"][:1], p.extra["schedule"][:1], 10.0, 1400.0, 1600.0,
-                        mask, M[:1])
+                        p.extra["freqs"][:1], sched, 5.0, 1400.0, 1600.0, mask, M)
     e0 = inv.model_error(p.vp, p.vp_true, mask)
     e1 = inv.model_error(vp, p.vp_true, mask)
-    assert e1 < 0.95 * e0
+    assert e1 < 0.9 * e0, (e0, e1)                         # measured 23.8 -> 20.7 m/s
     np.testing.assert_array_equal(vp[mask == 0], p.vp[mask == 0])
+
+
+def test_filtered_data_agree_at_the_true_model():
+    """Low-passing the wavelet stands for low-passing the modelled traces; the
+    two differ only where the traces' low-pass would need samples after the
+    record.  At half scale (and at full scale, 1e-4) that leaves the misfit of
+    the true model negligible against the starting model's."""
+    p = inputs.config_inversion_2d(scale=2.0)
+    g = oracle.Grid(p.shape, p.spacing, p.dt, p.nt, p.order, p.nb, p.c_ref)
+    s = [5]
+    f = p.extra["freqs"][0]
+    M = int(np.ceil(p.extra["filter_cycles"] / (f * p.dt)))
+    obs = oracle.forward(g, p.vp_true, None, p.src_xyz[s], p.wavelet[s], p.rec_xyz)
+    wf = inv.lowpass(p.wavelet[s], p.dt, f, M)
+    of = inv.lowpass(obs, p.dt, f, M)
+    J_true = oracle.gradient(g, p.vp_true, None, p.src_xyz[s], wf, p.rec_xyz, of)[0]
+    J_start = oracle.gradient(g, p.vp, None, p.src_xyz[s], wf, p.rec_xyz, of)[0]
+    assert J_true < 2e-3 * J_start, (J_true, J_start)      # measured 5e-4
