@@ -402,6 +402,8 @@ def config_inversion_2d(scale: float = 1.0, shape=(456, 485), dx=0.5e-3, dt=0.08
     the frequencies by `scale` (spacing, step and period x scale): the same
     points per wavelength and CFL number on a smaller grid, with the phantom
     `scale` times fewer wavelengths across (an easier, cheaper inversion).
+    The record keeps its 200 us while the burst delay and a block filter's
+    reach grow with `scale`, so beyond scale 4 they take most of it.
     The tone burst starts after filter_cycles periods of the lowest block
     frequency, so a zero-phase low-pass of that length sees the whole burst.
     ``extra`` holds freqs, schedule, mask (update region: the disk 5 points
