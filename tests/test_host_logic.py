@@ -133,3 +133,28 @@ def test_inversion_filter_half_width():
     assert invert.half_width(300e3, 0.08e-6, cycles=1.0) == 42
     with pytest.raises(ValueError):
         invert.half_width(1e3, 0.08e-6)                            # beyond the kernel's 2048
+
+
+def test_inversion_driver_checks_its_arguments_on_the_host():
+    """invert.Inversion and binding.lowpass reject inconsistent arrays before
+    any device work (CPU tensors stand in for the device arrays here)."""
+    torch = pytest.importorskip("torch")
+    from paper_2110_03345_gb300 import binding, invert
+    plan = types.SimpleNamespace(nt=50, dt=1e-7, shape=(16, 16), stream=None)
+    src = np.zeros((4, 1, 2))
+    rec = np.zeros((6, 2))
+    wav = torch.zeros((4, 1, 50))
+    obs = torch.zeros((4, 6, 50))
+    invert.Inversion(plan, src, rec, wav, obs)                          # consistent: accepted
+    with pytest.raises(ValueError):
+        invert.Inversion(plan, src, rec, wav, torch.zeros((3, 6, 50)))  # shot count
+    with pytest.raises(ValueError):
+        invert.Inversion(plan, src, rec, torch.zeros((4, 1, 40)), torch.zeros((4, 6, 40)))  # nt
+    with pytest.raises(ValueError):
+        invert.Inversion(plan, src, np.zeros((5, 2)), wav, obs)         # receiver count
+    run = invert.Inversion(plan, src, rec, wav, obs, max_shots=2)
+    with pytest.raises(ValueError):
+        run.iterate(torch.zeros((16, 16)), [0, 1, 2], 1e6, 1.0)         # more than max_shots
+    assert run.iterate(torch.zeros((16, 16)), [], 1e6, 1.0) == 0.0     # nothing to do
+    with pytest.raises(ValueError):
+        binding.lowpass(torch.zeros((4, 50)), [0], 1e-7, 1e6, 8)        # not [n][rows][nt]
