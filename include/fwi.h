@@ -82,7 +82,7 @@ typedef struct {
 typedef struct {
     int nshots;               /* >= 1 */
     int nsrc;                 /* sources per shot, >= 1 */
-    int nrec;                 /* receivers, >= 1 */
+    int nrec;                 /* receivers, 1 .. 2^20 */
     const double* src_xyz;    /* host [nshots][nsrc][ndim] metres */
     const double* rec_xyz;    /* host [nrec][ndim] metres */
 } fwi_geometry;
@@ -133,8 +133,9 @@ typedef struct {
  * within hbm_budget_bytes (0: 90% of the free device memory at creation).
  * stream: a cudaStream_t (NULL = legacy default stream) the plan enqueues on.
  * Errors: FWI_ERR_INVALID_ARG for a bad grid (including one whose padded
- * field would hold 2^31 floats or more: in-field offsets are 32-bit), nt < 1
- * or dt <= 0. */
+ * field would hold 2^31 floats or more, in-field offsets being 32-bit, or
+ * whose second-fastest axis exceeds 524280 points, the CTA grid's y limit),
+ * nt < 1 or dt <= 0. */
 fwi_status fwi_plan_create(fwi_plan** plan, const fwi_grid* grid, int nt, double dt,
                            size_t hbm_budget_bytes, void* stream);
 

@@ -370,6 +370,10 @@ fwi_status validate_grid(const fwi_grid* g) {
     if (g->sponge < 0 || 2 * (int64_t)g->sponge >= g->shape[d])
       return fail(FWI_ERR_INVALID_ARG, "sponge must be >= 0 and < shape/2");
   }
+  // The second-fastest axis is split over grid.y (at least 8 rows per CTA),
+  // which CUDA limits to 65535 blocks.
+  if (g->shape[g->ndim - 2] > 8LL * 65535)
+    return fail(FWI_ERR_INVALID_ARG, "shape out of range: the second-fastest axis exceeds 524280 points");
   // In-field offsets (receiver sampling tables, tile-local arithmetic) are
   // 32-bit: a padded field must hold fewer than 2^31 floats.
   if (padded_field_floats(g) > 0x7fffffffLL)
@@ -456,8 +460,8 @@ fwi_status validate_geometry(const fwi_plan* P, const fwi_geometry* g) {
   if (g->nshots < 1 || g->nsrc < 1 || g->nrec < 1)
     return fail(FWI_ERR_INVALID_ARG, "nshots, nsrc and nrec must be >= 1");
   if (!g->src_xyz || !g->rec_xyz) return fail(FWI_ERR_INVALID_ARG, "coordinates are NULL");
-  if ((long long)g->nshots * g->nsrc > (1LL << 24) || g->nrec > (1 << 24))
-    return fail(FWI_ERR_INVALID_ARG, "too many sources or receivers");
+  if ((long long)g->nshots * g->nsrc > (1LL << 24) || g->nrec > (1 << 20))
+    return fail(FWI_ERR_INVALID_ARG, "too many sources (2^24) or receivers (2^20)");
   // wavelet and trace samples are addressed with 32-bit indices
   if ((long long)g->nshots * g->nsrc * P->nt > 0x7fffffffLL ||
       (long long)g->nshots * g->nrec * P->nt > 0x7fffffffLL)
@@ -593,6 +597,10 @@ fwi_status choose_plan(const fwi_plan* P, const fwi_geometry* g, bool vd, bool g
                                              std::to_string(budget) + " bytes)");
   if (P->opt.batch > 0) B = std::min(B, P->opt.batch);
   B = std::min(B, ns);
+  if (!resolve_tile(P, P->opt.tile, &out.tile, &out.shape, &out.tma, &out.x2))
+    return fail(FWI_ERR_INVALID_ARG, "tile variant out of range");
+  // slots x z chunks go on grid.z, which CUDA limits to 65535 blocks
+  B = std::min(B, std::max(1, 65535 / std::max(1, tile_geo(P, out.shape, out.tma, out.x2).nzc)));
   // equal batches: the same number of batches, none left nearly empty
   // (16 shots at 15 per batch run as 8 + 8, not 15 + 1)
   B = (ns + (ns + B - 1) / B - 1) / ((ns + B - 1) / B);
@@ -602,8 +610,6 @@ fwi_status choose_plan(const fwi_plan* P, const fwi_geometry* g, bool vd, bool g
   out.gradient = grad;
   out.split = split;
   out.nbatches = (ns + B - 1) / B;
-  if (!resolve_tile(P, P->opt.tile, &out.tile, &out.shape, &out.tma, &out.x2))
-    return fail(FWI_ERR_INVALID_ARG, "tile variant out of range");
   out.S = 1;
   if (out.tma && P->grid.ndim == 2) {   // the 3D kernels take one shot per CTA
     if (P->opt.shots_per_cta > 0) {

@@ -104,13 +104,15 @@ def test_inversion_entry_points_validate_on_the_host():
 
 def test_grids_beyond_32_bit_field_offsets_are_rejected_on_the_host():
     """A padded field must hold fewer than 2^31 floats (in-field offsets are
-    32-bit); larger grids fail with FWI_ERR_INVALID_ARG before any device call."""
+    32-bit) and the second-fastest axis at most 524280 points (grid.y); larger
+    grids fail with FWI_ERR_INVALID_ARG before any device call."""
     lib = binding.load()
-    for shape in [(1300, 1300, 1300), (1 << 20, 4096), (40000, 60000)]:
+    for shape in [(1300, 1300, 1300), (1 << 20, 4096), (40000, 60000),
+                  (600000, 20), (20, 600000, 20)]:                   # grid.y beyond 65535 CTAs
         plan = ctypes.c_void_p()
         g = binding.make_grid(shape, 1e-3, 8, 8, 1500.0)
         assert lib.fwi_plan_create(ctypes.byref(plan), ctypes.byref(g), 20, 1e-7, 0, None) == 1
-        assert b"2^31" in lib.fwi_last_error()
+        assert b"2^31" in lib.fwi_last_error() or b"524280" in lib.fwi_last_error()
     for shape in [(1200, 1200, 1200), (20000, 20000)]:              # below the limit
         plan = ctypes.c_void_p()
         g = binding.make_grid(shape, 1e-3, 8, 8, 1500.0)
