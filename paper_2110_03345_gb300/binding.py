@@ -197,6 +197,11 @@ def forward_noalloc(shape, spacing, nt, dt, vp, rho, geometry, wavelet, traces=N
                              dtype=torch.float32)
     if stream is None:
         stream = torch.cuda.current_stream()
+    n = int(np.prod(tuple(int(v) for v in shape)))
+    check_array(vp, n, "vp", vp.device)
+    check_array(rho, n, "rho", vp.device, optional=True)
+    check_array(wavelet, geometry.nshots * geometry.nsrc * int(nt), "wavelet", vp.device)
+    check_array(traces, geometry.nshots * geometry.nrec * int(nt), "traces", vp.device)
     g = make_grid(shape, spacing, order, sponge, c_ref)
     m = CModel(_ptr(vp), _ptr(rho))
     _check(load().fwi_forward_noalloc(ctypes.byref(g), int(nt), float(dt), ctypes.byref(m),
@@ -261,6 +266,8 @@ def vp_update(vp, grad_m, step, vp_min, vp_max, mask=None, work=None, stream=Non
         raise ValueError("vp, grad_m and mask must have the same size")
     if work is None:
         work = torch.empty(1, device=vp.device, dtype=torch.float32)
+    if work.numel() < 1:
+        raise ValueError("work must hold at least one element")
     if stream is None:
         stream = torch.cuda.current_stream()
     _check(load().fwi_vp_update(_ptr(vp), _ptr(grad_m), _ptr(mask), int(vp.numel()),
@@ -279,6 +286,20 @@ def _ptr(t):
     if t.dtype != torch.float32 or not t.is_contiguous():
         raise TypeError("expected a contiguous float32 CUDA tensor")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def check_array(t, count, name, device=None, optional=False):
+    """Raise ValueError unless `t` holds exactly `count` elements (and lies on
+    `device` when given).  The C ABI takes bare device pointers and cannot see
+    a tensor's size: a short array would be read or written past its end."""
+    if t is None:
+        if optional:
+            return
+        raise ValueError(f"{name} is required")
+    if int(t.numel()) != int(count):
+        raise ValueError(f"{name} holds {int(t.numel())} elements, expected {int(count)}")
+    if device is not None and getattr(t, "device", None) is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, the plan runs on {device}")
 
 
 class Geometry:
@@ -330,6 +351,9 @@ class Plan:
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
+        self.device = torch.device("cuda", stream.device.index if stream.device.index is not None
+                                   else torch.cuda.current_device())
+        self.npoints = int(np.prod(shape))
         h = ctypes.c_void_p()
         _check(lib.fwi_plan_create(ctypes.byref(h), ctypes.byref(g), self.nt, self.dt,
                                    int(budget), ctypes.c_void_p(stream.cuda_stream)))
@@ -365,7 +389,15 @@ class Plan:
         return int(b.value)
 
     def _model(self, vp, rho, param=PARAM_VP):
+        check_array(vp, self.npoints, "vp", self.device)
+        check_array(rho, self.npoints, "rho", self.device, optional=True)
         return CModel(_ptr(vp), _ptr(rho), int(param))
+
+    def _check_shots(self, geometry, wavelet, traces=None, observed=None):
+        ns, nrec = geometry.nshots, geometry.nrec
+        check_array(wavelet, ns * geometry.nsrc * self.nt, "wavelet", self.device)
+        check_array(observed, ns * nrec * self.nt, "observed", self.device, optional=True)
+        check_array(traces, ns * nrec * self.nt, "traces", self.device, optional=True)
 
     def forward(self, vp, rho, geometry: Geometry, wavelet, traces=None):
         """Traces [nshots][nrec][nt] (CUDA float32) for the given wavelets."""
@@ -374,6 +406,7 @@ class Plan:
             traces = torch.empty((geometry.nshots, geometry.nrec, self.nt), device=vp.device,
                                  dtype=torch.float32)
         m = self._model(vp, rho)
+        self._check_shots(geometry, wavelet, traces=traces)
         _check(load().fwi_forward(self._h, ctypes.byref(m), ctypes.byref(geometry.c),
                                   _ptr(wavelet), self.nt, self.dt, _ptr(traces)))
         return traces
@@ -389,6 +422,8 @@ class Plan:
                              dtype=torch.float32)
         J = ctypes.c_double()
         m = self._model(vp, rho, param)
+        self._check_shots(geometry, wavelet, traces=tr, observed=observed)
+        check_array(observed, geometry.nshots * geometry.nrec * self.nt, "observed", self.device)
         self._kept = (vp, rho, geometry, wavelet, observed)   # must outlive the backward
         _check(load().fwi_misfit_forward(self._h, ctypes.byref(m), ctypes.byref(geometry.c),
                                          _ptr(wavelet), _ptr(observed), ctypes.byref(J), _ptr(tr)))
@@ -402,6 +437,7 @@ class Plan:
         vp = self._kept[0]
         if grad is None:
             grad = torch.empty(vp.shape, device=vp.device, dtype=torch.float32)
+        check_array(grad, self.npoints, "grad", self.device)
         try:
             _check(load().fwi_misfit_backward(self._h, _ptr(grad)))
         finally:
@@ -421,6 +457,9 @@ class Plan:
             tr = traces
         J = ctypes.c_double()
         m = self._model(vp, rho)
+        self._check_shots(geometry, wavelet, traces=tr, observed=observed)
+        check_array(observed, geometry.nshots * geometry.nrec * self.nt, "observed", self.device)
+        check_array(grad, self.npoints, "grad", self.device)
         _check(load().fwi_gradient(self._h, ctypes.byref(m), ctypes.byref(geometry.c),
                                    _ptr(wavelet), _ptr(observed), ctypes.byref(J), _ptr(grad),
                                    _ptr(tr)))
@@ -446,6 +485,12 @@ class Batch:
         arr = (CProblem * len(problems))()
         for i, pr in enumerate(problems):
             geo = pr["geometry"]
+            n = int(np.prod(tuple(int(v) for v in pr["shape"])))
+            dev = pr["vp"].device
+            check_array(pr["vp"], n, f"problem {i} vp", dev)
+            check_array(pr.get("rho"), n, f"problem {i} rho", dev, optional=True)
+            check_array(pr["wavelet"], geo.nshots * geo.nsrc * int(pr["nt"]),
+                        f"problem {i} wavelet", dev)
             tr = torch.empty((geo.nshots, geo.nrec, int(pr["nt"])), device=pr["vp"].device,
                              dtype=torch.float32)
             self.traces.append(tr)

@@ -158,3 +158,19 @@ def test_inversion_driver_checks_its_arguments_on_the_host():
     assert run.iterate(torch.zeros((16, 16)), [], 1e6, 1.0) == 0.0     # nothing to do
     with pytest.raises(ValueError):
         binding.lowpass(torch.zeros((4, 50)), [0], 1e-7, 1e6, 8)        # not [n][rows][nt]
+
+
+def test_binding_checks_array_sizes_and_devices():
+    """The C ABI takes bare pointers; the binding checks element counts and
+    devices before any call, so a short array cannot be read past its end."""
+    torch = pytest.importorskip("torch")
+    from paper_2110_03345_gb300 import binding
+    t = torch.zeros((3, 4, 5))
+    binding.check_array(t, 60, "t")                                    # exact count: accepted
+    binding.check_array(None, 60, "t", optional=True)
+    with pytest.raises(ValueError, match="expected 64"):
+        binding.check_array(t, 64, "t")
+    with pytest.raises(ValueError, match="required"):
+        binding.check_array(None, 60, "t")
+    with pytest.raises(ValueError, match="plan runs on"):
+        binding.check_array(t, 60, "t", device=torch.device("cuda", 0))
