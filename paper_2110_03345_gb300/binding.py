@@ -351,8 +351,11 @@ class Plan:
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
-        self.device = torch.device("cuda", stream.device.index if stream.device.index is not None
-                                   else torch.cuda.current_device())
+        try:
+            idx = stream.device.index
+        except AttributeError:
+            idx = None
+        self.device = torch.device("cuda", idx if idx is not None else torch.cuda.current_device())
         self.npoints = int(np.prod(shape))
         h = ctypes.c_void_p()
         _check(lib.fwi_plan_create(ctypes.byref(h), ctypes.byref(g), self.nt, self.dt,
