@@ -26,10 +26,11 @@ f_max, pass and stop band; brute force against numpy.convolve; the solver
 commutes with the filter); vp_gradient pinned (finite differences of J in
 vp); vp_update pinned (descent, step normalisation, clipping, mask);
 invert pinned by invariants (zero step keeps the model and reproduces the
-oracle misfit, the misfit of a block falls, the error to the true model
-falls).  The paper prints no reconstruction values (its Fig. 5 error is an
-image label of a dataset that is not available): parity with them is
-unpinned.
+oracle misfit of each shot subset; the error to the true model falls; at the
+true model the filtered data agree, up to the record-end edge of the trace
+filter).  The paper prints no reconstruction values in its text (the error
+of its 2D breast reconstruction is a figure label on a dataset that is not
+available): parity with them is unpinned.
 """
 from __future__ import annotations
 
