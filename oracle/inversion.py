@@ -13,8 +13,8 @@ The paper names these steps but not their formulas; the readings taken here:
     with cut-off f_max: a Hann-windowed sinc of half-width M samples,
     normalised to unit gain at zero frequency, applied to the wavelet and the
     observed traces (the modelled traces follow from the filtered wavelet);
-  * the gradient-descent step (Sec. 2.3, "a step in the direction of the
-    derivative") is taken on vp with dJ/dvp = -2 (dJ/dm) / vp^3, scaled so
+  * the gradient-descent step (Sec. 2.3: one optimiser step per computed
+    gradient) is taken on vp with dJ/dvp = -2 (dJ/dm) / vp^3, scaled so
     that the largest change of any point is `step` m/s, restricted to a mask
     and clipped to [vp_min, vp_max];
   * each block draws a permutation of the shots and every iteration takes the
