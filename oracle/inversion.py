@@ -9,7 +9,7 @@ gradient itself comes from the C oracle (``oracle.gradient``); the steps below
 are numpy written out from their definitions.
 
 The paper names these steps but not their formulas; the readings taken here:
-  * the per-block "processing" of wavelets and traces is a zero-phase low-pass
+  * the per-block processing of wavelets and traces is a zero-phase low-pass
     with cut-off f_max: a Hann-windowed sinc of half-width M samples,
     normalised to unit gain at zero frequency, applied to the wavelet and the
     observed traces (the modelled traces follow from the filtered wavelet);

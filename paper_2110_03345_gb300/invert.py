@@ -6,8 +6,8 @@ Host orchestration only.  Per iteration it enqueues, on the plan's stream,
 the low-pass of the selected shots' wavelets and observed traces
 (``fwi_lowpass``), the misfit gradient of those shots (``fwi_gradient``) and
 the model update (``fwi_vp_update``); every step runs in the CUDA library.
-The shot subsets are an input (``inputs.shot_schedule`` draws the paper's
-"random, without replacement" schedule).
+The shot subsets are an input (``inputs.shot_schedule`` draws them as in
+Sec. 3.2: random subsets, each shot once per block).
 """
 from __future__ import annotations
 
