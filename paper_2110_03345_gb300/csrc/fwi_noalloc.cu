@@ -18,7 +18,7 @@
 // call reuses the same array: calls that overlap on the GPU (different
 // streams, threads or processes sharing a context) race on it.  Each call
 // clears what must start at zero before use.
-#include "fwi.h"
+#include "fwi_plan.cuh"
 
 #include <cuda_runtime.h>
 
@@ -26,11 +26,68 @@
 #include <string>
 
 namespace fwi {
-void set_last_error(const std::string& msg);
+
+// Runs fwi_forward on a plan that lives on the stack and whose every device
+// buffer is carved out of [base, base + bytes): no device allocation happens.
+// Used by the fixed-scratch entry point (fwi_noalloc.cu).
 fwi_status forward_in_buffer(const fwi_grid* grid, int nt, double dt, const fwi_model* model,
                              const fwi_geometry* geom, const float* wavelet, float* traces,
-                             void* stream, char* base, size_t bytes, int device);
+                             void* stream, char* base, size_t bytes, int device) {
+  FWI_TRY(validate_grid(grid));
+  if (nt < 1 || nt > (1 << 24)) return fail(FWI_ERR_INVALID_ARG, "nt must be in [1, 2^24]");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(FWI_ERR_INVALID_ARG, "dt must be positive");
+  if (!traces) return fail(FWI_ERR_INVALID_ARG, "traces is NULL");
+  if (!model || !model->vp) return fail(FWI_ERR_INVALID_ARG, "model or vp is NULL");
+  fwi_plan P;
+  P.grid = *grid;
+  P.nt = nt;
+  P.dt = dt;
+  P.st = reinterpret_cast<cudaStream_t>(stream);
+  P.device = device;
+  P.c_ref = grid->c_ref;
+  P.fixed_memory = true;
+  if (cudaDeviceGetAttribute(&P.nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    cudaGetLastError();
+    P.nsm = 152;
+  }
+  build_layout(&P);
+  FWI_TRY(validate_geometry(&P, geom));
+  constexpr int JCAP = 4096;
+  Carve C(base);
+  P.d_stats = C.take<unsigned int>(16);
+  P.d_flags = C.take<int>(16);
+  P.d_J = C.take<double>(JCAP);
+  P.d_J_cap = JCAP;
+  P.spx = C.take<float>(P.L.nx_r + 8);
+  P.spy = C.take<float>(P.L.ny_r + 8);
+  P.spz = C.take<float>(std::max(P.L.nz, 1) + 8);
+  Plan all;   // table bound for every shot in one batch, at the tile variant the call will use
+  all.B = geom->nshots;
+  if (!resolve_tile(&P, P.opt.tile, &all.tile, &all.shape, &all.tma, &all.x2))
+    return fail(FWI_ERR_INVALID_ARG, "tile variant out of range");
+  const size_t tab = align_up(tables_bound(&P, geom, all) * 2, 256);
+  P.tab = C.take<char>(tab);
+  P.tab_cap = tab;
+  C.off = align_up(C.off, 256);
+  if (C.off >= bytes)
+    return fail(FWI_ERR_BUDGET, "tables need " + std::to_string(C.off) +
+                                    " bytes, more than the static scratch of " +
+                                    std::to_string(bytes) + " bytes");
+  P.arena = base + C.off;
+  P.arena_cap = bytes - C.off;
+  P.budget = P.arena_cap;
+  Plan pl;
+  if (choose_plan(&P, geom, model->rho != nullptr, false, pl) != FWI_OK)
+    return fail(FWI_ERR_BUDGET, "one shot of this grid needs more than the static scratch of " +
+                                    std::to_string(bytes) + " bytes (use fwi_forward)");
+  if ((geom->nshots + pl.B - 1) / pl.B > JCAP)
+    return fail(FWI_ERR_BUDGET, "too many shot batches for the static scratch");
+  if (P.c_ref > 0.0) FWI_TRY(build_sponge(&P));
+  return fwi_forward(&P, model, geom, wavelet, nt, dt, traces);
 }
+
+}  // namespace fwi
+
 
 namespace {
 
