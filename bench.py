@@ -70,23 +70,33 @@ def parse():
     return ap.parse_args()
 
 
-def make_problem(args, rank=0):
-    """The workload; rank r > 0 fires its own sources (the transducer set
-    rotated by r), so the ranks of a multi-GPU run process distinct shots."""
+def make_problem(args, rank=0, world=1):
+    """The workload of one rank.  A multi-GPU run processes world x 128 (2D)
+    or world x 32 (3D) distinct shots, sharded by distributed.shard: in 2D
+    firing f is element 2 (f mod 128) of the ring turned by (f div 128) /
+    world element pitches (a rotated acquisition of the same phantom), in 3D
+    firing f is receiver 16 (f mod 32) + (f div 32) of the sphere (distinct
+    for up to 16 ranks)."""
     from paper_2110_03345_gb300 import inputs
+    from paper_2110_03345_gb300.distributed import shard
     if args.workload == "breast2d":
         n = args.n or 1024
         nt = args.nt or 4000
         dx = 0.1e-3 * 1024 / n
-        shots = None if rank == 0 else [(2 * i + rank) % 256 for i in range(128)]
-        p = inputs.config_breast_2d(n=n, dx=dx, nt=nt, shots=shots)
+        fires = shard(128 * world, rank, world)
+        turns = sorted({f // 128 for f in fires})
+        assert len(turns) == 1 and len(fires) == 128
+        p = inputs.config_breast_2d(n=n, dx=dx, nt=nt, shots=[2 * (f % 128) for f in fires],
+                                    rotation=turns[0] / world)
     elif args.workload == "invert":
         p = inputs.config_inversion_2d(scale=args.scale)
     else:
         n = args.n or 256
         nt = args.nt or 2000
         dx = 0.25e-3 * 256 / n
-        shots = None if rank == 0 else [(16 * i + rank) % 512 for i in range(32)]
+        fires = shard(32 * world, rank, world)
+        shots = [16 * (f % 32) + f // 32 for f in fires]
+        assert world <= 16 and len(shots) == 32
         p = inputs.config_skull_3d(n=n, dx=dx, nt=nt, shots=shots)
     if args.shots:
         p.src_xyz = p.src_xyz[:args.shots]
@@ -220,6 +230,7 @@ def cpu_baseline(p, budget_s: float):
     t = run(nt)
     upd = 2 * p.npoints * (nt - 1)
     return {"value": upd / t / 1e9, "unit": "Gpts/s", "cores": cores, "kind": "oracle",
+            "seconds": t,
             "sample": f"1 shot of {p.nshots}, {nt} of {p.nt} steps, full grid "
                       f"{'x'.join(map(str, p.shape))}, FP64 C oracle (OpenMP), observed data = 0, "
                       f"checkpointed gradient; {t:.1f} s"}
@@ -259,10 +270,17 @@ def run_reference(args):
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return 0
+    sample_ms = statistics.median(s["seconds"] for s in steps) * 1e3
     line = {
         "impl": "reference", "metric": "Gpts/s (grid-point updates per second, gradient: forward + adjoint)",
         "value": val, "unit": "Gpts/s", "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": upd / (val * 1e9) * 1e3, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": sample_ms, "higher_is_better": True,
+        "step": "one bounded sample of the workload: " + steps[-1]["sample"],
+        "extrapolated": True,
+        "extrapolation": {"ms_per_full_step": upd / (val * 1e9) * 1e3,
+                          "basis": "the measured Gpts/s applied to the full workload's updates "
+                                   f"({upd} per step: {p.nshots} shots x {p.nt} steps); "
+                                   "the full step is not run"},
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "shots": p.nshots, "nt": p.nt,
                    "grid": list(p.shape), "sample": steps[-1]["sample"]},
@@ -458,6 +476,76 @@ def serving_stream(nreq=650, warm=50, seed=5, lanes=4, rate=20.0, **kw):
 
 # ---------------------------------------------------------------- GPU arm
 
+def roofline(acc, steps, ms, vd, ndim, tile):
+    """Roofline record of the dominant stencil kernel from the plan's counters
+    summed over the timed steps (CUDA events around every PROFILE_EVERY-th
+    launch on the plan's stream)."""
+    per_launch = {k: acc[f"{k}_ms"] / max(acc[f"{k}_timed"], 1) for k in ("fwd", "adj")}
+    kind = "adj" if per_launch["adj"] * acc["adj_launches"] >= per_launch["fwd"] * acc["fwd_launches"] \
+        else "fwd"
+    n_l = max(acc[f"{kind}_launches"], 1)
+    t_launch = per_launch[kind] * 1e-3
+    pts_launch = acc[f"{kind}_points"] / n_l
+    bpu = BYTES_PER_UPDATE[(kind, vd)]
+    achieved = bpu * pts_launch / t_launch / 1e9
+    peak, peak_src = measured_hbm_peak()
+    tr = traffic_record(f"{ndim}d-{kind}", tile)
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": (tr["dram_bytes_per_point"] * pts_launch) if tr else None,
+            "kernel": ("%s %s" % (kernel_name(ndim, tile),
+                                  "adjoint+imaging" if kind == "adj" else "forward+store")),
+            "bytes_per_update": bpu, "points_per_launch": int(pts_launch),
+            "launch_ms": t_launch * 1e3, "peak_source": peak_src,
+            "timed_launches": int(acc[f"{kind}_timed"]),
+            "share_of_step": per_launch[kind] * n_l / steps / ms}
+
+
+STAT_KEYS = ("fwd_ms", "adj_ms", "fwd_launches", "adj_launches", "fwd_points", "adj_points",
+             "launches", "fwd_timed", "adj_timed")
+
+
+def skull3d_sample(shots=2, steps=2, warmup=1, **opts):
+    """The 3D workload at full grid size and time axis (256^3, 0.25 mm,
+    10th order, variable density, 2000 steps, 512 receivers) with `shots`
+    of its 32 shots: gradient Gpts/s and the roofline of its dominant kernel,
+    device-timed like the main line (inputs resident)."""
+    import torch
+    from paper_2110_03345_gb300 import binding, inputs
+    p = inputs.config_skull_3d(shots=list(range(0, 16 * shots, 16)))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+    vp, rho, wav = f32(p.vp), f32(p.rho), f32(p.wavelet)
+    geo = binding.Geometry(p.src_xyz, p.rec_xyz)
+    stream = torch.cuda.current_stream()
+    plan = binding.Plan(p.shape, p.spacing, p.nt, p.dt, order=p.order, sponge=p.nb, c_ref=p.c_ref,
+                        stream=stream)
+    obs = plan.forward(f32(p.vp_true), rho, geo, wav)
+    grad = torch.empty(p.shape, device=dev, dtype=torch.float32)
+    plan.set_options(profile=PROFILE_EVERY, **opts)
+    for _ in range(warmup):
+        plan.gradient(vp, rho, geo, wav, obs, grad=grad)
+    acc = dict.fromkeys(STAT_KEYS, 0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        plan.gradient(vp, rho, geo, wav, obs, grad=grad)
+        st = plan.stats()
+        for k in acc:
+            acc[k] += st[k]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    st = plan.stats()
+    plan.close()
+    upd = useful_updates(p)
+    return {"workload": f"skull3d 256^3 x 2000 steps, {shots} of the 32 shots, vd, o10, 512 receivers",
+            "value": upd / (ms * 1e-3) / 1e9, "unit": "Gpts/s", "ms_per_gradient": ms,
+            "steps": steps, "warmup": warmup, "batch": st["batch"], "ckpt_every": st["ckpt_every"],
+            "tile": st["tile"], "gpu_launches": int(acc["launches"]),
+            "roofline": roofline(acc, steps, ms, True, 3, st["tile"])}
+
+
 def run_mine(args):
     import torch
     from paper_2110_03345_gb300 import binding
@@ -478,7 +566,7 @@ def run_mine(args):
         if dist is not None:
             dist.barrier()
 
-    p = make_problem(args, rank)
+    p = make_problem(args, rank, world)
     vd = p.rho is not None
     f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
     vp_h = torch.from_numpy(f32(p.vp)).pin_memory()
@@ -511,8 +599,7 @@ def run_mine(args):
     torch.cuda.synchronize()
 
     clocks = ClockSampler(gpu_uuid())
-    acc = {"fwd_ms": 0.0, "adj_ms": 0.0, "fwd_launches": 0, "adj_launches": 0, "fwd_points": 0,
-           "adj_points": 0, "launches": 0, "fwd_timed": 0, "adj_timed": 0}
+    acc = dict.fromkeys(STAT_KEYS, 0)
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -540,34 +627,17 @@ def run_mine(args):
 
     upd = useful_updates(p)
     value = world * upd / (ms * 1e-3) / 1e9
-    # roofline of the dominant kernel
-    per_launch = {k: acc[f"{k}_ms"] / max(acc[f"{k}_timed"], 1) for k in ("fwd", "adj")}
-    kind = "adj" if per_launch["adj"] * acc["adj_launches"] >= per_launch["fwd"] * acc["fwd_launches"] \
-        else "fwd"
-    n_l = max(acc[f"{kind}_launches"], 1)
-    t_launch = per_launch[kind] * 1e-3
-    pts_launch = acc[f"{kind}_points"] / n_l
-    bpu = BYTES_PER_UPDATE[(kind, vd)]
-    achieved = bpu * pts_launch / t_launch / 1e9
-    peak, peak_src = measured_hbm_peak()
-    tr = traffic_record(f"{p.ndim}d-{kind}", stats["tile"])
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": (tr["dram_bytes_per_point"] * pts_launch) if tr else None,
-            "kernel": ("%s %s" % (kernel_name(p.ndim, stats["tile"]),
-                                  "adjoint+imaging" if kind == "adj" else "forward+store")),
-            "bytes_per_update": bpu, "points_per_launch": int(pts_launch),
-            "launch_ms": t_launch * 1e3, "peak_source": peak_src,
-            "timed_launches": int(acc[f"{kind}_timed"]),
-            "share_of_step": per_launch[kind] * n_l / args.steps / ms}
+    roof = roofline(acc, args.steps, ms, vd, p.ndim, stats["tile"])
 
     e2e = None
     if not args.no_e2e:
         gh = torch.empty(p.shape, dtype=torch.float32).pin_memory()
         nb = vp_h.numel() * 4 + rho_h.numel() * 4 + wav_h.numel() * 4 + obs_h.numel() * 4
-        ke = 1
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        ke = 3
+        te_all = []
         for _ in range(ke):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             vp_d = vp_h.to(dev, non_blocking=True)
             rho_d = rho_h.to(dev, non_blocking=True)
             wav_d = wav_h.to(dev, non_blocking=True)
@@ -575,9 +645,11 @@ def run_mine(args):
             Je, gd, _ = plan.gradient(vp_d, rho_d, geo, wav_d, obs_d)
             gh.copy_(gd, non_blocking=True)
             torch.cuda.synchronize()
-        te = (time.perf_counter() - t0) / ke
+            te_all.append(time.perf_counter() - t0)
+        te = statistics.median(te_all)
         e2e = {"value": world * upd / te / 1e9, "unit": "Gpts/s", "h2d_bytes_per_step": nb,
-               "d2h_bytes_per_step": gh.numel() * 4 + 8, "steps": ke}
+               "d2h_bytes_per_step": gh.numel() * 4 + 8, "steps": ke, "statistic": "median",
+               "samples_s": te_all}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -590,6 +662,8 @@ def run_mine(args):
     if rank == 0 and world == 1 and not args.no_extras:
         # reduced samples of the uneven-batch and serving patterns (full size:
         # --workload uneven / serving)
+        if args.workload == "breast2d":
+            extras["skull3d"] = skull3d_sample()
         extras["batched"] = uneven_batch(nprob=16, seed=4, reps=1)
         extras["serving"] = serving_stream(nreq=80, warm=10, seed=5)
         try:                               # the full Sec. 3.2 loop: ~3 s on one GB300

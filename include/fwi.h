@@ -196,6 +196,19 @@ fwi_status fwi_misfit_forward(fwi_plan* plan, const fwi_model* model, const fwi_
                               float* traces_opt);
 fwi_status fwi_misfit_backward(fwi_plan* plan, float* grad_m);
 
+/* fwi_misfit_backward with an optional second output: the gradient of the
+ * misfit with respect to the source wavelets,
+ *   grad_wavelet[s][i][n] = dJ/dq_{s,i}^n,   device [nshots][nsrc][nt] out,
+ * i.e. the adjoint field of each shot sampled at its sources with the
+ * injection weights / cell volume (the transpose of the source injection of
+ * Sec. 2.4; with the wavelets as the linear input of the forward map
+ * F: q -> traces, this is F* applied to the residual, the operator of the
+ * adjoint-state method of Sec. 2.2, Eqs. 7-9, for the wavelet variable).
+ * dJ/dq^{nt-1} is 0 (the last sample reaches no trace).  Either output may be
+ * NULL, not both.  Errors: as fwi_misfit_backward, FWI_ERR_BUDGET when the
+ * per-step source samples (nt x batch x nsrc floats) cannot be allocated. */
+fwi_status fwi_misfit_backward_ex(fwi_plan* plan, float* grad_m, float* grad_wavelet);
+
 /* ---- Uneven batches (many independent problems in one CUDA graph) ---- */
 
 /* One independent forward-modelling problem of a batch: its own grid, time
@@ -260,10 +273,15 @@ void fwi_batch_destroy(fwi_batch* batch);
  *     inputs and the output.  Shots run in batches that fit the scratch.
  *   stream: cudaStream_t to enqueue on; the call synchronises it before
  *     returning.
- * The first call on a device looks up the scratch address (once per device,
- * with that device current); make that first call before any stream capture.
- * All calls share the scratch and keep the last call's contents, so calls
- * that overlap on the GPU race; each call clears what must start at zero.
+ * The call runs on the current device; every device array must live there
+ * (FWI_ERR_INVALID_ARG otherwise).  The first call on a device looks up the
+ * scratch address (once per device, with that device current); make that
+ * first call before any stream capture.  The address is kept for the life of
+ * the process, so the entry point must not be used on a device after a
+ * cudaDeviceReset of it.  All calls share the scratch and keep the last
+ * call's contents, so calls that overlap on the GPU race; each call clears
+ * what must start at zero, and returns only when its own work on the scratch
+ * has finished, on success and on error.
  * Errors: FWI_ERR_BUDGET (with the required and available sizes in
  * fwi_last_error) when one shot of the grid does not fit the scratch, plus
  * the errors of fwi_plan_create and fwi_forward. */

@@ -27,6 +27,7 @@ STATUS = {0: "FWI_OK", 1: "FWI_ERR_INVALID_ARG", 2: "FWI_ERR_UNSTABLE_CFL", 3: "
 EXPORTS = ("fwi_plan_create", "fwi_plan_set_options", "fwi_plan_stats", "fwi_plan_estimate",
            "fwi_plan_destroy", "fwi_forward", "fwi_gradient", "fwi_last_error", "fwi_cfl_limit",
            "fwi_forward_noalloc", "fwi_misfit_forward", "fwi_misfit_backward",
+           "fwi_misfit_backward_ex",
            "fwi_batch_create", "fwi_batch_run", "fwi_batch_stats_get", "fwi_batch_destroy",
            "fwi_mem_available", "fwi_lowpass", "fwi_vp_update", "fwi_point_weights")
 
@@ -128,6 +129,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.fwi_misfit_forward.restype = ctypes.c_int
         lib.fwi_misfit_backward.argtypes = [vp, vp]
         lib.fwi_misfit_backward.restype = ctypes.c_int
+        lib.fwi_misfit_backward_ex.argtypes = [vp, vp, vp]
+        lib.fwi_misfit_backward_ex.restype = ctypes.c_int
         lib.fwi_batch_create.argtypes = [P(vp), ctypes.c_int, P(CProblem), P(COptions),
                                          ctypes.c_size_t, vp, ctypes.c_int]
         lib.fwi_batch_create.restype = ctypes.c_int
@@ -192,22 +195,37 @@ def forward_noalloc(shape, spacing, nt, dt, vp, rho, geometry, wavelet, traces=N
     that must not allocate device memory while they run; the caller still
     provides the inputs and the traces array."""
     import torch
-    if traces is None:
-        traces = torch.empty((geometry.nshots, geometry.nrec, int(nt)), device=vp.device,
-                             dtype=torch.float32)
     if stream is None:
-        stream = torch.cuda.current_stream()
+        stream = torch.cuda.current_stream(vp.device)
+    # the C side runs on the current device: make it the stream's device, on
+    # which every array must live (as for Plan)
+    dev = _stream_device(stream)
+    if traces is None:
+        traces = torch.empty((geometry.nshots, geometry.nrec, int(nt)), device=dev,
+                             dtype=torch.float32)
     n = int(np.prod(tuple(int(v) for v in shape)))
-    check_array(vp, n, "vp", vp.device)
-    check_array(rho, n, "rho", vp.device, optional=True)
-    check_array(wavelet, geometry.nshots * geometry.nsrc * int(nt), "wavelet", vp.device)
-    check_array(traces, geometry.nshots * geometry.nrec * int(nt), "traces", vp.device)
+    check_array(vp, n, "vp", dev)
+    check_array(rho, n, "rho", dev, optional=True)
+    check_array(wavelet, geometry.nshots * geometry.nsrc * int(nt), "wavelet", dev)
+    check_array(traces, geometry.nshots * geometry.nrec * int(nt), "traces", dev)
     g = make_grid(shape, spacing, order, sponge, c_ref)
     m = CModel(_ptr(vp), _ptr(rho))
-    _check(load().fwi_forward_noalloc(ctypes.byref(g), int(nt), float(dt), ctypes.byref(m),
-                                      ctypes.byref(geometry.c), _ptr(wavelet), _ptr(traces),
-                                      ctypes.c_void_p(stream.cuda_stream)))
+    with torch.cuda.device(dev):
+        _check(load().fwi_forward_noalloc(ctypes.byref(g), int(nt), float(dt), ctypes.byref(m),
+                                          ctypes.byref(geometry.c), _ptr(wavelet), _ptr(traces),
+                                          ctypes.c_void_p(stream.cuda_stream)))
     return traces
+
+
+def _stream_device(stream):
+    """torch.device of a CUDA stream (streams without a device attribute: the
+    current device)."""
+    import torch
+    try:
+        idx = stream.device.index
+    except AttributeError:
+        idx = None
+    return torch.device("cuda", idx if idx is not None else torch.cuda.current_device())
 
 
 LOWPASS_MAX_HALF_WIDTH = 2048
@@ -351,11 +369,7 @@ class Plan:
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
-        try:
-            idx = stream.device.index
-        except AttributeError:
-            idx = None
-        self.device = torch.device("cuda", idx if idx is not None else torch.cuda.current_device())
+        self.device = _stream_device(stream)
         self.npoints = int(np.prod(shape))
         h = ctypes.c_void_p()
         _check(lib.fwi_plan_create(ctypes.byref(h), ctypes.byref(g), self.nt, self.dt,
@@ -446,6 +460,28 @@ class Plan:
         finally:
             self._kept = None
         return grad
+
+    def misfit_backward_ex(self, grad=True, grad_wavelet=True):
+        """(dJ/dm or None, dJ/dq or None) of the last misfit_forward: the
+        gradient with respect to m = 1/vp^2 and with respect to the source
+        wavelets ([nshots][nsrc][nt]); True allocates an output, None skips it,
+        a tensor is written in place."""
+        import torch
+        if getattr(self, "_kept", None) is None:
+            raise FwiError(1, "no pending misfit_forward on this plan")
+        vp, _, geometry, wavelet, _ = self._kept
+        if grad is True:
+            grad = torch.empty(vp.shape, device=vp.device, dtype=torch.float32)
+        if grad_wavelet is True:
+            grad_wavelet = torch.empty(tuple(wavelet.shape), device=vp.device, dtype=torch.float32)
+        check_array(grad, self.npoints, "grad", self.device, optional=True)
+        check_array(grad_wavelet, geometry.nshots * geometry.nsrc * self.nt, "grad_wavelet",
+                    self.device, optional=True)
+        try:
+            _check(load().fwi_misfit_backward_ex(self._h, _ptr(grad), _ptr(grad_wavelet)))
+        finally:
+            self._kept = None
+        return grad, grad_wavelet
 
     def gradient(self, vp, rho, geometry: Geometry, wavelet, observed, grad=None, traces=False):
         """(J, grad_m, traces or None): L2 misfit and its gradient w.r.t. m = 1/vp^2."""

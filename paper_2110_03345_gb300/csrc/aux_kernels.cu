@@ -105,6 +105,18 @@ __global__ void k_sample(StepParams p) {
   }
 }
 
+__global__ void k_sample_slots(const float* __restrict__ u, long long fstride,
+                               const int* __restrict__ node, const float* __restrict__ w, int nc,
+                               int npts, int per_slot, float* __restrict__ out, long long off) {
+  const int pt = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt < npts) {
+    const float* ub = u + (long long)(pt / per_slot) * fstride;
+    float acc = 0.f;
+    for (int c = 0; c < nc; ++c) acc = fmaf(w[pt * nc + c], ub[node[pt * nc + c]], acc);
+    out[off + pt] = acc;
+  }
+}
+
 // Residual r = d - d_obs in place over the trace workspace [nt][B][nrec],
 // traces copied out to [shot][nrec][nt], J partials per block (FP64).
 // Block (32, 8) handles a 32 (time) x 32 (receiver) tile of one shot.
@@ -241,6 +253,15 @@ cudaError_t launch_sample(const StepParams& p, cudaStream_t st) {
   const long long n = (long long)p.B * p.nrec;
   if (n == 0) return cudaSuccess;
   k_sample<<<(int)((n + 255) / 256), 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample_slots(const float* u, long long fstride, const int* node, const float* w,
+                                int nc, int npts, int per_slot, float* out, long long off,
+                                cudaStream_t st) {
+  if (npts <= 0) return cudaSuccess;
+  k_sample_slots<<<(npts + 127) / 128, 128, 0, st>>>(u, fstride, node, w, nc, npts, per_slot, out,
+                                                     off);
   return cudaGetLastError();
 }
 

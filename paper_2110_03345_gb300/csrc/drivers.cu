@@ -459,6 +459,14 @@ fwi_status gradient_adjoint_batch(Call& c, int j, int shot0, int nb, const DevTa
     p.step_off = (long long)k * B * c.geom->nrec;
     FWI_TRY(launch_step(c, p, true));
     std::swap(LA, LB);
+    if (c.Dw) {   // dJ/dq^{k-1}: lambda^{k-1} sampled at the sources (weights / cell volume)
+      const int nsrc = c.geom->nsrc;
+      cudaError_t e = launch_sample_slots(LA, (long long)fs, c.ws_node, c.ws_w, c.ncorner,
+                                          nb * nsrc, nsrc, c.Dw,
+                                          (long long)(k - 1) * B * nsrc, P->st);
+      if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
+      c.launches++;
+    }
   }
   if (nt >= 2) {   // imaging term of lambda^0
     FWI_TRY(ensure_segment(0));
@@ -474,9 +482,11 @@ fwi_status gradient_adjoint_batch(Call& c, int j, int shot0, int nb, const DevTa
 fwi_status gradient_finish(Call& c, int batches, double* misfit, float* grad_m) {
   fwi_plan* P = c.P;
   const int G = (c.pl.B + c.pl.S - 1) / c.pl.S;   // gradient slots in use
-  cudaError_t e = launch_grad_finalize(P->L, c.W.G, G, 1.0 / (P->dt * P->dt), grad_m, P->d_flags, P->st);
-  if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
-  c.launches++;
+  if (grad_m) {
+    cudaError_t e = launch_grad_finalize(P->L, c.W.G, G, 1.0 / (P->dt * P->dt), grad_m, P->d_flags, P->st);
+    if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
+    c.launches++;
+  }
   std::vector<double> J(std::max(batches, 1));
   if (batches > 0)
     CUDA_TRY(cudaMemcpyAsync(J.data(), P->d_J, sizeof(double) * batches, cudaMemcpyDeviceToHost, P->st));
@@ -598,7 +608,13 @@ fwi_status fwi_misfit_forward(fwi_plan* P, const fwi_model* model, const fwi_geo
 }
 
 fwi_status fwi_misfit_backward(fwi_plan* P, float* grad_m) {
-  if (!P || !grad_m) return fail(FWI_ERR_INVALID_ARG, "plan or grad_m is NULL");
+  if (!grad_m) return fail(FWI_ERR_INVALID_ARG, "grad_m is NULL");
+  return fwi_misfit_backward_ex(P, grad_m, nullptr);
+}
+
+fwi_status fwi_misfit_backward_ex(fwi_plan* P, float* grad_m, float* grad_wavelet) {
+  if (!P) return fail(FWI_ERR_INVALID_ARG, "plan is NULL");
+  if (!grad_m && !grad_wavelet) return fail(FWI_ERR_INVALID_ARG, "grad_m and grad_wavelet are both NULL");
   SavedGrad* S = P->saved;
   if (!S) return fail(FWI_ERR_INVALID_ARG, "no pending fwi_misfit_forward on this plan");
   P->saved = nullptr;   // the state is used once
@@ -611,13 +627,45 @@ fwi_status fwi_misfit_backward(fwi_plan* P, float* grad_m) {
   cudaError_t e = cudaMemsetAsync(c.W.G, 0, fs * c.pl.B * sizeof(float), P->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(P->d_flags, 0, sizeof(int) * 4, P->st);
   if (e != cudaSuccess) st = fail(FWI_ERR_CUDA, cudaGetErrorString(e));
+  // dJ/dq workspace: per-step source samples and the batch's sampling table
+  const int nsrc = S->geom.nsrc;
+  const size_t npt = (size_t)c.pl.B * nsrc;
+  void* wbuf = nullptr;
+  if (st == FWI_OK && grad_wavelet) {
+    const size_t bytes = align_up((size_t)P->nt * npt * 4, 256) + 2 * align_up(npt * c.ncorner * 4, 256);
+    e = pool_alloc(&wbuf, bytes, P->st, P->device);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      wbuf = nullptr;
+      st = fail(FWI_ERR_BUDGET, std::string("dJ/dq workspace: ") + cudaGetErrorString(e));
+    } else {
+      Carve wc(static_cast<char*>(wbuf));
+      c.Dw = wc.take<float>((size_t)P->nt * npt);
+      int* node = wc.take<int>(npt * c.ncorner);
+      float* w = wc.take<float>(npt * c.ncorner);
+      c.ws_node = node;
+      c.ws_w = w;
+    }
+  }
   int batch = 0;
   for (int shot0 = 0; shot0 < S->geom.nshots && st == FWI_OK; shot0 += c.pl.B, ++batch) {
     const int nb = std::min(c.pl.B, S->geom.nshots - shot0);
     Carve srcC = S->tabC;
     DevTable src;
     st = build_source_table(c, shot0, nb, srcC, src);
+    if (st == FWI_OK && c.Dw) {
+      e = cudaMemsetAsync(c.Dw, 0, (size_t)P->nt * npt * 4, P->st);   // dJ/dq^{nt-1} = 0
+      if (e != cudaSuccess) st = fail(FWI_ERR_CUDA, cudaGetErrorString(e));
+      if (st == FWI_OK)
+        st = build_source_sampling(c, shot0, nb, const_cast<int*>(c.ws_node),
+                                   const_cast<float*>(c.ws_w));
+    }
     if (st == FWI_OK) st = gradient_adjoint_batch(c, batch, shot0, nb, src);
+    if (st == FWI_OK && c.Dw) {
+      e = launch_traces_out(c.Dw, grad_wavelet, c.pl.B, shot0, nb, nsrc, P->nt, P->d_flags, P->st);
+      if (e != cudaSuccess) st = fail(FWI_ERR_CUDA, cudaGetErrorString(e));
+      c.launches++;
+    }
     if (st == FWI_OK && shot0 + c.pl.B < S->geom.nshots) {
       e = cudaStreamSynchronize(P->st);
       if (e != cudaSuccess) st = fail(FWI_ERR_CUDA, cudaGetErrorString(e));
@@ -625,6 +673,14 @@ fwi_status fwi_misfit_backward(fwi_plan* P, float* grad_m) {
   }
   double J = 0.0;
   if (st == FWI_OK) st = gradient_finish(c, 0, &J, grad_m);
+  if (wbuf) {
+    cudaStreamSynchronize(P->st);
+    cudaFreeAsync(wbuf, P->st);
+    cudaGetLastError();
+  }
+  c.Dw = nullptr;
+  c.ws_node = nullptr;
+  c.ws_w = nullptr;
   delete_saved(S);
   return st;
 }

@@ -181,6 +181,11 @@ cudaError_t launch_density_grad(const Layout& L, const float* lnr, const AxisW& 
                                 const AxisW& wy, const AxisW& wz, float* bx, float* by,
                                 float* bz, cudaStream_t st);
 cudaError_t launch_sample(const StepParams& p, cudaStream_t st);
+// out[off + pt] = sum_c w[pt][c] u[pt / per_slot][node[pt][c]] for pt < npts: samples of
+// per-slot point sets (e.g. the sources of each shot of a batch), nc corners each
+cudaError_t launch_sample_slots(const float* u, long long fstride, const int* node, const float* w,
+                                int nc, int npts, int per_slot, float* out, long long off,
+                                cudaStream_t st);
 cudaError_t launch_misfit(const float* d_ws, const float* obs, float* traces_out, int B,
                           int shot0, int nshots_batch, int nrec, int nt, double* partials,
                           int* nonfinite, int npartials, cudaStream_t st);

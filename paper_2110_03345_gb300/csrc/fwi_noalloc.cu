@@ -14,10 +14,14 @@
 // allocated until the process exits.  Its host-side name is only a stand-in:
 // host code must use the device address returned by cudaGetSymbolAddress,
 // which is looked up once per device, with that device current, on the first
-// call made on it (so make the first call before any stream capture).  Every
-// call reuses the same array: calls that overlap on the GPU (different
-// streams, threads or processes sharing a context) race on it.  Each call
-// clears what must start at zero before use.
+// call made on it (so make the first call before any stream capture).  The
+// address is kept for the life of the process: after a cudaDeviceReset the
+// entry point must not be used on that device again.  Every call reuses the
+// same array: calls that overlap on the GPU (different streams, threads or
+// processes sharing a context) race on it.  Each call clears what must start
+// at zero before use, and returns only once its work on the scratch is
+// finished (on success and on error).  All device arrays of a call must live
+// on the current device; others are rejected.
 #include "fwi_plan.cuh"
 
 #include <cuda_runtime.h>
@@ -83,7 +87,36 @@ fwi_status forward_in_buffer(const fwi_grid* grid, int nt, double dt, const fwi_
   if ((geom->nshots + pl.B - 1) / pl.B > JCAP)
     return fail(FWI_ERR_BUDGET, "too many shot batches for the static scratch");
   if (P.c_ref > 0.0) FWI_TRY(build_sponge(&P));
-  return fwi_forward(&P, model, geom, wavelet, nt, dt, traces);
+  const fwi_status st = fwi_forward(&P, model, geom, wavelet, nt, dt, traces);
+  if (st != FWI_OK) {
+    // an error after work was enqueued: wait for it, so that no kernel of this
+    // call still uses the shared scratch when the caller issues the next call
+    cudaStreamSynchronize(P.st);
+    cudaGetLastError();
+  }
+  return st;
+}
+
+// The device arrays of a call must live on the device the call runs on: the
+// scratch is that device's, and a pointer to another device's memory would be
+// read through the wrong address space.
+fwi_status check_on_device(const void* ptr, const char* name, int dev) {
+  if (!ptr) return FWI_OK;
+  cudaPointerAttributes a{};
+  const cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(FWI_ERR_INVALID_ARG, std::string("fwi_forward_noalloc: ") + name +
+                                         " is not a CUDA pointer: " + cudaGetErrorString(e));
+  }
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+    return fail(FWI_ERR_INVALID_ARG, std::string("fwi_forward_noalloc: ") + name +
+                                         " is not device memory");
+  if (a.device != dev)
+    return fail(FWI_ERR_INVALID_ARG, std::string("fwi_forward_noalloc: ") + name + " lives on device " +
+                                         std::to_string(a.device) + ", the call runs on device " +
+                                         std::to_string(dev));
+  return FWI_OK;
 }
 
 }  // namespace fwi
@@ -107,6 +140,17 @@ extern "C" fwi_status fwi_forward_noalloc(const fwi_grid* grid, int nt, double d
     cudaGetLastError();
     fwi::set_last_error("fwi_forward_noalloc: no usable CUDA device");
     return FWI_ERR_CUDA;
+  }
+  if (!model || !model->vp || !wavelet || !traces) {
+    fwi::set_last_error("fwi_forward_noalloc: model, vp, wavelet or traces is NULL");
+    return FWI_ERR_INVALID_ARG;
+  }
+  for (const auto& a : {std::make_pair((const void*)model->vp, "vp"),
+                        std::make_pair((const void*)model->rho, "rho"),
+                        std::make_pair((const void*)wavelet, "wavelet"),
+                        std::make_pair((const void*)traces, "traces")}) {
+    const fwi_status s = fwi::check_on_device(a.first, a.second, dev);
+    if (s != FWI_OK) return s;
   }
   void* base = nullptr;
   {

@@ -182,6 +182,11 @@ struct Call {
   int64_t fwd_launches = 0, adj_launches = 0;
   int64_t fwd_points = 0, adj_points = 0;
   int64_t fwd_timed = 0, adj_timed = 0;   // launches that carried events
+  // optional dJ/dq (the adjoint of wavelet -> traces sampled at the sources):
+  // per-step samples [nt][B][nsrc] and the batch's source sampling table
+  float* Dw = nullptr;
+  const int* ws_node = nullptr;   // [B * nsrc][ncorner] node of each source corner
+  const float* ws_w = nullptr;    // its weight / cell volume
 };
 
 // State kept between fwi_misfit_forward and fwi_misfit_backward.
@@ -237,6 +242,9 @@ fwi_status build_source_table(Call& c, int shot0, int nb, Carve& C, DevTable& D)
 fwi_status prepare_common(Call& c, Carve& tabC);
 size_t tables_bound(const fwi_plan* P, const fwi_geometry* g, const Plan& pl);
 
+// ---- fwi_noalloc.cu
+fwi_status check_on_device(const void* ptr, const char* name, int dev);
+
 // ---- drivers.cu: launches, forward and adjoint sweeps, call set-up
 fwi_status make_tensor_map(const fwi_plan* P, const float* base, int nslots, int shape,
                            CUtensorMap* out);
@@ -260,5 +268,6 @@ fwi_status gradient_forward_batch(Call& c, int j, int shot0, int nb, const DevTa
                                   const float* observed, float* traces_opt);
 fwi_status gradient_adjoint_batch(Call& c, int j, int shot0, int nb, const DevTable& src);
 fwi_status gradient_finish(Call& c, int batches, double* misfit, float* grad_m);
+fwi_status build_source_sampling(Call& c, int shot0, int nb, int* d_node, float* d_w);
 
 }  // namespace fwi

@@ -139,6 +139,35 @@ fwi_status build_source_table(Call& c, int shot0, int nb, Carve& C, DevTable& D)
   return upload_table(P, H, C, D);
 }
 
+// Sampling table of the sources of shots shot0 .. shot0+nb-1: per (slot,
+// source) point its corner nodes and weight / cell volume (the transpose of
+// the injection, so that sampling an adjoint field there gives dJ/dq).
+fwi_status build_source_sampling(Call& c, int shot0, int nb, int* d_node, float* d_w) {
+  fwi_plan* P = c.P;
+  const fwi_geometry* g = c.geom;
+  const int nd = P->grid.ndim;
+  double dV = 1.0;
+  for (int a = 0; a < nd; ++a) dV *= P->h[a];
+  std::vector<int> node((size_t)nb * g->nsrc * c.ncorner, 0);
+  std::vector<float> w(node.size(), 0.f);
+  for (int b = 0; b < nb; ++b)
+    for (int k = 0; k < g->nsrc; ++k) {
+      const Corners cr = point_corners(P, g->src_xyz + ((long long)(shot0 + b) * g->nsrc + k) * nd);
+      const size_t pt = (size_t)b * g->nsrc + k;
+      for (int q = 0; q < cr.n; ++q) {
+        node[pt * c.ncorner + q] = (int)node_index(P->L, cr.node[q]);
+        w[pt * c.ncorner + q] = (float)(cr.w[q] / dV);
+      }
+    }
+  // pageable sources: the copies have staged them when cudaMemcpyAsync returns
+  CUDA_TRY(cudaMemcpyAsync(d_node, node.data(), node.size() * 4, cudaMemcpyHostToDevice, P->st));
+  CUDA_TRY(cudaMemcpyAsync(d_w, w.data(), w.size() * 4, cudaMemcpyHostToDevice, P->st));
+  CUDA_TRY(cudaStreamSynchronize(P->st));
+  c.ws_node = d_node;
+  c.ws_w = d_w;
+  return FWI_OK;
+}
+
 fwi_status prepare_common(Call& c, Carve& tabC) {
   fwi_plan* P = c.P;
   const fwi_geometry* g = c.geom;

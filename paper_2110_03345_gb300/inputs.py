@@ -44,9 +44,10 @@ def ricker_fn(f0: float, t0: float | None = None, amp: float = 1.0):
     return q
 
 
-def ring(n: int, centre, radius: float):
-    """n points on a circle; coordinates in axis order (y, x)."""
-    th = 2.0 * np.pi * np.arange(n) / n
+def ring(n: int, centre, radius: float, rotation: float = 0.0):
+    """n points on a circle, turned by `rotation` element pitches; coordinates
+    in axis order (y, x)."""
+    th = 2.0 * np.pi * (np.arange(n) + rotation) / n
     return np.stack([centre[0] + radius * np.sin(th), centre[1] + radius * np.cos(th)], 1)
 
 
@@ -179,13 +180,15 @@ def gaussian_blobs(shape, dx, seed, n=3, amp=20.0, sigma=3e-3, extent=0.3):
 
 def breast_problem(shape, dx, nt, nelem=256, shots=None, order=8, nb=20, seed=2, f0=500e3,
                    c_max=1600.0, radius=None, perturb_seed=20, fat_vp=(1430.0, 1470.0),
-                   incl_vp=(1400.0, 1600.0)):
+                   incl_vp=(1400.0, 1600.0), rotation=0.0):
     """Breast-like 2D problem on a (possibly non-square) grid: the phantom of
     ``breast_model_2d`` scaled to the smaller side and centre-cropped, a ring of
     ``nelem`` elements about the centre (default radius: 0.4395 x the smaller
     side, i.e. 45 mm on a 1024 x 0.1 mm grid); shots fire the
     given elements (default every second one); all elements receive.  The
-    observed-data model adds 3 Gaussian blobs (+-20 m/s, 3 mm x scale)."""
+    observed-data model adds 3 Gaussian blobs (+-20 m/s, 3 mm x scale).
+    rotation turns the whole array by that many element pitches (a rotated
+    acquisition with the same phantom)."""
     ny, nx = (int(s) for s in shape)
     m, full = min(ny, nx), max(ny, nx)
     scale = m * dx / (1024 * 0.1e-3)
@@ -196,7 +199,7 @@ def breast_problem(shape, dx, nt, nelem=256, shots=None, order=8, nb=20, seed=2,
     dt = cfl_dt(dx, c_max)
     ctr = ((ny / 2) * dx, (nx / 2) * dx)
     rad = 0.4395 * m * dx if radius is None else radius
-    elems = ring(nelem, ctr, rad)
+    elems = ring(nelem, ctr, rad, rotation)
     fire = np.arange(0, nelem, 2) if shots is None else np.asarray(shots)
     src = elems[fire][:, None, :]
     w = ricker(f0, dt, nt)
@@ -208,7 +211,7 @@ def breast_problem(shape, dx, nt, nelem=256, shots=None, order=8, nb=20, seed=2,
 
 
 def config_breast_2d(n=1024, dx=0.1e-3, nt=4000, nelem=256, radius=45e-3, f0=500e3,
-                     order=8, nb=20, seed=2, shots=None, c_max=1600.0):
+                     order=8, nb=20, seed=2, shots=None, c_max=1600.0, rotation=0.0):
     """Breast-like 2D problem: n^2 grid, 256-element ring of radius 45 mm (scaled
     with n dx) about the centre; shots fire elements 0, 2, ..., all elements
     receive.  The observed-data model is the phantom plus 3 Gaussian blobs
@@ -216,7 +219,7 @@ def config_breast_2d(n=1024, dx=0.1e-3, nt=4000, nelem=256, radius=45e-3, f0=500
     0.1 mm, 128 shots of 4000 steps, dt = 25 ns)."""
     scale = n * dx / (1024 * 0.1e-3)
     return breast_problem((n, n), dx, nt, nelem=nelem, shots=shots, order=order, nb=nb,
-                          seed=seed, f0=f0, c_max=c_max, radius=radius * scale)
+                          seed=seed, f0=f0, c_max=c_max, radius=radius * scale, rotation=rotation)
 
 
 def skull_model_3d(n: int, dx: float, scale: float = 1.0):

@@ -58,3 +58,21 @@ def test_gradient_sum_over_two_ranks(tmp_path):
     J, grad, _ = oracle.gradient(g, p.vp, p.rho, p.src_xyz, p.wavelet, p.rec_xyz, obs)
     assert res[0] == pytest.approx(J, rel=1e-12)
     np.testing.assert_allclose(res[1:].reshape(p.shape), grad, rtol=1e-10, atol=1e-12 * abs(grad).max())
+
+
+@pytest.mark.parametrize("workload", ["breast2d", "skull3d"])
+def test_bench_ranks_fire_distinct_shots(workload):
+    """The benchmark's ranks together fire world x (128 | 32) distinct shots
+    (no rank repeats another rank's source positions)."""
+    import argparse
+    import bench
+    for world in (1, 2, 8):
+        seen = set()
+        for r in range(world):
+            a = argparse.Namespace(workload=workload, n=64 if workload == "breast2d" else 32,
+                                   nt=8, shots=0)
+            p = bench.make_problem(a, r, world)
+            pts = {tuple(np.round(s, 15)) for s in p.src_xyz[:, 0, :]}
+            assert len(pts) == p.nshots
+            seen |= pts
+        assert len(seen) == world * (128 if workload == "breast2d" else 32)
