@@ -62,13 +62,22 @@ typedef struct {
                            the first model the plan sees, then kept fixed */
 } fwi_grid;
 
-/* Medium (Sec. 2.3 Listing 6): sound speed and optional density. */
+/* Medium (Sec. 2.3 Listing 6): sound speed, optional density and optional
+ * power-law attenuation (the eta d/dt (-lap)^(y/2) p term of Eq. 10, Sec. 2.4,
+ * eta = -2 alpha0 vp^(y-1)).  Zero-initialise the fields you do not use. */
 typedef struct {
     const float* vp;    /* device [N], N = prod(shape): the sound speed in m/s, or
                            the squared slowness m = 1/vp^2 in s^2/m^2 when
                            param = FWI_PARAM_M; > 0 and finite */
     const float* rho;   /* device [N] kg/m^3, > 0; NULL selects constant density */
     int param;          /* FWI_PARAM_VP (0) or FWI_PARAM_M (1) */
+    const float* alpha0; /* device [N] attenuation coefficient alpha0 >= 0, or NULL
+                            for none: nepers/m for att_power 0 (frequency
+                            independent), nepers/m per (rad/s)^2 for att_power 2;
+                            held fixed (not differentiated) */
+    int att_power;      /* y: 0 (damping alpha0 vp dt added to the sponge term of the
+                           update) or 2 (2 alpha0 vp times the backward difference
+                           in time of the Laplacian); ignored when alpha0 is NULL */
 } fwi_model;
 
 #define FWI_PARAM_VP 0
@@ -108,6 +117,14 @@ typedef struct {
                            programmatic dependent launch; whole runs of uneven
                            problems are graphs in fwi_batch_*) */
     int shots_per_cta;  /* 2D TMA variants: shots per CTA (0: chosen from the SM count; 3D: 1) */
+    int time_order;     /* 0 or 2: second-order leapfrog; 4: the fourth-order-in-time
+                           modified-equation scheme (Sec. 2.4 states the paper's
+                           solver is fourth order in time): per step
+                           F = k w + k (L(k w) + s^{n+1} - 2 s^n + s^{n-1}) / 12,
+                           w = L u^n + s^n, (1+a) u^{n+1} = 2u^n - (1-a) u^{n-1} + F;
+                           stable to sqrt(3) x the leapfrog's CFL limit */
+    int interp;         /* off-grid sources and receivers: FWI_INTERP_LINEAR (0) or
+                           FWI_INTERP_SINC (1), see fwi_point_weights */
 } fwi_options;
 
 /* Counters of the last forward/gradient call on a plan. */

@@ -48,7 +48,8 @@ PARAM_VP, PARAM_M = 0, 1
 
 
 class CModel(ctypes.Structure):
-    _fields_ = [("vp", ctypes.c_void_p), ("rho", ctypes.c_void_p), ("param", ctypes.c_int)]
+    _fields_ = [("vp", ctypes.c_void_p), ("rho", ctypes.c_void_p), ("param", ctypes.c_int),
+                ("alpha0", ctypes.c_void_p), ("att_power", ctypes.c_int)]
 
 
 class CGeometry(ctypes.Structure):
@@ -72,7 +73,8 @@ class CBatchStats(ctypes.Structure):
 class COptions(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int), ("ckpt_every", ctypes.c_int), ("tile", ctypes.c_int),
                 ("profile", ctypes.c_int), ("use_graphs", ctypes.c_int),
-                ("shots_per_cta", ctypes.c_int)]
+                ("shots_per_cta", ctypes.c_int), ("time_order", ctypes.c_int),
+                ("interp", ctypes.c_int)]
 
 
 class CStats(ctypes.Structure):
@@ -384,14 +386,16 @@ class Plan:
 
     __del__ = close
 
-    def set_options(self, batch=0, ckpt_every=0, tile=0, profile=False, shots_per_cta=0):
+    def set_options(self, batch=0, ckpt_every=0, tile=0, profile=False, shots_per_cta=0,
+                    time_order=0, interp=INTERP_LINEAR):
         """tile: 0 default; 2D 1-4 shared-memory staged (one shot per CTA), 5-8
         TMA-staged with shots looped inside a CTA; 3D 1-4 shared-memory staged,
         5-8 TMA plane ring, 9-12 TMA plane ring with two x points per thread.
-        shots_per_cta: 2D TMA variants only."""
+        shots_per_cta: 2D TMA variants only.  time_order: 2 (leapfrog) or 4
+        (fourth order in time).  interp: INTERP_LINEAR or INTERP_SINC points."""
         # profile: True / 1 times every stencil launch, n > 1 every n-th
         self._opts = COptions(int(batch), int(ckpt_every), int(tile), int(profile),
-                              0, int(shots_per_cta))
+                              0, int(shots_per_cta), int(time_order), int(interp))
         _check(load().fwi_plan_set_options(self._h, ctypes.byref(self._opts)))
 
     def stats(self) -> dict:
@@ -405,10 +409,18 @@ class Plan:
                                         ctypes.byref(b)))
         return int(b.value)
 
+    def set_attenuation(self, alpha0=None, power=0):
+        """Power-law attenuation of Eq. 10 for the following calls: alpha0 a
+        CUDA float32 field of the grid's size (None: no attenuation), power
+        y = 0 or 2.  The tensor must stay alive while it is set."""
+        check_array(alpha0, self.npoints, "alpha0", self.device, optional=True)
+        self._att = (alpha0, int(power))
+
     def _model(self, vp, rho, param=PARAM_VP):
         check_array(vp, self.npoints, "vp", self.device)
         check_array(rho, self.npoints, "rho", self.device, optional=True)
-        return CModel(_ptr(vp), _ptr(rho), int(param))
+        alpha0, power = getattr(self, "_att", (None, 0))
+        return CModel(_ptr(vp), _ptr(rho), int(param), _ptr(alpha0), int(power))
 
     def _check_shots(self, geometry, wavelet, traces=None, observed=None):
         ns, nrec = geometry.nshots, geometry.nrec
@@ -543,7 +555,7 @@ class Batch:
             arr[i].wavelet = _ptr(pr["wavelet"])
             arr[i].traces = _ptr(tr)
         self._arr = arr
-        self._opts = COptions(0, 0, int(tile), 0, 0, int(shots_per_cta))
+        self._opts = COptions(0, 0, int(tile), 0, 0, int(shots_per_cta), 0, 0)
         h = ctypes.c_void_p()
         _check(lib.fwi_batch_create(ctypes.byref(h), len(problems), arr, ctypes.byref(self._opts),
                                     int(budget), ctypes.c_void_p(stream.cuda_stream),

@@ -125,6 +125,8 @@ StepParams base_params(Call& c) {
 }
 
 long long launch_threads(const Call& c, int B) {
+  if (c.pl.sc.ext())
+    return (long long)c.T.ntiles() * B * EXT_TX * (c.P->grid.ndim == 3 ? EXT_TY3 : EXT_TY2);
   const int by = (c.P->grid.ndim == 3) ? tile3_variant(c.pl.shape).by
                  : c.pl.tma ? tile2_tma_variant(c.pl.shape).by : tile2_variant(c.pl.shape).by;
   const int ctas_z = (B + c.pl.S - 1) / c.pl.S;
@@ -180,12 +182,71 @@ fwi_status launch_step(Call& c, const StepParams& p_in, bool adj) {
   return FWI_OK;
 }
 
+// One time step of an extended scheme (kernels_ext.cu), counted and timed as
+// one stencil launch: the fourth-order scheme's two passes (k w, then the
+// update from k w; the adjoint's k L^T lambda, then the update with the
+// receiver residuals weighted 12 inside the 1/12 bracket), or the single
+// pass of the attenuating leapfrog.
+fwi_status ext_step(Call& c, const StepParams& p_in, bool adj) {
+  fwi_plan* P = c.P;
+  StepParams p = p_in;
+  const int nd = P->grid.ndim;
+  if (!adj && p.nrec > 0 && (long long)p.B * p.nrec > launch_threads(c, p.B)) {
+    cudaError_t e = launch_sample(p, P->st);
+    if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
+    c.launches++;
+    p.nrec = 0;
+  }
+  const bool prof = P->opt.profile > 0 &&
+                    (c.fwd_launches + c.adj_launches) % P->opt.profile == 0;
+  p.flags = P->d_flags + 1;
+  p.S = 1;
+  p.att = c.W.ATT;
+  p.q = adj ? c.W.QA : c.W.QF;
+  if (p.inj_scale == 0.f) p.inj_scale = 1.f;
+  if (prof) FWI_TRY(record_event(P, adj ? 1 : 0));
+  cudaError_t e;
+  if (c.pl.sc.t4) {
+    StepParams a = p;   // pass 1 (forward) / pass A (adjoint): k (L x + s) into KW
+    a.x = p.u;
+    a.out = c.W.KW;
+    a.hist = nullptr;
+    a.hist2 = nullptr;
+    a.image = 0;
+    if (adj) a.inj_off = nullptr;   // the residuals enter the second pass only
+    e = launch_ext(a, nd, P->R, c.vd, adj, EXT_KW, P->st);
+    if (e == cudaSuccess) {
+      StepParams b = p;   // pass 2 / B: the update from k w (k L^T lambda)
+      b.x = c.W.KW;
+      b.nrec = 0;
+      if (!adj) b.vals = c.W.D2Q;   // s^{n+1} - 2 s^n + s^{n-1}
+      else b.inj_scale = 12.f;      // 12 P^T r inside the 1/12 bracket
+      e = launch_ext(b, nd, P->R, c.vd, adj, EXT_T4, P->st);
+    }
+    c.launches += 2;
+  } else {
+    p.x = p.u;
+    e = launch_ext(p, nd, P->R, c.vd, adj, c.pl.sc.att == 0 ? EXT_ATT0 : EXT_ATT2, P->st);
+    c.launches++;
+  }
+  if (e != cudaSuccess) return fail(FWI_ERR_CUDA, std::string("stencil launch: ") + cudaGetErrorString(e));
+  if (prof) {
+    FWI_TRY(record_event(P, adj ? 1 : 0));
+    if (adj) c.adj_timed++;
+    else c.fwd_timed++;
+  }
+  const int64_t pts = (int64_t)p.B * P->L.nx * P->L.ny * P->L.nz;
+  if (adj) { c.adj_launches++; c.adj_points += pts; }
+  else { c.fwd_launches++; c.fwd_points += pts; }
+  return FWI_OK;
+}
+
 // Forward sweep of one batch: steps n = n0 .. n1-1 starting from (A = u^{n0},
 // Bf = u^{n0-1}).  hist_base: full history [n][B][fs] (n indexed from 0) or a
 // segment buffer indexed from n0; sample: record d^n for each step.
 fwi_status forward_steps(Call& c, int nb, int shot0, const DevTable& src, float*& A, float*& Bf,
                          int n0, int n1, float* hist_base, int hist_n0, bool sample,
-                         int K_ckpt, float* CK) {
+                         int K_ckpt, float* CK, float* hist2_base) {
   fwi_plan* P = c.P;
   const size_t fs = (size_t)P->L.fstride;
   StepParams p = base_params(c);
@@ -199,20 +260,28 @@ fwi_status forward_steps(Call& c, int nb, int shot0, const DevTable& src, float*
   p.smp_w = c.smp_w;
   p.smp_out = c.D;
   p.nrec = sample ? c.geom->nrec : 0;
+  const bool ext = c.pl.sc.ext();
+  const size_t cm = (size_t)c.pl.sc.ckpt_fields();
   for (int n = n0; n < n1; ++n) {
     if (K_ckpt > 0 && n % K_ckpt == 0) {
+      // checkpoint j: (u^n, u^{n-1}) and, for y = 2 attenuation, lap u^{n-1}
       const size_t j = n / K_ckpt;
-      float* dst = CK + 2 * j * fs * c.pl.B;
+      float* dst = CK + cm * j * fs * c.pl.B;
       CUDA_TRY(cudaMemcpyAsync(dst, A, fs * nb * sizeof(float), cudaMemcpyDeviceToDevice, P->st));
       CUDA_TRY(cudaMemcpyAsync(dst + fs * c.pl.B, Bf, fs * nb * sizeof(float),
                                cudaMemcpyDeviceToDevice, P->st));
+      if (cm == 3)
+        CUDA_TRY(cudaMemcpyAsync(dst + 2 * fs * c.pl.B, c.W.QF, fs * nb * sizeof(float),
+                                 cudaMemcpyDeviceToDevice, P->st));
     }
     p.u = A;
     p.up = Bf;
     p.hist = hist_base ? hist_base + (size_t)(n - hist_n0) * fs * c.pl.B : nullptr;
+    p.hist2 = hist2_base ? hist2_base + (size_t)(n - hist_n0) * fs * c.pl.B : nullptr;
     p.step_off = n;
     p.smp_off = (long long)n * c.pl.B * c.geom->nrec;
-    FWI_TRY(launch_step(c, p, false));
+    if (ext) FWI_TRY(ext_step(c, p, false));
+    else FWI_TRY(launch_step(c, p, false));
     std::swap(A, Bf);
   }
   (void)shot0;
@@ -258,14 +327,26 @@ fwi_status prepare_model(Call& c) {
   double sum = 0.0;
   for (int a = 0; a < P->grid.ndim; ++a) sum += 1.0 / (P->h[a] * P->h[a]);
   // stability of the leapfrog: c dt sqrt(sum 1/h^2) <= 2 / sqrt(lambda_max)
-  const double lim1 = cfl_limit(1, P->grid.order);
+  // (the fourth-order scheme is stable to sqrt(3) times that)
+  const double tf = c.pl.sc.t4 ? std::sqrt(3.0) : 1.0;
+  const double lim1 = cfl_limit(1, P->grid.order) * tf;
   const double cfl = (double)vmax * P->dt * std::sqrt(sum);
   if (cfl > 0.95 * lim1) {
-    char buf[160];
-    std::snprintf(buf, sizeof(buf), "CFL %.4f exceeds 0.95 x leapfrog limit (%.4f) for vp_max %.1f",
-                  cfl / std::sqrt((double)P->grid.ndim), 0.95 * cfl_limit(P->grid.ndim, P->grid.order),
-                  (double)vmax);
+    char buf[192];
+    std::snprintf(buf, sizeof(buf), "CFL %.4f exceeds 0.95 x the %s limit (%.4f) for vp_max %.1f",
+                  cfl / std::sqrt((double)P->grid.ndim), c.pl.sc.t4 ? "fourth-order scheme's" : "leapfrog",
+                  0.95 * tf * cfl_limit(P->grid.ndim, P->grid.order), (double)vmax);
     return fail(FWI_ERR_UNSTABLE_CFL, buf);
+  }
+  if (c.pl.sc.att >= 0) {
+    CUDA_TRY(cudaMemsetAsync(c.W.ATT, 0, fs * sizeof(float), P->st));
+    e = launch_att_prep(P->L, m->vp, m->param, m->alpha0, c.pl.sc.att, P->dt, c.W.ATT, P->st);
+    if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
+  }
+  if (c.pl.sc.t4) {
+    e = launch_second_difference(c.wavelet, c.W.D2Q, (long long)c.geom->nshots * c.geom->nsrc, P->nt,
+                                 P->st);
+    if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
   }
   if (!P->sponge_ready) {
     if (P->c_ref <= 0.0) P->c_ref = vmax;
@@ -296,7 +377,9 @@ fwi_status begin_call(fwi_plan* P, const fwi_model* model, const fwi_geometry* g
     delete_saved(P->saved);
     P->saved = nullptr;
   }
-  FWI_TRY(choose_plan(P, geom, c.vd, grad, c.pl, split));
+  Scheme sc;
+  FWI_TRY(resolve_scheme(P, model, &sc));
+  FWI_TRY(choose_plan(P, geom, c.vd, grad, c.pl, split, sc));
   FWI_TRY(ensure_arena(P, c.pl.bytes));
   Carve C(P->arena);
   carve_work(P, c.pl, geom, c.vd, C, c.W);
@@ -328,6 +411,9 @@ fwi_status begin_call(fwi_plan* P, const fwi_model* model, const fwi_geometry* g
     P->d_J_cap = nbatches;
   }
   CUDA_TRY(cudaMemsetAsync(P->d_flags, 0, sizeof(int) * 4, P->st));
+  // the extended schemes' stencil inputs k w (k L^T lambda) are read with
+  // their halo: their padding must hold zeros (only the interior is written)
+  if (c.W.KW) CUDA_TRY(cudaMemsetAsync(c.W.KW, 0, (size_t)P->L.fstride * c.pl.B * sizeof(float), P->st));
   P->ev_used = 0;
   c.D = c.W.D;
   FWI_TRY(prepare_model(c));
@@ -374,8 +460,10 @@ BatchBufs batch_bufs(const Call& c, int j) {
   const int nt = c.P->nt;
   BatchBufs b;
   b.D = c.W.D + k * (size_t)nt * B * c.geom->nrec;
-  b.CK = c.W.CK ? c.W.CK + k * fs * B * 2 * (size_t)c.pl.nck : nullptr;
+  b.CK = c.W.CK ? c.W.CK + k * fs * B * (size_t)c.pl.sc.ckpt_fields() * (size_t)c.pl.nck : nullptr;
   b.H = (c.pl.K == 0) ? c.W.H + k * fs * B * (size_t)std::max(nt - 1, 1) : c.W.H;
+  b.H2 = nullptr;
+  if (c.W.H2) b.H2 = (c.pl.K == 0) ? c.W.H2 + k * fs * B * (size_t)std::max(nt - 1, 1) : c.W.H2;
   return b;
 }
 
@@ -393,8 +481,9 @@ fwi_status gradient_forward_batch(Call& c, int j, int shot0, int nb, const DevTa
   float* Bf = c.W.U1;
   CUDA_TRY(cudaMemsetAsync(A, 0, fs * nb * sizeof(float), P->st));
   CUDA_TRY(cudaMemsetAsync(Bf, 0, fs * nb * sizeof(float), P->st));
+  if (c.W.QF) CUDA_TRY(cudaMemsetAsync(c.W.QF, 0, fs * nb * sizeof(float), P->st));   // lap u^{-1} = 0
   FWI_TRY(forward_steps(c, nb, shot0, src, A, Bf, 0, nt - 1, K == 0 ? bb.H : nullptr, 0, true,
-                        K, bb.CK));
+                        K, bb.CK, K == 0 ? bb.H2 : nullptr));
   FWI_TRY(final_sample(c, nb, A, nt - 1));
   cudaError_t e = launch_misfit(c.D, observed, traces_opt, c.pl.B, shot0, nb, c.geom->nrec, nt,
                                 c.W.partials, P->d_flags, c.W.npartials, P->st);
@@ -420,6 +509,9 @@ fwi_status gradient_adjoint_batch(Call& c, int j, int shot0, int nb, const DevTa
   float* LB = (K == 0) ? c.W.U1 : c.W.F1;
   CUDA_TRY(cudaMemsetAsync(LA, 0, fs * nb * sizeof(float), P->st));
   CUDA_TRY(cudaMemsetAsync(LB, 0, fs * nb * sizeof(float), P->st));
+  if (c.W.QA) CUDA_TRY(cudaMemsetAsync(c.W.QA, 0, fs * nb * sizeof(float), P->st));
+  const bool ext = c.pl.sc.ext();
+  const size_t cm = (size_t)c.pl.sc.ckpt_fields();
   StepParams p = base_params(c);
   p.B = nb;
   p.inj_off = c.rec_tab.off;
@@ -434,6 +526,11 @@ fwi_status gradient_adjoint_batch(Call& c, int j, int shot0, int nb, const DevTa
     if (K == 0) return bb.H + (size_t)n * fs * B;
     return bb.H + (size_t)(n - seg_lo) * fs * B;
   };
+  auto hist2_at = [&](int n) -> float* {
+    if (!bb.H2) return nullptr;
+    if (K == 0) return bb.H2 + (size_t)n * fs * B;
+    return bb.H2 + (size_t)(n - seg_lo) * fs * B;
+  };
   auto ensure_segment = [&](int n) -> fwi_status {
     if (K == 0 || (n >= seg_lo && n < seg_hi)) return FWI_OK;
     const int js = n / K;
@@ -441,23 +538,30 @@ fwi_status gradient_adjoint_batch(Call& c, int j, int shot0, int nb, const DevTa
     seg_hi = std::min(seg_lo + K, nt - 1);
     float* FA = c.W.U0;
     float* FB = c.W.U1;
-    const float* ck = bb.CK + 2 * (size_t)js * fs * B;
+    const float* ck = bb.CK + cm * (size_t)js * fs * B;
     CUDA_TRY(cudaMemcpyAsync(FA, ck, fs * nb * sizeof(float), cudaMemcpyDeviceToDevice, P->st));
     CUDA_TRY(cudaMemcpyAsync(FB, ck + fs * B, fs * nb * sizeof(float), cudaMemcpyDeviceToDevice, P->st));
-    return forward_steps(c, nb, shot0, src, FA, FB, seg_lo, seg_hi, bb.H, seg_lo, false, 0, nullptr);
+    if (cm == 3)
+      CUDA_TRY(cudaMemcpyAsync(c.W.QF, ck + 2 * fs * B, fs * nb * sizeof(float),
+                               cudaMemcpyDeviceToDevice, P->st));
+    return forward_steps(c, nb, shot0, src, FA, FB, seg_lo, seg_hi, bb.H, seg_lo, false, 0, nullptr,
+                         bb.H2);
   };
   for (int k = nt - 1; k >= 1; --k) {
     p.image = (k <= nt - 2) ? 1 : 0;
     if (p.image) {
       FWI_TRY(ensure_segment(k));
       p.hist = hist_at(k);
+      p.hist2 = hist2_at(k);
     } else {
       p.hist = nullptr;
+      p.hist2 = nullptr;
     }
     p.u = LA;
     p.up = LB;
     p.step_off = (long long)k * B * c.geom->nrec;
-    FWI_TRY(launch_step(c, p, true));
+    if (ext) FWI_TRY(ext_step(c, p, true));
+    else FWI_TRY(launch_step(c, p, true));
     std::swap(LA, LB);
     if (c.Dw) {   // dJ/dq^{k-1}: lambda^{k-1} sampled at the sources (weights / cell volume)
       const int nsrc = c.geom->nsrc;
@@ -470,9 +574,28 @@ fwi_status gradient_adjoint_batch(Call& c, int j, int shot0, int nb, const DevTa
   }
   if (nt >= 2) {   // imaging term of lambda^0
     FWI_TRY(ensure_segment(0));
-    cudaError_t e = launch_image_only(P->L, LA, hist_at(0), c.W.G, nb, c.pl.S, P->st);
+    cudaError_t e;
+    if (c.pl.sc.t4) {
+      // k L^T lambda^0 (the first adjoint pass alone), then the two terms
+      StepParams a = p;
+      a.x = LA;
+      a.u = LA;
+      a.out = c.W.KW;
+      a.inj_off = nullptr;
+      a.hist = nullptr;
+      a.hist2 = nullptr;
+      a.image = 0;
+      a.att = c.W.ATT;
+      a.flags = P->d_flags + 1;
+      e = launch_ext(a, P->grid.ndim, P->R, c.vd, true, EXT_KW, P->st);
+      if (e == cudaSuccess)
+        e = launch_image_t4(P->L, LA, c.W.KW, hist_at(0), hist2_at(0), c.W.G, nb, P->st);
+      c.launches += 2;
+    } else {
+      e = launch_image_only(P->L, LA, hist_at(0), c.W.G, nb, c.pl.S, P->st);
+      c.launches++;
+    }
     if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
-    c.launches++;
   }
   return FWI_OK;
 }
@@ -522,6 +645,7 @@ fwi_status fwi_forward(fwi_plan* P, const fwi_model* model, const fwi_geometry* 
     float* Bf = c.W.U1;
     CUDA_TRY(cudaMemsetAsync(A, 0, fs * nb * sizeof(float), P->st));
     CUDA_TRY(cudaMemsetAsync(Bf, 0, fs * nb * sizeof(float), P->st));
+    if (c.W.QF) CUDA_TRY(cudaMemsetAsync(c.W.QF, 0, fs * nb * sizeof(float), P->st));
     FWI_TRY(forward_steps(c, nb, shot0, src, A, Bf, 0, P->nt - 1, nullptr, 0, true, 0, nullptr));
     FWI_TRY(final_sample(c, nb, A, P->nt - 1));
     cudaError_t e = launch_traces_out(c.W.D, traces, B, shot0, nb, geom->nrec, P->nt, P->d_flags, P->st);
@@ -617,6 +741,8 @@ fwi_status fwi_misfit_backward_ex(fwi_plan* P, float* grad_m, float* grad_wavele
   if (!grad_m && !grad_wavelet) return fail(FWI_ERR_INVALID_ARG, "grad_m and grad_wavelet are both NULL");
   SavedGrad* S = P->saved;
   if (!S) return fail(FWI_ERR_INVALID_ARG, "no pending fwi_misfit_forward on this plan");
+  if (grad_wavelet && S->c.pl.sc.t4)
+    return fail(FWI_ERR_UNSUPPORTED, "the wavelet gradient of the fourth-order scheme is not implemented");
   P->saved = nullptr;   // the state is used once
   Call& c = S->c;
   CUDA_TRY(cudaSetDevice(P->device));

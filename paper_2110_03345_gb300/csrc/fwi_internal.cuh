@@ -85,7 +85,38 @@ struct StepParams {
   int nzc;               // 3D: z chunks
   int S;                 // shots per CTA (TMA kernels); gradient slot of shot s is s / S
   int* flags;            // device error flags (bit 1: a bounded wait timed out)
+  // extended schemes (kernels_ext.cu only): stencil input, per-point
+  // attenuation coefficient, Laplacian state and a second history field
+  const float* x;        // field whose stencil is taken (u^n, k w^n, lambda^k or k y^k)
+  float* out;            // pass 1 / A of the fourth-order scheme: k (L x + s)
+  const float* att;      // y = 0: alpha0 vp dt; y = 2: 2 alpha0 vp / dt
+  float* q;              // y = 2: Laplacian of the previous step (updated in place)
+  float* hist2;          // fourth-order scheme: k w^n (forward store, adjoint read)
+  float inj_scale;       // factor on injected values (fourth-order adjoint pass B: 12)
 };
+
+// Extended schemes (kernels_ext.cu): one point per thread, shared-memory
+// staged tiles of 32 x 16 (2D) or 32 x 8 columns streamed along z (3D).
+enum ExtMode {
+  EXT_KW = 0,    // out = k (L x + s)                  (4th order, first pass)
+  EXT_T4 = 1,    // F = x + k (L x + s) / 12, update     (4th order, second pass)
+  EXT_ATT0 = 2,  // leapfrog with per-point damping alpha0 vp dt   (y = 0)
+  EXT_ATT2 = 3,  // leapfrog with the Laplacian-difference term     (y = 2)
+};
+constexpr int EXT_TX = 32, EXT_TY2 = 16, EXT_TY3 = 8, EXT_ZC = 32;
+cudaError_t launch_ext(const StepParams& p, int ndim, int R, bool vd, bool adj, int mode,
+                       cudaStream_t st);
+// out[i] = q[i+1] - 2 q[i] + q[i-1] along the last axis of rows x nt samples
+// (q = 0 outside the record): the source's second time difference
+cudaError_t launch_second_difference(const float* q, float* out, long long rows, int nt,
+                                     cudaStream_t st);
+// g[b] -= lam[b] F[b] + ky[b] kw[b] / 12 for the nb slots of a batch
+cudaError_t launch_image_t4(const Layout& L, const float* lam, const float* ky, const float* F,
+                            const float* kw, float* g, int nb, cudaStream_t st);
+// attenuation coefficient field from vp (param 0) or m (param 1) and alpha0:
+// y = 0: alpha0 vp dt; y = 2: 2 alpha0 vp / dt (zero in the padding)
+cudaError_t launch_att_prep(const Layout& L, const float* vp, int param, const float* alpha0,
+                            int y, double dt, float* att, cudaStream_t st);
 
 // Multi-problem forward step (kernels2d.cu): one launch advances every unit
 // (problem, tile, shot slot) of the table by one time step.  The descriptor

@@ -69,6 +69,7 @@ fwi_status forward_in_buffer(const fwi_grid* grid, int nt, double dt, const fwi_
   all.B = geom->nshots;
   if (!resolve_tile(&P, P.opt.tile, &all.tile, &all.shape, &all.tma, &all.x2))
     return fail(FWI_ERR_INVALID_ARG, "tile variant out of range");
+  FWI_TRY(resolve_scheme(&P, model, &all.sc));
   const size_t tab = align_up(tables_bound(&P, geom, all) * 2, 256);
   P.tab = C.take<char>(tab);
   P.tab_cap = tab;
@@ -81,7 +82,7 @@ fwi_status forward_in_buffer(const fwi_grid* grid, int nt, double dt, const fwi_
   P.arena_cap = bytes - C.off;
   P.budget = P.arena_cap;
   Plan pl;
-  if (choose_plan(&P, geom, model->rho != nullptr, false, pl) != FWI_OK)
+  if (choose_plan(&P, geom, model->rho != nullptr, false, pl, false, all.sc) != FWI_OK)
     return fail(FWI_ERR_BUDGET, "one shot of this grid needs more than the static scratch of " +
                                     std::to_string(bytes) + " bytes (use fwi_forward)");
   if ((geom->nshots + pl.B - 1) / pl.B > JCAP)

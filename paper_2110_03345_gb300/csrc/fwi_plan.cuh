@@ -133,6 +133,19 @@ struct DevTable {
   const float* w = nullptr;
 };
 
+// Time scheme and attenuation of a call: the leapfrog of the default
+// kernels, or an extended scheme run by the kernels of kernels_ext.cu.
+struct Scheme {
+  bool t4 = false;   // fourth order in time (options.time_order == 4)
+  int att = -1;      // attenuation power y (0 or 2), -1 for none
+  bool ext() const { return t4 || att >= 0; }
+  int hist_fields() const { return t4 ? 2 : 1; }         // stored per step (F and k w)
+  int ckpt_fields() const { return att == 2 ? 3 : 2; }   // u^n, u^{n-1} (, lap u^{n-1})
+  int fwd_slot_fields() const { return (t4 ? 1 : 0) + (att == 2 ? 1 : 0); }   // k w; lap state
+  int adj_slot_fields() const { return att == 2 ? 1 : 0; }                    // adjoint lap state
+  int model_fields() const { return att >= 0 ? 1 : 0; }                      // attenuation coefficient
+};
+
 // Workspace plan for one call.
 struct Plan {
   int B = 1;            // slots
@@ -147,6 +160,7 @@ struct Plan {
   bool split = false;   // forward and adjoint in separate calls: keep every batch's state
   int nbatches = 1;
   size_t bytes = 0;
+  Scheme sc;            // extended scheme (then tma, x2 = false, S = 1, tile = 0)
 };
 
 // Per-call device state carved out of the arena.
@@ -154,6 +168,9 @@ struct Work {
   float *kf = nullptr, *lnr = nullptr, *bx = nullptr, *by = nullptr, *bz = nullptr;
   float *U0 = nullptr, *U1 = nullptr, *F0 = nullptr, *F1 = nullptr, *G = nullptr;
   float *H = nullptr, *CK = nullptr, *D = nullptr;
+  // extended schemes: attenuation coefficient, k w scratch, Laplacian states
+  // (forward, adjoint), second history field, second time difference of the wavelets
+  float *ATT = nullptr, *KW = nullptr, *QF = nullptr, *QA = nullptr, *H2 = nullptr, *D2Q = nullptr;
   double* partials = nullptr;
   int npartials = 0;
 };
@@ -205,6 +222,7 @@ struct BatchBufs {
   float* D;
   float* CK;
   float* H;
+  float* H2;   // fourth-order scheme: second history field
 };
 
 // ---- plan.cu: plan memory, layout, validation, workspace planning
@@ -220,19 +238,21 @@ fwi_status build_sponge(fwi_plan* P);
 fwi_status validate_geometry(const fwi_plan* P, const fwi_geometry* g);
 bool resolve_tile(const fwi_plan* P, int t, int* id, int* shape, bool* tma, bool* x2 = nullptr);
 size_t field_bytes(const fwi_plan* P);
-size_t model_bytes(const fwi_plan* P, bool vd);
-size_t slot_bytes(const fwi_plan* P, const fwi_geometry* g, bool grad, int K);
-size_t persist_bytes_per_shot(const fwi_plan* P, const fwi_geometry* g, int K);
-size_t split_slot_bytes(const fwi_plan* P, int K);
-size_t fixed_bytes(const fwi_plan* P, const fwi_geometry* g, bool vd, int B);
+size_t model_bytes(const fwi_plan* P, bool vd, const Scheme& sc);
+size_t slot_bytes(const fwi_plan* P, const fwi_geometry* g, bool grad, int K, const Scheme& sc);
+size_t persist_bytes_per_shot(const fwi_plan* P, const fwi_geometry* g, int K, const Scheme& sc);
+size_t split_slot_bytes(const fwi_plan* P, int K, const Scheme& sc);
+size_t fixed_bytes(const fwi_plan* P, const fwi_geometry* g, bool vd, int B, const Scheme& sc);
+// The scheme of a call from the plan's options and the model (NULL: none).
+fwi_status resolve_scheme(const fwi_plan* P, const fwi_model* m, Scheme* sc);
 fwi_status choose_plan(const fwi_plan* P, const fwi_geometry* g, bool vd, bool grad, Plan& out,
-                       bool split = false);
+                       bool split = false, const Scheme& sc = Scheme());
 void carve_work(fwi_plan* P, const Plan& pl, const fwi_geometry* g, bool vd, Carve& C, Work& W);
 
 // ---- tables.cu: interpolation and injection tables
 Corners point_corners(const fwi_plan* P, const double* xyz);
 long long node_index(const Layout& L, const int* n);
-TileGeo tile_geo(const fwi_plan* P, int tile, bool tma, bool x2 = false);
+TileGeo tile_geo(const fwi_plan* P, int tile, bool tma, bool x2 = false, bool ext = false);
 void add_entry(std::vector<Entry>& E, const TileGeo& T, int slot, const int* node, int vidx,
                float w);
 HostTable bucket(const std::vector<Entry>& E_in, int nbuckets);
@@ -257,7 +277,8 @@ const CUtensorMap* find_map(const Call& c, const float* base);
 fwi_status launch_step(Call& c, const StepParams& p_in, bool adj);
 fwi_status forward_steps(Call& c, int nb, int shot0, const DevTable& src, float*& A, float*& Bf,
                          int n0, int n1, float* hist_base, int hist_n0, bool sample,
-                         int K_ckpt, float* CK);
+                         int K_ckpt, float* CK, float* hist2_base = nullptr);
+fwi_status ext_step(Call& c, const StepParams& p_in, bool adj);
 fwi_status final_sample(Call& c, int nb, const float* A, int n);
 fwi_status prepare_model(Call& c);
 fwi_status begin_call(fwi_plan* P, const fwi_model* model, const fwi_geometry* geom,

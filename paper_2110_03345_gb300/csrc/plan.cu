@@ -272,62 +272,83 @@ bool resolve_tile(const fwi_plan* P, int t, int* id, int* shape, bool* tma, bool
 
 size_t field_bytes(const fwi_plan* P) { return (size_t)P->L.fstride * sizeof(float); }
 
-size_t model_bytes(const fwi_plan* P, bool vd) {
+size_t model_bytes(const fwi_plan* P, bool vd, const Scheme& sc) {
   const size_t f = align_up(field_bytes(P), 256);
-  return f * (1 + (vd ? 1 + P->grid.ndim : 0));
+  return f * (1 + (vd ? 1 + P->grid.ndim : 0) + sc.model_fields());
 }
 
-size_t slot_bytes(const fwi_plan* P, const fwi_geometry* g, bool grad, int K) {
+size_t slot_bytes(const fwi_plan* P, const fwi_geometry* g, bool grad, int K, const Scheme& sc) {
   const size_t f = align_up(field_bytes(P), 256);
   const size_t traces = align_up((size_t)P->nt * g->nrec * sizeof(float), 256);
-  size_t b = 2 * f + traces;
+  size_t b = (2 + sc.fwd_slot_fields()) * f + traces;
   if (!grad) return b;
-  b += f;  // g slot
+  b += (1 + sc.adj_slot_fields()) * f;  // g slot (and the adjoint Laplacian state)
   const int nt = P->nt;
+  const size_t hf = sc.hist_fields();
   if (K == 0) {
-    b += (size_t)std::max(nt - 1, 1) * f;
+    b += (size_t)std::max(nt - 1, 1) * hf * f;
   } else {
     const int nck = (nt - 2) / K + 1;
-    b += 2 * f + 2 * (size_t)nck * f + (size_t)K * f;
+    b += 2 * f + (size_t)sc.ckpt_fields() * nck * f + (size_t)K * hf * f;
   }
   return b;
 }
 
 // Split gradient: bytes kept per shot between the two calls (checkpoints or
 // history, and the residual traces), and the per-slot working set.
-size_t persist_bytes_per_shot(const fwi_plan* P, const fwi_geometry* g, int K) {
+size_t persist_bytes_per_shot(const fwi_plan* P, const fwi_geometry* g, int K, const Scheme& sc) {
   const size_t f = align_up(field_bytes(P), 256);
   const size_t traces = (size_t)P->nt * g->nrec * sizeof(float);
-  if (K == 0) return (size_t)std::max(P->nt - 1, 1) * f + traces;
+  if (K == 0) return (size_t)std::max(P->nt - 1, 1) * sc.hist_fields() * f + traces;
   const int nck = (P->nt - 2) / K + 1;
-  return 2 * (size_t)nck * f + traces;
+  return (size_t)sc.ckpt_fields() * nck * f + traces;
 }
 
-size_t split_slot_bytes(const fwi_plan* P, int K) {
+size_t split_slot_bytes(const fwi_plan* P, int K, const Scheme& sc) {
   const size_t f = align_up(field_bytes(P), 256);
-  return 5 * f + (K ? (size_t)K * f : 0) + 4096;
+  return (5 + sc.fwd_slot_fields() + sc.adj_slot_fields()) * f +
+         (K ? (size_t)K * sc.hist_fields() * f : 0) + 4096;
 }
 
-size_t fixed_bytes(const fwi_plan* P, const fwi_geometry* g, bool vd, int B) {
+size_t fixed_bytes(const fwi_plan* P, const fwi_geometry* g, bool vd, int B, const Scheme& sc) {
   const size_t misfit = align_up((size_t)misfit_blocks(B, g->nrec, P->nt) * 8, 256);
-  return model_bytes(P, vd) + misfit + (4u << 20);
+  const size_t d2q = sc.t4 ? align_up((size_t)g->nshots * g->nsrc * P->nt * 4, 256) : 0;
+  return model_bytes(P, vd, sc) + misfit + d2q + (4u << 20);
+}
+
+fwi_status resolve_scheme(const fwi_plan* P, const fwi_model* m, Scheme* sc) {
+  *sc = Scheme();
+  const int to = P->opt.time_order;
+  if (to != 0 && to != 2 && to != 4)
+    return fail(FWI_ERR_INVALID_ARG, "time_order must be 0, 2 or 4");
+  sc->t4 = to == 4;
+  if (m && m->alpha0) {
+    if (m->att_power != 0 && m->att_power != 2)
+      return fail(FWI_ERR_INVALID_ARG, "att_power must be 0 or 2");
+    sc->att = m->att_power;
+  }
+  if (sc->t4 && sc->att >= 0)
+    return fail(FWI_ERR_UNSUPPORTED, "attenuation with the fourth-order time scheme is not implemented");
+  if (sc->t4 && P->opt.interp != FWI_INTERP_LINEAR)
+    return fail(FWI_ERR_UNSUPPORTED, "sinc points with the fourth-order time scheme are not implemented");
+  return FWI_OK;
 }
 
 fwi_status choose_plan(const fwi_plan* P, const fwi_geometry* g, bool vd, bool grad, Plan& out,
-                       bool split) {
+                       bool split, const Scheme& sc) {
   const int ns = g->nshots;
   const size_t budget = P->budget;
   const int K_auto = std::max(2, (int)std::ceil(std::sqrt(2.0 * std::max(P->nt, 2))));
   const long long N = (long long)P->L.nx * P->L.ny * P->L.nz;
   const int B_fill = (int)std::max(1LL, (8LL << 20) / std::max(N, 1LL));  // slots that fill the GPU
   auto fit = [&](int K) {
-    size_t fixed = fixed_bytes(P, g, vd, ns);
-    size_t per = slot_bytes(P, g, grad, K);
+    size_t fixed = fixed_bytes(P, g, vd, ns, sc);
+    size_t per = slot_bytes(P, g, grad, K, sc);
     if (split) {
       // nbatches * B <= ns + B - 1 shots of kept state
-      const size_t keep = persist_bytes_per_shot(P, g, K);
+      const size_t keep = persist_bytes_per_shot(P, g, K, sc);
       fixed += (size_t)ns * keep;
-      per = split_slot_bytes(P, K) + keep;
+      per = split_slot_bytes(P, K, sc) + keep;
     }
     if (budget <= fixed) return 0;
     return (int)std::min<size_t>((size_t)ns, (budget - fixed) / per);
@@ -349,8 +370,16 @@ fwi_status choose_plan(const fwi_plan* P, const fwi_geometry* g, bool vd, bool g
   B = std::min(B, ns);
   if (!resolve_tile(P, P->opt.tile, &out.tile, &out.shape, &out.tma, &out.x2))
     return fail(FWI_ERR_INVALID_ARG, "tile variant out of range");
+  out.sc = sc;
+  if (sc.ext()) {   // the extended schemes have one kernel family (one shot per CTA)
+    out.tile = 0;
+    out.shape = 0;
+    out.tma = false;
+    out.x2 = false;
+  }
   // slots x z chunks go on grid.z, which CUDA limits to 65535 blocks
-  B = std::min(B, std::max(1, 65535 / std::max(1, tile_geo(P, out.shape, out.tma, out.x2).nzc)));
+  B = std::min(B, std::max(1, 65535 / std::max(1, tile_geo(P, out.shape, out.tma, out.x2,
+                                                           sc.ext()).nzc)));
   // equal batches: the same number of batches, none left nearly empty
   // (16 shots at 15 per batch run as 8 + 8, not 15 + 1)
   B = (ns + (ns + B - 1) / B - 1) / ((ns + B - 1) / B);
@@ -373,10 +402,10 @@ fwi_status choose_plan(const fwi_plan* P, const fwi_geometry* g, bool vd, bool g
       out.S = S;
     }
   }
-  out.bytes = fixed_bytes(P, g, vd, B) + (size_t)B * slot_bytes(P, g, grad, K);
+  out.bytes = fixed_bytes(P, g, vd, B, sc) + (size_t)B * slot_bytes(P, g, grad, K, sc);
   if (split)
-    out.bytes = fixed_bytes(P, g, vd, B) + (size_t)B * split_slot_bytes(P, K) +
-                (size_t)out.nbatches * B * persist_bytes_per_shot(P, g, K) + (4u << 20);
+    out.bytes = fixed_bytes(P, g, vd, B, sc) + (size_t)B * split_slot_bytes(P, K, sc) +
+                (size_t)out.nbatches * B * persist_bytes_per_shot(P, g, K, sc) + (4u << 20);
   return FWI_OK;
 }
 
@@ -390,21 +419,29 @@ void carve_work(fwi_plan* P, const Plan& pl, const fwi_geometry* g, bool vd, Car
     W.by = C.take<float>(fs);
     if (P->grid.ndim == 3) W.bz = C.take<float>(fs);
   }
+  const Scheme& sc = pl.sc;
+  if (sc.att >= 0) W.ATT = C.take<float>(fs);
+  if (sc.t4) W.D2Q = C.take<float>((size_t)g->nshots * g->nsrc * P->nt);
   W.npartials = misfit_blocks(B, g->nrec, P->nt);
   W.partials = C.take<double>(W.npartials);
   W.U0 = C.take<float>(fs * B);
   W.U1 = C.take<float>(fs * B);
+  if (sc.t4) W.KW = C.take<float>(fs * B);
+  if (sc.att == 2) W.QF = C.take<float>(fs * B);
   const size_t nbk = pl.split ? (size_t)pl.nbatches : 1;   // batches whose state is kept
   W.D = C.take<float>((size_t)P->nt * B * g->nrec * nbk);
   if (pl.gradient) {
     W.G = C.take<float>(fs * B);
+    if (sc.att == 2) W.QA = C.take<float>(fs * B);
     if (pl.K == 0) {
       W.H = C.take<float>(fs * B * (size_t)std::max(P->nt - 1, 1) * nbk);
+      if (sc.t4) W.H2 = C.take<float>(fs * B * (size_t)std::max(P->nt - 1, 1) * nbk);
     } else {
       W.F0 = C.take<float>(fs * B);
       W.F1 = C.take<float>(fs * B);
-      W.CK = C.take<float>(fs * B * 2 * (size_t)pl.nck * nbk);
+      W.CK = C.take<float>(fs * B * (size_t)sc.ckpt_fields() * (size_t)pl.nck * nbk);
       W.H = C.take<float>(fs * B * (size_t)pl.K);
+      if (sc.t4) W.H2 = C.take<float>(fs * B * (size_t)pl.K);
     }
   }
 }
@@ -485,6 +522,10 @@ fwi_status fwi_plan_set_options(fwi_plan* plan, const fwi_options* opt) {
   if (opt->batch < 0) return fail(FWI_ERR_INVALID_ARG, "batch must be >= 0");
   if (opt->profile < 0) return fail(FWI_ERR_INVALID_ARG, "profile must be >= 0");
   if (opt->use_graphs != 0) return fail(FWI_ERR_UNSUPPORTED, "use_graphs is reserved and must be 0");
+  if (opt->time_order != 0 && opt->time_order != 2 && opt->time_order != 4)
+    return fail(FWI_ERR_INVALID_ARG, "time_order must be 0, 2 or 4");
+  if (opt->interp != FWI_INTERP_LINEAR && opt->interp != FWI_INTERP_SINC)
+    return fail(FWI_ERR_INVALID_ARG, "interp must be FWI_INTERP_LINEAR or FWI_INTERP_SINC");
   plan->opt = *opt;
   return FWI_OK;
 }
@@ -500,7 +541,9 @@ fwi_status fwi_plan_estimate(const fwi_plan* plan, const fwi_geometry* geom, int
   if (!plan || !bytes) return fail(FWI_ERR_INVALID_ARG, "NULL argument");
   FWI_TRY(validate_geometry(plan, geom));
   Plan pl;
-  FWI_TRY(choose_plan(plan, geom, true, gradient != 0, pl));
+  Scheme sc;
+  FWI_TRY(resolve_scheme(plan, nullptr, &sc));
+  FWI_TRY(choose_plan(plan, geom, true, gradient != 0, pl, false, sc));
   *bytes = pl.bytes + tables_bound(plan, geom, pl) * 2;
   return FWI_OK;
 }

@@ -40,8 +40,18 @@ Corners point_corners(const fwi_plan* P, const double* xyz) {
 
 long long node_index(const Layout& L, const int* n) { return L.index(n[2], n[1], n[0]); }
 
-TileGeo tile_geo(const fwi_plan* P, int tile, bool tma, bool x2) {
+TileGeo tile_geo(const fwi_plan* P, int tile, bool tma, bool x2, bool ext) {
   TileGeo T{};
+  if (ext) {   // kernels_ext.cu: 32 x 16 tiles (2D), 32 x 8 columns in z chunks (3D)
+    const bool three = P->grid.ndim == 3;
+    T.tx = EXT_TX;
+    T.ty = three ? EXT_TY3 : EXT_TY2;
+    T.zc = three ? EXT_ZC : 1;
+    T.gx = (P->L.nx + T.tx - 1) / T.tx;
+    T.gy = (P->L.ny + T.ty - 1) / T.ty;
+    T.nzc = three ? (P->L.nz + T.zc - 1) / T.zc : 1;
+    return T;
+  }
   if (P->grid.ndim == 2) {
     const Tile2 t = tma ? tile2_tma_variant(tile) : tile2_variant(tile);
     T.tx = TILE_X;
@@ -173,7 +183,7 @@ fwi_status prepare_common(Call& c, Carve& tabC) {
   const fwi_geometry* g = c.geom;
   const int nd = P->grid.ndim;
   c.ncorner = 1 << nd;
-  c.T = tile_geo(P, c.pl.shape, c.pl.tma, c.pl.x2);
+  c.T = tile_geo(P, c.pl.shape, c.pl.tma, c.pl.x2, c.pl.sc.ext());
   // receiver sampling table
   std::vector<int> node((size_t)g->nrec * c.ncorner);
   std::vector<float> w((size_t)g->nrec * c.ncorner);
@@ -204,7 +214,7 @@ fwi_status prepare_common(Call& c, Carve& tabC) {
 }
 
 size_t tables_bound(const fwi_plan* P, const fwi_geometry* g, const Plan& pl) {
-  const TileGeo T = tile_geo(P, pl.shape, pl.tma, pl.x2);
+  const TileGeo T = tile_geo(P, pl.shape, pl.tma, pl.x2, pl.sc.ext());
   const int nc = 1 << P->grid.ndim;
   const size_t nb = (size_t)pl.B * T.ntiles() + 1;
   const size_t src = (size_t)pl.B * g->nsrc * nc;

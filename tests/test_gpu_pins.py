@@ -6,11 +6,20 @@
   residual is then exactly y; relative difference <= 1e-5.  F* y is also
   compared with the oracle's adjoint sweep sampled at the sources.
 * Symmetry: homogeneous medium, on-node centred source on an odd grid
-  (257^2, otherwise the homogeneous 2D setup): receivers related by a mirror
-  or a quarter turn record the same traces within 1e-6 of the largest sample.
-* Linearity: doubling the wavelet doubles the traces bit for bit (scaling by
-  two is exact in FP32 except for subnormal results, so samples below 2^-100
-  are compared to within 2^-120); a zero wavelet gives zero traces.
+  (257^2, otherwise the homogeneous 2D setup; the 256^2 grid has no centre
+  node, so its sponge is one node closer on one side): receivers related by
+  the mirror y -> -y record the same traces within 1e-6 of the largest
+  sample (the y taps are summed symmetrically).  A quarter turn or the
+  diagonal mirror swaps the x and y taps, which the kernels sum in different
+  orders: those traces agree to the FP32 rounding accumulated over the 1000
+  steps (measured 1.0e-6 of the largest sample; bound 1e-5).
+* Linearity: doubling the wavelet doubles the traces.  Scaling by two is
+  exact in FP32 except where a subnormal result is rounded, and the fields
+  start from zero, so the stencil's precursor ahead of every wavefront passes
+  through the subnormal range: the rounding differences that enter there
+  grow with the precursor and reach one unit in the last place of normal
+  samples.  The test requires relative L2 <= 1e-6, at least 90% of the
+  samples bit for bit, and zero traces for a zero wavelet.
 """
 import numpy as np
 import pytest
@@ -118,14 +127,18 @@ def test_symmetry_centred_source_odd_grid():
     tr = tr[0]
     nrec = tr.shape[0]
     scale = np.abs(tr).max()
-    for k in range(1, nrec // 4):
+    ks = np.arange(1, nrec // 4)
+    for k in ks:
         assert np.abs(tr[k] - tr[nrec - k]).max() <= 1e-6 * scale          # mirror y -> -y
-        assert np.abs(tr[k] - tr[k + nrec // 4]).max() <= 1e-6 * scale     # quarter turn
-        assert np.abs(tr[k] - tr[nrec // 4 - k]).max() <= 1e-6 * scale     # mirror about the diagonal
+        assert np.abs(tr[k] - tr[k + nrec // 4]).max() <= 1e-5 * scale     # quarter turn
+        assert np.abs(tr[k] - tr[nrec // 4 - k]).max() <= 1e-5 * scale     # mirror about the diagonal
+    print("symmetry: quarter turn %.2e, diagonal %.2e of the largest sample" % (
+        np.abs(tr[ks + nrec // 4] - tr[ks]).max() / scale,
+        np.abs(tr[nrec // 4 - ks] - tr[ks]).max() / scale))
 
 
 @pytest.mark.parametrize("case", ["2d-vd", "3d-cd"])
-def test_linearity_bit_exact(case):
+def test_linearity(case):
     if case == "2d-vd":
         p = inputs.breast_problem((150, 203), 0.3e-3, 400, nelem=64, shots=[0, 21, 42], order=8,
                                   nb=16, radius=0.35 * 150 * 0.3e-3)
@@ -138,10 +151,11 @@ def test_linearity_bit_exact(case):
     p2 = inputs.Problem(p.name, p.shape, p.spacing, p.dt, p.nt, p.order, p.nb, p.vp, p.rho,
                         p.src_xyz, p.rec_xyz, 2.0 * p.wavelet, c_ref=p.c_ref)
     t2, _ = gpu_forward(p2, variable_density=vd)
-    big = np.abs(2.0 * t1) >= 2.0 ** -100
-    assert big.mean() > 0.5
-    assert np.array_equal(t2[big], 2.0 * t1[big])
-    assert np.abs(t2[~big] - 2.0 * t1[~big]).max(initial=0.0) <= 2.0 ** -120
+    assert rel_l2(t2, 2.0 * t1) <= 1e-6
+    same = t2 == 2.0 * t1
+    print(f"linearity: {same.mean():.4f} of the samples bit for bit, relative L2 "
+          f"{rel_l2(t2, 2.0 * t1):.2e}")
+    assert same.mean() >= 0.9
     p0 = inputs.Problem(p.name, p.shape, p.spacing, p.dt, p.nt, p.order, p.nb, p.vp, p.rho,
                         p.src_xyz, p.rec_xyz, 0.0 * p.wavelet, c_ref=p.c_ref)
     t0, _ = gpu_forward(p0, variable_density=vd)
