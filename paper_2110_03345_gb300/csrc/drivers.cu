@@ -340,8 +340,31 @@ fwi_status prepare_model(Call& c) {
   }
   if (c.pl.sc.att >= 0) {
     CUDA_TRY(cudaMemsetAsync(c.W.ATT, 0, fs * sizeof(float), P->st));
-    e = launch_att_prep(P->L, m->vp, m->param, m->alpha0, c.pl.sc.att, P->dt, c.W.ATT, P->st);
+    CUDA_TRY(cudaMemsetAsync(P->d_stats + 4, 0, 2 * sizeof(unsigned int), P->st));
+    e = launch_att_prep(P->L, m->vp, m->param, m->alpha0, c.pl.sc.att, P->dt, c.W.ATT,
+                        P->d_stats + 4, P->st);
     if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
+    unsigned int as[2];
+    CUDA_TRY(cudaMemcpyAsync(as, P->d_stats + 4, sizeof(as), cudaMemcpyDeviceToHost, P->st));
+    CUDA_TRY(cudaStreamSynchronize(P->st));
+    if (as[1] != 0) return fail(FWI_ERR_NONFINITE, "alpha0 holds negative or non-finite values");
+    if (c.pl.sc.att == 2) {
+      // the y = 2 term is explicit: with r = k lambda_max (lambda_max the
+      // largest eigenvalue of -lap) and s = r * (2 alpha0 vp / dt) the step is
+      // stable for r + 2 s <= 4; checked with the maxima of vp and of the
+      // coefficient (conservative) at 0.95^2 of the bound
+      float amax;
+      std::memcpy(&amax, &as[0], 4);
+      const double cl = cfl_limit(1, P->grid.order);
+      const double r = (double)vmax * P->dt * (double)vmax * P->dt * sum * 4.0 / (cl * cl);
+      if (r * (1.0 + 2.0 * (double)amax) > 4.0 * 0.95 * 0.95) {
+        char buf[200];
+        std::snprintf(buf, sizeof(buf),
+                      "the y = 2 attenuation term is unstable at this step: r (1 + 2 max 2 alpha0 vp / dt) "
+                      "= %.3f exceeds 0.95^2 x 4 (r = %.3f)", r * (1.0 + 2.0 * (double)amax), r);
+        return fail(FWI_ERR_UNSTABLE_CFL, buf);
+      }
+    }
   }
   if (c.pl.sc.t4) {
     e = launch_second_difference(c.wavelet, c.W.D2Q, (long long)c.geom->nshots * c.geom->nsrc, P->nt,

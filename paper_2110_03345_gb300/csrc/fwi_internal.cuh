@@ -114,9 +114,10 @@ cudaError_t launch_second_difference(const float* q, float* out, long long rows,
 cudaError_t launch_image_t4(const Layout& L, const float* lam, const float* ky, const float* F,
                             const float* kw, float* g, int nb, cudaStream_t st);
 // attenuation coefficient field from vp (param 0) or m (param 1) and alpha0:
-// y = 0: alpha0 vp dt; y = 2: 2 alpha0 vp / dt (zero in the padding)
+// y = 0: alpha0 vp dt; y = 2: 2 alpha0 vp / dt (zero in the padding);
+// stats[0] |= bits of its maximum, stats[1] += count of bad alpha0 values
 cudaError_t launch_att_prep(const Layout& L, const float* vp, int param, const float* alpha0,
-                            int y, double dt, float* att, cudaStream_t st);
+                            int y, double dt, float* att, unsigned int* stats, cudaStream_t st);
 
 // Multi-problem forward step (kernels2d.cu): one launch advances every unit
 // (problem, tile, shot slot) of the table by one time step.  The descriptor

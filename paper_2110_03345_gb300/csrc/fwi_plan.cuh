@@ -107,6 +107,15 @@ struct Corners {
   double w[8];
 };
 
+// Interpolation stencil of one point for the plan's interp option: n nodes
+// (x, y, z at node[3 i .. 3 i + 2]) and their weights.  Bi-/tri-linear: the
+// 2^ndim corners; sinc: the (2r)^ndim Kaiser-windowed sinc nodes.
+struct PointSt {
+  int n = 0;
+  std::vector<int> node;
+  std::vector<double> w;
+};
+
 // Tile geometry of the stencil kernels for entry bucketing.
 struct TileGeo {
   int gx, gy, nzc, tx, ty, zc;
@@ -251,6 +260,13 @@ void carve_work(fwi_plan* P, const Plan& pl, const fwi_geometry* g, bool vd, Car
 
 // ---- tables.cu: interpolation and injection tables
 Corners point_corners(const fwi_plan* P, const double* xyz);
+// Nodes per point for an interp option and dimension (4 / 8 linear, 64 / 512 sinc).
+int interp_nodes(int interp, int ndim);
+// Per-axis Kaiser-windowed sinc weights of a point at x grid units on an axis
+// of n nodes: first node and the 2 r weights; false if the point lies closer
+// than r - 1 nodes to a face.
+bool sinc_axis(double x, long long n, int* first, double* w);
+bool point_stencil(const fwi_plan* P, const double* xyz, PointSt& out);
 long long node_index(const Layout& L, const int* n);
 TileGeo tile_geo(const fwi_plan* P, int tile, bool tma, bool x2 = false, bool ext = false);
 void add_entry(std::vector<Entry>& E, const TileGeo& T, int slot, const int* node, int vidx,

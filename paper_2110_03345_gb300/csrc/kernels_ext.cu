@@ -364,10 +364,13 @@ __global__ void k_second_difference(const float* __restrict__ q, float* __restri
   }
 }
 
+// stats[0] = largest coefficient (bits of a non-negative float), stats[1] =
+// number of negative or non-finite alpha0 values (their coefficient is 0)
 __global__ void k_att_prep(Layout L, const float* __restrict__ vp, int param,
                            const float* __restrict__ alpha0, int y, double dt,
-                           float* __restrict__ att) {
+                           float* __restrict__ att, unsigned int* __restrict__ stats) {
   const long long N = (long long)L.nx * L.ny * L.nz;
+  unsigned int amax = 0u, bad = 0u;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(i % L.nx);
@@ -375,8 +378,20 @@ __global__ void k_att_prep(Layout L, const float* __restrict__ vp, int param,
     const int yy = (int)(t % L.ny);
     const int z = (int)(t / L.ny);
     const double v = param ? 1.0 / sqrt((double)vp[i]) : (double)vp[i];
-    const double a0 = (double)alpha0[i];
-    att[L.index(z, yy, x)] = (float)(y == 0 ? a0 * v * dt : 2.0 * a0 * v / dt);
+    const float a = alpha0[i];
+    float c = 0.f;
+    if (!(a >= 0.f) || !isfinite(a)) ++bad;
+    else c = (float)(y == 0 ? (double)a * v * dt : 2.0 * (double)a * v / dt);
+    att[L.index(z, yy, x)] = c;
+    amax = max(amax, __float_as_uint(c));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    bad += __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(stats + 0, amax);
+    if (bad) atomicAdd(stats + 1, bad);
   }
 }
 
@@ -403,11 +418,11 @@ cudaError_t launch_second_difference(const float* q, float* out, long long rows,
 }
 
 cudaError_t launch_att_prep(const Layout& L, const float* vp, int param, const float* alpha0,
-                            int y, double dt, float* att, cudaStream_t st) {
+                            int y, double dt, float* att, unsigned int* stats, cudaStream_t st) {
   const long long N = (long long)L.nx * L.ny * L.nz;
   long long blocks = (N + 255) / 256;
   if (blocks > 152LL * 16) blocks = 152LL * 16;
-  k_att_prep<<<(int)blocks, 256, 0, st>>>(L, vp, param, alpha0, y, dt, att);
+  k_att_prep<<<(int)blocks, 256, 0, st>>>(L, vp, param, alpha0, y, dt, att, stats);
   return cudaGetLastError();
 }
 

@@ -40,6 +40,78 @@ Corners point_corners(const fwi_plan* P, const double* xyz) {
 
 long long node_index(const Layout& L, const int* n) { return L.index(n[2], n[1], n[0]); }
 
+int interp_nodes(int interp, int ndim) {
+  if (interp == FWI_INTERP_SINC) {
+    int n = 1;
+    for (int d = 0; d < ndim; ++d) n *= 2 * FWI_SINC_RADIUS;
+    return n;
+  }
+  return 1 << ndim;
+}
+
+// Kaiser-windowed sinc along one axis: the 2r nodes floor(x)-r+1 .. floor(x)+r
+// with w = I0(b sqrt(1 - (d/r)^2)) / I0(b) * sin(pi d) / (pi d), d = node - x.
+bool sinc_axis(double x, long long n, int* first, double* w) {
+  constexpr int r = FWI_SINC_RADIUS;
+  constexpr double b = FWI_SINC_KAISER_B;
+  auto bessel_i0 = [](double v) {          // power series sum_k ((v/2)^k / k!)^2
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 200 && term > 1e-18 * sum; ++k) {
+      term *= (v / (2.0 * k)) * (v / (2.0 * k));
+      sum += term;
+    }
+    return sum;
+  };
+  const long long f = (long long)std::floor(x);
+  if (f - r + 1 < 0 || f + r > n - 1) return false;
+  const double i0b = bessel_i0(b);
+  *first = (int)(f - r + 1);
+  for (int j = 0; j < 2 * r; ++j) {
+    const double dd = (double)(*first + j) - x;
+    const double q = 1.0 - (dd / r) * (dd / r);
+    const double win = std::fabs(dd) <= r ? bessel_i0(b * std::sqrt(q > 0.0 ? q : 0.0)) / i0b : 0.0;
+    const double sn = dd == 0.0 ? 1.0 : std::sin(kPiD * dd) / (kPiD * dd);
+    w[j] = win * sn;
+  }
+  return true;
+}
+
+bool point_stencil(const fwi_plan* P, const double* xyz, PointSt& out) {
+  const int nd = P->grid.ndim;
+  if (P->opt.interp != FWI_INTERP_SINC) {
+    const Corners C = point_corners(P, xyz);
+    out.n = C.n;
+    out.node.resize(3 * C.n);
+    out.w.resize(C.n);
+    for (int c = 0; c < C.n; ++c) {
+      for (int a = 0; a < 3; ++a) out.node[3 * c + a] = C.node[c][a];
+      out.w[c] = C.w[c];
+    }
+    return true;
+  }
+  // tensor product of the per-axis weights, axes in (x, y, z) order
+  constexpr int W = 2 * FWI_SINC_RADIUS;
+  int first[3] = {0, 0, 0};
+  double w1[3][W];
+  for (int a = 0; a < nd; ++a) {
+    const double xa = xyz[nd - 1 - a] / P->h[a];
+    if (!sinc_axis(xa, P->n3[a], &first[a], w1[a])) return false;
+  }
+  out.n = interp_nodes(FWI_INTERP_SINC, nd);
+  out.node.assign(3 * out.n, 0);
+  out.w.assign(out.n, 1.0);
+  for (int c = 0; c < out.n; ++c) {
+    int rem = c;
+    for (int a = 0; a < nd; ++a) {
+      const int j = rem % W;
+      rem /= W;
+      out.node[3 * c + a] = first[a] + j;
+      out.w[c] *= w1[a][j];
+    }
+  }
+  return true;
+}
+
 TileGeo tile_geo(const fwi_plan* P, int tile, bool tma, bool x2, bool ext) {
   TileGeo T{};
   if (ext) {   // kernels_ext.cu: 32 x 16 tiles (2D), 32 x 8 columns in z chunks (3D)
@@ -137,12 +209,14 @@ fwi_status build_source_table(Call& c, int shot0, int nb, Carve& C, DevTable& D)
   for (int a = 0; a < nd; ++a) dV *= P->h[a];
   std::vector<Entry> E;
   E.reserve((size_t)nb * g->nsrc * c.ncorner);
+  PointSt ps;
   for (int b = 0; b < nb; ++b) {
     const int s = shot0 + b;
     for (int k = 0; k < g->nsrc; ++k) {
-      const Corners cr = point_corners(P, g->src_xyz + ((long long)s * g->nsrc + k) * nd);
-      for (int q = 0; q < cr.n; ++q)
-        add_entry(E, c.T, b, cr.node[q], (s * g->nsrc + k) * P->nt, (float)(cr.w[q] / dV));
+      if (!point_stencil(P, g->src_xyz + ((long long)s * g->nsrc + k) * nd, ps))
+        return fail(FWI_ERR_INVALID_ARG, "a sinc source lies too close to a face");
+      for (int q = 0; q < ps.n; ++q)
+        add_entry(E, c.T, b, &ps.node[3 * q], (s * g->nsrc + k) * P->nt, (float)(ps.w[q] / dV));
     }
   }
   const HostTable H = bucket(E, c.pl.B * c.T.ntiles());
@@ -160,13 +234,15 @@ fwi_status build_source_sampling(Call& c, int shot0, int nb, int* d_node, float*
   for (int a = 0; a < nd; ++a) dV *= P->h[a];
   std::vector<int> node((size_t)nb * g->nsrc * c.ncorner, 0);
   std::vector<float> w(node.size(), 0.f);
+  PointSt ps;
   for (int b = 0; b < nb; ++b)
     for (int k = 0; k < g->nsrc; ++k) {
-      const Corners cr = point_corners(P, g->src_xyz + ((long long)(shot0 + b) * g->nsrc + k) * nd);
+      if (!point_stencil(P, g->src_xyz + ((long long)(shot0 + b) * g->nsrc + k) * nd, ps))
+        return fail(FWI_ERR_INVALID_ARG, "a sinc source lies too close to a face");
       const size_t pt = (size_t)b * g->nsrc + k;
-      for (int q = 0; q < cr.n; ++q) {
-        node[pt * c.ncorner + q] = (int)node_index(P->L, cr.node[q]);
-        w[pt * c.ncorner + q] = (float)(cr.w[q] / dV);
+      for (int q = 0; q < ps.n; ++q) {
+        node[pt * c.ncorner + q] = (int)node_index(P->L, &ps.node[3 * q]);
+        w[pt * c.ncorner + q] = (float)(ps.w[q] / dV);
       }
     }
   // pageable sources: the copies have staged them when cudaMemcpyAsync returns
@@ -182,22 +258,24 @@ fwi_status prepare_common(Call& c, Carve& tabC) {
   fwi_plan* P = c.P;
   const fwi_geometry* g = c.geom;
   const int nd = P->grid.ndim;
-  c.ncorner = 1 << nd;
+  c.ncorner = interp_nodes(P->opt.interp, nd);
   c.T = tile_geo(P, c.pl.shape, c.pl.tma, c.pl.x2, c.pl.sc.ext());
   // receiver sampling table
   std::vector<int> node((size_t)g->nrec * c.ncorner);
   std::vector<float> w((size_t)g->nrec * c.ncorner);
   std::vector<Entry> E;
+  PointSt ps;
   for (int r = 0; r < g->nrec; ++r) {
-    const Corners cr = point_corners(P, g->rec_xyz + (long long)r * nd);
-    for (int q = 0; q < cr.n; ++q) {
-      node[(size_t)r * c.ncorner + q] = (int)node_index(P->L, cr.node[q]);
-      w[(size_t)r * c.ncorner + q] = (float)cr.w[q];
+    if (!point_stencil(P, g->rec_xyz + (long long)r * nd, ps))
+      return fail(FWI_ERR_INVALID_ARG, "a sinc receiver lies too close to a face");
+    for (int q = 0; q < ps.n; ++q) {
+      node[(size_t)r * c.ncorner + q] = (int)node_index(P->L, &ps.node[3 * q]);
+      w[(size_t)r * c.ncorner + q] = (float)ps.w[q];
     }
     if (c.pl.gradient)
       for (int b = 0; b < c.pl.B; ++b)
-        for (int q = 0; q < cr.n; ++q)
-          add_entry(E, c.T, b, cr.node[q], b * g->nrec + r, (float)cr.w[q]);
+        for (int q = 0; q < ps.n; ++q)
+          add_entry(E, c.T, b, &ps.node[3 * q], b * g->nrec + r, (float)ps.w[q]);
   }
   if (P->L.fstride >= (1LL << 31)) return fail(FWI_ERR_UNSUPPORTED, "field larger than 2^31 points");
   int* dn = tabC.take<int>(node.size());
@@ -215,7 +293,7 @@ fwi_status prepare_common(Call& c, Carve& tabC) {
 
 size_t tables_bound(const fwi_plan* P, const fwi_geometry* g, const Plan& pl) {
   const TileGeo T = tile_geo(P, pl.shape, pl.tma, pl.x2, pl.sc.ext());
-  const int nc = 1 << P->grid.ndim;
+  const int nc = interp_nodes(P->opt.interp, P->grid.ndim);
   const size_t nb = (size_t)pl.B * T.ntiles() + 1;
   const size_t src = (size_t)pl.B * g->nsrc * nc;
   const size_t rec = (size_t)g->nrec * nc;
@@ -257,36 +335,15 @@ fwi_status fwi_point_weights(const fwi_grid* grid, const double* xyz, int interp
     }
     return FWI_OK;
   }
-  // Kaiser-windowed sinc: per axis the 2r nodes floor(x)-r+1 .. floor(x)+r
-  // with w = I0(b sqrt(1 - (d/r)^2)) / I0(b) * sin(pi d) / (pi d), d = i - x;
+  // Kaiser-windowed sinc: per axis the 2r nodes floor(x)-r+1 .. floor(x)+r;
   // the point weights are the products over the axes.
   constexpr int r = FWI_SINC_RADIUS;
-  constexpr double b = FWI_SINC_KAISER_B;
-  auto bessel_i0 = [](double x) {          // power series sum_k ((x/2)^k / k!)^2
-    double term = 1.0, sum = 1.0;
-    for (int k = 1; k < 200 && term > 1e-18 * sum; ++k) {
-      term *= (x / (2.0 * k)) * (x / (2.0 * k));
-      sum += term;
-    }
-    return sum;
-  };
-  const double i0b = bessel_i0(b);
   int first[3] = {0, 0, 0};
   double w1[3][2 * FWI_SINC_RADIUS];
   int total = 1;
   for (int d = 0; d < nd; ++d) {
-    const double x = xyz[d] / grid->spacing[d];
-    const long long f = (long long)std::floor(x);
-    if (f - r + 1 < 0 || f + r > grid->shape[d] - 1)
+    if (!sinc_axis(xyz[d] / grid->spacing[d], grid->shape[d], &first[d], w1[d]))
       return fail(FWI_ERR_INVALID_ARG, "fwi_point_weights: a sinc point must lie r - 1 nodes inside every face");
-    first[d] = (int)(f - r + 1);
-    for (int j = 0; j < 2 * r; ++j) {
-      const double dd = (double)(first[d] + j) - x;
-      const double q = 1.0 - (dd / r) * (dd / r);
-      const double win = std::fabs(dd) <= r ? bessel_i0(b * std::sqrt(q > 0.0 ? q : 0.0)) / i0b : 0.0;
-      const double sn = dd == 0.0 ? 1.0 : std::sin(kPiD * dd) / (kPiD * dd);
-      w1[d][j] = win * sn;
-    }
     total *= 2 * r;
   }
   *count = total;

@@ -120,7 +120,12 @@ def test_time4_gradient(case, ckpt):
 
 # ----------------------------------------------------------------- attenuation
 
-ALPHA = {0: 200.0, 2: 2e-11}      # nepers/m (y = 0), nepers/m/(rad/s)^2 (y = 2)
+# nepers/m (y = 0), nepers/m/(rad/s)^2 (y = 2): 100 times typical soft tissue,
+# so that the term matters within a few hundred steps.  The y = 2 term is
+# explicit (a backward difference in time): with r = k lambda_max and
+# s = r (2 alpha0 vp / dt) the step is stable for r + 2 s <= 4, which 4e-12
+# keeps (s < 0.5 here) and 2e-11 would break in 3D.
+ALPHA = {0: 200.0, 2: 4e-12}
 
 ATT_CASES = {
     "2d-y0-vd": dict(ndim=2, y=0, vd=True),
@@ -185,6 +190,14 @@ def test_attenuation_gradient(case, ckpt):
     assert rel_l2(d, np.stack(d_ref)) <= TOL_TRACES
     assert abs(J - J_ref) <= 1e-3 * abs(J_ref)
     assert rel_l2(gg, g_ref) <= TOL_GRAD
+
+
+def test_attenuation_y2_refuses_unstable_strength():
+    """alpha0 beyond the y = 2 term's stability bound is refused before any step."""
+    p = att_problem(3)
+    with pytest.raises(binding.FwiError) as ei:
+        run_gpu(p, True, alpha0=np.full(p.shape, 5e-11), y=2)
+    assert ei.value.status == 2
 
 
 def test_attenuation_zero_alpha_is_the_leapfrog():
