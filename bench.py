@@ -500,6 +500,103 @@ def roofline(acc, steps, ms, vd, ndim, tile):
             "share_of_step": per_launch[kind] * n_l / steps / ms}
 
 
+# Algorithmic HBM bytes per point update of the extended schemes' steps, as
+# fused single passes (FP32 fields, constant density; variable density adds
+# the ln rho field, 4 B): fourth order in time: u^n, u^{n-1}, k read, u^{n+1},
+# F, k w written (adjoint: lambda^k, lambda^{k+1}, k, F, k w, g read,
+# lambda^{k-1}, g written); attenuation adds its coefficient (y = 0) or the
+# coefficient and the Laplacian state read and written (y = 2).
+SCHEME_BYTES = {("t4", "fwd"): 24, ("t4", "adj"): 32, ("att0", "fwd"): 24, ("att0", "adj"): 32,
+                ("att2", "fwd"): 32, ("att2", "adj"): 40}
+
+
+def scheme_sample(kind, shots=30, steps=1, warmup=1):
+    """The 2D breast workload (1024^2, 0.1 mm, vd, o8, 256 receivers, 100 us
+    record) with `shots` of its 128 shots, in an extended scheme: "t4" the
+    fourth-order time scheme at CFL 0.8 (2000 steps of 50 ns) against the
+    leapfrog at CFL 0.4 (4000 steps of 25 ns) on the same shots
+    (time-to-solution of the same record); "att0" / "att2" the attenuation
+    term of Eq. 10 with alpha0 of soft tissue (0.5 dB/cm at 1 MHz: 5.8 Np/m
+    for y = 0, 5.8 Np/m / (2 pi 1e6)^2 for y = 2); "sinc" Kaiser-windowed sinc
+    points.  Gradient Gpts/s (useful updates: 2 x points x steps x shots) and
+    the roofline of the dominant kernel, inputs resident."""
+    import torch
+    from paper_2110_03345_gb300 import binding, inputs
+    p = inputs.config_breast_2d(shots=list(range(0, 2 * shots, 2)))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+    geo = binding.Geometry(p.src_xyz, p.rec_xyz)
+    vp, rho = f32(p.vp), f32(p.rho)
+    stream = torch.cuda.current_stream()
+
+    def run(nt, dt, opts, alpha=None, y=0):
+        w = inputs.ricker(500e3, dt, nt)
+        wav = f32(np.broadcast_to(w, (p.nshots, 1, nt)))
+        plan = binding.Plan(p.shape, p.spacing, nt, dt, order=p.order, sponge=p.nb, c_ref=p.c_ref,
+                            stream=stream)
+        plan.set_options(profile=PROFILE_EVERY, **opts)
+        if alpha is not None:
+            plan.set_attenuation(f32(np.full(p.shape, alpha)), y)
+        obs = plan.forward(f32(p.vp_true), rho, geo, wav)
+        grad = torch.empty(p.shape, device=dev, dtype=torch.float32)
+        for _ in range(warmup):
+            plan.gradient(vp, rho, geo, wav, obs, grad=grad)
+        acc = dict.fromkeys(STAT_KEYS, 0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            plan.gradient(vp, rho, geo, wav, obs, grad=grad)
+            st = plan.stats()
+            for k in acc:
+                acc[k] += st[k]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        st = plan.stats()
+        plan.close()
+        upd = 2 * p.npoints * (nt - 1) * p.nshots
+        return {"nt": nt, "dt_ns": dt * 1e9, "s_per_gradient": ms * 1e-3,
+                "value": upd / (ms * 1e-3) / 1e9, "unit": "Gpts/s", "batch": st["batch"],
+                "gpu_launches": int(acc["launches"]), "acc": acc, "ms": ms}
+
+    def with_roof(r, key):
+        acc, ms = r.pop("acc"), r.pop("ms")
+        if key is None:
+            r["roofline"] = roofline(acc, steps, ms, True, 2, 6)
+            return r
+        per = {k: acc[f"{k}_ms"] / max(acc[f"{k}_timed"], 1) for k in ("fwd", "adj")}
+        kk = "adj" if per["adj"] * acc["adj_launches"] >= per["fwd"] * acc["fwd_launches"] else "fwd"
+        n_l = max(acc[f"{kk}_launches"], 1)
+        pts = acc[f"{kk}_points"] / n_l
+        bpu = SCHEME_BYTES[(key, kk)] + 4          # + ln rho (variable density)
+        ach = bpu * pts / (per[kk] * 1e-3) / 1e9
+        peak, src = measured_hbm_peak()
+        r["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                         "frac": ach / peak, "traffic": None, "peak_source": src,
+                         "kernel": "k_ext2d %s step (%s)" % ("adjoint+imaging" if kk == "adj"
+                                                             else "forward+store", key),
+                         "bytes_per_update": bpu, "points_per_launch": int(pts),
+                         "launch_ms": per[kk], "timed_launches": int(acc[f"{kk}_timed"])}
+        return r
+
+    out = {"workload": f"breast2d 1024^2, {p.nshots} of the 128 shots, vd, o8, 100 us record",
+           "scheme": kind}
+    if kind == "t4":
+        lf = with_roof(run(p.nt, p.dt, {}), None)
+        t4 = with_roof(run((p.nt - 1) // 2 + 1, 2 * p.dt, {"time_order": 4}), "t4")
+        out.update({"leapfrog_cfl_0.4": lf, "time4_cfl_0.8": t4,
+                    "time_to_solution_speedup": lf["s_per_gradient"] / t4["s_per_gradient"]})
+    elif kind in ("att0", "att2"):
+        y = 0 if kind == "att0" else 2
+        alpha = 5.8 if y == 0 else 5.8 / (2 * np.pi * 1e6) ** 2
+        out.update(with_roof(run(p.nt, p.dt, {}, alpha=alpha, y=y), kind))
+        out["alpha0"] = alpha
+    else:
+        out.update(with_roof(run(p.nt, p.dt, {"interp": 1}), None))
+    return out
+
+
 STAT_KEYS = ("fwd_ms", "adj_ms", "fwd_launches", "adj_launches", "fwd_points", "adj_points",
              "launches", "fwd_timed", "adj_timed")
 
@@ -664,6 +761,7 @@ def run_mine(args):
         # --workload uneven / serving)
         if args.workload == "breast2d":
             extras["skull3d"] = skull3d_sample()
+            extras["schemes"] = {k: scheme_sample(k) for k in ("t4", "att0", "att2", "sinc")}
         extras["batched"] = uneven_batch(nprob=16, seed=4, reps=1)
         extras["serving"] = serving_stream(nreq=80, warm=10, seed=5)
         try:                               # the full Sec. 3.2 loop: ~3 s on one GB300

@@ -194,6 +194,7 @@ fwi_status fwi_batch_create(fwi_batch** out, int nprob, const fwi_problem* probs
     p.inj_off = it->src.off;
     p.inj_loc = it->src.loc;
     p.inj_vidx = it->src.vidx;
+    p.inj_row = it->src.row;
     p.inj_w = it->src.w;
     p.vals = it->prob.wavelet;
     p.smp_node = c.smp_node;

@@ -126,7 +126,7 @@ StepParams base_params(Call& c) {
 
 long long launch_threads(const Call& c, int B) {
   if (c.pl.sc.ext())
-    return (long long)c.T.ntiles() * B * EXT_TX * (c.P->grid.ndim == 3 ? EXT_TY3 : EXT_TY2);
+    return (long long)c.T.ntiles() * B * (c.P->grid.ndim == 3 ? EXT_TX * EXT_TY3 : EXT_TX2 / 4 * EXT_TY2);
   const int by = (c.P->grid.ndim == 3) ? tile3_variant(c.pl.shape).by
                  : c.pl.tma ? tile2_tma_variant(c.pl.shape).by : tile2_variant(c.pl.shape).by;
   const int ctas_z = (B + c.pl.S - 1) / c.pl.S;
@@ -254,6 +254,7 @@ fwi_status forward_steps(Call& c, int nb, int shot0, const DevTable& src, float*
   p.inj_off = src.off;
   p.inj_loc = src.loc;
   p.inj_vidx = src.vidx;
+  p.inj_row = src.row;
   p.inj_w = src.w;
   p.vals = c.wavelet;
   p.smp_node = c.smp_node;
@@ -540,6 +541,7 @@ fwi_status gradient_adjoint_batch(Call& c, int j, int shot0, int nb, const DevTa
   p.inj_off = c.rec_tab.off;
   p.inj_loc = c.rec_tab.loc;
   p.inj_vidx = c.rec_tab.vidx;
+  p.inj_row = c.rec_tab.row;
   p.inj_w = c.rec_tab.w;
   p.vals = c.D;
   p.g = c.W.G;

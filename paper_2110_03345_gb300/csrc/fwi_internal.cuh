@@ -68,6 +68,7 @@ struct StepParams {
   const int* inj_off;
   const int* inj_loc;    // tile-local linear index (2D: ly*TX+lx; 3D: (lz*TY+ly)*TX+lx)
   const int* inj_vidx;   // index into vals (before step_off)
+  const int* inj_row;    // 2D: per bucket, entry range of each tile row (TY + 1 values)
   const float* inj_w;    // weight (source: w/dV; receiver residual: w)
   const float* vals;
   long long step_off;
@@ -95,15 +96,16 @@ struct StepParams {
   float inj_scale;       // factor on injected values (fourth-order adjoint pass B: 12)
 };
 
-// Extended schemes (kernels_ext.cu): one point per thread, shared-memory
-// staged tiles of 32 x 16 (2D) or 32 x 8 columns streamed along z (3D).
+// Extended schemes (kernels_ext.cu): shared-memory staged tiles of 128 x 16
+// points, a float4 per thread (2D), or 32 x 8 columns streamed along z, one
+// point per thread (3D).
 enum ExtMode {
   EXT_KW = 0,    // out = k (L x + s)                  (4th order, first pass)
   EXT_T4 = 1,    // F = x + k (L x + s) / 12, update     (4th order, second pass)
   EXT_ATT0 = 2,  // leapfrog with per-point damping alpha0 vp dt   (y = 0)
   EXT_ATT2 = 3,  // leapfrog with the Laplacian-difference term     (y = 2)
 };
-constexpr int EXT_TX = 32, EXT_TY2 = 16, EXT_TY3 = 8, EXT_ZC = 32;
+constexpr int EXT_TX2 = 128, EXT_TX = 32, EXT_TY2 = 16, EXT_TY3 = 8, EXT_ZC = 32;
 cudaError_t launch_ext(const StepParams& p, int ndim, int R, bool vd, bool adj, int mode,
                        cudaStream_t st);
 // out[i] = q[i+1] - 2 q[i] + q[i-1] along the last axis of rows x nt samples

@@ -133,6 +133,7 @@ struct Entry {
 struct HostTable {
   std::vector<int> off, loc, vidx;
   std::vector<float> w;
+  std::vector<int> row;   // 2D: per bucket, the first entry of each tile row (rows + 1 values)
 };
 
 struct DevTable {
@@ -140,6 +141,7 @@ struct DevTable {
   const int* loc = nullptr;
   const int* vidx = nullptr;
   const float* w = nullptr;
+  const int* row = nullptr;
 };
 
 // Time scheme and attenuation of a call: the leapfrog of the default
@@ -271,7 +273,9 @@ long long node_index(const Layout& L, const int* n);
 TileGeo tile_geo(const fwi_plan* P, int tile, bool tma, bool x2 = false, bool ext = false);
 void add_entry(std::vector<Entry>& E, const TileGeo& T, int slot, const int* node, int vidx,
                float w);
-HostTable bucket(const std::vector<Entry>& E_in, int nbuckets);
+// Entries grouped by bucket and sorted by tile-local index; with rows > 0 (2D
+// tiles of rows x tx points) also the per-row entry ranges of every bucket.
+HostTable bucket(const std::vector<Entry>& E_in, int nbuckets, int rows = 0, int tx = 0);
 size_t table_bytes(const HostTable& H);
 fwi_status upload_table(fwi_plan* P, const HostTable& H, Carve& C, DevTable& D);
 fwi_status build_source_table(Call& c, int shot0, int nb, Carve& C, DevTable& D);

@@ -202,10 +202,12 @@ __device__ __forceinline__ void step2d_tile(const StepParams& p, int bxi, int by
 
     // Point sources (forward) or receiver residuals (adjoint) owned by this thread.
     if (e1 > e0) {
-      for (int e = e0; e < e1; ++e) {
-        const int loc = p.inj_loc[e];
-        const int ely = loc / TX, elx = loc - ely * TX;
-        if (ely == ly && (elx >> 2) == tx) {
+      // only this row's entries (the bucket's per-row ranges)
+      const int* rr = p.inj_row + (size_t)(b * p.ntiles + byi * gx + bxi) * (TY + 1);
+      const int r1 = rr[ly + 1];
+      for (int e = rr[ly]; e < r1; ++e) {
+        const int elx = p.inj_loc[e] - ly * TX;
+        if ((elx >> 2) == tx) {
           const float val = p.inj_w[e] * p.vals[p.inj_vidx[e] + p.step_off];
           const int ix = elx & 3;
 #pragma unroll

@@ -266,10 +266,12 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
         acc[0] = A0.x; acc[1] = A0.y; acc[2] = A1.x; acc[3] = A1.y;
       }
       if (e1 > e0) {
-        for (int e = e0; e < e1; ++e) {
-          const int loc = p.inj_loc[e];
-          const int ely = loc / TX, elx = loc - ely * TX;
-          if (ely == ly && (elx >> 2) == tx) {
+        // only this row's entries (the bucket's per-row ranges)
+        const int* rr = p.inj_row + (size_t)(s * p.ntiles + tile_id) * (TY + 1);
+        const int r1 = rr[ly + 1];
+        for (int e = rr[ly]; e < r1; ++e) {
+          const int elx = p.inj_loc[e] - ly * TX;
+          if ((elx >> 2) == tx) {
             const float val = p.inj_w[e] * p.vals[p.inj_vidx[e] + p.step_off];
             const int ix = elx & 3;
 #pragma unroll

@@ -23,8 +23,9 @@
 //  In every mode the adjoint's imaging term is g -= lambda^k * hist^k (plus the
 //  kw term above), so the gradient with respect to m = 1/vp^2 is g / dt^2.
 //
-// Organisation: one grid point per thread.  2D: a CTA of 32 x 16 threads
-// stages its tile plus halo in shared memory.  3D: a CTA of 32 x 8 threads
+// Organisation.  2D: a CTA of 32 x 16 threads stages a 128 x 16 tile plus
+// halo in shared memory with 16-byte loads, each thread updating a float4 of
+// x points.  3D: one grid point per thread, a CTA of 32 x 8 threads
 // streams a column along z over a chunk of planes with the column's 2R+1
 // values in a register queue and the x-y plane (with halo) staged in shared
 // memory.  Sources and receiver residuals come from the per-tile bucket
@@ -120,20 +121,52 @@ __device__ __forceinline__ void ext_update(const StepParams& p, long long fo, lo
   }
 }
 
+__device__ __forceinline__ float4 ldg4(const float* q) {
+  return __ldg(reinterpret_cast<const float4*>(q));
+}
+__device__ __forceinline__ float4 ld4(const float* q) { return *reinterpret_cast<const float4*>(q); }
+__device__ __forceinline__ void st4(float* q, const float4& v) { *reinterpret_cast<float4*>(q) = v; }
+__device__ __forceinline__ float4 mul4(const float4& a, const float4& b) {
+  return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
+}
+__device__ __forceinline__ void unpack(const float4& t, float* v) {
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ float4 pack(const float* v) { return make_float4(v[0], v[1], v[2], v[3]); }
+
+// Shared-memory layout of the 2D kernel (float4 units): the stencil input
+// tile with halo [SH][SW]; for the variable-density adjoint b_x x on the tile
+// rows [TY][SW] and b_y x on the tile columns [SH][QW]; for the y = 2
+// adjoint att x in the same two shapes.
 template <int R, bool VD, bool ADJ, int MODE>
-__global__ void __launch_bounds__(EXT_TX * EXT_TY2) k_ext2d(const StepParams p) {
-  constexpr int TX = EXT_TX, TY = EXT_TY2;
-  constexpr int SW = TX + 2 * R, SH = TY + 2 * R;
-  constexpr int NT = TX * TY;
-  constexpr bool PSI = VD && ADJ;                    // b_d x for L^T
-  constexpr bool CL = (MODE == EXT_ATT2) && ADJ;     // att x for lap(att x)
-  __shared__ float s_x[SH][SW];
-  __shared__ float s_px[PSI ? TY : 1][PSI ? SW : 1];
-  __shared__ float s_py[PSI ? SH : 1][PSI ? TX : 1];
-  __shared__ float s_c[CL ? SH : 1][CL ? SW : 1];
+struct Ext2 {
+  static constexpr int TX = EXT_TX2, TY = EXT_TY2;
+  static constexpr int XH = (R <= 4) ? 4 : 8, NL = XH / 4;
+  static constexpr int SW = TX / 4 + 2 * NL, SH = TY + 2 * R, QW = TX / 4;
+  static constexpr bool PSI = VD && ADJ;
+  static constexpr bool CL = (MODE == EXT_ATT2) && ADJ;
+  static constexpr int CROSS = TY * SW + SH * QW;
+  static constexpr size_t SMEM = ((size_t)SH * SW + (PSI ? CROSS : 0) + (CL ? CROSS : 0)) * 16;
+};
+
+// One 128 x 16 tile of one shot; thread (tx, ty) owns the float4 of x points
+// 4 tx .. 4 tx + 3 of row ty.
+template <int R, bool VD, bool ADJ, int MODE>
+__global__ void __launch_bounds__(EXT_TX2 / 4 * EXT_TY2) k_ext2d(const StepParams p) {
+  using G = Ext2<R, VD, ADJ, MODE>;
+  constexpr int TX = G::TX, TY = G::TY, NL = G::NL, SW = G::SW, SH = G::SH, QW = G::QW;
+  constexpr int NT = TX / 4 * TY;
+  constexpr int NV = 4 + 8 * NL;
+  constexpr bool PSI = G::PSI, CL = G::CL;
+  extern __shared__ __align__(16) float4 sm[];
+  float4* s_x = sm;                          // [SH][SW]
+  float4* s_px = s_x + SH * SW;              // PSI: b_x x [TY][SW], then b_y x [SH][QW]
+  float4* s_py = s_px + TY * SW;
+  float4* s_cx = s_x + SH * SW + (PSI ? G::CROSS : 0);   // CL: att x, same shapes
+  float4* s_cy = s_cx + TY * SW;
 
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int tid = ty * TX + tx;
+  const int tid = ty * (TX / 4) + tx;
   const int b = blockIdx.z;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const long long fo = (long long)b * p.fstride;
@@ -142,66 +175,239 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY2) k_ext2d(const StepParams p) 
     const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     ext_sample(p, blk * NT + tid);
   }
-  const long long base = (long long)(y0 + p.oy - R) * p.sx + (x0 + p.ox - R);
+  const long long base = (long long)(y0 + p.oy - R) * p.sx + (x0 + p.ox - G::XH);
   for (int i = tid; i < SH * SW; i += NT) {
     const int r = i / SW, c = i - r * SW;
-    const long long o = base + (long long)r * p.sx + c;
-    const float v = X[o];
-    s_x[r][c] = v;
-    if (CL) s_c[r][c] = __ldg(p.att + o) * v;
+    s_x[i] = ldg4(X + base + (long long)r * p.sx + 4 * c);
   }
-  if (PSI) {
+  if (PSI || CL) {
     for (int i = tid; i < TY * SW; i += NT) {
       const int r = i / SW, c = i - r * SW;
-      const long long o = base + (long long)(r + R) * p.sx + c;
-      s_px[r][c] = __ldg(p.bx + o) * X[o];
+      const long long o = base + (long long)(r + R) * p.sx + 4 * c;
+      const float4 xv = ldg4(X + o);
+      if (PSI) s_px[i] = mul4(ldg4(p.bx + o), xv);
+      if (CL) s_cx[i] = mul4(ldg4(p.att + o), xv);
     }
-    for (int i = tid; i < SH * TX; i += NT) {
-      const int r = i / TX, c = i - r * TX;
-      const long long o = base + (long long)r * p.sx + c + R;
-      s_py[r][c] = __ldg(p.by + o) * X[o];
+    for (int i = tid; i < SH * QW; i += NT) {
+      const int r = i / QW, c = i - r * QW;
+      const long long o = base + (long long)r * p.sx + 4 * (c + NL);
+      const float4 xv = ldg4(X + o);
+      if (PSI) s_py[i] = mul4(ldg4(p.by + o), xv);
+      if (CL) s_cy[i] = mul4(ldg4(p.att + o), xv);
     }
   }
   __syncthreads();
 
-  const int xg = x0 + tx, yg = y0 + ty;
-  const int cx = tx + R, cy = ty + R;
-  const float cen = s_x[cy][cx];
-  const float c2 = cen + cen;
-  float lap = 0.f;
+  const int ly = ty, yg = y0 + ly, srow = ly + R;
+  const int xg = x0 + 4 * tx;
+  float v[NV];
 #pragma unroll
-  for (int j = 1; j <= R; ++j) lap = fmaf(p.wx.w2[j], (s_x[cy][cx + j] + s_x[cy][cx - j]) - c2, lap);
+  for (int q = 0; q <= 2 * NL; ++q) unpack(s_x[srow * SW + tx + q], v + 4 * q);
+  float acc[4], c2[4], cen[4];
 #pragma unroll
-  for (int j = 1; j <= R; ++j) lap = fmaf(p.wy.w2[j], (s_x[cy + j][cx] + s_x[cy - j][cx]) - c2, lap);
-  float acc = lap;
+  for (int ix = 0; ix < 4; ++ix) {
+    const int c = 4 * NL + ix;
+    cen[ix] = v[c];
+    c2[ix] = v[c] + v[c];
+    float t = 0.f;
+#pragma unroll
+    for (int j = 1; j <= R; ++j) t = fmaf(p.wx.w2[j], (v[c + j] + v[c - j]) - c2[ix], t);
+    acc[ix] = t;
+  }
+  float d1y[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int j = 1; j <= R; ++j) {
+    const float4 a = s_x[(srow - j) * SW + tx + NL];
+    const float4 c = s_x[(srow + j) * SW + tx + NL];
+    acc[0] = fmaf(p.wy.w2[j], (a.x + c.x) - c2[0], acc[0]);
+    acc[1] = fmaf(p.wy.w2[j], (a.y + c.y) - c2[1], acc[1]);
+    acc[2] = fmaf(p.wy.w2[j], (a.z + c.z) - c2[2], acc[2]);
+    acc[3] = fmaf(p.wy.w2[j], (a.w + c.w) - c2[3], acc[3]);
+    if (VD && !ADJ) {
+      d1y[0] = fmaf(p.wy.w1[j], c.x - a.x, d1y[0]);
+      d1y[1] = fmaf(p.wy.w1[j], c.y - a.y, d1y[1]);
+      d1y[2] = fmaf(p.wy.w1[j], c.z - a.z, d1y[2]);
+      d1y[3] = fmaf(p.wy.w1[j], c.w - a.w, d1y[3]);
+    }
+  }
+  float lap[4];
+#pragma unroll
+  for (int ix = 0; ix < 4; ++ix) lap[ix] = acc[ix];
   const long long pi = (long long)(yg + p.oy) * p.sx + (xg + p.ox);
-  if (VD && !ADJ) {
-    float dx = 0.f, dy = 0.f;
+  if (VD && !ADJ) {   // L_rho u = lap u - b . grad u
+    float bxv[4], byv[4];
+    unpack(ldg4(p.bx + pi), bxv);
+    unpack(ldg4(p.by + pi), byv);
 #pragma unroll
-    for (int j = 1; j <= R; ++j) {
-      dx = fmaf(p.wx.w1[j], s_x[cy][cx + j] - s_x[cy][cx - j], dx);
-      dy = fmaf(p.wy.w1[j], s_x[cy + j][cx] - s_x[cy - j][cx], dy);
-    }
-    acc -= __ldg(p.bx + pi) * dx + __ldg(p.by + pi) * dy;
-  }
-  if (PSI) {
+    for (int ix = 0; ix < 4; ++ix) {
+      const int c = 4 * NL + ix;
+      float d = 0.f;
 #pragma unroll
-    for (int j = 1; j <= R; ++j) {
-      acc = fmaf(p.wx.w1[j], s_px[ty][cx + j] - s_px[ty][cx - j], acc);
-      acc = fmaf(p.wy.w1[j], s_py[cy + j][tx] - s_py[cy - j][tx], acc);
+      for (int j = 1; j <= R; ++j) d = fmaf(p.wx.w1[j], v[c + j] - v[c - j], d);
+      acc[ix] -= bxv[ix] * d + byv[ix] * d1y[ix];
     }
   }
-  float lc = 0.f;
-  if (CL) {
-    const float cc2 = 2.f * s_c[cy][cx];
+  if (PSI) {          // L_rho^T x = lap x + D1x(b_x x) + D1y(b_y x)
+    float pv[NV];
 #pragma unroll
-    for (int j = 1; j <= R; ++j) lc = fmaf(p.wx.w2[j], (s_c[cy][cx + j] + s_c[cy][cx - j]) - cc2, lc);
+    for (int q = 0; q <= 2 * NL; ++q) unpack(s_px[ly * SW + tx + q], pv + 4 * q);
 #pragma unroll
-    for (int j = 1; j <= R; ++j) lc = fmaf(p.wy.w2[j], (s_c[cy + j][cx] + s_c[cy - j][cx]) - cc2, lc);
+    for (int ix = 0; ix < 4; ++ix) {
+      const int c = 4 * NL + ix;
+#pragma unroll
+      for (int j = 1; j <= R; ++j) acc[ix] = fmaf(p.wx.w1[j], pv[c + j] - pv[c - j], acc[ix]);
+    }
+#pragma unroll
+    for (int j = 1; j <= R; ++j) {
+      const float4 a = s_py[(srow - j) * QW + tx];
+      const float4 c = s_py[(srow + j) * QW + tx];
+      acc[0] = fmaf(p.wy.w1[j], c.x - a.x, acc[0]);
+      acc[1] = fmaf(p.wy.w1[j], c.y - a.y, acc[1]);
+      acc[2] = fmaf(p.wy.w1[j], c.z - a.z, acc[2]);
+      acc[3] = fmaf(p.wy.w1[j], c.w - a.w, acc[3]);
+    }
   }
-  acc = ext_inject(p, b * p.ntiles + blockIdx.y * gridDim.x + blockIdx.x, ty * TX + tx, acc);
-  if (xg < p.nx && yg < p.ny)
-    ext_update<ADJ, MODE>(p, fo, pi, cen, acc, lap, lc, p.spx[xg] + p.spy[yg]);
+  float lc[4] = {0.f, 0.f, 0.f, 0.f};
+  if (CL) {           // lap(att x)
+    float cv[NV];
+#pragma unroll
+    for (int q = 0; q <= 2 * NL; ++q) unpack(s_cx[ly * SW + tx + q], cv + 4 * q);
+    float cc2[4];
+#pragma unroll
+    for (int ix = 0; ix < 4; ++ix) {
+      const int c = 4 * NL + ix;
+      cc2[ix] = 2.f * cv[c];
+#pragma unroll
+      for (int j = 1; j <= R; ++j) lc[ix] = fmaf(p.wx.w2[j], (cv[c + j] + cv[c - j]) - cc2[ix], lc[ix]);
+    }
+#pragma unroll
+    for (int j = 1; j <= R; ++j) {
+      const float4 a = s_cy[(srow - j) * QW + tx];
+      const float4 c = s_cy[(srow + j) * QW + tx];
+      lc[0] = fmaf(p.wy.w2[j], (a.x + c.x) - cc2[0], lc[0]);
+      lc[1] = fmaf(p.wy.w2[j], (a.y + c.y) - cc2[1], lc[1]);
+      lc[2] = fmaf(p.wy.w2[j], (a.z + c.z) - cc2[2], lc[2]);
+      lc[3] = fmaf(p.wy.w2[j], (a.w + c.w) - cc2[3], lc[3]);
+    }
+  }
+  if (p.inj_off) {    // this row's entries of the tile's bucket
+    const int t = b * p.ntiles + blockIdx.y * gridDim.x + blockIdx.x;
+    if (p.inj_off[t + 1] > p.inj_off[t]) {
+      const int* rr = p.inj_row + (size_t)t * (TY + 1);
+      const int r1 = rr[ly + 1];
+      for (int e = rr[ly]; e < r1; ++e) {
+        const int elx = p.inj_loc[e] - ly * TX;
+        if ((elx >> 2) == tx) {
+          const float val = p.inj_scale * p.inj_w[e] * p.vals[p.inj_vidx[e] + p.step_off];
+          const int ix = elx & 3;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[q] += (q == ix) ? val : 0.f;
+        }
+      }
+    }
+  }
+
+  // epilogue on the float4 of points (lanes outside the grid keep the padding at 0)
+  bool in[4];
+#pragma unroll
+  for (int ix = 0; ix < 4; ++ix) in[ix] = (yg < p.ny) && (xg + ix < p.nx);
+  float k[4], a0[4];
+  unpack(ldg4(p.kf + pi), k);
+  {
+    float ax[4];
+    unpack(ldg4(p.spx + xg), ax);
+    const float ay = p.spy[yg];
+#pragma unroll
+    for (int ix = 0; ix < 4; ++ix) a0[ix] = ax[ix] + ay;
+  }
+  float* upp = p.up + fo + pi;
+  if (MODE == EXT_KW) {
+    float o[4];
+#pragma unroll
+    for (int ix = 0; ix < 4; ++ix) o[ix] = in[ix] ? k[ix] * acc[ix] : 0.f;
+    st4(p.out + fo + pi, pack(o));
+    return;
+  }
+  float uo[4], r[4];
+  unpack(ld4(upp), uo);
+  if (MODE == EXT_T4) {
+    float uc[4], F[4];
+    unpack(ld4(p.u + fo + pi), uc);
+#pragma unroll
+    for (int ix = 0; ix < 4; ++ix) {
+      F[ix] = cen[ix] + __fdiv_rn(k[ix] * acc[ix], 12.f);
+      r[ix] = in[ix] ? (2.f * uc[ix] - (1.f - a0[ix]) * uo[ix] + F[ix]) * __frcp_rn(1.f + a0[ix]) : 0.f;
+    }
+    st4(upp, pack(r));
+    if (!ADJ) {
+      if (p.hist) {
+        float f[4], w[4];
+#pragma unroll
+        for (int ix = 0; ix < 4; ++ix) {
+          f[ix] = in[ix] ? F[ix] : 0.f;
+          w[ix] = in[ix] ? cen[ix] : 0.f;
+        }
+        __stcs(reinterpret_cast<float4*>(p.hist + fo + pi), pack(f));
+        __stcs(reinterpret_cast<float4*>(p.hist2 + fo + pi), pack(w));
+      }
+    } else if (p.image) {
+      float h[4], h2[4], g[4];
+      unpack(__ldcs(reinterpret_cast<const float4*>(p.hist + fo + pi)), h);
+      unpack(__ldcs(reinterpret_cast<const float4*>(p.hist2 + fo + pi)), h2);
+      unpack(ld4(p.g + fo + pi), g);
+#pragma unroll
+      for (int ix = 0; ix < 4; ++ix)
+        if (in[ix]) g[ix] = g[ix] - (uc[ix] * h[ix] + __fdiv_rn(cen[ix] * h2[ix], 12.f));
+      st4(p.g + fo + pi, pack(g));
+    }
+    return;
+  }
+  float at[4], hh[4];
+  unpack(ldg4(p.att + pi), at);
+  if (MODE == EXT_ATT0) {
+#pragma unroll
+    for (int ix = 0; ix < 4; ++ix) {
+      const float a = a0[ix] + at[ix];
+      const float h = k[ix] * acc[ix];
+      const float rv = (2.f * cen[ix] - (1.f - a) * uo[ix] + h) * __frcp_rn(1.f + a);
+      r[ix] = in[ix] ? rv : 0.f;
+      hh[ix] = in[ix] ? h - 0.5f * at[ix] * (rv - uo[ix]) : 0.f;
+    }
+  } else {   // EXT_ATT2
+    float qv[4], qn[4];
+    unpack(ld4(p.q + fo + pi), qv);
+#pragma unroll
+    for (int ix = 0; ix < 4; ++ix) {
+      float E, extra = 0.f;
+      if (!ADJ) {
+        const float dl = lap[ix] - qv[ix];
+        E = fmaf(at[ix], dl, acc[ix]);
+        qn[ix] = lap[ix];
+        extra = 0.5f * k[ix] * at[ix] * dl;
+      } else {
+        E = acc[ix] + (lc[ix] - qv[ix]);
+        qn[ix] = lc[ix];
+      }
+      const float h = k[ix] * E;
+      const float rv = (2.f * cen[ix] - (1.f - a0[ix]) * uo[ix] + h) * __frcp_rn(1.f + a0[ix]);
+      r[ix] = in[ix] ? rv : 0.f;
+      hh[ix] = in[ix] ? h + extra : 0.f;
+      qn[ix] = in[ix] ? qn[ix] : 0.f;
+    }
+    st4(p.q + fo + pi, pack(qn));
+  }
+  st4(upp, pack(r));
+  if (!ADJ) {
+    if (p.hist) __stcs(reinterpret_cast<float4*>(p.hist + fo + pi), pack(hh));
+  } else if (p.image) {
+    float h[4], g[4];
+    unpack(__ldcs(reinterpret_cast<const float4*>(p.hist + fo + pi)), h);
+    unpack(ld4(p.g + fo + pi), g);
+#pragma unroll
+    for (int ix = 0; ix < 4; ++ix)
+      if (in[ix]) g[ix] = fmaf(-cen[ix], h[ix], g[ix]);
+    st4(p.g + fo + pi, pack(g));
+  }
 }
 
 template <int R, bool VD, bool ADJ, int MODE>
@@ -332,8 +538,16 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_ext3d(const StepParams p) 
 template <int R, bool VD, bool ADJ, int MODE>
 cudaError_t launch_m(const StepParams& p, int ndim, cudaStream_t st) {
   if (ndim == 2) {
-    dim3 grid((p.nx + EXT_TX - 1) / EXT_TX, (p.ny + EXT_TY2 - 1) / EXT_TY2, p.B);
-    k_ext2d<R, VD, ADJ, MODE><<<grid, dim3(EXT_TX, EXT_TY2), 0, st>>>(p);
+    constexpr size_t smem = Ext2<R, VD, ADJ, MODE>::SMEM;
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaError_t e = cudaFuncSetAttribute(k_ext2d<R, VD, ADJ, MODE>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr_set = true;
+    }
+    dim3 grid((p.nx + EXT_TX2 - 1) / EXT_TX2, (p.ny + EXT_TY2 - 1) / EXT_TY2, p.B);
+    k_ext2d<R, VD, ADJ, MODE><<<grid, dim3(EXT_TX2 / 4, EXT_TY2), smem, st>>>(p);
   } else {
     dim3 grid((p.nx + EXT_TX - 1) / EXT_TX, (p.ny + EXT_TY3 - 1) / EXT_TY3, p.B * p.nzc);
     k_ext3d<R, VD, ADJ, MODE><<<grid, dim3(EXT_TX, EXT_TY3), 0, st>>>(p);

@@ -114,9 +114,9 @@ bool point_stencil(const fwi_plan* P, const double* xyz, PointSt& out) {
 
 TileGeo tile_geo(const fwi_plan* P, int tile, bool tma, bool x2, bool ext) {
   TileGeo T{};
-  if (ext) {   // kernels_ext.cu: 32 x 16 tiles (2D), 32 x 8 columns in z chunks (3D)
+  if (ext) {   // kernels_ext.cu: 128 x 16 tiles (2D), 32 x 8 columns in z chunks (3D)
     const bool three = P->grid.ndim == 3;
-    T.tx = EXT_TX;
+    T.tx = three ? EXT_TX : EXT_TX2;
     T.ty = three ? EXT_TY3 : EXT_TY2;
     T.zc = three ? EXT_ZC : 1;
     T.gx = (P->L.nx + T.tx - 1) / T.tx;
@@ -153,7 +153,7 @@ void add_entry(std::vector<Entry>& E, const TileGeo& T, int slot, const int* nod
   E.push_back({slot * T.ntiles() + tile, loc, vidx, w});
 }
 
-HostTable bucket(const std::vector<Entry>& E_in, int nbuckets) {
+HostTable bucket(const std::vector<Entry>& E_in, int nbuckets, int rows, int tx) {
   // within a bucket, entries in increasing tile-local index (the 3D kernels
   // walk them plane by plane with one cursor); stable, so the entries of one
   // node keep their order and its sum the same rounding
@@ -175,12 +175,22 @@ HostTable bucket(const std::vector<Entry>& E_in, int nbuckets) {
     H.vidx[k] = e.vidx;
     H.w[k] = e.w;
   }
+  if (rows > 0) {   // entries of tile row r of bucket b: [row[b (rows+1) + r], row[b (rows+1) + r + 1])
+    H.row.assign((size_t)nbuckets * (rows + 1), 0);
+    for (int b = 0; b < nbuckets; ++b) {
+      int k = H.off[b];
+      for (int r = 0; r <= rows; ++r) {
+        while (k < H.off[b + 1] && H.loc[k] < r * tx) ++k;
+        H.row[(size_t)b * (rows + 1) + r] = k;
+      }
+    }
+  }
   return H;
 }
 
 size_t table_bytes(const HostTable& H) {
   return align_up(H.off.size() * 4, 256) + align_up(H.loc.size() * 4 + 4, 256) * 2 +
-         align_up(H.w.size() * 4 + 4, 256);
+         align_up(H.w.size() * 4 + 4, 256) + align_up(H.row.size() * 4 + 4, 256);
 }
 
 fwi_status upload_table(fwi_plan* P, const HostTable& H, Carve& C, DevTable& D) {
@@ -198,6 +208,12 @@ fwi_status upload_table(fwi_plan* P, const HostTable& H, Carve& C, DevTable& D) 
   D.loc = loc;
   D.vidx = vidx;
   D.w = w;
+  D.row = nullptr;
+  if (!H.row.empty()) {
+    int* row = C.take<int>(H.row.size());
+    CUDA_TRY(cudaMemcpyAsync(row, H.row.data(), H.row.size() * 4, cudaMemcpyHostToDevice, P->st));
+    D.row = row;
+  }
   return FWI_OK;
 }
 
@@ -219,7 +235,7 @@ fwi_status build_source_table(Call& c, int shot0, int nb, Carve& C, DevTable& D)
         add_entry(E, c.T, b, &ps.node[3 * q], (s * g->nsrc + k) * P->nt, (float)(ps.w[q] / dV));
     }
   }
-  const HostTable H = bucket(E, c.pl.B * c.T.ntiles());
+  const HostTable H = bucket(E, c.pl.B * c.T.ntiles(), P->grid.ndim == 2 ? c.T.ty : 0, c.T.tx);
   return upload_table(P, H, C, D);
 }
 
@@ -285,7 +301,7 @@ fwi_status prepare_common(Call& c, Carve& tabC) {
   c.smp_node = dn;
   c.smp_w = dw;
   if (c.pl.gradient) {
-    const HostTable H = bucket(E, c.pl.B * c.T.ntiles());
+    const HostTable H = bucket(E, c.pl.B * c.T.ntiles(), nd == 2 ? c.T.ty : 0, c.T.tx);
     FWI_TRY(upload_table(P, H, tabC, c.rec_tab));
   }
   return FWI_OK;
@@ -297,8 +313,9 @@ size_t tables_bound(const fwi_plan* P, const fwi_geometry* g, const Plan& pl) {
   const size_t nb = (size_t)pl.B * T.ntiles() + 1;
   const size_t src = (size_t)pl.B * g->nsrc * nc;
   const size_t rec = (size_t)g->nrec * nc;
+  const size_t rows = P->grid.ndim == 2 ? nb * (T.ty + 1) * 4 * 2 + 2 * 256 : 0;   // per-row ranges
   return 8 * 256 + nb * 4 * 2 + (src + 1) * 12 + rec * 8 + (pl.gradient ? rec * pl.B * 12 + 4096 : 0) +
-         4096 * 4;
+         4096 * 4 + rows;
 }
 
 }  // namespace fwi
