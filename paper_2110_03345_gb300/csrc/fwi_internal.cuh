@@ -94,6 +94,11 @@ struct StepParams {
   float* q;              // y = 2: Laplacian of the previous step (updated in place)
   float* hist2;          // fourth-order scheme: k w^n (forward store, adjoint read)
   float inj_scale;       // factor on injected values (fourth-order adjoint pass B: 12)
+  // perfectly matched layer (kernels_pml.cu): auxiliary fields phi_x, phi_y,
+  // phi_z (forward) or their adjoints, the time step, the layer width
+  float* ph[3];
+  float dt;
+  int nb;
 };
 
 // Extended schemes (kernels_ext.cu): shared-memory staged tiles of 128 x 16
@@ -106,6 +111,12 @@ enum ExtMode {
   EXT_ATT2 = 3,  // leapfrog with the Laplacian-difference term     (y = 2)
 };
 constexpr int EXT_TX2 = 128, EXT_TX = 32, EXT_TY2 = 16, EXT_TY3 = 8, EXT_ZC = 32;
+// Perfectly matched layer passes (kernels_pml.cu), same tiles as the extended
+// schemes: forward u update, forward phi update, adjoint pass A (the phi and
+// q adjoints into ubar^{n+1}, c^n, imaging), adjoint pass B (L^T(k c) and the
+// phi adjoints).
+enum PmlMode { PML_U = 0, PML_PHI = 1, PML_A = 2, PML_B = 3 };
+cudaError_t launch_pml(const StepParams& p, int ndim, int R, bool vd, int mode, cudaStream_t st);
 cudaError_t launch_ext(const StepParams& p, int ndim, int R, bool vd, bool adj, int mode,
                        cudaStream_t st);
 // out[i] = q[i+1] - 2 q[i] + q[i-1] along the last axis of rows x nt samples
