@@ -125,6 +125,14 @@ typedef struct {
                            stable to sqrt(3) x the leapfrog's CFL limit */
     int interp;         /* off-grid sources and receivers: FWI_INTERP_LINEAR (0) or
                            FWI_INTERP_SINC (1), see fwi_point_weights */
+    int boundary;       /* absorbing boundary over the grid's sponge width (Sec. 2.4):
+                           0 the sponge; 1 a perfectly matched layer (unsplit,
+                           second-order form of the coordinate stretching
+                           d_j -> d_j / (1 + z_j / p) with the sponge's damping
+                           profile z_j per axis, auxiliary fields phi_j and, in
+                           3D, the time integral q of u; leapfrog without
+                           attenuation; the density must be constant over the
+                           layer and the stencil reach next to it) */
 } fwi_options;
 
 /* Counters of the last forward/gradient call on a plan. */

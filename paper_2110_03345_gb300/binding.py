@@ -74,7 +74,7 @@ class COptions(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int), ("ckpt_every", ctypes.c_int), ("tile", ctypes.c_int),
                 ("profile", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("shots_per_cta", ctypes.c_int), ("time_order", ctypes.c_int),
-                ("interp", ctypes.c_int)]
+                ("interp", ctypes.c_int), ("boundary", ctypes.c_int)]
 
 
 class CStats(ctypes.Structure):
@@ -232,6 +232,7 @@ def _stream_device(stream):
 
 LOWPASS_MAX_HALF_WIDTH = 2048
 INTERP_LINEAR, INTERP_SINC = 0, 1
+BOUNDARY_SPONGE, BOUNDARY_PML = 0, 1
 
 
 def point_weights(shape, spacing, xyz, interp=INTERP_LINEAR, order=8, sponge=0):
@@ -387,15 +388,16 @@ class Plan:
     __del__ = close
 
     def set_options(self, batch=0, ckpt_every=0, tile=0, profile=False, shots_per_cta=0,
-                    time_order=0, interp=INTERP_LINEAR):
+                    time_order=0, interp=INTERP_LINEAR, boundary=BOUNDARY_SPONGE):
         """tile: 0 default; 2D 1-4 shared-memory staged (one shot per CTA), 5-8
         TMA-staged with shots looped inside a CTA; 3D 1-4 shared-memory staged,
         5-8 TMA plane ring, 9-12 TMA plane ring with two x points per thread.
         shots_per_cta: 2D TMA variants only.  time_order: 2 (leapfrog) or 4
-        (fourth order in time).  interp: INTERP_LINEAR or INTERP_SINC points."""
+        (fourth order in time).  interp: INTERP_LINEAR or INTERP_SINC points.
+        boundary: BOUNDARY_SPONGE or BOUNDARY_PML."""
         # profile: True / 1 times every stencil launch, n > 1 every n-th
         self._opts = COptions(int(batch), int(ckpt_every), int(tile), int(profile),
-                              0, int(shots_per_cta), int(time_order), int(interp))
+                              0, int(shots_per_cta), int(time_order), int(interp), int(boundary))
         _check(load().fwi_plan_set_options(self._h, ctypes.byref(self._opts)))
 
     def stats(self) -> dict:
@@ -555,7 +557,7 @@ class Batch:
             arr[i].wavelet = _ptr(pr["wavelet"])
             arr[i].traces = _ptr(tr)
         self._arr = arr
-        self._opts = COptions(0, 0, int(tile), 0, 0, int(shots_per_cta), 0, 0)
+        self._opts = COptions(0, 0, int(tile), 0, 0, int(shots_per_cta), 0, 0, 0)
         h = ctypes.c_void_p()
         _check(lib.fwi_batch_create(ctypes.byref(h), len(problems), arr, ctypes.byref(self._opts),
                                     int(budget), ctypes.c_void_p(stream.cuda_stream),

@@ -137,9 +137,10 @@ fwi_status fwi_batch_create(fwi_batch** out, int nprob, const fwi_problem* probs
       return bail(fail(FWI_ERR_UNSUPPORTED, "a batch shares one stencil order and density mode"));
     }
     if (!pr.traces || !pr.wavelet) return bail(fail(FWI_ERR_INVALID_ARG, "problem arrays are NULL"));
-    if (pr.model.alpha0 || (opt && (opt->time_order == 4 || opt->interp != FWI_INTERP_LINEAR)))
+    if (pr.model.alpha0 ||
+        (opt && (opt->time_order == 4 || opt->interp != FWI_INTERP_LINEAR || opt->boundary != 0)))
       return bail(fail(FWI_ERR_UNSUPPORTED,
-                       "batches run the leapfrog without attenuation and with bi-/tri-linear points"));
+                       "batches run the leapfrog with the sponge, without attenuation and with bi-/tri-linear points"));
     BatchProblem* it = new BatchProblem();
     b->items.push_back(it);
     it->prob = pr;

@@ -114,6 +114,8 @@ StepParams base_params(Call& c) {
   }
   p.ntiles = c.T.ntiles();
   p.ncorner = c.ncorner;
+  p.dt = (float)P->dt;
+  p.nb = P->grid.sponge;
   if (P->grid.ndim == 3) {
     p.zchunk = c.T.zc;
     p.nzc = c.T.nzc;
@@ -241,6 +243,45 @@ fwi_status ext_step(Call& c, const StepParams& p_in, bool adj) {
   return FWI_OK;
 }
 
+// One PML time step (kernels_pml.cu), counted and timed as one stencil
+// launch: the u update (u^{n+1} over u^{n-1}, q^{n+1}, h^n), then the phi
+// update from u^{n+1} and q^{n+1}.
+fwi_status pml_step(Call& c, const StepParams& p_in) {
+  fwi_plan* P = c.P;
+  StepParams p = p_in;
+  const int nd = P->grid.ndim;
+  if (p.nrec > 0 && (long long)p.B * p.nrec > launch_threads(c, p.B)) {
+    cudaError_t e = launch_sample(p, P->st);
+    if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
+    c.launches++;
+    p.nrec = 0;
+  }
+  const bool prof = P->opt.profile > 0 &&
+                    (c.fwd_launches + c.adj_launches) % P->opt.profile == 0;
+  p.x = p.u;
+  p.q = c.W.PQ;
+  for (int d = 0; d < 3; ++d) p.ph[d] = c.W.PH[d];
+  if (prof) FWI_TRY(record_event(P, 0));
+  cudaError_t e = launch_pml(p, nd, P->R, c.vd, PML_U, P->st);
+  if (e == cudaSuccess) {
+    StepParams b = p;
+    b.x = p.up;            // u^{n+1}
+    b.nrec = 0;
+    b.inj_off = nullptr;
+    b.hist = nullptr;
+    e = launch_pml(b, nd, P->R, c.vd, PML_PHI, P->st);
+  }
+  c.launches += 2;
+  if (e != cudaSuccess) return fail(FWI_ERR_CUDA, std::string("PML launch: ") + cudaGetErrorString(e));
+  if (prof) {
+    FWI_TRY(record_event(P, 0));
+    c.fwd_timed++;
+  }
+  c.fwd_launches++;
+  c.fwd_points += (int64_t)p.B * P->L.nx * P->L.ny * P->L.nz;
+  return FWI_OK;
+}
+
 // Forward sweep of one batch: steps n = n0 .. n1-1 starting from (A = u^{n0},
 // Bf = u^{n0-1}).  hist_base: full history [n][B][fs] (n indexed from 0) or a
 // segment buffer indexed from n0; sample: record d^n for each step.
@@ -262,17 +303,19 @@ fwi_status forward_steps(Call& c, int nb, int shot0, const DevTable& src, float*
   p.smp_out = c.D;
   p.nrec = sample ? c.geom->nrec : 0;
   const bool ext = c.pl.sc.ext();
+  const bool pml = c.pl.sc.pml;
   const size_t cm = (size_t)c.pl.sc.ckpt_fields();
   for (int n = n0; n < n1; ++n) {
     if (K_ckpt > 0 && n % K_ckpt == 0) {
-      // checkpoint j: (u^n, u^{n-1}) and, for y = 2 attenuation, lap u^{n-1}
+      // checkpoint j: (u^n, u^{n-1}) and the scheme's other state (the
+      // Laplacian of u^{n-1} for y = 2 attenuation; q and phi for the PML)
       const size_t j = n / K_ckpt;
       float* dst = CK + cm * j * fs * c.pl.B;
       CUDA_TRY(cudaMemcpyAsync(dst, A, fs * nb * sizeof(float), cudaMemcpyDeviceToDevice, P->st));
       CUDA_TRY(cudaMemcpyAsync(dst + fs * c.pl.B, Bf, fs * nb * sizeof(float),
                                cudaMemcpyDeviceToDevice, P->st));
-      if (cm == 3)
-        CUDA_TRY(cudaMemcpyAsync(dst + 2 * fs * c.pl.B, c.W.QF, fs * nb * sizeof(float),
+      for (size_t i = 0; i < c.fstate.size(); ++i)
+        CUDA_TRY(cudaMemcpyAsync(dst + (2 + i) * fs * c.pl.B, c.fstate[i], fs * nb * sizeof(float),
                                  cudaMemcpyDeviceToDevice, P->st));
     }
     p.u = A;
@@ -281,7 +324,8 @@ fwi_status forward_steps(Call& c, int nb, int shot0, const DevTable& src, float*
     p.hist2 = hist2_base ? hist2_base + (size_t)(n - hist_n0) * fs * c.pl.B : nullptr;
     p.step_off = n;
     p.smp_off = (long long)n * c.pl.B * c.geom->nrec;
-    if (ext) FWI_TRY(ext_step(c, p, false));
+    if (pml) FWI_TRY(pml_step(c, p));
+    else if (ext) FWI_TRY(ext_step(c, p, false));
     else FWI_TRY(launch_step(c, p, false));
     std::swap(A, Bf);
   }
@@ -408,6 +452,11 @@ fwi_status begin_call(fwi_plan* P, const fwi_model* model, const fwi_geometry* g
   Carve C(P->arena);
   carve_work(P, c.pl, geom, c.vd, C, c.W);
   if (C.off > P->arena_cap) return fail(FWI_ERR_BUDGET, "workspace carve exceeds allocation");
+  c.fstate.clear();
+  if (c.W.QF) c.fstate.push_back(c.W.QF);
+  if (c.W.PQ) c.fstate.push_back(c.W.PQ);
+  for (float* ph : c.W.PH)
+    if (ph) c.fstate.push_back(ph);
   if (c.pl.tma) {
     const bool three = P->grid.ndim == 3;
     for (float* buf : {c.W.U0, c.W.U1, c.W.F0, c.W.F1}) {
@@ -505,7 +554,8 @@ fwi_status gradient_forward_batch(Call& c, int j, int shot0, int nb, const DevTa
   float* Bf = c.W.U1;
   CUDA_TRY(cudaMemsetAsync(A, 0, fs * nb * sizeof(float), P->st));
   CUDA_TRY(cudaMemsetAsync(Bf, 0, fs * nb * sizeof(float), P->st));
-  if (c.W.QF) CUDA_TRY(cudaMemsetAsync(c.W.QF, 0, fs * nb * sizeof(float), P->st));   // lap u^{-1} = 0
+  for (float* f : c.fstate)   // lap u^{-1} = 0; q^0 = 0, phi^0 = 0
+    CUDA_TRY(cudaMemsetAsync(f, 0, fs * nb * sizeof(float), P->st));
   FWI_TRY(forward_steps(c, nb, shot0, src, A, Bf, 0, nt - 1, K == 0 ? bb.H : nullptr, 0, true,
                         K, bb.CK, K == 0 ? bb.H2 : nullptr));
   FWI_TRY(final_sample(c, nb, A, nt - 1));
@@ -566,12 +616,63 @@ fwi_status gradient_adjoint_batch(Call& c, int j, int shot0, int nb, const DevTa
     const float* ck = bb.CK + cm * (size_t)js * fs * B;
     CUDA_TRY(cudaMemcpyAsync(FA, ck, fs * nb * sizeof(float), cudaMemcpyDeviceToDevice, P->st));
     CUDA_TRY(cudaMemcpyAsync(FB, ck + fs * B, fs * nb * sizeof(float), cudaMemcpyDeviceToDevice, P->st));
-    if (cm == 3)
-      CUDA_TRY(cudaMemcpyAsync(c.W.QF, ck + 2 * fs * B, fs * nb * sizeof(float),
+    for (size_t i = 0; i < c.fstate.size(); ++i)
+      CUDA_TRY(cudaMemcpyAsync(c.fstate[i], ck + (2 + i) * fs * B, fs * nb * sizeof(float),
                                cudaMemcpyDeviceToDevice, P->st));
     return forward_steps(c, nb, shot0, src, FA, FB, seg_lo, seg_hi, bb.H, seg_lo, false, 0, nullptr,
                          bb.H2);
   };
+  if (c.pl.sc.pml) {
+    // PML adjoint (kernels_pml.cu): ubar^{n+1} in XN, ubar^n in XC, c^n, qbar,
+    // the phi adjoints; ubar^{nt-1} = P^T r^{nt-1}, ubar^{nt-2} = P^T r^{nt-2}
+    float* XN = LA;
+    float* XC = LB;
+    for (float* f : {c.W.PC, c.W.PQB, c.W.PHB[0], c.W.PHB[1], c.W.PHB[2]})
+      if (f) CUDA_TRY(cudaMemsetAsync(f, 0, fs * nb * sizeof(float), P->st));
+    const int nd = P->grid.ndim;
+    for (int m = 0; m < 2 && nt - 1 - m >= 0; ++m) {
+      StepParams pi = p;
+      pi.step_off = (long long)(nt - 1 - m) * B * c.geom->nrec;
+      cudaError_t e = launch_inject_buckets(pi, m == 0 ? XN : XC, c.T.tx, c.T.ty, c.T.zc, c.T.gx,
+                                            c.T.gy, P->st);
+      if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
+      c.launches++;
+    }
+    for (int n = nt - 2; n >= 0; --n) {
+      FWI_TRY(ensure_segment(n));
+      const bool prof = P->opt.profile > 0 &&
+                        (c.fwd_launches + c.adj_launches) % P->opt.profile == 0;
+      if (prof) FWI_TRY(record_event(P, 1));
+      StepParams pa = p;
+      pa.up = XN;
+      pa.out = c.W.PC;
+      pa.q = c.W.PQB;
+      for (int d = 0; d < 3; ++d) pa.ph[d] = c.W.PHB[d];
+      pa.hist = hist_at(n);
+      pa.image = 1;
+      pa.step_off = (long long)(n - 1) * B * c.geom->nrec;
+      if (n < 1) pa.inj_off = nullptr;   // no residual before the record
+      cudaError_t e = launch_pml(pa, nd, P->R, c.vd, PML_A, P->st);
+      if (e == cudaSuccess) {
+        StepParams pb = p;
+        pb.x = c.W.PC;
+        pb.up = XC;
+        for (int d = 0; d < 3; ++d) pb.ph[d] = c.W.PHB[d];
+        pb.inj_off = nullptr;
+        e = launch_pml(pb, nd, P->R, c.vd, PML_B, P->st);
+      }
+      if (e != cudaSuccess) return fail(FWI_ERR_CUDA, std::string("PML launch: ") + cudaGetErrorString(e));
+      c.launches += 2;
+      if (prof) {
+        FWI_TRY(record_event(P, 1));
+        c.adj_timed++;
+      }
+      c.adj_launches++;
+      c.adj_points += (int64_t)nb * P->L.nx * P->L.ny * P->L.nz;
+      std::swap(XN, XC);
+    }
+    return FWI_OK;
+  }
   for (int k = nt - 1; k >= 1; --k) {
     p.image = (k <= nt - 2) ? 1 : 0;
     if (p.image) {
@@ -670,7 +771,8 @@ fwi_status fwi_forward(fwi_plan* P, const fwi_model* model, const fwi_geometry* 
     float* Bf = c.W.U1;
     CUDA_TRY(cudaMemsetAsync(A, 0, fs * nb * sizeof(float), P->st));
     CUDA_TRY(cudaMemsetAsync(Bf, 0, fs * nb * sizeof(float), P->st));
-    if (c.W.QF) CUDA_TRY(cudaMemsetAsync(c.W.QF, 0, fs * nb * sizeof(float), P->st));
+    for (float* f : c.fstate)
+      CUDA_TRY(cudaMemsetAsync(f, 0, fs * nb * sizeof(float), P->st));
     FWI_TRY(forward_steps(c, nb, shot0, src, A, Bf, 0, P->nt - 1, nullptr, 0, true, 0, nullptr));
     FWI_TRY(final_sample(c, nb, A, P->nt - 1));
     cudaError_t e = launch_traces_out(c.W.D, traces, B, shot0, nb, geom->nrec, P->nt, P->d_flags, P->st);
@@ -766,8 +868,9 @@ fwi_status fwi_misfit_backward_ex(fwi_plan* P, float* grad_m, float* grad_wavele
   if (!grad_m && !grad_wavelet) return fail(FWI_ERR_INVALID_ARG, "grad_m and grad_wavelet are both NULL");
   SavedGrad* S = P->saved;
   if (!S) return fail(FWI_ERR_INVALID_ARG, "no pending fwi_misfit_forward on this plan");
-  if (grad_wavelet && S->c.pl.sc.t4)
-    return fail(FWI_ERR_UNSUPPORTED, "the wavelet gradient of the fourth-order scheme is not implemented");
+  if (grad_wavelet && (S->c.pl.sc.t4 || S->c.pl.sc.pml))
+    return fail(FWI_ERR_UNSUPPORTED,
+                "the wavelet gradient of the fourth-order scheme and of the PML is not implemented");
   P->saved = nullptr;   // the state is used once
   Call& c = S->c;
   CUDA_TRY(cudaSetDevice(P->device));

@@ -117,6 +117,10 @@ constexpr int EXT_TX2 = 128, EXT_TX = 32, EXT_TY2 = 16, EXT_TY3 = 8, EXT_ZC = 32
 // phi adjoints).
 enum PmlMode { PML_U = 0, PML_PHI = 1, PML_A = 2, PML_B = 3 };
 cudaError_t launch_pml(const StepParams& p, int ndim, int R, bool vd, int mode, cudaStream_t st);
+// field[slot][node] += w vals[vidx + step_off] over the buckets of p.B slots
+// (tile geometry tx x ty x zc, gx x gy tiles per plane chunk)
+cudaError_t launch_inject_buckets(const StepParams& p, float* field, int tx, int ty, int zc, int gx,
+                                  int gy, cudaStream_t st);
 cudaError_t launch_ext(const StepParams& p, int ndim, int R, bool vd, bool adj, int mode,
                        cudaStream_t st);
 // out[i] = q[i+1] - 2 q[i] + q[i-1] along the last axis of rows x nt samples

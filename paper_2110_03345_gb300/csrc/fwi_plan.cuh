@@ -149,12 +149,19 @@ struct DevTable {
 struct Scheme {
   bool t4 = false;   // fourth order in time (options.time_order == 4)
   int att = -1;      // attenuation power y (0 or 2), -1 for none
-  bool ext() const { return t4 || att >= 0; }
+  bool pml = false;  // perfectly matched layer instead of the sponge (options.boundary == 1)
+  int ndim = 2;
+  bool ext() const { return t4 || att >= 0 || pml; }
+  // PML state besides u^n, u^{n-1}: q (3D) and one phi per axis
+  int pml_state() const { return pml ? ndim + (ndim == 3 ? 1 : 0) : 0; }
   int hist_fields() const { return t4 ? 2 : 1; }         // stored per step (F and k w)
-  int ckpt_fields() const { return att == 2 ? 3 : 2; }   // u^n, u^{n-1} (, lap u^{n-1})
-  int fwd_slot_fields() const { return (t4 ? 1 : 0) + (att == 2 ? 1 : 0); }   // k w; lap state
-  int adj_slot_fields() const { return att == 2 ? 1 : 0; }                    // adjoint lap state
-  int model_fields() const { return att >= 0 ? 1 : 0; }                      // attenuation coefficient
+  int ckpt_fields() const {                               // u^n, u^{n-1} and the other state
+    return 2 + (att == 2 ? 1 : 0) + pml_state();
+  }
+  int fwd_slot_fields() const { return (t4 ? 1 : 0) + (att == 2 ? 1 : 0) + pml_state(); }
+  // adjoint: lap state (y = 2); c, qbar (3D) and the phi adjoints (PML)
+  int adj_slot_fields() const { return (att == 2 ? 1 : 0) + (pml ? 1 + pml_state() : 0); }
+  int model_fields() const { return att >= 0 ? 1 : 0; }  // attenuation coefficient
 };
 
 // Workspace plan for one call.
@@ -182,6 +189,9 @@ struct Work {
   // extended schemes: attenuation coefficient, k w scratch, Laplacian states
   // (forward, adjoint), second history field, second time difference of the wavelets
   float *ATT = nullptr, *KW = nullptr, *QF = nullptr, *QA = nullptr, *H2 = nullptr, *D2Q = nullptr;
+  // PML: q and phi (forward), c, qbar and the phi adjoints (adjoint)
+  float *PQ = nullptr, *PC = nullptr, *PQB = nullptr;
+  float *PH[3] = {nullptr, nullptr, nullptr}, *PHB[3] = {nullptr, nullptr, nullptr};
   double* partials = nullptr;
   int npartials = 0;
 };
@@ -206,6 +216,7 @@ struct Call {
     CUtensorMap map;
   };
   std::vector<MapEnt> maps;   // TMA descriptors of the wavefield buffers
+  std::vector<float*> fstate; // forward state besides u^n, u^{n-1} (checkpointed with them)
   int64_t launches = 0;
   int64_t fwd_launches = 0, adj_launches = 0;
   int64_t fwd_points = 0, adj_points = 0;
@@ -299,6 +310,7 @@ fwi_status forward_steps(Call& c, int nb, int shot0, const DevTable& src, float*
                          int n0, int n1, float* hist_base, int hist_n0, bool sample,
                          int K_ckpt, float* CK, float* hist2_base = nullptr);
 fwi_status ext_step(Call& c, const StepParams& p_in, bool adj);
+fwi_status pml_step(Call& c, const StepParams& p_in);
 fwi_status final_sample(Call& c, int nb, const float* A, int n);
 fwi_status prepare_model(Call& c);
 fwi_status begin_call(fwi_plan* P, const fwi_model* model, const fwi_geometry* geom,

@@ -548,3 +548,38 @@ cudaError_t launch_pml(const StepParams& p, int ndim, int R, bool vd, int mode, 
 }
 
 }  // namespace fwi
+
+namespace fwi {
+
+namespace {
+
+// field[slot][node] += w val for every entry of every (slot, tile) bucket, one
+// thread per bucket in its entries' order (no two tiles share a node): the
+// receiver residuals of one step spread onto an adjoint field.
+__global__ void k_inject_buckets(const StepParams p, float* __restrict__ field, int tx, int ty,
+                                 int zc, int gx, int gy, int nbuckets) {
+  const int bk = blockIdx.x * blockDim.x + threadIdx.x;
+  if (bk >= nbuckets) return;
+  const int slot = bk / p.ntiles, t = bk - slot * p.ntiles;
+  const int bx = t % gx, by = (t / gx) % gy, bz = t / (gx * gy);
+  float* f = field + (long long)slot * p.fstride;
+  for (int e = p.inj_off[bk]; e < p.inj_off[bk + 1]; ++e) {
+    const int loc = p.inj_loc[e];
+    const int lx = loc % tx, ly = (loc / tx) % ty, lz = loc / (tx * ty);
+    const long long idx = (long long)(bz * zc + lz + p.oz) * p.sxy +
+                          (long long)(by * ty + ly + p.oy) * p.sx + (bx * tx + lx + p.ox);
+    f[idx] += p.inj_w[e] * p.vals[p.inj_vidx[e] + p.step_off];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_inject_buckets(const StepParams& p, float* field, int tx, int ty, int zc, int gx,
+                                  int gy, cudaStream_t st) {
+  const int n = p.B * p.ntiles;
+  if (n <= 0 || !p.inj_off) return cudaSuccess;
+  k_inject_buckets<<<(n + 127) / 128, 128, 0, st>>>(p, field, tx, ty, zc, gx, gy, n);
+  return cudaGetLastError();
+}
+
+}  // namespace fwi

@@ -322,6 +322,10 @@ fwi_status resolve_scheme(const fwi_plan* P, const fwi_model* m, Scheme* sc) {
   if (to != 0 && to != 2 && to != 4)
     return fail(FWI_ERR_INVALID_ARG, "time_order must be 0, 2 or 4");
   sc->t4 = to == 4;
+  sc->ndim = P->grid.ndim;
+  if (P->opt.boundary != 0 && P->opt.boundary != 1)
+    return fail(FWI_ERR_INVALID_ARG, "boundary must be 0 (sponge) or 1 (PML)");
+  sc->pml = P->opt.boundary == 1;
   if (m && m->alpha0) {
     if (m->att_power != 0 && m->att_power != 2)
       return fail(FWI_ERR_INVALID_ARG, "att_power must be 0 or 2");
@@ -329,6 +333,8 @@ fwi_status resolve_scheme(const fwi_plan* P, const fwi_model* m, Scheme* sc) {
   }
   if (sc->t4 && sc->att >= 0)
     return fail(FWI_ERR_UNSUPPORTED, "attenuation with the fourth-order time scheme is not implemented");
+  if (sc->pml && (sc->t4 || sc->att >= 0))
+    return fail(FWI_ERR_UNSUPPORTED, "the PML runs with the second-order scheme without attenuation");
   if (sc->t4 && P->opt.interp != FWI_INTERP_LINEAR)
     return fail(FWI_ERR_UNSUPPORTED, "sinc points with the fourth-order time scheme are not implemented");
   return FWI_OK;
@@ -428,11 +434,20 @@ void carve_work(fwi_plan* P, const Plan& pl, const fwi_geometry* g, bool vd, Car
   W.U1 = C.take<float>(fs * B);
   if (sc.t4) W.KW = C.take<float>(fs * B);
   if (sc.att == 2) W.QF = C.take<float>(fs * B);
+  if (sc.pml) {
+    if (P->grid.ndim == 3) W.PQ = C.take<float>(fs * B);
+    for (int d = 0; d < P->grid.ndim; ++d) W.PH[d] = C.take<float>(fs * B);
+  }
   const size_t nbk = pl.split ? (size_t)pl.nbatches : 1;   // batches whose state is kept
   W.D = C.take<float>((size_t)P->nt * B * g->nrec * nbk);
   if (pl.gradient) {
     W.G = C.take<float>(fs * B);
     if (sc.att == 2) W.QA = C.take<float>(fs * B);
+    if (sc.pml) {
+      W.PC = C.take<float>(fs * B);
+      if (P->grid.ndim == 3) W.PQB = C.take<float>(fs * B);
+      for (int d = 0; d < P->grid.ndim; ++d) W.PHB[d] = C.take<float>(fs * B);
+    }
     if (pl.K == 0) {
       W.H = C.take<float>(fs * B * (size_t)std::max(P->nt - 1, 1) * nbk);
       if (sc.t4) W.H2 = C.take<float>(fs * B * (size_t)std::max(P->nt - 1, 1) * nbk);
@@ -526,6 +541,8 @@ fwi_status fwi_plan_set_options(fwi_plan* plan, const fwi_options* opt) {
     return fail(FWI_ERR_INVALID_ARG, "time_order must be 0, 2 or 4");
   if (opt->interp != FWI_INTERP_LINEAR && opt->interp != FWI_INTERP_SINC)
     return fail(FWI_ERR_INVALID_ARG, "interp must be FWI_INTERP_LINEAR or FWI_INTERP_SINC");
+  if (opt->boundary != 0 && opt->boundary != 1)
+    return fail(FWI_ERR_INVALID_ARG, "boundary must be 0 (sponge) or 1 (PML)");
   plan->opt = *opt;
   return FWI_OK;
 }
