@@ -67,7 +67,43 @@ def parse():
     ap.add_argument("--nreq", type=int, default=0, help="serving: requests (default 650)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="invert: the experiment in scaled units (grid / scale)")
+    ap.add_argument("--scheme", default="", choices=sorted(SCHEMES),
+                    help="breast2d / skull3d in an extended scheme (default: leapfrog, sponge, "
+                         "bilinear points)")
     return ap.parse_args()
+
+
+# Extended schemes of the solver for the breast2d / skull3d lines (--scheme):
+# the plan options and the attenuation (alpha0, y) they set.
+SCHEMES = {
+    "": "leapfrog (CFL 0.4), sponge, bilinear points",
+    "t4": "fourth order in time at CFL 0.8 in 2D / 0.66 in 3D (the same record in fewer steps)",
+    "att0": "power-law attenuation y = 0, alpha0 = 5.8 Np/m (0.5 dB/cm of soft tissue at 1 MHz)",
+    "att2": "power-law attenuation y = 2, alpha0 = 5.8 Np/m at 1 MHz",
+    "sinc": "Kaiser-windowed sinc sources and receivers",
+    "pml": "perfectly matched layer over the 20-point absorbing layer",
+}
+
+
+def scheme_setup(scheme):
+    """(plan options, (alpha0, y) or None) of an extended scheme."""
+    opts = {"t4": {"time_order": 4}, "sinc": {"interp": 1}, "pml": {"boundary": 1}}.get(scheme, {})
+    att = {"att0": (5.8, 0), "att2": (5.8 / (2 * np.pi * 1e6) ** 2, 2)}.get(scheme)
+    return opts, att
+
+
+def t4_time_axis(p):
+    """The fourth-order scheme's larger step on the same record: CFL 0.8 in 2D
+    (2x the leapfrog's 0.4), 0.66 in 3D (the paper's 3D constant), the
+    wavelet resampled."""
+    from paper_2110_03345_gb300 import inputs
+    f = 2.0 if p.ndim == 2 else 0.66 / 0.4
+    T = (p.nt - 1) * p.dt
+    p.dt = p.dt * f
+    p.nt = int(T / p.dt) + 1
+    w = inputs.ricker(500e3, p.dt, p.nt)
+    p.wavelet = np.broadcast_to(w, (p.nshots,) + p.wavelet.shape[1:2] + (p.nt,)).copy()
+    return p
 
 
 def make_problem(args, rank=0, world=1):
@@ -101,6 +137,8 @@ def make_problem(args, rank=0, world=1):
     if args.shots:
         p.src_xyz = p.src_xyz[:args.shots]
         p.wavelet = p.wavelet[:args.shots]
+    if getattr(args, "scheme", "") == "t4" and args.workload in ("breast2d", "skull3d"):
+        p = t4_time_axis(p)
     return p
 
 
@@ -476,24 +514,31 @@ def serving_stream(nreq=650, warm=50, seed=5, lanes=4, rate=20.0, **kw):
 
 # ---------------------------------------------------------------- GPU arm
 
-def roofline(acc, steps, ms, vd, ndim, tile):
+def roofline(acc, steps, ms, vd, ndim, tile, scheme=""):
     """Roofline record of the dominant stencil kernel from the plan's counters
     summed over the timed steps (CUDA events around every PROFILE_EVERY-th
-    launch on the plan's stream)."""
+    launch on the plan's stream; an extended scheme's step of two passes is
+    timed as one launch)."""
     per_launch = {k: acc[f"{k}_ms"] / max(acc[f"{k}_timed"], 1) for k in ("fwd", "adj")}
     kind = "adj" if per_launch["adj"] * acc["adj_launches"] >= per_launch["fwd"] * acc["fwd_launches"] \
         else "fwd"
     n_l = max(acc[f"{kind}_launches"], 1)
     t_launch = per_launch[kind] * 1e-3
     pts_launch = acc[f"{kind}_points"] / n_l
-    bpu = BYTES_PER_UPDATE[(kind, vd)]
+    ext = scheme in ("t4", "att0", "att2", "pml")
+    if ext:
+        bpu = SCHEME_BYTES[(scheme, kind)] + (4 if vd else 0)   # + ln rho
+        kname = "%s %s step (%s)" % ("k_pml%dd" % ndim if scheme == "pml" else "k_ext%dd" % ndim,
+                                     "adjoint+imaging" if kind == "adj" else "forward+store", scheme)
+    else:
+        bpu = BYTES_PER_UPDATE[(kind, vd)]
+        kname = "%s %s" % (kernel_name(ndim, tile), "adjoint+imaging" if kind == "adj" else "forward+store")
     achieved = bpu * pts_launch / t_launch / 1e9
     peak, peak_src = measured_hbm_peak()
-    tr = traffic_record(f"{ndim}d-{kind}", tile)
+    tr = traffic_record(f"{ndim}d-{kind}" + (f"-{scheme}" if scheme else ""), tile)
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": (tr["dram_bytes_per_point"] * pts_launch) if tr else None,
-            "kernel": ("%s %s" % (kernel_name(ndim, tile),
-                                  "adjoint+imaging" if kind == "adj" else "forward+store")),
+            "kernel": kname,
             "bytes_per_update": bpu, "points_per_launch": int(pts_launch),
             "launch_ms": t_launch * 1e3, "peak_source": peak_src,
             "timed_launches": int(acc[f"{kind}_timed"]),
@@ -507,7 +552,10 @@ def roofline(acc, steps, ms, vd, ndim, tile):
 # lambda^{k-1}, g written); attenuation adds its coefficient (y = 0) or the
 # coefficient and the Laplacian state read and written (y = 2).
 SCHEME_BYTES = {("t4", "fwd"): 24, ("t4", "adj"): 32, ("att0", "fwd"): 24, ("att0", "adj"): 32,
-                ("att2", "fwd"): 32, ("att2", "adj"): 40}
+                ("att2", "fwd"): 32, ("att2", "adj"): 40,
+                # the PML step is the leapfrog's away from the layer (its fields
+                # are touched in the layer only, a small fraction of the grid)
+                ("pml", "fwd"): 20, ("pml", "adj"): 28}
 
 
 def scheme_sample(kind, shots=30, steps=1, warmup=1):
@@ -518,7 +566,8 @@ def scheme_sample(kind, shots=30, steps=1, warmup=1):
     (time-to-solution of the same record); "att0" / "att2" the attenuation
     term of Eq. 10 with alpha0 of soft tissue (0.5 dB/cm at 1 MHz: 5.8 Np/m
     for y = 0, 5.8 Np/m / (2 pi 1e6)^2 for y = 2); "sinc" Kaiser-windowed sinc
-    points.  Gradient Gpts/s (useful updates: 2 x points x steps x shots) and
+    points; "pml" the perfectly matched layer.  Gradient Gpts/s (useful
+    updates: 2 x points x steps x shots) and
     the roofline of the dominant kernel, inputs resident."""
     import torch
     from paper_2110_03345_gb300 import binding, inputs
@@ -562,22 +611,7 @@ def scheme_sample(kind, shots=30, steps=1, warmup=1):
 
     def with_roof(r, key):
         acc, ms = r.pop("acc"), r.pop("ms")
-        if key is None:
-            r["roofline"] = roofline(acc, steps, ms, True, 2, 6)
-            return r
-        per = {k: acc[f"{k}_ms"] / max(acc[f"{k}_timed"], 1) for k in ("fwd", "adj")}
-        kk = "adj" if per["adj"] * acc["adj_launches"] >= per["fwd"] * acc["fwd_launches"] else "fwd"
-        n_l = max(acc[f"{kk}_launches"], 1)
-        pts = acc[f"{kk}_points"] / n_l
-        bpu = SCHEME_BYTES[(key, kk)] + 4          # + ln rho (variable density)
-        ach = bpu * pts / (per[kk] * 1e-3) / 1e9
-        peak, src = measured_hbm_peak()
-        r["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                         "frac": ach / peak, "traffic": None, "peak_source": src,
-                         "kernel": "k_ext2d %s step (%s)" % ("adjoint+imaging" if kk == "adj"
-                                                             else "forward+store", key),
-                         "bytes_per_update": bpu, "points_per_launch": int(pts),
-                         "launch_ms": per[kk], "timed_launches": int(acc[f"{kk}_timed"])}
+        r["roofline"] = roofline(acc, steps, ms, True, 2, 6, key or "")
         return r
 
     out = {"workload": f"breast2d 1024^2, {p.nshots} of the 128 shots, vd, o8, 100 us record",
@@ -587,13 +621,12 @@ def scheme_sample(kind, shots=30, steps=1, warmup=1):
         t4 = with_roof(run((p.nt - 1) // 2 + 1, 2 * p.dt, {"time_order": 4}), "t4")
         out.update({"leapfrog_cfl_0.4": lf, "time4_cfl_0.8": t4,
                     "time_to_solution_speedup": lf["s_per_gradient"] / t4["s_per_gradient"]})
-    elif kind in ("att0", "att2"):
-        y = 0 if kind == "att0" else 2
-        alpha = 5.8 if y == 0 else 5.8 / (2 * np.pi * 1e6) ** 2
-        out.update(with_roof(run(p.nt, p.dt, {}, alpha=alpha, y=y), kind))
-        out["alpha0"] = alpha
     else:
-        out.update(with_roof(run(p.nt, p.dt, {"interp": 1}), None))
+        opts, att = scheme_setup(kind)
+        alpha, y = att if att else (None, 0)
+        out.update(with_roof(run(p.nt, p.dt, opts, alpha=alpha, y=y), kind if kind != "sinc" else None))
+        if att:
+            out["alpha0"] = alpha
     return out
 
 
@@ -674,6 +707,11 @@ def run_mine(args):
     stream = torch.cuda.current_stream()
     plan = binding.Plan(p.shape, p.spacing, p.nt, p.dt, order=p.order, sponge=p.nb, c_ref=p.c_ref,
                         stream=stream)
+    sopts, satt = scheme_setup(args.scheme)
+    if satt is not None:
+        alpha0 = torch.full(p.shape, satt[0], device=dev, dtype=torch.float32)
+        plan.set_attenuation(alpha0, satt[1])
+    plan.set_options(**sopts)
     # observed data: the same solver on the perturbed model (bench input only)
     obs = plan.forward(torch.from_numpy(f32(p.vp_true)).to(dev), rho, geo, wav)
     obs_h = obs.cpu().pin_memory()
@@ -681,10 +719,10 @@ def run_mine(args):
     # CUDA events around every PROFILE_EVERY-th stencil launch (the events
     # stay in the timed region; sampling keeps their cost small)
     plan.set_options(batch=args.batch, tile=args.tile, ckpt_every=args.ckpt, profile=PROFILE_EVERY,
-                     shots_per_cta=args.spc)
+                     shots_per_cta=args.spc, **sopts)
     plan.gradient(vp, rho, geo, wav, obs, grad=grad)      # first warm-up: sets the batch size
     tuned = None
-    if not args.tile and not args.spc:
+    if not args.tile and not args.spc and not args.scheme:
         # kernel variant and shots per CTA from the autotuner at the real batch size
         from paper_2110_03345_gb300 import autotune
         b_real = plan.stats()["batch"]
@@ -724,7 +762,7 @@ def run_mine(args):
 
     upd = useful_updates(p)
     value = world * upd / (ms * 1e-3) / 1e9
-    roof = roofline(acc, args.steps, ms, vd, p.ndim, stats["tile"])
+    roof = roofline(acc, args.steps, ms, vd, p.ndim, stats["tile"], args.scheme)
 
     e2e = None
     if not args.no_e2e:
@@ -759,9 +797,9 @@ def run_mine(args):
     if rank == 0 and world == 1 and not args.no_extras:
         # reduced samples of the uneven-batch and serving patterns (full size:
         # --workload uneven / serving)
-        if args.workload == "breast2d":
+        if args.workload == "breast2d" and not args.scheme:
             extras["skull3d"] = skull3d_sample()
-            extras["schemes"] = {k: scheme_sample(k) for k in ("t4", "att0", "att2", "sinc")}
+            extras["schemes"] = {k: scheme_sample(k) for k in ("t4", "att0", "att2", "sinc", "pml")}
         extras["batched"] = uneven_batch(nprob=16, seed=4, reps=1)
         extras["serving"] = serving_stream(nreq=80, warm=10, seed=5)
         try:                               # the full Sec. 3.2 loop: ~3 s on one GB300
@@ -775,7 +813,8 @@ def run_mine(args):
             "value": value, "unit": "Gpts/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload], "grid": list(p.shape),
+            "config": {"workload": WORKLOADS[args.workload], "scheme": SCHEMES[args.scheme],
+                       "dt_ns": p.dt * 1e9, "grid": list(p.shape),
                        "shots": p.nshots, "nt": p.nt, "receivers": int(p.rec_xyz.shape[0]),
                        "order": p.order, "variable_density": vd,
                        "batch": stats["batch"], "ckpt_every": stats["ckpt_every"], "tile": stats["tile"],
