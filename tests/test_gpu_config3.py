@@ -103,6 +103,40 @@ def test_config3_small_fd_and_oracle():
     assert floor < 1e-1
     check_fd(fd, gref)
     check_fd(fd, gv)
+    check_fd_per_voxel(fd, gref)
+
+
+def check_fd_per_voxel(fd, g, rel=1e-2, floor=0.1):
+    """Each voxel whose gradient is at least `floor` of the largest among the
+    8 within `rel` of its own value (the rounding noise of a misfit difference
+    is absolute, so voxels with a much smaller gradient are held to the
+    absolute bound of check_fd only)."""
+    big = np.abs(g) >= floor * np.abs(g).max()
+    assert big.sum() >= 2
+    assert np.all(np.abs(fd[big] - g[big]) <= rel * np.abs(g[big]))
+
+
+def test_config3_fullsize_fd_four_shots():
+    """The 256^3 skull at full size (0.25 mm, 10th order, variable density,
+    512 receivers, 2000 steps, K = 64 checkpoints through the autograd
+    Function) with 4 of its 32 shots spread over the sphere: central
+    differences (4-point, h = 0.1 m_i, misfit in FP64) at the 8 soft-tissue
+    voxels against the autograd gradient, per voxel within 1e-2 of its own
+    value where the gradient is within 10x of the largest."""
+    p = inputs.config_skull_3d(shots=[0, 128, 256, 384])
+    K = math.ceil(math.sqrt(2 * p.nt))
+    plan = gpu_plan(p, ckpt_every=K)
+    geo = binding.Geometry(p.src_xyz, p.rec_xyz)
+    rho, wav = to_dev(p.rho), to_dev(p.wavelet)
+    obs = plan.forward(to_dev(p.vp_true), rho, geo, wav)
+    vox = soft_tissue_voxels(p)
+    J, g, fd = fd_check(p, plan, obs, vox, rho, geo, wav, rel_h=1e-1, points=4)
+    gv = np.array([g[v] for v in vox])
+    err = np.abs(fd - gv) / np.abs(gv)
+    print("256^3, 4 shots: FD vs autograd per voxel", np.round(err, 5), "gradients", gv)
+    assert plan.stats()["ckpt_every"] == K
+    check_fd(fd, gv)
+    check_fd_per_voxel(fd, gv)
 
 
 @pytest.mark.skipif(os.environ.get("FWI_FULL_CONFIG3") != "1",
@@ -123,3 +157,4 @@ def test_config3_fullsize_fd():
           np.linalg.norm(fd - gv) / np.linalg.norm(gv))
     assert plan.stats()["ckpt_every"] == K
     check_fd(fd, gv)
+    check_fd_per_voxel(fd, gv)
