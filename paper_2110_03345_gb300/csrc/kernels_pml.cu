@@ -75,7 +75,7 @@ struct Pml2 {
 };
 
 template <int R, bool VD, int MODE>
-__global__ void __launch_bounds__(EXT_TX2 / 4 * EXT_TY2) k_pml2d(const StepParams p) {
+__global__ void __launch_bounds__(EXT_TX2 / 4 * EXT_TY2, 2) k_pml2d(const StepParams p) {
   using G = Pml2<R>;
   constexpr int TX = G::TX, TY = G::TY, NL = G::NL, SW = G::SW, SH = G::SH, QW = G::QW;
   constexpr int XH = G::XH;
@@ -96,6 +96,10 @@ __global__ void __launch_bounds__(EXT_TX2 / 4 * EXT_TY2) k_pml2d(const StepParam
   if (MODE == PML_PHI) {   // phi changes only inside the layer
     if (!(x0 < p.nb || x0 + TX > p.nx - p.nb || y0 < p.nb || y0 + TY > p.ny - p.nb)) return;
   }
+  // phi (phibar) matter only in the layer and are read within R of it: tiles
+  // farther away skip them (phi is 0 there; phibar is never read there)
+  const int reach = p.nb + R;
+  const bool near = x0 < reach || x0 + TX > p.nx - reach || y0 < reach || y0 + TY > p.ny - reach;
   if (MODE == PML_U) {
     const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     pml_sample(p, blk * NT + tid);
@@ -110,7 +114,8 @@ __global__ void __launch_bounds__(EXT_TX2 / 4 * EXT_TY2) k_pml2d(const StepParam
       s_x[i] = (MODE == PML_B) ? mul4(ldg4(p.kf + o), xv) : xv;
     }
   }
-  if (CROSS) {
+  const bool cross = CROSS && (near || MODE == PML_B);
+  if (cross) {
     for (int i = tid; i < TY * SW; i += NT) {
       const int r = i / SW, c = i - r * SW;
       const long long o = base + (long long)(r + R) * p.sx + 4 * c;
@@ -196,7 +201,7 @@ __global__ void __launch_bounds__(EXT_TX2 / 4 * EXT_TY2) k_pml2d(const StepParam
   // D1x of the row tile and D1y of the column tile: phi (PML_U), b phibar
   // (PML_A), b k c (PML_B, variable density)
   float dr[4] = {0.f, 0.f, 0.f, 0.f};
-  if (CROSS) {
+  if (cross) {
     float w[NV];
 #pragma unroll
     for (int q = 0; q <= 2 * NL; ++q) unpack(s_r[ly * SW + tx + q], w + 4 * q);
@@ -281,25 +286,31 @@ __global__ void __launch_bounds__(EXT_TX2 / 4 * EXT_TY2) k_pml2d(const StepParam
     st4(p.up + fo + pi, pack(un));
     st4(p.g + fo + pi, pack(g));
   } else {   // PML_B
-    float c[4], xc[4], fx[4], fy[4];
+    float c[4], xc[4];
     unpack(ld4(p.x + fo + pi), c);
     unpack(ld4(p.up + fo + pi), xc);
-    unpack(ld4(p.ph[0] + fo + pi), fx);
-    unpack(ld4(p.ph[1] + fo + pi), fy);
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
       const float e = 4.f * Ax[l] * Ay;
       const float LT = acc[l] + (VD ? dr[l] : 0.f);
       const float nxc = xc[l] + ((2.f - e) * c[l] + LT);
-      const float nfx = pml_p(Ax[l]) * fx[l] - d1x[l];
-      const float nfy = pml_p(Ay) * fy[l] - d1y[l];
       xc[l] = in[l] ? nxc : 0.f;
-      fx[l] = in[l] ? nfx : 0.f;
-      fy[l] = in[l] ? nfy : 0.f;
     }
     st4(p.up + fo + pi, pack(xc));
-    st4(p.ph[0] + fo + pi, pack(fx));
-    st4(p.ph[1] + fo + pi, pack(fy));
+    if (near) {
+      float fx[4], fy[4];
+      unpack(ld4(p.ph[0] + fo + pi), fx);
+      unpack(ld4(p.ph[1] + fo + pi), fy);
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const float nfx = pml_p(Ax[l]) * fx[l] - d1x[l];
+        const float nfy = pml_p(Ay) * fy[l] - d1y[l];
+        fx[l] = in[l] ? nfx : 0.f;
+        fy[l] = in[l] ? nfy : 0.f;
+      }
+      st4(p.ph[0] + fo + pi, pack(fx));
+      st4(p.ph[1] + fo + pi, pack(fy));
+    }
   }
 }
 
@@ -334,6 +345,10 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_pml3d(const StepParams p) 
           z0 < p.nb || z1 > p.nz - p.nb))
       return;
   }
+  const int reach = p.nb + R;
+  const bool near = x0 < reach || x0 + TX > p.nx - reach || y0 < reach || y0 + TY > p.ny - reach ||
+                    z0 < reach || z1 > p.nz - reach;
+  const bool cross = CROSS && (near || MODE == PML_B);
   if (MODE == PML_U) {
     const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     pml_sample(p, blk * NT + tid);
@@ -354,9 +369,9 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_pml3d(const StepParams p) 
     const float Az = sp_at(p.spz, zz, p.nz);
     v1 = v2 = v3 = 0.f;
     if (FULL) v1 = (MODE == PML_B) ? __ldg(p.kf + o) * X[o] : X[o];
-    if (MODE == PML_U) v2 = p.ph[2][fo + o];
+    if (MODE == PML_U && near) v2 = p.ph[2][fo + o];
     if (MODE == PML_PHI) v2 = p.q[fo + o];
-    if (MODE == PML_A) {
+    if (MODE == PML_A && near) {
       const float f = p.ph[2][fo + o];
       v2 = pml_b(Az, Ax, Ay) * f;
       v3 = pml_g(Az, Ax, Ay, p.dt) * f;
@@ -380,7 +395,7 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_pml3d(const StepParams p) 
         if (QQ) s_q[r][c] = p.q[fo + o];
       }
     }
-    if (CROSS) {
+    if (cross) {
       for (int i = tid; i < TY * SW; i += NT) {
         const int r = i / SW, c = i - r * SW;
         const long long o = pb + (long long)(r + R) * p.sx + c;
@@ -432,7 +447,7 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_pml3d(const StepParams p) 
     if (MODE == PML_U && VD)
       acc -= __ldg(p.bx + idx) * d1x + __ldg(p.by + idx) * d1y + __ldg(p.bz + idx) * d1z;
     float dr = 0.f, dr2 = 0.f;   // D1 of the cross tiles and queues
-    if (CROSS) {
+    if (cross) {
 #pragma unroll
       for (int j = 1; j <= R; ++j) {
         dr = fmaf(p.wx.w1[j], s_r[ty][cx + j] - s_r[ty][cx - j], dr);
@@ -493,12 +508,14 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_pml3d(const StepParams p) 
         const float c = X[idx];
         const float LT = acc + (VD ? dr : 0.f);
         p.up[fo + idx] = p.up[fo + idx] + ((2.f - e) * c + LT);
-        float* fx = p.ph[0] + fo + idx;
-        float* fy = p.ph[1] + fo + idx;
-        float* fz = p.ph[2] + fo + idx;
-        *fx = pml_p(Ax) * *fx - d1x;
-        *fy = pml_p(Ay) * *fy - d1y;
-        *fz = pml_p(Az) * *fz - d1z;
+        if (near) {
+          float* fx = p.ph[0] + fo + idx;
+          float* fy = p.ph[1] + fo + idx;
+          float* fz = p.ph[2] + fo + idx;
+          *fx = pml_p(Ax) * *fx - d1x;
+          *fy = pml_p(Ay) * *fy - d1y;
+          *fz = pml_p(Az) * *fz - d1z;
+        }
       }
     }
 #pragma unroll
