@@ -53,7 +53,7 @@ fwi_status make_tensor_map(const fwi_plan* P, const float* base, int nslots, int
 // 48-float-wide (80 for the two-point kernels) x-y tile (16-byte aligned
 // start) with its y halo, one plane.
 fwi_status make_tensor_map_3d(const fwi_plan* P, const float* base, int nslots, int shape,
-                              bool x2, CUtensorMap* out) {
+                              bool x2, CUtensorMap* out, int box_w, int box_h) {
   auto enc = tensor_map_encoder();
   if (!enc) return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
   const cuuint64_t dims[4] = {(cuuint64_t)P->L.sx, (cuuint64_t)P->L.rows, (cuuint64_t)P->L.planes,
@@ -61,7 +61,9 @@ fwi_status make_tensor_map_3d(const fwi_plan* P, const float* base, int nslots, 
   const cuuint64_t strides[3] = {(cuuint64_t)P->L.sx * sizeof(float),
                                  (cuuint64_t)P->L.sxy * sizeof(float),
                                  (cuuint64_t)P->L.fstride * sizeof(float)};
-  const cuuint32_t box[4] = {x2 ? 80u : 48u, (cuuint32_t)tma_box3d_rows(P->R, shape), 1u, 1u};
+  const cuuint32_t box[4] = {box_w > 0 ? (cuuint32_t)box_w : (x2 ? 80u : 48u),
+                             box_h > 0 ? (cuuint32_t)box_h : (cuuint32_t)tma_box3d_rows(P->R, shape),
+                             1u, 1u};
   const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
   const CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims,
                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -467,9 +469,15 @@ fwi_status begin_call(fwi_plan* P, const fwi_model* model, const fwi_geometry* g
       c.maps.push_back(m);
     }
     if (three && c.vd) {
-      for (float* buf : {c.W.bx, c.W.by}) {
-        Call::MapEnt m{buf, {}};
-        FWI_TRY(make_tensor_map_3d(P, buf, 1, c.pl.shape, c.pl.x2, &m.map));
+      // the two-point kernels stage b_x on the tile rows (80 x BY) and b_y on
+      // the tile columns (64 x BY + 2R); the one-point kernels whole planes
+      const int by = tile3_variant(c.pl.shape).by;
+      const int bw[2] = {c.pl.x2 ? 80 : 0, c.pl.x2 ? 64 : 0};
+      const int bh[2] = {c.pl.x2 ? by : 0, c.pl.x2 ? by + 2 * P->R : 0};
+      const float* bufs[2] = {c.W.bx, c.W.by};
+      for (int i = 0; i < 2; ++i) {
+        Call::MapEnt m{bufs[i], {}};
+        FWI_TRY(make_tensor_map_3d(P, bufs[i], 1, c.pl.shape, c.pl.x2, &m.map, bw[i], bh[i]));
         c.maps.push_back(m);
       }
     }

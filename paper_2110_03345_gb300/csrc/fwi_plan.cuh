@@ -299,8 +299,9 @@ fwi_status check_on_device(const void* ptr, const char* name, int dev);
 // ---- drivers.cu: launches, forward and adjoint sweeps, call set-up
 fwi_status make_tensor_map(const fwi_plan* P, const float* base, int nslots, int shape,
                            CUtensorMap* out);
+// box_w / box_h > 0 override the box's x extent and rows
 fwi_status make_tensor_map_3d(const fwi_plan* P, const float* base, int nslots, int shape,
-                              bool x2, CUtensorMap* out);
+                              bool x2, CUtensorMap* out, int box_w = 0, int box_h = 0);
 fwi_status record_event(fwi_plan* P, int kind);
 StepParams base_params(Call& c);
 long long launch_threads(const Call& c, int B);

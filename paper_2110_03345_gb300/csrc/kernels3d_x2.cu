@@ -16,7 +16,8 @@
 //  * the x-y planes (80 floats wide: x0-8 .. x0+71, 16-byte aligned) arrive by
 //    4D TMA copies into a ring of R+1+PF planes (the centre, the R planes up
 //    to the lead, PF planes in flight); the variable-density adjoint streams
-//    b_x, b_y planes through a second, four-stage ring (two trips).
+//    b_x on the tile rows and b_y on the tile columns through a second,
+//    four-stage ring (two trips), small enough for three CTAs per SM.
 // Every mbarrier wait is bounded: on time-out the error flag is set and the
 // kernel carries on, so no thread skips a barrier.
 #include "fwi_internal.cuh"
@@ -37,25 +38,33 @@ __device__ __forceinline__ float2 lds2(const float* p) {
   return *reinterpret_cast<const float2*>(p);
 }
 
-template <int R, int BY>
+template <int R, int BY, bool PSI = false>
 struct GeoX2 {
   static constexpr int TXP = 64;            // x points of a CTA row (32 threads x 2)
   static constexpr int BXW = 80;            // floats per staged row: x0-8 .. x0+71
   static constexpr int XOFF = 8;            // column of x0 in a staged row
   static constexpr int BYH = BY + 2 * R;    // staged rows: y0-R .. y0+BY+R-1
   static constexpr int PLANE = BYH * BXW;   // floats per staged plane (a multiple of 32)
-  static constexpr int PF = 3;              // planes in flight ahead of the lead
+  // planes in flight ahead of the lead (the variable-density adjoint keeps
+  // two, so that with its b stages three CTAs fit an SM's shared memory)
+  static constexpr int PF = PSI ? 2 : 3;
   static constexpr int NSU = R + 1 + PF;    // ring depth
   static constexpr int M = (R + 1) / 2;     // x pairs on each side of the own pair
   static constexpr uint32_t PLANE_BYTES = PLANE * 4;
+  // variable-density adjoint: a b stage holds b_x on the tile rows (80 x BY,
+  // x0-8 .. x0+71) and b_y on the tile columns (64 x BYH, x0 .. x0+63)
+  static constexpr int BXB = BXW * BY;
+  static constexpr int BYB = TXP * BYH;
+  static constexpr int BSTAGE = BXB + BYB;
+  static constexpr uint32_t BSTAGE_BYTES = BSTAGE * 4;
 };
 
 template <int R, bool VD, bool ADJ, int BY>
-__global__ void __launch_bounds__(32 * BY, ((VD && ADJ) ? 512 : 768) / (32 * BY))
+__global__ void __launch_bounds__(32 * BY, 768 / (32 * BY))
 k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
             const __grid_constant__ CUtensorMap bxmap, const __grid_constant__ CUtensorMap bymap) {
   pdl_trigger();
-  using G = GeoX2<R, BY>;
+  using G = GeoX2<R, BY, VD && ADJ>;
   constexpr int TY = BY;
   constexpr int NT = 32 * BY;
   constexpr int Q = 2 * R + 1;
@@ -66,7 +75,7 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
   extern __shared__ __align__(128) float smem3x[];
   float* ring = smem3x;                       // [NSU][BYH][BXW]
   constexpr int NBS = 4;                      // b stages: two loop trips of two planes
-  float* bring = ring + NSU * G::PLANE;       // PSI: [NBS stages][b_x, b_y][BYH][BXW]
+  float* bring = ring + NSU * G::PLANE;       // PSI: [NBS stages][b_x [BY][BXW], b_y [BYH][TXP]]
   __shared__ uint64_t bar[NSU];
   __shared__ uint64_t bbar[NBS];
   __shared__ int s_pe[MAX_ZCHUNK + 1];        // first source entry of each plane of the chunk
@@ -138,9 +147,10 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
     }
     if (PSI) {
       for (int i = 0; i < NBS && i < nz_c; ++i) {
-        mbar_arrive_expect_tx(&bbar[i], 2 * G::PLANE_BYTES);
-        tma_load_4d(bring + (2 * i) * G::PLANE, &bxmap, &bbar[i], tmx, tmy, z0 + i + p.oz, 0);
-        tma_load_4d(bring + (2 * i + 1) * G::PLANE, &bymap, &bbar[i], tmx, tmy, z0 + i + p.oz, 0);
+        float* st = bring + i * G::BSTAGE;
+        mbar_arrive_expect_tx(&bbar[i], G::BSTAGE_BYTES);
+        tma_load_4d(st, &bxmap, &bbar[i], tmx, y0 + p.oy, z0 + i + p.oz, 0);
+        tma_load_4d(st + G::BXB, &bymap, &bbar[i], x0 + p.ox, tmy, z0 + i + p.oz, 0);
       }
     }
   }
@@ -230,8 +240,8 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
         q[s + 2 * R] = lds2(ring + sl * G::PLANE + own);
         if (PSI) qz[s + 2 * R] = __fmul2_rn(cur.bzl, q[s + 2 * R]);
         const float* cp = ring + ((i + R) % NSU) * G::PLANE;   // centre plane z
-        const float* bxp = bring + (2 * (i % NBS)) * G::PLANE;
-        const float* byp = bxp + G::PLANE;
+        const float* bxp = bring + (i % NBS) * G::BSTAGE;   // b_x rows of the tile
+        const float* byp = bxp + G::BXB;                    // b_y columns with the y halo
         if (PSI && !mbar_wait_bounded(&bbar[i % NBS], (uint32_t)((i / NBS) & 1))) timed_out = true;
 
         // x pairs of the centre row: columns c0 - 2M .. c0 + 2M + 1
@@ -288,7 +298,7 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
           float2 PX[2 * M + 1];
 #pragma unroll
           for (int k = 0; k <= 2 * M; ++k)
-            PX[k] = __fmul2_rn(lds2(bxp + (ty + R) * BXW + c0 - 2 * M + 2 * k), X[k]);
+            PX[k] = __fmul2_rn(lds2(bxp + ty * BXW + c0 - 2 * M + 2 * k), X[k]);
           auto px = [&](int d) {
             const int e = d + 2 * M;
             return (e & 1) ? PX[e >> 1].y : PX[e >> 1].x;
@@ -299,8 +309,8 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
             const float2 pp = make_float2(px(j), px(j + 1));
             const float2 pm = make_float2(px(-j), px(1 - j));
             sx = __ffma2_rn(bc2(w1c<R>(j)), __fadd2_rn(pp, neg2(pm)), sx);
-            const float2 yb = __fmul2_rn(lds2(byp + (ty + R + j) * BXW + c0), Yp[j]);
-            const float2 ya = __fmul2_rn(lds2(byp + (ty + R - j) * BXW + c0), Ym[j]);
+            const float2 yb = __fmul2_rn(lds2(byp + (ty + R + j) * G::TXP + c0 - G::XOFF), Yp[j]);
+            const float2 ya = __fmul2_rn(lds2(byp + (ty + R - j) * G::TXP + c0 - G::XOFF), Ym[j]);
             sy = __ffma2_rn(bc2(w1c<R>(j)), __fadd2_rn(yb, neg2(ya)), sy);
             sz = __ffma2_rn(bc2(w1c<R>(j)),
                             __fadd2_rn(qz[s + R + j], neg2(qz[s + R - j])), sz);
@@ -362,10 +372,11 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
           if (PSI && i + NBS < nz_c) {
             const int st = i % NBS;
             const int zb = z0 + i + NBS + p.oz;
+            float* sb = bring + st * G::BSTAGE;
             fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&bbar[st], 2 * G::PLANE_BYTES);
-            tma_load_4d(bring + (2 * st) * G::PLANE, &bxmap, &bbar[st], tmx, tmy, zb, 0);
-            tma_load_4d(bring + (2 * st + 1) * G::PLANE, &bymap, &bbar[st], tmx, tmy, zb, 0);
+            mbar_arrive_expect_tx(&bbar[st], G::BSTAGE_BYTES);
+            tma_load_4d(sb, &bxmap, &bbar[st], tmx, y0 + p.oy, zb, 0);
+            tma_load_4d(sb + G::BXB, &bymap, &bbar[st], x0 + p.ox, tmy, zb, 0);
           }
         }
       }
@@ -381,9 +392,9 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
 
 template <int R, bool VD, bool ADJ, int BY>
 constexpr size_t smem_bytes_x2() {
-  using G = GeoX2<R, BY>;
+  using G = GeoX2<R, BY, VD && ADJ>;
   size_t n = (size_t)G::NSU * G::PLANE;
-  if (VD && ADJ) n += 2 * 4 * (size_t)G::PLANE;   // NBS = 4 stages of b_x, b_y
+  if (VD && ADJ) n += 4 * (size_t)G::BSTAGE;   // NBS = 4 stages of b_x, b_y
   return n * sizeof(float);
 }
 
