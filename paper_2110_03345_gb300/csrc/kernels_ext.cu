@@ -175,23 +175,6 @@ __global__ void __launch_bounds__(EXT_TX2 / 4 * EXT_TY2) k_ext2d(const StepParam
     const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     ext_sample(p, blk * NT + tid);
   }
-  // the epilogue's pointwise operands are issued first: their latency
-  // overlaps the staging of the tile
-  const int ly = ty, yg = y0 + ly, srow = ly + R;
-  const int xg = x0 + 4 * tx;
-  const long long pi = (long long)(yg + p.oy) * p.sx + (xg + p.ox);
-  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  const float4 k4 = ldg4(p.kf + pi);
-  const float4 uo4 = (MODE != EXT_KW) ? ld4(p.up + fo + pi) : z4;
-  const float4 uc4 = (MODE == EXT_T4) ? ld4(p.u + fo + pi) : z4;
-  const float4 at4 = (MODE == EXT_ATT0 || MODE == EXT_ATT2) ? ldg4(p.att + pi) : z4;
-  const float4 q4 = (MODE == EXT_ATT2) ? ld4(p.q + fo + pi) : z4;
-  const bool img = ADJ && MODE != EXT_KW && p.image;
-  const float4 h4 = img ? __ldcs(reinterpret_cast<const float4*>(p.hist + fo + pi)) : z4;
-  const float4 h24 = (img && MODE == EXT_T4) ? __ldcs(reinterpret_cast<const float4*>(p.hist2 + fo + pi)) : z4;
-  const float4 g4 = img ? ld4(p.g + fo + pi) : z4;
-  const float4 bx4 = (VD && !ADJ) ? ldg4(p.bx + pi) : z4;
-  const float4 by4 = (VD && !ADJ) ? ldg4(p.by + pi) : z4;
   const long long base = (long long)(y0 + p.oy - R) * p.sx + (x0 + p.ox - G::XH);
   for (int i = tid; i < SH * SW; i += NT) {
     const int r = i / SW, c = i - r * SW;
@@ -215,6 +198,8 @@ __global__ void __launch_bounds__(EXT_TX2 / 4 * EXT_TY2) k_ext2d(const StepParam
   }
   __syncthreads();
 
+  const int ly = ty, yg = y0 + ly, srow = ly + R;
+  const int xg = x0 + 4 * tx;
   float v[NV];
 #pragma unroll
   for (int q = 0; q <= 2 * NL; ++q) unpack(s_x[srow * SW + tx + q], v + 4 * q);
@@ -248,10 +233,11 @@ __global__ void __launch_bounds__(EXT_TX2 / 4 * EXT_TY2) k_ext2d(const StepParam
   float lap[4];
 #pragma unroll
   for (int ix = 0; ix < 4; ++ix) lap[ix] = acc[ix];
+  const long long pi = (long long)(yg + p.oy) * p.sx + (xg + p.ox);
   if (VD && !ADJ) {   // L_rho u = lap u - b . grad u
     float bxv[4], byv[4];
-    unpack(bx4, bxv);
-    unpack(by4, byv);
+    unpack(ldg4(p.bx + pi), bxv);
+    unpack(ldg4(p.by + pi), byv);
 #pragma unroll
     for (int ix = 0; ix < 4; ++ix) {
       const int c = 4 * NL + ix;
@@ -326,7 +312,7 @@ __global__ void __launch_bounds__(EXT_TX2 / 4 * EXT_TY2) k_ext2d(const StepParam
 #pragma unroll
   for (int ix = 0; ix < 4; ++ix) in[ix] = (yg < p.ny) && (xg + ix < p.nx);
   float k[4], a0[4];
-  unpack(k4, k);
+  unpack(ldg4(p.kf + pi), k);
   {
     float ax[4];
     unpack(ldg4(p.spx + xg), ax);
@@ -343,10 +329,10 @@ __global__ void __launch_bounds__(EXT_TX2 / 4 * EXT_TY2) k_ext2d(const StepParam
     return;
   }
   float uo[4], r[4];
-  unpack(uo4, uo);
+  unpack(ld4(upp), uo);
   if (MODE == EXT_T4) {
     float uc[4], F[4];
-    unpack(uc4, uc);
+    unpack(ld4(p.u + fo + pi), uc);
 #pragma unroll
     for (int ix = 0; ix < 4; ++ix) {
       F[ix] = cen[ix] + __fdiv_rn(k[ix] * acc[ix], 12.f);
@@ -364,11 +350,11 @@ __global__ void __launch_bounds__(EXT_TX2 / 4 * EXT_TY2) k_ext2d(const StepParam
         __stcs(reinterpret_cast<float4*>(p.hist + fo + pi), pack(f));
         __stcs(reinterpret_cast<float4*>(p.hist2 + fo + pi), pack(w));
       }
-    } else if (img) {
+    } else if (p.image) {
       float h[4], h2[4], g[4];
-      unpack(h4, h);
-      unpack(h24, h2);
-      unpack(g4, g);
+      unpack(__ldcs(reinterpret_cast<const float4*>(p.hist + fo + pi)), h);
+      unpack(__ldcs(reinterpret_cast<const float4*>(p.hist2 + fo + pi)), h2);
+      unpack(ld4(p.g + fo + pi), g);
 #pragma unroll
       for (int ix = 0; ix < 4; ++ix)
         if (in[ix]) g[ix] = g[ix] - (uc[ix] * h[ix] + __fdiv_rn(cen[ix] * h2[ix], 12.f));
@@ -377,7 +363,7 @@ __global__ void __launch_bounds__(EXT_TX2 / 4 * EXT_TY2) k_ext2d(const StepParam
     return;
   }
   float at[4], hh[4];
-  unpack(at4, at);
+  unpack(ldg4(p.att + pi), at);
   if (MODE == EXT_ATT0) {
 #pragma unroll
     for (int ix = 0; ix < 4; ++ix) {
@@ -389,7 +375,7 @@ __global__ void __launch_bounds__(EXT_TX2 / 4 * EXT_TY2) k_ext2d(const StepParam
     }
   } else {   // EXT_ATT2
     float qv[4], qn[4];
-    unpack(q4, qv);
+    unpack(ld4(p.q + fo + pi), qv);
 #pragma unroll
     for (int ix = 0; ix < 4; ++ix) {
       float E, extra = 0.f;
@@ -413,10 +399,10 @@ __global__ void __launch_bounds__(EXT_TX2 / 4 * EXT_TY2) k_ext2d(const StepParam
   st4(upp, pack(r));
   if (!ADJ) {
     if (p.hist) __stcs(reinterpret_cast<float4*>(p.hist + fo + pi), pack(hh));
-  } else if (img) {
+  } else if (p.image) {
     float h[4], g[4];
-    unpack(h4, h);
-    unpack(g4, g);
+    unpack(__ldcs(reinterpret_cast<const float4*>(p.hist + fo + pi)), h);
+    unpack(ld4(p.g + fo + pi), g);
 #pragma unroll
     for (int ix = 0; ix < 4; ++ix)
       if (in[ix]) g[ix] = fmaf(-cen[ix], h[ix], g[ix]);
