@@ -17,7 +17,7 @@
 //    4D TMA copies into a ring of R+1+PF planes (the centre, the R planes up
 //    to the lead, PF planes in flight); the variable-density adjoint streams
 //    b_x on the tile rows and b_y on the tile columns through a second,
-//    four-stage ring (two trips), small enough for three CTAs per SM.
+//    four-stage ring (two trips).
 // Every mbarrier wait is bounded: on time-out the error flag is set and the
 // kernel carries on, so no thread skips a barrier.
 #include "fwi_internal.cuh"
@@ -46,7 +46,7 @@ struct GeoX2 {
   static constexpr int BYH = BY + 2 * R;    // staged rows: y0-R .. y0+BY+R-1
   static constexpr int PLANE = BYH * BXW;   // floats per staged plane (a multiple of 32)
   // planes in flight ahead of the lead (the variable-density adjoint keeps
-  // two, so that with its b stages three CTAs fit an SM's shared memory)
+  // two: with its b stages the ring then takes 73 KB of shared memory)
   static constexpr int PF = PSI ? 2 : 3;
   static constexpr int NSU = R + 1 + PF;    // ring depth
   static constexpr int M = (R + 1) / 2;     // x pairs on each side of the own pair
@@ -60,7 +60,7 @@ struct GeoX2 {
 };
 
 template <int R, bool VD, bool ADJ, int BY>
-__global__ void __launch_bounds__(32 * BY, 768 / (32 * BY))
+__global__ void __launch_bounds__(32 * BY, ((VD && ADJ) ? 512 : 768) / (32 * BY))
 k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
             const __grid_constant__ CUtensorMap bxmap, const __grid_constant__ CUtensorMap bymap) {
   pdl_trigger();
