@@ -528,8 +528,11 @@ def roofline(acc, steps, ms, vd, ndim, tile, scheme=""):
     ext = scheme in ("t4", "att0", "att2", "pml")
     if ext:
         bpu = SCHEME_BYTES[(scheme, kind)] + (4 if vd else 0)   # + ln rho
-        kname = "%s %s step (%s)" % ("k_pml%dd" % ndim if scheme == "pml" else "k_ext%dd" % ndim,
-                                     "adjoint+imaging" if kind == "adj" else "forward+store", scheme)
+        # 2D sponge-boundary schemes run on the TMA shot-loop kernels
+        kern = ("k_pml%dd" % ndim if scheme == "pml" else
+                "k_step2d_tma_ext" if ndim == 2 else "k_ext3d")
+        kname = "%s %s step (%s)" % (kern, "adjoint+imaging" if kind == "adj" else "forward+store",
+                                     scheme)
     else:
         bpu = BYTES_PER_UPDATE[(kind, vd)]
         kname = "%s %s" % (kernel_name(ndim, tile), "adjoint+imaging" if kind == "adj" else "forward+store")

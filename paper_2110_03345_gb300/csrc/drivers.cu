@@ -129,7 +129,7 @@ StepParams base_params(Call& c) {
 }
 
 long long launch_threads(const Call& c, int B) {
-  if (c.pl.sc.ext())
+  if (c.pl.sc.ext() && !c.pl.tma)
     return (long long)c.T.ntiles() * B * (c.P->grid.ndim == 3 ? EXT_TX * EXT_TY3 : EXT_TX2 / 4 * EXT_TY2);
   const int by = (c.P->grid.ndim == 3) ? tile3_variant(c.pl.shape).by
                  : c.pl.tma ? tile2_tma_variant(c.pl.shape).by : tile2_variant(c.pl.shape).by;
@@ -191,6 +191,18 @@ fwi_status launch_step(Call& c, const StepParams& p_in, bool adj) {
 // update from k w; the adjoint's k L^T lambda, then the update with the
 // receiver residuals weighted 12 inside the 1/12 bracket), or the single
 // pass of the attenuating leapfrog.
+// One pass of an extended scheme: the TMA shot-loop kernels (2D, sponge
+// boundary; the tensor map of the stencil input p.x) or kernels_ext.cu.
+cudaError_t ext_pass(const Call& c, const StepParams& p, bool adj, int mode) {
+  const fwi_plan* P = c.P;
+  if (c.pl.tma) {
+    const CUtensorMap* map = find_map(c, p.x);
+    if (!map) return cudaErrorInvalidValue;
+    return launch_step2d_tma_ext(p, *map, P->R, c.vd, adj, mode, P->st);
+  }
+  return launch_ext(p, P->grid.ndim, P->R, c.vd, adj, mode, P->st);
+}
+
 fwi_status ext_step(Call& c, const StepParams& p_in, bool adj) {
   fwi_plan* P = c.P;
   StepParams p = p_in;
@@ -204,7 +216,7 @@ fwi_status ext_step(Call& c, const StepParams& p_in, bool adj) {
   const bool prof = P->opt.profile > 0 &&
                     (c.fwd_launches + c.adj_launches) % P->opt.profile == 0;
   p.flags = P->d_flags + 1;
-  p.S = 1;
+  p.S = c.pl.tma ? c.pl.S : 1;
   p.att = c.W.ATT;
   p.q = adj ? c.W.QA : c.W.QF;
   if (p.inj_scale == 0.f) p.inj_scale = 1.f;
@@ -218,19 +230,19 @@ fwi_status ext_step(Call& c, const StepParams& p_in, bool adj) {
     a.hist2 = nullptr;
     a.image = 0;
     if (adj) a.inj_off = nullptr;   // the residuals enter the second pass only
-    e = launch_ext(a, nd, P->R, c.vd, adj, EXT_KW, P->st);
+    e = ext_pass(c, a, adj, EXT_KW);
     if (e == cudaSuccess) {
       StepParams b = p;   // pass 2 / B: the update from k w (k L^T lambda)
       b.x = c.W.KW;
       b.nrec = 0;
       if (!adj) b.vals = c.W.D2Q;   // s^{n+1} - 2 s^n + s^{n-1}
       else b.inj_scale = 12.f;      // 12 P^T r inside the 1/12 bracket
-      e = launch_ext(b, nd, P->R, c.vd, adj, EXT_T4, P->st);
+      e = ext_pass(c, b, adj, EXT_T4);
     }
     c.launches += 2;
   } else {
     p.x = p.u;
-    e = launch_ext(p, nd, P->R, c.vd, adj, c.pl.sc.att == 0 ? EXT_ATT0 : EXT_ATT2, P->st);
+    e = ext_pass(c, p, adj, c.pl.sc.att == 0 ? EXT_ATT0 : EXT_ATT2);
     c.launches++;
   }
   if (e != cudaSuccess) return fail(FWI_ERR_CUDA, std::string("stencil launch: ") + cudaGetErrorString(e));
@@ -461,7 +473,7 @@ fwi_status begin_call(fwi_plan* P, const fwi_model* model, const fwi_geometry* g
     if (ph) c.fstate.push_back(ph);
   if (c.pl.tma) {
     const bool three = P->grid.ndim == 3;
-    for (float* buf : {c.W.U0, c.W.U1, c.W.F0, c.W.F1}) {
+    for (float* buf : {c.W.U0, c.W.U1, c.W.F0, c.W.F1, c.W.KW}) {
       if (!buf) continue;
       Call::MapEnt m{buf, {}};
       if (three) FWI_TRY(make_tensor_map_3d(P, buf, c.pl.B, c.pl.shape, c.pl.x2, &m.map));
@@ -723,7 +735,7 @@ fwi_status gradient_adjoint_batch(Call& c, int j, int shot0, int nb, const DevTa
       a.flags = P->d_flags + 1;
       e = launch_ext(a, P->grid.ndim, P->R, c.vd, true, EXT_KW, P->st);
       if (e == cudaSuccess)
-        e = launch_image_t4(P->L, LA, c.W.KW, hist_at(0), hist2_at(0), c.W.G, nb, P->st);
+        e = launch_image_t4(P->L, LA, c.W.KW, hist_at(0), hist2_at(0), c.W.G, nb, c.pl.S, P->st);
       c.launches += 2;
     } else {
       e = launch_image_only(P->L, LA, hist_at(0), c.W.G, nb, c.pl.S, P->st);

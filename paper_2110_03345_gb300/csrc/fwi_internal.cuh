@@ -127,9 +127,10 @@ cudaError_t launch_ext(const StepParams& p, int ndim, int R, bool vd, bool adj, 
 // (q = 0 outside the record): the source's second time difference
 cudaError_t launch_second_difference(const float* q, float* out, long long rows, int nt,
                                      cudaStream_t st);
-// g[b] -= lam[b] F[b] + ky[b] kw[b] / 12 for the nb slots of a batch
+// g[b / S] -= lam[b] F[b] + ky[b] kw[b] / 12 for the nb slots of a batch
+// (S shots share a gradient slot)
 cudaError_t launch_image_t4(const Layout& L, const float* lam, const float* ky, const float* F,
-                            const float* kw, float* g, int nb, cudaStream_t st);
+                            const float* kw, float* g, int nb, int S, cudaStream_t st);
 // attenuation coefficient field from vp (param 0) or m (param 1) and alpha0:
 // y = 0: alpha0 vp dt; y = 2: 2 alpha0 vp / dt (zero in the padding);
 // stats[0] |= bits of its maximum, stats[1] += count of bad alpha0 values
@@ -208,6 +209,11 @@ cudaError_t launch_step2d_multi(const MultiDesc* descs, const MultiUnit* units, 
 cudaError_t launch_step2d_tma(const StepParams& p, const CUtensorMap& map, int R, bool vd, bool adj,
                               int tile, cudaStream_t st);
 void tma_box2d(int R, int tile, int* bx, int* by);
+// The extended schemes' 2D kernels on the same pipeline (kernels2d_tma_ext.cu):
+// mode = EXT_KW / EXT_T4 / EXT_ATT0 / EXT_ATT2, map = the tensor map of the
+// stencil input p.x for tile shape 1 (128 x 16), p.S shots per CTA.
+cudaError_t launch_step2d_tma_ext(const StepParams& p, const CUtensorMap& map, int R, bool vd,
+                                  bool adj, int mode, cudaStream_t st);
 size_t step3d_smem(int R, bool vd, bool adj, int tile);
 // TMA-staged 3D kernels (kernels3d_tma.cu): um maps the wavefield buffer p.u
 // as (x, y, z, slot); bxm / bym map the b_x / b_y fields (variable-density

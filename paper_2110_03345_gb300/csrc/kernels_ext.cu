@@ -23,9 +23,10 @@
 //  In every mode the adjoint's imaging term is g -= lambda^k * hist^k (plus the
 //  kw term above), so the gradient with respect to m = 1/vp^2 is g / dt^2.
 //
-// Organisation.  2D: a CTA of 32 x 16 threads stages a 128 x 16 tile plus
-// halo in shared memory with 16-byte loads, each thread updating a float4 of
-// x points.  3D: one grid point per thread, a CTA of 32 x 8 threads
+// Organisation.  2D (the steps themselves run on the TMA shot-loop kernels of
+// kernels2d_tma_ext.cu; this one serves the adjoint's last k L^T lambda^0
+// pass): a CTA of 32 x 16 threads stages a 128 x 16 tile plus halo in shared
+// memory with 16-byte loads, each thread updating a float4 of x points.  3D: one grid point per thread, a CTA of 32 x 8 threads
 // streams a column along z over a chunk of planes with the column's 2R+1
 // values in a register queue and the x-y plane (with halo) staged in shared
 // memory.  Sources and receiver residuals come from the per-tile bucket
@@ -650,12 +651,14 @@ namespace {
 // fourth-order imaging term of lambda^0, which no adjoint step follows).
 __global__ void k_image_t4(const float* __restrict__ lam, const float* __restrict__ ky,
                            const float* __restrict__ F, const float* __restrict__ kw,
-                           float* __restrict__ g, long long fs, int nb) {
+                           float* __restrict__ g, long long fs, int nb, int S) {
+  // slot b images into gradient slot b / S (S shots per CTA in the step kernels)
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < fs;
        i += (long long)gridDim.x * blockDim.x) {
     for (int b = 0; b < nb; ++b) {
       const long long o = (long long)b * fs + i;
-      g[o] = g[o] - (lam[o] * F[o] + __fdiv_rn(ky[o] * kw[o], 12.f));
+      const long long og = (long long)(b / S) * fs + i;
+      g[og] = g[og] - (lam[o] * F[o] + __fdiv_rn(ky[o] * kw[o], 12.f));
     }
   }
 }
@@ -663,11 +666,11 @@ __global__ void k_image_t4(const float* __restrict__ lam, const float* __restric
 }  // namespace
 
 cudaError_t launch_image_t4(const Layout& L, const float* lam, const float* ky, const float* F,
-                            const float* kw, float* g, int nb, cudaStream_t st) {
+                            const float* kw, float* g, int nb, int S, cudaStream_t st) {
   const long long fs = L.fstride;
   long long blocks = (fs + 255) / 256;
   if (blocks > 152LL * 16) blocks = 152LL * 16;
-  k_image_t4<<<(int)blocks, 256, 0, st>>>(lam, ky, F, kw, g, fs, nb);
+  k_image_t4<<<(int)blocks, 256, 0, st>>>(lam, ky, F, kw, g, fs, nb, S);
   return cudaGetLastError();
 }
 

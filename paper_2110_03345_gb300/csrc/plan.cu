@@ -377,15 +377,19 @@ fwi_status choose_plan(const fwi_plan* P, const fwi_geometry* g, bool vd, bool g
   if (!resolve_tile(P, P->opt.tile, &out.tile, &out.shape, &out.tma, &out.x2))
     return fail(FWI_ERR_INVALID_ARG, "tile variant out of range");
   out.sc = sc;
-  if (sc.ext()) {   // the extended schemes have one kernel family (one shot per CTA)
-    out.tile = 0;
-    out.shape = 0;
-    out.tma = false;
+  if (sc.ext()) {
+    // the extended schemes have one tile shape: in 2D (sponge boundary) the
+    // TMA shot-loop kernels of 128 x 16 tiles (variant 6), otherwise one
+    // shot per CTA (kernels_ext.cu, kernels_pml.cu)
+    const bool tma2 = P->grid.ndim == 2 && !sc.pml;
+    out.tile = tma2 ? 6 : 0;
+    out.shape = tma2 ? 1 : 0;
+    out.tma = tma2;
     out.x2 = false;
   }
   // slots x z chunks go on grid.z, which CUDA limits to 65535 blocks
   B = std::min(B, std::max(1, 65535 / std::max(1, tile_geo(P, out.shape, out.tma, out.x2,
-                                                           sc.ext()).nzc)));
+                                                           sc.ext() && !out.tma).nzc)));
   // equal batches: the same number of batches, none left nearly empty
   // (16 shots at 15 per batch run as 8 + 8, not 15 + 1)
   B = (ns + (ns + B - 1) / B - 1) / ((ns + B - 1) / B);

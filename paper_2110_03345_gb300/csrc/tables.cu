@@ -275,7 +275,7 @@ fwi_status prepare_common(Call& c, Carve& tabC) {
   const fwi_geometry* g = c.geom;
   const int nd = P->grid.ndim;
   c.ncorner = interp_nodes(P->opt.interp, nd);
-  c.T = tile_geo(P, c.pl.shape, c.pl.tma, c.pl.x2, c.pl.sc.ext());
+  c.T = tile_geo(P, c.pl.shape, c.pl.tma, c.pl.x2, c.pl.sc.ext() && !c.pl.tma);
   // receiver sampling table
   std::vector<int> node((size_t)g->nrec * c.ncorner);
   std::vector<float> w((size_t)g->nrec * c.ncorner);
@@ -308,7 +308,7 @@ fwi_status prepare_common(Call& c, Carve& tabC) {
 }
 
 size_t tables_bound(const fwi_plan* P, const fwi_geometry* g, const Plan& pl) {
-  const TileGeo T = tile_geo(P, pl.shape, pl.tma, pl.x2, pl.sc.ext());
+  const TileGeo T = tile_geo(P, pl.shape, pl.tma, pl.x2, pl.sc.ext() && !pl.tma);
   const int nc = interp_nodes(P->opt.interp, P->grid.ndim);
   const size_t nb = (size_t)pl.B * T.ntiles() + 1;
   const size_t src = (size_t)pl.B * g->nsrc * nc;
