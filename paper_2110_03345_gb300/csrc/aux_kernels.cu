@@ -93,16 +93,7 @@ __global__ void k_density_grad(Layout L, const float* __restrict__ lnr, AxisW wx
 }
 
 __global__ void k_sample(StepParams p) {
-  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (gid < (long long)p.B * p.nrec) {
-    const int bb = (int)(gid / p.nrec);
-    const int r = (int)(gid - (long long)bb * p.nrec);
-    const float* ub = p.u + (long long)bb * p.fstride;
-    float acc = 0.f;
-    for (int c = 0; c < p.ncorner; ++c)
-      acc = fmaf(p.smp_w[r * p.ncorner + c], ub[p.smp_node[r * p.ncorner + c]], acc);
-    p.smp_out[p.smp_off + (long long)bb * p.nrec + r] = acc;
-  }
+  sample_receivers(p, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
 
 __global__ void k_sample_slots(const float* __restrict__ u, long long fstride,
@@ -250,7 +241,7 @@ cudaError_t launch_density_grad(const Layout& L, const float* lnr, const AxisW& 
 }
 
 cudaError_t launch_sample(const StepParams& p, cudaStream_t st) {
-  const long long n = (long long)p.B * p.nrec;
+  const long long n = (long long)p.B * p.nrec * (p.smp_group > 1 ? p.smp_group : 1);
   if (n == 0) return cudaSuccess;
   k_sample<<<(int)((n + 255) / 256), 256, 0, st>>>(p);
   return cudaGetLastError();

@@ -116,6 +116,7 @@ StepParams base_params(Call& c) {
   }
   p.ntiles = c.T.ntiles();
   p.ncorner = c.ncorner;
+  p.smp_group = sample_group(c.ncorner);
   p.dt = (float)P->dt;
   p.nb = P->grid.sponge;
   if (P->grid.ndim == 3) {
@@ -146,7 +147,7 @@ const CUtensorMap* find_map(const Call& c, const float* base) {
 fwi_status launch_step(Call& c, const StepParams& p_in, bool adj) {
   fwi_plan* P = c.P;
   StepParams p = p_in;
-  if (!adj && p.nrec > 0 && (long long)p.B * p.nrec > launch_threads(c, p.B)) {
+  if (!adj && p.nrec > 0 && (long long)p.B * p.nrec * p.smp_group > launch_threads(c, p.B)) {
     // too few threads in the stencil launch to sample every receiver: do it apart
     cudaError_t e = launch_sample(p, P->st);
     if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
@@ -207,7 +208,7 @@ fwi_status ext_step(Call& c, const StepParams& p_in, bool adj) {
   fwi_plan* P = c.P;
   StepParams p = p_in;
   const int nd = P->grid.ndim;
-  if (!adj && p.nrec > 0 && (long long)p.B * p.nrec > launch_threads(c, p.B)) {
+  if (!adj && p.nrec > 0 && (long long)p.B * p.nrec * p.smp_group > launch_threads(c, p.B)) {
     cudaError_t e = launch_sample(p, P->st);
     if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
     c.launches++;
@@ -264,7 +265,7 @@ fwi_status pml_step(Call& c, const StepParams& p_in) {
   fwi_plan* P = c.P;
   StepParams p = p_in;
   const int nd = P->grid.ndim;
-  if (p.nrec > 0 && (long long)p.B * p.nrec > launch_threads(c, p.B)) {
+  if (p.nrec > 0 && (long long)p.B * p.nrec * p.smp_group > launch_threads(c, p.B)) {
     cudaError_t e = launch_sample(p, P->st);
     if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
     c.launches++;

@@ -80,13 +80,14 @@ struct StepParams {
   long long smp_off;
   int nrec;
   int ncorner;
+  int smp_group;         // lanes per (slot, receiver) sample: 1, or 32 for sinc points
   int B;                 // shot slots in this launch
   int image;             // adjoint: accumulate g -= lambda^k h^k
   int zchunk;            // 3D: planes per CTA
   int nzc;               // 3D: z chunks
   int S;                 // shots per CTA (TMA kernels); gradient slot of shot s is s / S
   int* flags;            // device error flags (bit 1: a bounded wait timed out)
-  // extended schemes (kernels_ext.cu only): stencil input, per-point
+  // extended schemes (kernels_ext.cu, kernels2d_tma_ext.cu): stencil input, per-point
   // attenuation coefficient, Laplacian state and a second history field
   const float* x;        // field whose stencil is taken (u^n, k w^n, lambda^k or k y^k)
   float* out;            // pass 1 / A of the fourth-order scheme: k (L x + s)
@@ -100,6 +101,37 @@ struct StepParams {
   float dt;
   int nb;
 };
+
+// Lanes per receiver sample: the 64- / 512-node sinc points split their
+// nodes over a warp (one thread each would serialise 64-512 gathers in the
+// few threads that sample and hold up their CTAs), the 4 / 8 corners of the
+// linear points take one thread.
+inline int sample_group(int ncorner) { return ncorner > 8 ? 32 : 1; }
+
+#ifdef __CUDACC__
+// Receiver sampling d = P u^n by a launch's first threads: thread gid serves
+// the sample (slot, receiver) = gid / G with the nodes c = gid % G + k G,
+// and a group of G > 1 lanes (a whole warp, gid aligned to it) sums its
+// partial sums by shuffles in a fixed order.  Every thread of a warp calls it.
+__device__ __forceinline__ void sample_receivers(const StepParams& p, long long gid) {
+  const int G = p.smp_group > 1 ? p.smp_group : 1;
+  if (p.nrec <= 0 || gid >= (long long)p.B * p.nrec * G) return;
+  const long long pt = gid / G;
+  const int lane = (int)(gid - pt * G);
+  const int bb = (int)(pt / p.nrec);
+  const int r = (int)(pt - (long long)bb * p.nrec);
+  const float* ub = p.u + (long long)bb * p.fstride;
+  const int* nd = p.smp_node + (long long)r * p.ncorner;
+  const float* w = p.smp_w + (long long)r * p.ncorner;
+  float acc = 0.f;
+  for (int c = lane; c < p.ncorner; c += G) acc = fmaf(w[c], ub[nd[c]], acc);
+  if (G > 1) {
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane != 0) return;
+  }
+  p.smp_out[p.smp_off + pt] = acc;
+}
+#endif
 
 // Extended schemes (kernels_ext.cu): shared-memory staged tiles of 128 x 16
 // points, a float4 per thread (2D), or 32 x 8 columns streamed along z, one

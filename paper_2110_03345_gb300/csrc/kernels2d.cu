@@ -45,18 +45,6 @@ __device__ __forceinline__ void unpack(const float4& t, float* v) {
   v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
 }
 
-// Receiver sampling d = P u (one thread per slot x receiver).
-__device__ __forceinline__ void sample_prologue(const StepParams& p, long long gid) {
-  if (gid < (long long)p.B * p.nrec) {
-    const int bb = (int)(gid / p.nrec);
-    const int r = (int)(gid - (long long)bb * p.nrec);
-    const float* ub = p.u + (long long)bb * p.fstride;
-    float acc = 0.f;
-    for (int c = 0; c < p.ncorner; ++c)
-      acc = fmaf(p.smp_w[r * p.ncorner + c], ub[p.smp_node[r * p.ncorner + c]], acc);
-    p.smp_out[p.smp_off + (long long)bb * p.nrec + r] = acc;
-  }
-}
 
 // One tile (bxi, byi) of shot slot b: the body shared by the single-problem
 // kernel (indices from the launch grid) and the multi-problem kernel (indices
@@ -85,7 +73,7 @@ __device__ __forceinline__ void step2d_tile(const StepParams& p, int bxi, int by
   const long long fo = (long long)b * p.fstride;
   const float* __restrict__ u = p.u + fo;
 
-  if (!ADJ && p.nrec > 0) sample_prologue(p, samp_rank * NT + tid);
+  if (!ADJ && p.nrec > 0) sample_receivers(p, samp_rank * NT + tid);
 
   // Stage the tile and its halo.
   const long long base = (long long)(y0 + p.oy - R) * p.sx + (x0 + p.ox - XH);

@@ -44,15 +44,7 @@ k_step3d(const StepParams p) {
   if (!ADJ && p.nrec > 0) {
     const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     const long long gid = blk * NT + tid;
-    if (gid < (long long)p.B * p.nrec) {
-      const int bb = (int)(gid / p.nrec);
-      const int r = (int)(gid - (long long)bb * p.nrec);
-      const float* ub = p.u + (long long)bb * p.fstride;
-      float acc = 0.f;
-      for (int c = 0; c < p.ncorner; ++c)
-        acc = fmaf(p.smp_w[r * p.ncorner + c], ub[p.smp_node[r * p.ncorner + c]], acc);
-      p.smp_out[p.smp_off + (long long)bb * p.nrec + r] = acc;
-    }
+    sample_receivers(p, gid);
   }
 
   // Register queues: q[j] = u at plane z - R + j of this thread's column.

@@ -125,18 +125,10 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
   }
   pdl_wait();   // the previous step's wavefields are complete from here on
   if (!ADJ && p.nrec > 0) {
-    // receiver sampling of u^n (not written during this step), one thread per slot x receiver
+    // receiver sampling of u^n (not written during this step), a thread or a warp per slot x receiver
     const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     const long long gid = blk * NT + tid;
-    if (gid < (long long)p.B * p.nrec) {
-      const int bb = (int)(gid / p.nrec);
-      const int r = (int)(gid - (long long)bb * p.nrec);
-      const float* ub = p.u + (long long)bb * p.fstride;
-      float acc = 0.f;
-      for (int c = 0; c < p.ncorner; ++c)
-        acc = fmaf(p.smp_w[r * p.ncorner + c], ub[p.smp_node[r * p.ncorner + c]], acc);
-      p.smp_out[p.smp_off + (long long)bb * p.nrec + r] = acc;
-    }
+    sample_receivers(p, gid);
   }
   if (nz_c <= 0) return;
   __syncthreads();

@@ -38,17 +38,8 @@ namespace fwi {
 
 namespace {
 
-__device__ __forceinline__ void ext_sample(const StepParams& p, long long gid) {
-  if (p.nrec > 0 && gid < (long long)p.B * p.nrec) {
-    const int bb = (int)(gid / p.nrec);
-    const int r = (int)(gid - (long long)bb * p.nrec);
-    const float* ub = p.u + (long long)bb * p.fstride;
-    float acc = 0.f;
-    for (int c = 0; c < p.ncorner; ++c)
-      acc = fmaf(p.smp_w[r * p.ncorner + c], ub[p.smp_node[r * p.ncorner + c]], acc);
-    p.smp_out[p.smp_off + (long long)bb * p.nrec + r] = acc;
-  }
-}
+
+constexpr float INV12 = 1.f / 12.f;   // the 1/12 of the fourth-order terms, rounded once
 
 __device__ __forceinline__ float ext_inject(const StepParams& p, int tile, int loc, float acc) {
   if (p.inj_off) {
@@ -70,7 +61,7 @@ __device__ __forceinline__ void ext_update(const StepParams& p, long long fo, lo
   if (MODE == EXT_KW) {
     p.out[fo + pi] = k * acc;
   } else if (MODE == EXT_T4) {
-    const float F = cen + __fdiv_rn(k * acc, 12.f);
+    const float F = fmaf(k * acc, INV12, cen);
     const float uc = p.u[fo + pi];
     const float uo = *upp;
     *upp = (2.f * uc - (1.f - a0) * uo + F) * __frcp_rn(1.f + a0);
@@ -81,7 +72,7 @@ __device__ __forceinline__ void ext_update(const StepParams& p, long long fo, lo
       }
     } else if (p.image) {
       float* gp = p.g + fo + pi;
-      *gp = *gp - (uc * p.hist[fo + pi] + __fdiv_rn(cen * p.hist2[fo + pi], 12.f));
+      *gp = *gp - fmaf(cen * p.hist2[fo + pi], INV12, uc * p.hist[fo + pi]);
     }
   } else if (MODE == EXT_ATT0) {
     const float at = __ldg(p.att + pi);
@@ -174,7 +165,7 @@ __global__ void __launch_bounds__(EXT_TX2 / 4 * EXT_TY2) k_ext2d(const StepParam
   const float* __restrict__ X = p.x + fo;
   if (!ADJ) {
     const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    ext_sample(p, blk * NT + tid);
+    sample_receivers(p, blk * NT + tid);
   }
   const long long base = (long long)(y0 + p.oy - R) * p.sx + (x0 + p.ox - G::XH);
   for (int i = tid; i < SH * SW; i += NT) {
@@ -336,7 +327,7 @@ __global__ void __launch_bounds__(EXT_TX2 / 4 * EXT_TY2) k_ext2d(const StepParam
     unpack(ld4(p.u + fo + pi), uc);
 #pragma unroll
     for (int ix = 0; ix < 4; ++ix) {
-      F[ix] = cen[ix] + __fdiv_rn(k[ix] * acc[ix], 12.f);
+      F[ix] = fmaf(k[ix] * acc[ix], INV12, cen[ix]);
       r[ix] = in[ix] ? (2.f * uc[ix] - (1.f - a0[ix]) * uo[ix] + F[ix]) * __frcp_rn(1.f + a0[ix]) : 0.f;
     }
     st4(upp, pack(r));
@@ -358,7 +349,7 @@ __global__ void __launch_bounds__(EXT_TX2 / 4 * EXT_TY2) k_ext2d(const StepParam
       unpack(ld4(p.g + fo + pi), g);
 #pragma unroll
       for (int ix = 0; ix < 4; ++ix)
-        if (in[ix]) g[ix] = g[ix] - (uc[ix] * h[ix] + __fdiv_rn(cen[ix] * h2[ix], 12.f));
+        if (in[ix]) g[ix] = g[ix] - fmaf(cen[ix] * h2[ix], INV12, uc[ix] * h[ix]);
       st4(p.g + fo + pi, pack(g));
     }
     return;
@@ -437,7 +428,7 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_ext3d(const StepParams p) 
   const long long col = (long long)(yg + p.oy) * p.sx + (xg + p.ox);
   if (!ADJ) {
     const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    ext_sample(p, blk * NT + tid);
+    sample_receivers(p, blk * NT + tid);
   }
   // register queues along z: q[j] = x at plane z - R + j of this column
   float q[Q];
@@ -658,7 +649,7 @@ __global__ void k_image_t4(const float* __restrict__ lam, const float* __restric
     for (int b = 0; b < nb; ++b) {
       const long long o = (long long)b * fs + i;
       const long long og = (long long)(b / S) * fs + i;
-      g[og] = g[og] - (lam[o] * F[o] + __fdiv_rn(ky[o] * kw[o], 12.f));
+      g[og] = g[og] - fmaf(ky[o] * kw[o], INV12, lam[o] * F[o]);
     }
   }
 }

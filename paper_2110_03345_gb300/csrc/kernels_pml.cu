@@ -54,17 +54,6 @@ __device__ __forceinline__ float pml_g(float Aj, float Ak, float Al, float dt) {
 }
 __device__ __forceinline__ float pml_p(float Aj) { return (1.f - Aj) / (1.f + Aj); }
 
-__device__ __forceinline__ void pml_sample(const StepParams& p, long long gid) {
-  if (p.nrec > 0 && gid < (long long)p.B * p.nrec) {
-    const int bb = (int)(gid / p.nrec);
-    const int r = (int)(gid - (long long)bb * p.nrec);
-    const float* ub = p.u + (long long)bb * p.fstride;
-    float acc = 0.f;
-    for (int c = 0; c < p.ncorner; ++c)
-      acc = fmaf(p.smp_w[r * p.ncorner + c], ub[p.smp_node[r * p.ncorner + c]], acc);
-    p.smp_out[p.smp_off + (long long)bb * p.nrec + r] = acc;
-  }
-}
 
 template <int R>
 struct Pml2 {
@@ -102,7 +91,7 @@ __global__ void __launch_bounds__(EXT_TX2 / 4 * EXT_TY2, 2) k_pml2d(const StepPa
   const bool near = x0 < reach || x0 + TX > p.nx - reach || y0 < reach || y0 + TY > p.ny - reach;
   if (MODE == PML_U) {
     const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    pml_sample(p, blk * NT + tid);
+    sample_receivers(p, blk * NT + tid);
   }
   const float* __restrict__ X = p.x + fo;
   const long long base = (long long)(y0 + p.oy - R) * p.sx + (x0 + p.ox - XH);
@@ -351,7 +340,7 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_pml3d(const StepParams p) 
   const bool cross = CROSS && (near || MODE == PML_B);
   if (MODE == PML_U) {
     const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    pml_sample(p, blk * NT + tid);
+    sample_receivers(p, blk * NT + tid);
   }
   const float* __restrict__ X = p.x + fo;
   const int xg = x0 + tx, yg = y0 + ty;

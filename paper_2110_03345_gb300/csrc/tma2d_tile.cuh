@@ -48,6 +48,8 @@ struct Geo {
 // arithmetic of kernels_ext.cu's epilogue): cen = x at the points, acc =
 // (L x + injection), lap = its plain Laplacian part (y = 2 forward), lc =
 // lap(att lambda) (y = 2 adjoint); the adjoint's imaging terms are added to gs.
+constexpr float INV12 = 1.f / 12.f;   // the 1/12 of the fourth-order terms, rounded once
+
 template <bool ADJ, int MODE>
 __device__ __forceinline__ void ext_epilogue(const StepParams& p, int s, int pix, int xg, int yg,
                                              const float4& ax4, float ay, const float4& kk,
@@ -60,7 +62,8 @@ __device__ __forceinline__ void ext_epilogue(const StepParams& p, int s, int pix
   unpack(ax4, ax);
   unpack(at4, at);
   unpack(uo4, uo);
-  unpack(uc4, uc);
+  if (MODE == EXT_T4 && ADJ) unpack(ld4(p.u + fo + pix), uc);
+  else unpack(uc4, uc);
   unpack(h4, h);
   if (MODE == EXT_T4 && ADJ && p.image)
     unpack(__ldcs(reinterpret_cast<const float4*>(p.hist2 + fo + pix)), h2);
@@ -76,11 +79,11 @@ __device__ __forceinline__ void ext_epilogue(const StepParams& p, int s, int pix
     if (MODE == EXT_KW) {
       v1 = k[ix] * acc[ix];
     } else if (MODE == EXT_T4) {
-      const float F = cen[ix] + __fdiv_rn(k[ix] * acc[ix], 12.f);
+      const float F = fmaf(k[ix] * acc[ix], INV12, cen[ix]);
       rv = (2.f * uc[ix] - (1.f - a0) * uo[ix] + F) * __frcp_rn(1.f + a0);
       v1 = F;
       v2 = cen[ix];
-      if (ADJ && p.image) gs[ix] += uc[ix] * h[ix] + __fdiv_rn(cen[ix] * h2[ix], 12.f);
+      if (ADJ && p.image) gs[ix] = fmaf(cen[ix] * h2[ix], INV12, fmaf(uc[ix], h[ix], gs[ix]));
     } else if (MODE == EXT_ATT0) {
       const float a = a0 + at[ix];
       const float hv = k[ix] * acc[ix];
@@ -214,17 +217,9 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
   pdl_wait();   // the previous step's wavefields are complete from here on
 
   if (!ADJ && p.nrec > 0) {
-    // receiver sampling of u^n (not written during this step), one thread per slot x receiver
+    // receiver sampling of u^n (not written during this step), a thread or a warp per slot x receiver
     const long long gid = samp_rank * NT + tid;
-    if (gid < (long long)p.B * p.nrec) {
-      const int bb = (int)(gid / p.nrec);
-      const int r = (int)(gid - (long long)bb * p.nrec);
-      const float* ub = p.u + (long long)bb * p.fstride;
-      float acc = 0.f;
-      for (int c = 0; c < p.ncorner; ++c)
-        acc = fmaf(p.smp_w[r * p.ncorner + c], ub[p.smp_node[r * p.ncorner + c]], acc);
-      p.smp_out[p.smp_off + (long long)bb * p.nrec + r] = acc;
-    }
+    sample_receivers(p, gid);
   }
   if (ns <= 0) return;
   __syncthreads();   // barrier initialisation and the b_x / b_y tiles are visible
@@ -252,8 +247,9 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
     // latency overlaps it: u^{n-1}, and h^k (adjoint) or b_x, b_y (forward);
     // the extended schemes' u^n (fourth order), k w^k and the Laplacian state
     constexpr bool T4 = MODE == EXT_T4;
-    // (the fourth-order adjoint's k w^k and the Laplacian state are read in
-    // the update: issued here they would hold registers across the stencil)
+    // (the fourth-order adjoint's lambda^k and k w^k and the Laplacian state
+    // are read in the update: issued here they would hold registers across
+    // the stencil)
     float4 uo[RY], hv[ADJ ? RY : 1], uc[T4 ? RY : 1];
     float4 bxf[VD && !ADJ ? RY : 1], byf[VD && !ADJ ? RY : 1];
 #pragma unroll
@@ -261,7 +257,7 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
       if (MODE != EXT_KW) uo[iy] = ld4(up_s + pix[iy]);
       if (ADJ && MODE != EXT_KW && p.image)
         hv[iy] = __ldcs(reinterpret_cast<const float4*>(h_s + pix[iy]));
-      if (T4) uc[iy] = ld4(p.u + (size_t)s * p.fstride + pix[iy]);
+      if (T4 && !ADJ) uc[iy] = ld4(p.u + (size_t)s * p.fstride + pix[iy]);
       if (VD && !ADJ) {
         bxf[iy] = ldg4(p.bx + pix[iy]);
         byf[iy] = ldg4(p.by + pix[iy]);
