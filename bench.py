@@ -235,11 +235,14 @@ def traffic_record(kernel_kind, tile):
     if not rec or rec.get("tile") != tile:
         return None
     import hashlib
-    src = os.path.join(ROOT, "paper_2110_03345_gb300", "csrc", rec.get("source", "kernels2d.cu"))
+    srcs = rec.get("source", "kernels2d.cu")
+    hs = hashlib.sha256()
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for f in ([srcs] if isinstance(srcs, str) else srcs):   # the kernel's source files, in order
+            hs.update(open(os.path.join(ROOT, "paper_2110_03345_gb300", "csrc", f), "rb").read())
     except OSError:
         return None
+    h = hs.hexdigest()[:16]
     if h != rec.get("source_sha256_16"):
         return None
     return rec

@@ -134,6 +134,7 @@ struct HostTable {
   std::vector<int> off, loc, vidx;
   std::vector<float> w;
   std::vector<int> row;   // 2D: per bucket, the first entry of each tile row (rows + 1 values)
+  int max_row = 0;        // 2D: most entries in one tile row of one bucket
 };
 
 struct DevTable {
@@ -142,6 +143,7 @@ struct DevTable {
   const int* vidx = nullptr;
   const float* w = nullptr;
   const int* row = nullptr;
+  int crowded = 0;        // some tile row holds more than 32 entries
 };
 
 // Time scheme and attenuation of a call: the leapfrog of the default

@@ -25,15 +25,15 @@ namespace fwi {
 
 namespace {
 
-template <int R, bool VD, bool ADJ, int RY, int BY>
+template <int R, bool VD, bool ADJ, int RY, int BY, bool CROWD>
 __global__ void __launch_bounds__(32 * BY, (RY == 1 ? 1024 : 512) / (32 * BY))
 k_step2d_tma(const StepParams p, const __grid_constant__ CUtensorMap tmap) {
   pdl_trigger();
   extern __shared__ __align__(128) float4 smem[];
   __shared__ uint64_t bar[4];
   const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  step2d_tma_tile<R, VD, ADJ, RY, BY>(p, p.wx, p.wy, &tmap, blockIdx.x, blockIdx.y, gridDim.x,
-                                      blockIdx.z, blk, smem, bar);
+  step2d_tma_tile<R, VD, ADJ, RY, BY, LEAP, CROWD>(p, p.wx, p.wy, &tmap, blockIdx.x, blockIdx.y,
+                                                   gridDim.x, blockIdx.z, blk, smem, bar);
 }
 
 // Multi-problem forward step with TMA staging: CTA i advances unit units[i]
@@ -72,16 +72,16 @@ k_step2d_tma_multi(const MultiDesc* __restrict__ descs, const MultiUnit* __restr
                                         d->gx, un.slot, un.rank, smem, bar);
 }
 
-template <int R, bool VD, bool ADJ, int RY, int BY>
+template <int R, bool VD, bool ADJ, int RY, int BY, bool CROWD = false>
 cudaError_t launch_t(const StepParams& p, const CUtensorMap& map, cudaStream_t st) {
   constexpr int TY = RY * BY;
   constexpr size_t smem = smem_bytes<R, VD, ADJ, RY, BY>();
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_step2d_tma<R, VD, ADJ, RY, BY>,
+    cudaError_t e = cudaFuncSetAttribute(k_step2d_tma<R, VD, ADJ, RY, BY, CROWD>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_step2d_tma<R, VD, ADJ, RY, BY>,
+    e = cudaFuncSetAttribute(k_step2d_tma<R, VD, ADJ, RY, BY, CROWD>,
                              cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
@@ -89,13 +89,16 @@ cudaError_t launch_t(const StepParams& p, const CUtensorMap& map, cudaStream_t s
   }
   dim3 grid((p.nx + TILE_X - 1) / TILE_X, (p.ny + TY - 1) / TY, (p.B + p.S - 1) / p.S);
   dim3 block(32, BY);
-  return launch_pdl(k_step2d_tma<R, VD, ADJ, RY, BY>, grid, block, smem, st, p, map);
+  return launch_pdl(k_step2d_tma<R, VD, ADJ, RY, BY, CROWD>, grid, block, smem, st, p, map);
 }
 
+// the default shape (128 x 16) has a crowded-row instantiation (sinc points)
 template <int R, bool VD, bool ADJ>
 cudaError_t launch_tile(const StepParams& p, const CUtensorMap& map, int tile, cudaStream_t st) {
   switch (tile) {
-    case 1: return launch_t<R, VD, ADJ, 1, 16>(p, map, st);
+    case 1:
+      return p.inj_crowded ? launch_t<R, VD, ADJ, 1, 16, true>(p, map, st)
+                           : launch_t<R, VD, ADJ, 1, 16>(p, map, st);
     case 2: return launch_t<R, VD, ADJ, 2, 16>(p, map, st);
     case 3: return launch_t<R, VD, ADJ, 2, 8>(p, map, st);
     default: return launch_t<R, VD, ADJ, 1, 32>(p, map, st);

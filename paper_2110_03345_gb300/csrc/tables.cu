@@ -182,6 +182,7 @@ HostTable bucket(const std::vector<Entry>& E_in, int nbuckets, int rows, int tx)
       for (int r = 0; r <= rows; ++r) {
         while (k < H.off[b + 1] && H.loc[k] < r * tx) ++k;
         H.row[(size_t)b * (rows + 1) + r] = k;
+        if (r > 0) H.max_row = std::max(H.max_row, k - H.row[(size_t)b * (rows + 1) + r - 1]);
       }
     }
   }
@@ -209,6 +210,7 @@ fwi_status upload_table(fwi_plan* P, const HostTable& H, Carve& C, DevTable& D) 
   D.vidx = vidx;
   D.w = w;
   D.row = nullptr;
+  D.crowded = H.max_row > 32;
   if (!H.row.empty()) {
     int* row = C.take<int>(H.row.size());
     CUDA_TRY(cudaMemcpyAsync(row, H.row.data(), H.row.size() * 4, cudaMemcpyHostToDevice, P->st));

@@ -136,10 +136,13 @@ __device__ __forceinline__ void ext_epilogue(const StepParams& p, int s, int pix
 // scratch of the fourth-order scheme), the model data of the tile (k, the
 // attenuation coefficient, its tiles for the y = 2 adjoint) are loaded once
 // for the S shots, and the imaging term is summed over the S shots in
-// registers.
+// registers.  CROWD: the injection tables have tile rows of more than 32
+// entries (sinc points), whose threads find their own entries by bisection
+// (a separate instantiation: the unused branch alone cost the leapfrog
+// adjoint 2%).
 constexpr int LEAP = -1;
 
-template <int R, bool VD, bool ADJ, int RY, int BY, int MODE = LEAP>
+template <int R, bool VD, bool ADJ, int RY, int BY, int MODE = LEAP, bool CROWD = false>
 __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW& wx,
                                                 const AxisW& wy, const CUtensorMap* tmap,
                                                 int bxi, int byi, int gx, int grp,
@@ -409,8 +412,29 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
       if (e1 > e0) {
         // only this row's entries (the bucket's per-row ranges)
         const int* rr = p.inj_row + (size_t)(s * p.ntiles + tile_id) * (TY + 1);
-        const int r1 = rr[ly + 1];
-        for (int e = rr[ly]; e < r1; ++e) {
+        int e = rr[ly], r1 = rr[ly + 1];
+        if (CROWD && r1 - e > 32) {
+          // a crowded row (sinc points, 8 nodes per point and row): the row's
+          // entries sort by position, so this thread's range [e, r1) of
+          // positions [lo, lo + 4) comes from two bisections
+          const int lo = ly * TX + 4 * tx;
+          int a = e, b = r1;
+          while (a < b) {
+            const int m = (a + b) >> 1;
+            if (p.inj_loc[m] < lo) a = m + 1;
+            else b = m;
+          }
+          int c = a;
+          b = r1;
+          while (c < b) {
+            const int m = (c + b) >> 1;
+            if (p.inj_loc[m] < lo + 4) c = m + 1;
+            else b = m;
+          }
+          e = a;
+          r1 = c;
+        }
+        for (; e < r1; ++e) {
           const int elx = p.inj_loc[e] - ly * TX;
           if ((elx >> 2) == tx) {
             const float w = (MODE == LEAP) ? p.inj_w[e] : p.inj_scale * p.inj_w[e];
