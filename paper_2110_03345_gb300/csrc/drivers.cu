@@ -30,11 +30,12 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // 3D tensor map over nslots padded 2D fields: dims (x = sx, y = rows, slot),
 // box = one tile plus its halo of one slot.
 fwi_status make_tensor_map(const fwi_plan* P, const float* base, int nslots, int shape,
-                           CUtensorMap* out) {
+                           CUtensorMap* out, bool interior) {
   auto enc = tensor_map_encoder();
   if (!enc) return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
   int bx = 0, by = 0;
-  tma_box2d(P->R, shape, &bx, &by);
+  if (interior) tma_box2d_interior(shape, &bx, &by);
+  else tma_box2d(P->R, shape, &bx, &by);
   const cuuint64_t dims[3] = {(cuuint64_t)P->L.sx, (cuuint64_t)P->L.rows, (cuuint64_t)nslots};
   const cuuint64_t strides[2] = {(cuuint64_t)P->L.sx * sizeof(float),
                                  (cuuint64_t)P->L.fstride * sizeof(float)};
@@ -46,6 +47,30 @@ fwi_status make_tensor_map(const fwi_plan* P, const float* base, int nslots, int
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS)
     return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+  return FWI_OK;
+}
+
+// 4D tensor map over a 2D history buffer of nsteps x nslots padded fields:
+// dims (x = sx, y = rows, slot, step), box = one tile without halo.
+fwi_status make_tensor_map_hist(const fwi_plan* P, const float* base, int nslots, int nsteps,
+                                int shape, CUtensorMap* out) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  int bx = 0, by = 0;
+  tma_box2d_interior(shape, &bx, &by);
+  const cuuint64_t dims[4] = {(cuuint64_t)P->L.sx, (cuuint64_t)P->L.rows, (cuuint64_t)nslots,
+                              (cuuint64_t)nsteps};
+  const cuuint64_t strides[3] = {(cuuint64_t)P->L.sx * sizeof(float),
+                                 (cuuint64_t)P->L.fstride * sizeof(float),
+                                 (cuuint64_t)P->L.fstride * nslots * sizeof(float)};
+  const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1u, 1u};
+  const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+  const CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled (history) failed with code " + std::to_string((int)r));
   return FWI_OK;
 }
 
@@ -138,9 +163,9 @@ long long launch_threads(const Call& c, int B) {
   return (long long)c.T.ntiles() * ctas_z * 32 * by;
 }
 
-const CUtensorMap* find_map(const Call& c, const float* base) {
+const CUtensorMap* find_map(const Call& c, const float* base, int kind) {
   for (const auto& m : c.maps)
-    if (m.base == base) return &m.map;
+    if (m.base == base && m.kind == kind) return &m.map;
   return nullptr;
 }
 
@@ -172,7 +197,15 @@ fwi_status launch_step(Call& c, const StepParams& p_in, bool adj) {
     e = c.pl.x2 ? launch_step3d_x2(p, *map, *bxm, *bym, P->R, c.vd, adj, c.pl.shape, P->st)
                 : launch_step3d_tma(p, *map, *bxm, *bym, P->R, c.vd, adj, c.pl.shape, P->st);
   } else if (P->grid.ndim == 3) e = launch_step3d(p, P->R, c.vd, adj, c.pl.shape, P->st);
-  else if (c.pl.tma) e = launch_step2d_tma(p, *map, P->R, c.vd, adj, c.pl.shape, P->st);
+  else if (c.pl.tma) {
+    // u^{n-1} (p.up) without halo; the history map only when the adjoint images
+    const CUtensorMap* um = find_map(c, p.up, 1);
+    if (!um) return fail(FWI_ERR_INVALID_ARG, "internal: no tensor map for u^{n-1}");
+    if (adj && p.image && !c.hmap_ok)
+      return fail(FWI_ERR_INVALID_ARG, "internal: no tensor map for the history");
+    e = launch_step2d_tma(p, *map, *um, (adj && p.image) ? c.hmap : *um, P->R, c.vd, adj,
+                          c.pl.shape, P->st);
+  }
   else e = launch_step2d(p, P->R, c.vd, adj, c.pl.shape, P->st);
   if (e != cudaSuccess) return fail(FWI_ERR_CUDA, std::string("stencil launch: ") + cudaGetErrorString(e));
   if (prof) {
@@ -481,6 +514,11 @@ fwi_status begin_call(fwi_plan* P, const fwi_model* model, const fwi_geometry* g
       if (three) FWI_TRY(make_tensor_map_3d(P, buf, c.pl.B, c.pl.shape, c.pl.x2, &m.map));
       else FWI_TRY(make_tensor_map(P, buf, c.pl.B, c.pl.shape, &m.map));
       c.maps.push_back(m);
+      if (!three && !c.pl.sc.ext()) {   // the leapfrog kernels also stage u^{n-1} by TMA
+        Call::MapEnt mi{buf, {}, 1};
+        FWI_TRY(make_tensor_map(P, buf, c.pl.B, c.pl.shape, &mi.map, true));
+        c.maps.push_back(mi);
+      }
     }
     if (three && c.vd) {
       // the two-point kernels stage b_x on the tile rows (80 x BY) and b_y on
@@ -696,12 +734,20 @@ fwi_status gradient_adjoint_batch(Call& c, int j, int shot0, int nb, const DevTa
     }
     return FWI_OK;
   }
+  // the 2D leapfrog adjoint reads h^k by TMA through a map of this batch's
+  // history buffer (nt - 1 steps, or one segment of K)
+  c.hmap_ok = false;
+  if (c.pl.tma && P->grid.ndim == 2 && !ext) {
+    FWI_TRY(make_tensor_map_hist(P, bb.H, B, K == 0 ? std::max(nt - 1, 1) : K, c.pl.shape, &c.hmap));
+    c.hmap_ok = true;
+  }
   for (int k = nt - 1; k >= 1; --k) {
     p.image = (k <= nt - 2) ? 1 : 0;
     if (p.image) {
       FWI_TRY(ensure_segment(k));
       p.hist = hist_at(k);
       p.hist2 = hist2_at(k);
+      p.hstep = (int)((size_t)(p.hist - bb.H) / (fs * B));
     } else {
       p.hist = nullptr;
       p.hist2 = nullptr;

@@ -70,6 +70,7 @@ struct StepParams {
   const int* inj_vidx;   // index into vals (before step_off)
   const int* inj_row;    // 2D: per bucket, entry range of each tile row (TY + 1 values)
   int inj_crowded;       // 2D: some tile row holds more than 32 entries
+  int hstep;             // 2D TMA adjoint: step of hist within the history buffer's tensor map
   const float* inj_w;    // weight (source: w/dV; receiver residual: w)
   const float* vals;
   long long step_off;
@@ -239,9 +240,14 @@ cudaError_t launch_step2d_multi(const MultiDesc* descs, const MultiUnit* units, 
                                 int R, bool vd, cudaStream_t st);
 // TMA-staged 2D kernels with a loop over p.S shots per CTA (kernels2d_tma.cu);
 // tile = 0..NUM_TILE2-1 selects the same tile shapes as tile2_variant.
-cudaError_t launch_step2d_tma(const StepParams& p, const CUtensorMap& map, int R, bool vd, bool adj,
-                              int tile, cudaStream_t st);
+// um maps p.up without halo (box tma_box2d_interior); hm maps the adjoint's
+// history buffer as (x, y, slot, step) with the same box, step p.hstep (read
+// only when p.image); both move u^{n-1} and h^k by TMA with the tile.
+cudaError_t launch_step2d_tma(const StepParams& p, const CUtensorMap& map, const CUtensorMap& um,
+                              const CUtensorMap& hm, int R, bool vd, bool adj, int tile,
+                              cudaStream_t st);
 void tma_box2d(int R, int tile, int* bx, int* by);
+void tma_box2d_interior(int tile, int* bx, int* by);
 // The extended schemes' 2D kernels on the same pipeline (kernels2d_tma_ext.cu):
 // mode = EXT_KW / EXT_T4 / EXT_ATT0 / EXT_ATT2, map = the tensor map of the
 // stencil input p.x for tile shape 1 (128 x 16), p.S shots per CTA.

@@ -216,8 +216,11 @@ struct Call {
   struct MapEnt {
     const float* base;
     CUtensorMap map;
+    int kind = 0;   // 0: tile with halo; 1: 2D tile without halo (u^{n-1})
   };
   std::vector<MapEnt> maps;   // TMA descriptors of the wavefield buffers
+  CUtensorMap hmap{};         // 2D TMA adjoint: the current batch's history buffer
+  bool hmap_ok = false;
   std::vector<float*> fstate; // forward state besides u^n, u^{n-1} (checkpointed with them)
   int64_t launches = 0;
   int64_t fwd_launches = 0, adj_launches = 0;
@@ -299,15 +302,20 @@ size_t tables_bound(const fwi_plan* P, const fwi_geometry* g, const Plan& pl);
 fwi_status check_on_device(const void* ptr, const char* name, int dev);
 
 // ---- drivers.cu: launches, forward and adjoint sweeps, call set-up
+// 2D tensor maps over nslots padded fields: the tile with halo (interior =
+// false) or without (interior = true); make_tensor_map_hist: a history
+// buffer of nsteps x nslots fields, box = one tile without halo
+fwi_status make_tensor_map_hist(const fwi_plan* P, const float* base, int nslots, int nsteps,
+                                int shape, CUtensorMap* out);
 fwi_status make_tensor_map(const fwi_plan* P, const float* base, int nslots, int shape,
-                           CUtensorMap* out);
+                           CUtensorMap* out, bool interior = false);
 // box_w / box_h > 0 override the box's x extent and rows
 fwi_status make_tensor_map_3d(const fwi_plan* P, const float* base, int nslots, int shape,
                               bool x2, CUtensorMap* out, int box_w = 0, int box_h = 0);
 fwi_status record_event(fwi_plan* P, int kind);
 StepParams base_params(Call& c);
 long long launch_threads(const Call& c, int B);
-const CUtensorMap* find_map(const Call& c, const float* base);
+const CUtensorMap* find_map(const Call& c, const float* base, int kind = 0);
 fwi_status launch_step(Call& c, const StepParams& p_in, bool adj);
 fwi_status forward_steps(Call& c, int nb, int shot0, const DevTable& src, float*& A, float*& Bf,
                          int n0, int n1, float* hist_base, int hist_n0, bool sample,

@@ -27,13 +27,15 @@ namespace {
 
 template <int R, bool VD, bool ADJ, int RY, int BY, bool CROWD>
 __global__ void __launch_bounds__(32 * BY, (RY == 1 ? 1024 : 512) / (32 * BY))
-k_step2d_tma(const StepParams p, const __grid_constant__ CUtensorMap tmap) {
+k_step2d_tma(const StepParams p, const __grid_constant__ CUtensorMap tmap,
+             const __grid_constant__ CUtensorMap upmap, const __grid_constant__ CUtensorMap hmap) {
   pdl_trigger();
   extern __shared__ __align__(128) float4 smem[];
   __shared__ uint64_t bar[4];
   const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  step2d_tma_tile<R, VD, ADJ, RY, BY, LEAP, CROWD>(p, p.wx, p.wy, &tmap, blockIdx.x, blockIdx.y,
-                                                   gridDim.x, blockIdx.z, blk, smem, bar);
+  step2d_tma_tile<R, VD, ADJ, RY, BY, LEAP, CROWD, true>(p, p.wx, p.wy, &tmap, &upmap, &hmap,
+                                                         blockIdx.x, blockIdx.y, gridDim.x,
+                                                         blockIdx.z, blk, smem, bar);
 }
 
 // Multi-problem forward step with TMA staging: CTA i advances unit units[i]
@@ -68,14 +70,16 @@ k_step2d_tma_multi(const MultiDesc* __restrict__ descs, const MultiUnit* __restr
   }
   __syncthreads();
   const CUtensorMap* map = (n & 1) ? &d->map1 : &d->map0;
-  step2d_tma_tile<R, VD, false, RY, BY>(sp, UW ? wx : sp.wx, UW ? wy : sp.wy, map, un.tx, un.ty,
+  step2d_tma_tile<R, VD, false, RY, BY>(sp, UW ? wx : sp.wx, UW ? wy : sp.wy, map, nullptr, nullptr,
+                                        un.tx, un.ty,
                                         d->gx, un.slot, un.rank, smem, bar);
 }
 
 template <int R, bool VD, bool ADJ, int RY, int BY, bool CROWD = false>
-cudaError_t launch_t(const StepParams& p, const CUtensorMap& map, cudaStream_t st) {
+cudaError_t launch_t(const StepParams& p, const CUtensorMap& map, const CUtensorMap& upmap,
+                     const CUtensorMap& hmap, cudaStream_t st) {
   constexpr int TY = RY * BY;
-  constexpr size_t smem = smem_bytes<R, VD, ADJ, RY, BY>();
+  constexpr size_t smem = smem_bytes<R, VD, ADJ, RY, BY, LEAP, true>();
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_step2d_tma<R, VD, ADJ, RY, BY, CROWD>,
@@ -89,19 +93,21 @@ cudaError_t launch_t(const StepParams& p, const CUtensorMap& map, cudaStream_t s
   }
   dim3 grid((p.nx + TILE_X - 1) / TILE_X, (p.ny + TY - 1) / TY, (p.B + p.S - 1) / p.S);
   dim3 block(32, BY);
-  return launch_pdl(k_step2d_tma<R, VD, ADJ, RY, BY, CROWD>, grid, block, smem, st, p, map);
+  return launch_pdl(k_step2d_tma<R, VD, ADJ, RY, BY, CROWD>, grid, block, smem, st, p, map, upmap,
+                    hmap);
 }
 
 // the default shape (128 x 16) has a crowded-row instantiation (sinc points)
 template <int R, bool VD, bool ADJ>
-cudaError_t launch_tile(const StepParams& p, const CUtensorMap& map, int tile, cudaStream_t st) {
+cudaError_t launch_tile(const StepParams& p, const CUtensorMap& map, const CUtensorMap& um,
+                        const CUtensorMap& hm, int tile, cudaStream_t st) {
   switch (tile) {
     case 1:
-      return p.inj_crowded ? launch_t<R, VD, ADJ, 1, 16, true>(p, map, st)
-                           : launch_t<R, VD, ADJ, 1, 16>(p, map, st);
-    case 2: return launch_t<R, VD, ADJ, 2, 16>(p, map, st);
-    case 3: return launch_t<R, VD, ADJ, 2, 8>(p, map, st);
-    default: return launch_t<R, VD, ADJ, 1, 32>(p, map, st);
+      return p.inj_crowded ? launch_t<R, VD, ADJ, 1, 16, true>(p, map, um, hm, st)
+                           : launch_t<R, VD, ADJ, 1, 16>(p, map, um, hm, st);
+    case 2: return launch_t<R, VD, ADJ, 2, 16>(p, map, um, hm, st);
+    case 3: return launch_t<R, VD, ADJ, 2, 8>(p, map, um, hm, st);
+    default: return launch_t<R, VD, ADJ, 1, 32>(p, map, um, hm, st);
   }
 }
 
@@ -156,14 +162,26 @@ cudaError_t launch_step2d_tma_multi(const MultiDesc* descs, const MultiUnit* uni
 }
 
 // tile: 0..3, the shapes of tile2_tma_variant
-cudaError_t launch_step2d_tma(const StepParams& p, const CUtensorMap& map, int R, bool vd, bool adj,
-                              int tile, cudaStream_t st) {
+cudaError_t launch_step2d_tma(const StepParams& p, const CUtensorMap& map, const CUtensorMap& um,
+                              const CUtensorMap& hm, int R, bool vd, bool adj, int tile,
+                              cudaStream_t st) {
   if (R == 4) {
-    if (vd) return adj ? launch_tile<4, true, true>(p, map, tile, st) : launch_tile<4, true, false>(p, map, tile, st);
-    return adj ? launch_tile<4, false, true>(p, map, tile, st) : launch_tile<4, false, false>(p, map, tile, st);
+    if (vd) return adj ? launch_tile<4, true, true>(p, map, um, hm, tile, st)
+                       : launch_tile<4, true, false>(p, map, um, hm, tile, st);
+    return adj ? launch_tile<4, false, true>(p, map, um, hm, tile, st)
+               : launch_tile<4, false, false>(p, map, um, hm, tile, st);
   }
-  if (vd) return adj ? launch_tile<5, true, true>(p, map, tile, st) : launch_tile<5, true, false>(p, map, tile, st);
-  return adj ? launch_tile<5, false, true>(p, map, tile, st) : launch_tile<5, false, false>(p, map, tile, st);
+  if (vd) return adj ? launch_tile<5, true, true>(p, map, um, hm, tile, st)
+                     : launch_tile<5, true, false>(p, map, um, hm, tile, st);
+  return adj ? launch_tile<5, false, true>(p, map, um, hm, tile, st)
+             : launch_tile<5, false, false>(p, map, um, hm, tile, st);
+}
+
+// TMA box (floats) of a tile variant without halo: {x extent, y extent}.
+void tma_box2d_interior(int tile, int* bx, int* by) {
+  const Tile2 t = tile2_tma_variant(tile);
+  *bx = TILE_X;
+  *by = t.ry * t.by;
 }
 
 // TMA box (floats) of a tile variant: {x extent, y extent}.

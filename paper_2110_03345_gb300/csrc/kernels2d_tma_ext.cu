@@ -25,8 +25,8 @@ k_step2d_tma_ext(const StepParams p, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) float4 smem[];
   __shared__ uint64_t bar[4];
   const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  step2d_tma_tile<R, VD, ADJ, 1, EXT_BY, MODE>(p, p.wx, p.wy, &tmap, blockIdx.x, blockIdx.y,
-                                               gridDim.x, blockIdx.z, blk, smem, bar);
+  step2d_tma_tile<R, VD, ADJ, 1, EXT_BY, MODE>(p, p.wx, p.wy, &tmap, nullptr, nullptr, blockIdx.x,
+                                               blockIdx.y, gridDim.x, blockIdx.z, blk, smem, bar);
 }
 
 template <int R, bool VD, bool ADJ, int MODE>

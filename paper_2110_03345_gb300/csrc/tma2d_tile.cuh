@@ -42,6 +42,11 @@ struct Geo {
   static constexpr int SH = TY + 2 * R;
   static constexpr int QW = TX / 4;
   static constexpr uint32_t TILE_BYTES = (uint32_t)SH * SW * 16;
+  // float4 offset of the STG tiles: after the two wavefield buffers and the
+  // b_x / b_y (psi) and attenuation (cl) tiles, rounded to 128 bytes
+  __host__ __device__ static constexpr int STG_OFF(bool psi, bool cl) {
+    return (2 * SH * SW + (psi ? TY * SW + SH * QW : 0) + (cl ? TY * SW + SH * QW : 0) + 7) / 8 * 8;
+  }
 };
 
 // Update of the float4 of points of one row in an extended scheme (the
@@ -139,12 +144,17 @@ __device__ __forceinline__ void ext_epilogue(const StepParams& p, int s, int pix
 // registers.  CROWD: the injection tables have tile rows of more than 32
 // entries (sinc points), whose threads find their own entries by bisection
 // (a separate instantiation: the unused branch alone cost the leapfrog
-// adjoint 2%).
+// adjoint 2%).  STG: u^{n-1} (upmap, the tile without halo) and, in the
+// adjoint, h^k (hmap: (x, y, slot, step), step p.hstep) of each shot arrive
+// by TMA with its wavefield tile, two shots ahead, instead of by loads
+// that each thread issues before its tile wait.
 constexpr int LEAP = -1;
 
-template <int R, bool VD, bool ADJ, int RY, int BY, int MODE = LEAP, bool CROWD = false>
+template <int R, bool VD, bool ADJ, int RY, int BY, int MODE = LEAP, bool CROWD = false,
+          bool STG = false>
 __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW& wx,
                                                 const AxisW& wy, const CUtensorMap* tmap,
+                                                const CUtensorMap* upmap, const CUtensorMap* hmap,
                                                 int bxi, int byi, int gx, int grp,
                                                 long long samp_rank, float4* smem, uint64_t* bar) {
   using G = Geo<R, RY, BY>;
@@ -161,6 +171,11 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
   // y = 2 adjoint: the attenuation coefficient on the tile rows / columns
   float4* s_ax = smem + 2 * SH * SW + ((VD && ADJ) ? TY * SW + SH * QW : 0);
   float4* s_ay = s_ax + TY * SW;
+  // STG: u^{n-1} and h^k tiles [TY][QW] of buffers 0 / 1
+  static_assert(G::STG_OFF(VD && ADJ, CL) % 8 == 0, "TMA destinations on 128-byte boundaries");
+  float4* s_uo = smem + G::STG_OFF(VD && ADJ, CL);
+  float4* s_hv = s_uo + 2 * TY * QW;
+  constexpr uint32_t IN_BYTES = (uint32_t)TY * QW * 16;   // one tile without halo
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * 32 + tx;
@@ -226,13 +241,21 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
   }
   if (ns <= 0) return;
   __syncthreads();   // barrier initialisation and the b_x / b_y tiles are visible
-  if (tid == 0) {
-    mbar_arrive_expect_tx(&bar[0], G::TILE_BYTES);
-    tma_load_3d(s_t0, tmap, &bar[0], tmx, tmy, s0);
-    if (ns > 1) {
-      mbar_arrive_expect_tx(&bar[1], G::TILE_BYTES);
-      tma_load_3d(s_t1, tmap, &bar[1], tmx, tmy, s0 + 1);
+  // shot k of the group into buffer k & 1: its wavefield tile with halo and,
+  // STG, its u^{n-1} and h^k tiles, all on the buffer's full barrier
+  const bool stg_h = STG && ADJ && p.image;
+  auto issue = [&](int k) {
+    const int bf = k & 1;
+    mbar_arrive_expect_tx(&bar[bf], G::TILE_BYTES + (STG ? IN_BYTES : 0u) + (stg_h ? IN_BYTES : 0u));
+    tma_load_3d(bf ? s_t1 : s_t0, tmap, &bar[bf], tmx, tmy, s0 + k);
+    if (STG) {
+      tma_load_3d(s_uo + bf * TY * QW, upmap, &bar[bf], x0 + p.ox, y0 + p.oy, s0 + k);
+      if (stg_h) tma_load_4d(s_hv + bf * TY * QW, hmap, &bar[bf], x0 + p.ox, y0 + p.oy, s0 + k, p.hstep);
     }
+  };
+  if (tid == 0) {
+    issue(0);
+    if (ns > 1) issue(1);
   }
   float gs[RY][4];
 #pragma unroll
@@ -253,12 +276,12 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
     // (the fourth-order adjoint's lambda^k and k w^k and the Laplacian state
     // are read in the update: issued here they would hold registers across
     // the stencil)
-    float4 uo[RY], hv[ADJ ? RY : 1], uc[T4 ? RY : 1];
+    float4 uo[RY], hv[ADJ ? RY : 1], uc[T4 ? RY : 1];   // (STG: unused)
     float4 bxf[VD && !ADJ ? RY : 1], byf[VD && !ADJ ? RY : 1];
 #pragma unroll
     for (int iy = 0; iy < RY; ++iy) {
-      if (MODE != EXT_KW) uo[iy] = ld4(up_s + pix[iy]);
-      if (ADJ && MODE != EXT_KW && p.image)
+      if (!STG && MODE != EXT_KW) uo[iy] = ld4(up_s + pix[iy]);
+      if (!STG && ADJ && MODE != EXT_KW && p.image)
         hv[iy] = __ldcs(reinterpret_cast<const float4*>(h_s + pix[iy]));
       if (T4 && !ADJ) uc[iy] = ld4(p.u + (size_t)s * p.fstride + pix[iy]);
       if (VD && !ADJ) {
@@ -453,7 +476,7 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
         continue;
       }
       float* upp = up_s + pix[iy];
-      const float4 uoi = uo[iy];
+      const float4 uoi = STG ? s_uo[buf * TY * QW + ly * QW + tx] : uo[iy];
       float res[4], upd[4];
 #pragma unroll
       for (int ix = 0; ix < 4; ++ix) {
@@ -471,10 +494,11 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
           __stcs(reinterpret_cast<float4*>(h_s + pix[iy]),
                  make_float4(upd[0], upd[1], upd[2], upd[3]));
       } else if (p.image) {
-        gs[iy][0] = fmaf(v[4 * NL + 0], hv[iy].x, gs[iy][0]);
-        gs[iy][1] = fmaf(v[4 * NL + 1], hv[iy].y, gs[iy][1]);
-        gs[iy][2] = fmaf(v[4 * NL + 2], hv[iy].z, gs[iy][2]);
-        gs[iy][3] = fmaf(v[4 * NL + 3], hv[iy].w, gs[iy][3]);
+        const float4 hvi = STG ? s_hv[buf * TY * QW + ly * QW + tx] : hv[iy];
+        gs[iy][0] = fmaf(v[4 * NL + 0], hvi.x, gs[iy][0]);
+        gs[iy][1] = fmaf(v[4 * NL + 1], hvi.y, gs[iy][1]);
+        gs[iy][2] = fmaf(v[4 * NL + 2], hvi.z, gs[iy][2]);
+        gs[iy][3] = fmaf(v[4 * NL + 3], hvi.w, gs[iy][3]);
       }
     }
     // This warp is done with the buffer.  Thread 0 refills it for shot k + 2
@@ -486,8 +510,7 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
       if (!mbar_wait_bounded(&bar[2 + buf], (uint32_t)((k >> 1) & 1)) && p.flags)
         atomicOr(p.flags, 2);
       fence_proxy_async_smem();
-      mbar_arrive_expect_tx(&bar[buf], G::TILE_BYTES);
-      tma_load_3d(buf ? s_t1 : s_t0, tmap, &bar[buf], tmx, tmy, s + 2);
+      issue(k + 2);
     }
   }
   if (ADJ && MODE != EXT_KW && p.image) {
@@ -509,13 +532,11 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
 // Dynamic shared memory of the tile body: two wavefield buffers, the b_x /
 // b_y tiles of the variable-density adjoint, the attenuation tiles of the
 // y = 2 adjoint.
-template <int R, bool VD, bool ADJ, int RY, int BY, int MODE = LEAP>
+template <int R, bool VD, bool ADJ, int RY, int BY, int MODE = LEAP, bool STG = false>
 constexpr size_t smem_bytes() {
   using G = Geo<R, RY, BY>;
-  constexpr size_t cross = (size_t)G::TY * G::SW + (size_t)G::SH * G::QW;
-  size_t n = 2 * (size_t)G::SH * G::SW;
-  if (VD && ADJ) n += cross;
-  if (MODE == EXT_ATT2 && ADJ) n += cross;
+  size_t n = G::STG_OFF(VD && ADJ, MODE == EXT_ATT2 && ADJ);
+  if (STG) n += (size_t)(ADJ ? 4 : 2) * G::TY * G::QW;   // u^{n-1} (and h^k) tiles, two buffers
   return n * sizeof(float4);
 }
 
