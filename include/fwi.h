@@ -324,6 +324,16 @@ const char* fwi_last_error(void);
  * FWI_ERR_INVALID_ARG (NULL), FWI_ERR_CUDA (no device). */
 fwi_status fwi_mem_available(size_t* bytes);
 
+/* Self-check of the bounded device wait that guards the step kernels' TMA
+ * pipelines (a wait on a copy that never lands gives up, flags the step and
+ * the call returns FWI_ERR_TIMEOUT instead of hanging the GPU): one thread on
+ * the current device waits, with a limit of `polls` polls, on an mbarrier
+ * phase that nothing completes.  Returns FWI_ERR_TIMEOUT when the wait gave
+ * up and the flag reached the host, which is the expected outcome; the
+ * device stays usable.  Host utility, no counterpart in the paper.  Errors:
+ * FWI_ERR_INVALID_ARG (polls outside [1, 2^22]), FWI_ERR_CUDA. */
+fwi_status fwi_check_bounded_wait(unsigned int polls);
+
 /* ------------------------------------------------------------------------
  * The inversion loop around the gradient (Sec. 2.3: a gradient-descent
  * optimiser steps the model after each gradient; Sec. 3.2: blocks of

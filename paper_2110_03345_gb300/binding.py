@@ -29,7 +29,8 @@ EXPORTS = ("fwi_plan_create", "fwi_plan_set_options", "fwi_plan_stats", "fwi_pla
            "fwi_forward_noalloc", "fwi_misfit_forward", "fwi_misfit_backward",
            "fwi_misfit_backward_ex",
            "fwi_batch_create", "fwi_batch_run", "fwi_batch_stats_get", "fwi_batch_destroy",
-           "fwi_mem_available", "fwi_lowpass", "fwi_vp_update", "fwi_point_weights")
+           "fwi_mem_available", "fwi_lowpass", "fwi_vp_update", "fwi_point_weights",
+           "fwi_check_bounded_wait")
 
 
 class FwiError(RuntimeError):
@@ -155,6 +156,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.fwi_batch_stats_get.restype = ctypes.c_int
         lib.fwi_batch_destroy.argtypes = [vp]
         lib.fwi_batch_destroy.restype = None
+        lib.fwi_check_bounded_wait.argtypes = [ctypes.c_uint]
+        lib.fwi_check_bounded_wait.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -175,6 +178,13 @@ def mem_available() -> int:
     n = ctypes.c_size_t(0)
     _check(load().fwi_mem_available(ctypes.byref(n)))
     return int(n.value)
+
+
+def check_bounded_wait(polls: int = 1000) -> int:
+    """fwi_check_bounded_wait: one device thread waits, `polls` polls at most,
+    on an mbarrier phase that nothing completes; returns the status
+    (FWI_ERR_TIMEOUT when the wait gave up and flagged it, as expected)."""
+    return int(load().fwi_check_bounded_wait(int(polls)))
 
 
 def make_grid(shape, spacing, order=8, sponge=20, c_ref=0.0) -> CGrid:

@@ -1,7 +1,8 @@
 """Error handling of the C ABI on a GPU: every failure is a status code and a
 message; the CUDA context stays usable afterwards.  No test faults the GPU:
-the failures are bad arguments caught on the host or values flagged by the
-model-validation kernel."""
+the failures are bad arguments caught on the host, values flagged by the
+model-validation kernel, and a bounded device wait made to give up on an
+mbarrier that nothing completes (no copy in flight)."""
 import numpy as np
 import pytest
 
@@ -135,3 +136,15 @@ def test_equal_batches():
     plan.forward(to_dev(p.vp), None, binding.Geometry(p.src_xyz, p.rec_xyz), to_dev(p.wavelet))
     s = plan.stats()
     assert s["batch"] == 8 and s["fwd_launches"] == 2 * (p.nt - 1)
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """The guard of every TMA pipeline wait: a wait that cannot complete gives
+    up after its poll limit, the flag reaches the host as FWI_ERR_TIMEOUT,
+    and the next call runs normally."""
+    assert binding.check_bounded_wait(1000) == 6   # FWI_ERR_TIMEOUT
+    assert "gave up after 1000 polls" in binding.load().fwi_last_error().decode()
+    assert binding.check_bounded_wait(0) == 1      # FWI_ERR_INVALID_ARG
+    p = _problem()
+    ref, _ = gpu_forward(p)
+    assert np.isfinite(ref).all() and np.abs(ref).max() > 0
