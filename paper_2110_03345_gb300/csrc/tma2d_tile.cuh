@@ -250,7 +250,9 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
     tma_load_3d(bf ? s_t1 : s_t0, tmap, &bar[bf], tmx, tmy, s0 + k);
     if (STG) {
       tma_load_3d(s_uo + bf * TY * QW, upmap, &bar[bf], x0 + p.ox, y0 + p.oy, s0 + k);
-      if (stg_h) tma_load_4d(s_hv + bf * TY * QW, hmap, &bar[bf], x0 + p.ox, y0 + p.oy, s0 + k, p.hstep);
+      if (stg_h)   // read once: evict first from L2
+        tma_load_4d_hint(s_hv + bf * TY * QW, hmap, &bar[bf], x0 + p.ox, y0 + p.oy, s0 + k, p.hstep,
+                         policy_evict_first());
     }
   };
   if (tid == 0) {
