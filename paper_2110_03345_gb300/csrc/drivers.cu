@@ -230,9 +230,15 @@ fwi_status launch_step(Call& c, const StepParams& p_in, bool adj) {
 cudaError_t ext_pass(const Call& c, const StepParams& p, bool adj, int mode) {
   const fwi_plan* P = c.P;
   if (c.pl.tma) {
+    // p.x with halo, p.up without, and the history fields the adjoint images with
     const CUtensorMap* map = find_map(c, p.x);
-    if (!map) return cudaErrorInvalidValue;
-    return launch_step2d_tma_ext(p, *map, P->R, c.vd, adj, mode, P->st);
+    const CUtensorMap* um = find_map(c, p.up, 1);
+    if (!map || !um) return cudaErrorInvalidValue;
+    const bool img = adj && p.image && mode != EXT_KW;
+    if (img && (!c.hmap_ok || (mode == EXT_T4 && !c.h2map_ok))) return cudaErrorInvalidValue;
+    return launch_step2d_tma_ext(p, *map, *um, img ? c.hmap : *um,
+                                 (img && mode == EXT_T4) ? c.h2map : *um, P->R, c.vd, adj, mode,
+                                 P->st);
   }
   return launch_ext(p, P->grid.ndim, P->R, c.vd, adj, mode, P->st);
 }
@@ -514,7 +520,7 @@ fwi_status begin_call(fwi_plan* P, const fwi_model* model, const fwi_geometry* g
       if (three) FWI_TRY(make_tensor_map_3d(P, buf, c.pl.B, c.pl.shape, c.pl.x2, &m.map));
       else FWI_TRY(make_tensor_map(P, buf, c.pl.B, c.pl.shape, &m.map));
       c.maps.push_back(m);
-      if (!three && !c.pl.sc.ext()) {   // the leapfrog kernels also stage u^{n-1} by TMA
+      if (!three) {   // the 2D kernels also stage u^{n-1} by TMA
         Call::MapEnt mi{buf, {}, 1};
         FWI_TRY(make_tensor_map(P, buf, c.pl.B, c.pl.shape, &mi.map, true));
         c.maps.push_back(mi);
@@ -736,10 +742,15 @@ fwi_status gradient_adjoint_batch(Call& c, int j, int shot0, int nb, const DevTa
   }
   // the 2D leapfrog adjoint reads h^k by TMA through a map of this batch's
   // history buffer (nt - 1 steps, or one segment of K)
-  c.hmap_ok = false;
-  if (c.pl.tma && P->grid.ndim == 2 && !ext) {
-    FWI_TRY(make_tensor_map_hist(P, bb.H, B, K == 0 ? std::max(nt - 1, 1) : K, c.pl.shape, &c.hmap));
+  c.hmap_ok = c.h2map_ok = false;
+  if (c.pl.tma && P->grid.ndim == 2) {
+    const int nsteps = K == 0 ? std::max(nt - 1, 1) : K;
+    FWI_TRY(make_tensor_map_hist(P, bb.H, B, nsteps, c.pl.shape, &c.hmap));
     c.hmap_ok = true;
+    if (bb.H2) {
+      FWI_TRY(make_tensor_map_hist(P, bb.H2, B, nsteps, c.pl.shape, &c.h2map));
+      c.h2map_ok = true;
+    }
   }
   for (int k = nt - 1; k >= 1; --k) {
     p.image = (k <= nt - 2) ? 1 : 0;

@@ -220,7 +220,8 @@ struct Call {
   };
   std::vector<MapEnt> maps;   // TMA descriptors of the wavefield buffers
   CUtensorMap hmap{};         // 2D TMA adjoint: the current batch's history buffer
-  bool hmap_ok = false;
+  CUtensorMap h2map{};        // and its second history field (fourth-order scheme)
+  bool hmap_ok = false, h2map_ok = false;
   std::vector<float*> fstate; // forward state besides u^n, u^{n-1} (checkpointed with them)
   int64_t launches = 0;
   int64_t fwd_launches = 0, adj_launches = 0;

@@ -59,8 +59,9 @@ template <bool ADJ, int MODE>
 __device__ __forceinline__ void ext_epilogue(const StepParams& p, int s, int pix, int xg, int yg,
                                              const float4& ax4, float ay, const float4& kk,
                                              const float4& at4, const float4& uo4, const float4& uc4,
-                                             const float4& h4, const float* cen, const float* acc,
-                                             const float* lap, const float* lc, float* gs) {
+                                             const float4& h4, const float4* h2s, const float* cen,
+                                             const float* acc, const float* lap, const float* lc,
+                                             float* gs) {
   const size_t fo = (size_t)s * p.fstride;
   float k[4], ax[4], at[4], uo[4], uc[4], h[4], h2[4], qv[4];
   unpack(kk, k);
@@ -70,8 +71,8 @@ __device__ __forceinline__ void ext_epilogue(const StepParams& p, int s, int pix
   if (MODE == EXT_T4 && ADJ) unpack(ld4(p.u + fo + pix), uc);
   else unpack(uc4, uc);
   unpack(h4, h);
-  if (MODE == EXT_T4 && ADJ && p.image)
-    unpack(__ldcs(reinterpret_cast<const float4*>(p.hist2 + fo + pix)), h2);
+  if (MODE == EXT_T4 && ADJ && p.image)   // k w^k: staged by TMA (h2s) or read here
+    unpack(h2s ? *h2s : __ldcs(reinterpret_cast<const float4*>(p.hist2 + fo + pix)), h2);
   if (MODE == EXT_ATT2) unpack(ld4(p.q + fo + pix), qv);
   bool in[4];
 #pragma unroll
@@ -155,6 +156,7 @@ template <int R, bool VD, bool ADJ, int RY, int BY, int MODE = LEAP, bool CROWD 
 __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW& wx,
                                                 const AxisW& wy, const CUtensorMap* tmap,
                                                 const CUtensorMap* upmap, const CUtensorMap* hmap,
+                                                const CUtensorMap* h2map,
                                                 int bxi, int byi, int gx, int grp,
                                                 long long samp_rank, float4* smem, uint64_t* bar) {
   using G = Geo<R, RY, BY>;
@@ -171,10 +173,14 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
   // y = 2 adjoint: the attenuation coefficient on the tile rows / columns
   float4* s_ax = smem + 2 * SH * SW + ((VD && ADJ) ? TY * SW + SH * QW : 0);
   float4* s_ay = s_ax + TY * SW;
-  // STG: u^{n-1} and h^k tiles [TY][QW] of buffers 0 / 1
+  // STG: u^{n-1}, h^k and (fourth-order adjoint) k w^k tiles [TY][QW] of
+  // buffers 0 / 1; the first pass of the fourth-order scheme stages nothing
+  constexpr bool SU = STG && MODE != EXT_KW;
+  constexpr bool SH2 = SU && MODE == EXT_T4 && ADJ;
   static_assert(G::STG_OFF(VD && ADJ, CL) % 8 == 0, "TMA destinations on 128-byte boundaries");
   float4* s_uo = smem + G::STG_OFF(VD && ADJ, CL);
   float4* s_hv = s_uo + 2 * TY * QW;
+  float4* s_h2 = s_hv + 2 * TY * QW;
   constexpr uint32_t IN_BYTES = (uint32_t)TY * QW * 16;   // one tile without halo
 
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -243,15 +249,20 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
   __syncthreads();   // barrier initialisation and the b_x / b_y tiles are visible
   // shot k of the group into buffer k & 1: its wavefield tile with halo and,
   // STG, its u^{n-1} and h^k tiles, all on the buffer's full barrier
-  const bool stg_h = STG && ADJ && p.image;
+  const bool stg_h = SU && ADJ && p.image;
+  const bool stg_h2 = SH2 && p.image;
   auto issue = [&](int k) {
     const int bf = k & 1;
-    mbar_arrive_expect_tx(&bar[bf], G::TILE_BYTES + (STG ? IN_BYTES : 0u) + (stg_h ? IN_BYTES : 0u));
+    mbar_arrive_expect_tx(&bar[bf], G::TILE_BYTES + (SU ? IN_BYTES : 0u) + (stg_h ? IN_BYTES : 0u) +
+                                        (stg_h2 ? IN_BYTES : 0u));
     tma_load_3d(bf ? s_t1 : s_t0, tmap, &bar[bf], tmx, tmy, s0 + k);
-    if (STG) {
+    if (SU) {
       tma_load_3d(s_uo + bf * TY * QW, upmap, &bar[bf], x0 + p.ox, y0 + p.oy, s0 + k);
       if (stg_h)   // read once: evict first from L2
         tma_load_4d_hint(s_hv + bf * TY * QW, hmap, &bar[bf], x0 + p.ox, y0 + p.oy, s0 + k, p.hstep,
+                         policy_evict_first());
+      if (stg_h2)
+        tma_load_4d_hint(s_h2 + bf * TY * QW, h2map, &bar[bf], x0 + p.ox, y0 + p.oy, s0 + k, p.hstep,
                          policy_evict_first());
     }
   };
@@ -282,8 +293,8 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
     float4 bxf[VD && !ADJ ? RY : 1], byf[VD && !ADJ ? RY : 1];
 #pragma unroll
     for (int iy = 0; iy < RY; ++iy) {
-      if (!STG && MODE != EXT_KW) uo[iy] = ld4(up_s + pix[iy]);
-      if (!STG && ADJ && MODE != EXT_KW && p.image)
+      if (!SU && MODE != EXT_KW) uo[iy] = ld4(up_s + pix[iy]);
+      if (!SU && ADJ && MODE != EXT_KW && p.image)
         hv[iy] = __ldcs(reinterpret_cast<const float4*>(h_s + pix[iy]));
       if (T4 && !ADJ) uc[iy] = ld4(p.u + (size_t)s * p.fstride + pix[iy]);
       if (VD && !ADJ) {
@@ -471,14 +482,18 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
         }
       }
       if (MODE != LEAP) {
+        const int so = buf * TY * QW + ly * QW + tx;   // this thread's float4 in a staged tile
+        const float4 uoe = SU ? s_uo[so] : uo[iy];
+        const float4 hve = (SU && ADJ && MODE != EXT_KW) ? s_hv[so]
+                           : ((ADJ && MODE != EXT_KW) ? hv[iy] : uo[iy]);
         ext_epilogue<ADJ, MODE>(p, s, pix[iy], xg, yg, ax4, ay[iy], kk[iy],
-                                AT ? atv[iy] : make_float4(0.f, 0.f, 0.f, 0.f), uo[iy],
-                                T4 ? uc[iy] : uo[iy], (ADJ && MODE != EXT_KW) ? hv[iy] : uo[iy],
-                                v + 4 * NL, acc, LAPF ? lapx : acc, CL ? lc : acc, gs[iy]);
+                                AT ? atv[iy] : make_float4(0.f, 0.f, 0.f, 0.f), uoe,
+                                T4 ? uc[iy] : uo[iy], hve, SH2 ? s_h2 + so : nullptr, v + 4 * NL,
+                                acc, LAPF ? lapx : acc, CL ? lc : acc, gs[iy]);
         continue;
       }
       float* upp = up_s + pix[iy];
-      const float4 uoi = STG ? s_uo[buf * TY * QW + ly * QW + tx] : uo[iy];
+      const float4 uoi = SU ? s_uo[buf * TY * QW + ly * QW + tx] : uo[iy];
       float res[4], upd[4];
 #pragma unroll
       for (int ix = 0; ix < 4; ++ix) {
@@ -496,7 +511,7 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
           __stcs(reinterpret_cast<float4*>(h_s + pix[iy]),
                  make_float4(upd[0], upd[1], upd[2], upd[3]));
       } else if (p.image) {
-        const float4 hvi = STG ? s_hv[buf * TY * QW + ly * QW + tx] : hv[iy];
+        const float4 hvi = SU ? s_hv[buf * TY * QW + ly * QW + tx] : hv[iy];
         gs[iy][0] = fmaf(v[4 * NL + 0], hvi.x, gs[iy][0]);
         gs[iy][1] = fmaf(v[4 * NL + 1], hvi.y, gs[iy][1]);
         gs[iy][2] = fmaf(v[4 * NL + 2], hvi.z, gs[iy][2]);
@@ -538,7 +553,9 @@ template <int R, bool VD, bool ADJ, int RY, int BY, int MODE = LEAP, bool STG = 
 constexpr size_t smem_bytes() {
   using G = Geo<R, RY, BY>;
   size_t n = G::STG_OFF(VD && ADJ, MODE == EXT_ATT2 && ADJ);
-  if (STG) n += (size_t)(ADJ ? 4 : 2) * G::TY * G::QW;   // u^{n-1} (and h^k) tiles, two buffers
+  // u^{n-1} (and h^k, and the fourth-order adjoint's k w^k) tiles, two buffers
+  if (STG && MODE != EXT_KW)
+    n += (size_t)(ADJ ? (MODE == EXT_T4 ? 6 : 4) : 2) * G::TY * G::QW;
   return n * sizeof(float4);
 }
 
