@@ -233,12 +233,13 @@ cudaError_t ext_pass(const Call& c, const StepParams& p, bool adj, int mode) {
     // p.x with halo, p.up without, and the history fields the adjoint images with
     const CUtensorMap* map = find_map(c, p.x);
     const CUtensorMap* um = find_map(c, p.up, 1);
-    if (!map || !um) return cudaErrorInvalidValue;
+    const CUtensorMap* ucm = find_map(c, p.u, 1);
+    if (!map || !um || !ucm) return cudaErrorInvalidValue;
     const bool img = adj && p.image && mode != EXT_KW;
     if (img && (!c.hmap_ok || (mode == EXT_T4 && !c.h2map_ok))) return cudaErrorInvalidValue;
     return launch_step2d_tma_ext(p, *map, *um, img ? c.hmap : *um,
-                                 (img && mode == EXT_T4) ? c.h2map : *um, P->R, c.vd, adj, mode,
-                                 P->st);
+                                 (img && mode == EXT_T4) ? c.h2map : *um, *ucm, P->R, c.vd, adj,
+                                 mode, P->st);
   }
   return launch_ext(p, P->grid.ndim, P->R, c.vd, adj, mode, P->st);
 }

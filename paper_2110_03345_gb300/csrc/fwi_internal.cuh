@@ -251,12 +251,12 @@ void tma_box2d_interior(int tile, int* bx, int* by);
 // The extended schemes' 2D kernels on the same pipeline (kernels2d_tma_ext.cu):
 // mode = EXT_KW / EXT_T4 / EXT_ATT0 / EXT_ATT2, map = the tensor map of the
 // stencil input p.x for tile shape 1 (128 x 16), um of p.up without halo, hm
-// / h2m of the history fields (read by the adjoint when p.image), p.S shots
-// per CTA.
+// / h2m of the history fields (read by the adjoint when p.image), ucm of
+// p.u without halo (read by the fourth-order update), p.S shots per CTA.
 cudaError_t launch_step2d_tma_ext(const StepParams& p, const CUtensorMap& map,
                                   const CUtensorMap& um, const CUtensorMap& hm,
-                                  const CUtensorMap& h2m, int R, bool vd, bool adj, int mode,
-                                  cudaStream_t st);
+                                  const CUtensorMap& h2m, const CUtensorMap& ucm, int R, bool vd,
+                                  bool adj, int mode, cudaStream_t st);
 size_t step3d_smem(int R, bool vd, bool adj, int tile);
 // TMA-staged 3D kernels (kernels3d_tma.cu): um maps the wavefield buffer p.u
 // as (x, y, z, slot); bxm / bym map the b_x / b_y fields (variable-density

@@ -34,7 +34,7 @@ k_step2d_tma(const StepParams p, const __grid_constant__ CUtensorMap tmap,
   __shared__ uint64_t bar[4];
   const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   step2d_tma_tile<R, VD, ADJ, RY, BY, LEAP, CROWD, true>(p, p.wx, p.wy, &tmap, &upmap, &hmap,
-                                                         nullptr, blockIdx.x, blockIdx.y,
+                                                         nullptr, nullptr, blockIdx.x, blockIdx.y,
                                                          gridDim.x, blockIdx.z, blk, smem, bar);
 }
 
@@ -71,7 +71,7 @@ k_step2d_tma_multi(const MultiDesc* __restrict__ descs, const MultiUnit* __restr
   __syncthreads();
   const CUtensorMap* map = (n & 1) ? &d->map1 : &d->map0;
   step2d_tma_tile<R, VD, false, RY, BY>(sp, UW ? wx : sp.wx, UW ? wy : sp.wy, map, nullptr, nullptr,
-                                        nullptr, un.tx, un.ty,
+                                        nullptr, nullptr, un.tx, un.ty,
                                         d->gx, un.slot, un.rank, smem, bar);
 }
 

@@ -22,13 +22,14 @@ template <int R, bool VD, bool ADJ, int MODE>
 __global__ void __launch_bounds__(32 * EXT_BY, 2)
 k_step2d_tma_ext(const StepParams p, const __grid_constant__ CUtensorMap tmap,
                  const __grid_constant__ CUtensorMap upmap, const __grid_constant__ CUtensorMap hmap,
-                 const __grid_constant__ CUtensorMap h2map) {
+                 const __grid_constant__ CUtensorMap h2map,
+                 const __grid_constant__ CUtensorMap ucmap) {
   pdl_trigger();
   extern __shared__ __align__(128) float4 smem[];
   __shared__ uint64_t bar[4];
   const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   step2d_tma_tile<R, VD, ADJ, 1, EXT_BY, MODE, false, true>(p, p.wx, p.wy, &tmap, &upmap, &hmap,
-                                                            &h2map, blockIdx.x, blockIdx.y,
+                                                            &h2map, &ucmap, blockIdx.x, blockIdx.y,
                                                             gridDim.x, blockIdx.z, blk, smem, bar);
 }
 
@@ -48,7 +49,7 @@ cudaError_t launch_e(const StepParams& p, const CUtensorMap* const* maps, cudaSt
   }
   dim3 grid((p.nx + TILE_X - 1) / TILE_X, (p.ny + EXT_BY - 1) / EXT_BY, (p.B + p.S - 1) / p.S);
   return launch_pdl(k_step2d_tma_ext<R, VD, ADJ, MODE>, grid, dim3(32, EXT_BY), smem, st, p,
-                    *maps[0], *maps[1], *maps[2], *maps[3]);
+                    *maps[0], *maps[1], *maps[2], *maps[3], *maps[4]);
 }
 
 template <int R, bool VD, bool ADJ>
@@ -66,12 +67,13 @@ cudaError_t launch_mode(const StepParams& p, const CUtensorMap* const* maps, int
 
 // maps: the stencil input p.x with halo, p.up without halo, the history and
 // the second history field (4D, step p.hstep; read only by the adjoint when
-// p.image); tile variant 1 of tile2_tma_variant (128 x 16 points).
+// p.image), p.u without halo (fourth-order update); tile variant 1 of
+// tile2_tma_variant (128 x 16 points).
 cudaError_t launch_step2d_tma_ext(const StepParams& p, const CUtensorMap& map,
                                   const CUtensorMap& um, const CUtensorMap& hm,
-                                  const CUtensorMap& h2m, int R, bool vd, bool adj, int mode,
-                                  cudaStream_t st) {
-  const CUtensorMap* maps[4] = {&map, &um, &hm, &h2m};
+                                  const CUtensorMap& h2m, const CUtensorMap& ucm, int R, bool vd,
+                                  bool adj, int mode, cudaStream_t st) {
+  const CUtensorMap* maps[5] = {&map, &um, &hm, &h2m, &ucm};
   if (R == 4) {
     if (vd) return adj ? launch_mode<4, true, true>(p, maps, mode, st) : launch_mode<4, true, false>(p, maps, mode, st);
     return adj ? launch_mode<4, false, true>(p, maps, mode, st) : launch_mode<4, false, false>(p, maps, mode, st);

@@ -59,7 +59,8 @@ template <bool ADJ, int MODE>
 __device__ __forceinline__ void ext_epilogue(const StepParams& p, int s, int pix, int xg, int yg,
                                              const float4& ax4, float ay, const float4& kk,
                                              const float4& at4, const float4& uo4, const float4& uc4,
-                                             const float4& h4, const float4* h2s, const float* cen,
+                                             const float4& h4, const float4* h2s,
+                                             const float4* ucs, const float* cen,
                                              const float* acc, const float* lap, const float* lc,
                                              float* gs) {
   const size_t fo = (size_t)s * p.fstride;
@@ -68,7 +69,8 @@ __device__ __forceinline__ void ext_epilogue(const StepParams& p, int s, int pix
   unpack(ax4, ax);
   unpack(at4, at);
   unpack(uo4, uo);
-  if (MODE == EXT_T4 && ADJ) unpack(ld4(p.u + fo + pix), uc);
+  if (ucs) unpack(*ucs, uc);   // u^n (lambda^k) staged by TMA
+  else if (MODE == EXT_T4 && ADJ) unpack(ld4(p.u + fo + pix), uc);
   else unpack(uc4, uc);
   unpack(h4, h);
   if (MODE == EXT_T4 && ADJ && p.image)   // k w^k: staged by TMA (h2s) or read here
@@ -156,7 +158,7 @@ template <int R, bool VD, bool ADJ, int RY, int BY, int MODE = LEAP, bool CROWD 
 __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW& wx,
                                                 const AxisW& wy, const CUtensorMap* tmap,
                                                 const CUtensorMap* upmap, const CUtensorMap* hmap,
-                                                const CUtensorMap* h2map,
+                                                const CUtensorMap* h2map, const CUtensorMap* ucmap,
                                                 int bxi, int byi, int gx, int grp,
                                                 long long samp_rank, float4* smem, uint64_t* bar) {
   using G = Geo<R, RY, BY>;
@@ -177,10 +179,12 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
   // buffers 0 / 1; the first pass of the fourth-order scheme stages nothing
   constexpr bool SU = STG && MODE != EXT_KW;
   constexpr bool SH2 = SU && MODE == EXT_T4 && ADJ;
+  constexpr bool SUC = SU && MODE == EXT_T4;   // u^n (lambda^k) of the fourth-order update
   static_assert(G::STG_OFF(VD && ADJ, CL) % 8 == 0, "TMA destinations on 128-byte boundaries");
   float4* s_uo = smem + G::STG_OFF(VD && ADJ, CL);
   float4* s_hv = s_uo + 2 * TY * QW;
   float4* s_h2 = s_hv + 2 * TY * QW;
+  float4* s_uc = s_h2 + 2 * TY * QW;
   constexpr uint32_t IN_BYTES = (uint32_t)TY * QW * 16;   // one tile without halo
 
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -254,7 +258,7 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
   auto issue = [&](int k) {
     const int bf = k & 1;
     mbar_arrive_expect_tx(&bar[bf], G::TILE_BYTES + (SU ? IN_BYTES : 0u) + (stg_h ? IN_BYTES : 0u) +
-                                        (stg_h2 ? IN_BYTES : 0u));
+                                        (stg_h2 ? IN_BYTES : 0u) + (SUC ? IN_BYTES : 0u));
     tma_load_3d(bf ? s_t1 : s_t0, tmap, &bar[bf], tmx, tmy, s0 + k);
     if (SU) {
       tma_load_3d(s_uo + bf * TY * QW, upmap, &bar[bf], x0 + p.ox, y0 + p.oy, s0 + k);
@@ -264,6 +268,7 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
       if (stg_h2)
         tma_load_4d_hint(s_h2 + bf * TY * QW, h2map, &bar[bf], x0 + p.ox, y0 + p.oy, s0 + k, p.hstep,
                          policy_evict_first());
+      if (SUC) tma_load_3d(s_uc + bf * TY * QW, ucmap, &bar[bf], x0 + p.ox, y0 + p.oy, s0 + k);
     }
   };
   if (tid == 0) {
@@ -296,7 +301,7 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
       if (!SU && MODE != EXT_KW) uo[iy] = ld4(up_s + pix[iy]);
       if (!SU && ADJ && MODE != EXT_KW && p.image)
         hv[iy] = __ldcs(reinterpret_cast<const float4*>(h_s + pix[iy]));
-      if (T4 && !ADJ) uc[iy] = ld4(p.u + (size_t)s * p.fstride + pix[iy]);
+      if (T4 && !ADJ && !SUC) uc[iy] = ld4(p.u + (size_t)s * p.fstride + pix[iy]);
       if (VD && !ADJ) {
         bxf[iy] = ldg4(p.bx + pix[iy]);
         byf[iy] = ldg4(p.by + pix[iy]);
@@ -488,7 +493,8 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
                            : ((ADJ && MODE != EXT_KW) ? hv[iy] : uo[iy]);
         ext_epilogue<ADJ, MODE>(p, s, pix[iy], xg, yg, ax4, ay[iy], kk[iy],
                                 AT ? atv[iy] : make_float4(0.f, 0.f, 0.f, 0.f), uoe,
-                                T4 ? uc[iy] : uo[iy], hve, SH2 ? s_h2 + so : nullptr, v + 4 * NL,
+                                T4 ? uc[iy] : uo[iy], hve, SH2 ? s_h2 + so : nullptr,
+                                SUC ? s_uc + so : nullptr, v + 4 * NL,
                                 acc, LAPF ? lapx : acc, CL ? lc : acc, gs[iy]);
         continue;
       }
@@ -554,8 +560,9 @@ constexpr size_t smem_bytes() {
   using G = Geo<R, RY, BY>;
   size_t n = G::STG_OFF(VD && ADJ, MODE == EXT_ATT2 && ADJ);
   // u^{n-1} (and h^k, and the fourth-order adjoint's k w^k) tiles, two buffers
+  // (fourth order: u^{n-1}, h^k, k w^k and u^n slots in both directions)
   if (STG && MODE != EXT_KW)
-    n += (size_t)(ADJ ? (MODE == EXT_T4 ? 6 : 4) : 2) * G::TY * G::QW;
+    n += (size_t)(MODE == EXT_T4 ? 8 : (ADJ ? 4 : 2)) * G::TY * G::QW;
   return n * sizeof(float4);
 }
 
