@@ -120,9 +120,16 @@ def test_config3_fullsize_fd_four_shots():
     """The 256^3 skull at full size (0.25 mm, 10th order, variable density,
     512 receivers, 2000 steps, K = 64 checkpoints through the autograd
     Function) with 4 of its 32 shots spread over the sphere: central
-    differences (4-point, h = 0.1 m_i, misfit in FP64) at the 8 soft-tissue
+    differences (4-point, h = 0.2 m_i, misfit in FP64) at the 8 soft-tissue
     voxels against the autograd gradient, per voxel within 1e-2 of its own
-    value where the gradient is within 10x of the largest."""
+    value where the gradient is within 10x of the largest.
+
+    Step size: the FP32 rounding noise of a misfit difference is absolute, so
+    it enters the difference as 1/h.  At the soft-tissue voxel with a
+    gradient of -294 (7x below the largest) the 4-point difference is off by
+    86, 21, 7 and 2.6 at h = 0.025, 0.05, 0.1 and 0.2 m_i, while at the
+    larger voxels h = 0.2 m_i agrees with the gradient to 1e-4 - 5e-4: the
+    truncation error is still far below the noise there."""
     p = inputs.config_skull_3d(shots=[0, 128, 256, 384])
     K = math.ceil(math.sqrt(2 * p.nt))
     plan = gpu_plan(p, ckpt_every=K)
@@ -130,7 +137,7 @@ def test_config3_fullsize_fd_four_shots():
     rho, wav = to_dev(p.rho), to_dev(p.wavelet)
     obs = plan.forward(to_dev(p.vp_true), rho, geo, wav)
     vox = soft_tissue_voxels(p)
-    J, g, fd = fd_check(p, plan, obs, vox, rho, geo, wav, rel_h=1e-1, points=4)
+    J, g, fd = fd_check(p, plan, obs, vox, rho, geo, wav, rel_h=2e-1, points=4)
     gv = np.array([g[v] for v in vox])
     err = np.abs(fd - gv) / np.abs(gv)
     print("256^3, 4 shots: FD vs autograd per voxel", np.round(err, 5), "gradients", gv)
@@ -143,7 +150,8 @@ def test_config3_fullsize_fd_four_shots():
                     reason="full 256^3 x 2000 x 32-shot run: set FWI_FULL_CONFIG3=1")
 def test_config3_fullsize_fd():
     """Full size: 256^3 at 0.25 mm, 10th order, 32 shots x 2000 steps, K = 64
-    checkpoints through the autograd Function; FD at 8 voxels."""
+    checkpoints through the autograd Function; FD at 8 voxels (h = 0.2 m_i,
+    as in the 4-shot test)."""
     p = inputs.config_skull_3d()
     K = math.ceil(math.sqrt(2 * p.nt))
     plan = gpu_plan(p, ckpt_every=K)
@@ -151,7 +159,7 @@ def test_config3_fullsize_fd():
     rho, wav = to_dev(p.rho), to_dev(p.wavelet)
     obs = plan.forward(to_dev(p.vp_true), rho, geo, wav)
     vox = soft_tissue_voxels(p)
-    J, g, fd = fd_check(p, plan, obs, vox, rho, geo, wav, rel_h=1e-1, points=4)
+    J, g, fd = fd_check(p, plan, obs, vox, rho, geo, wav, rel_h=2e-1, points=4)
     gv = np.array([g[v] for v in vox])
     print("fullsize fd vs autograd: max", (np.abs(fd - gv) / np.abs(gv)).max(), "rel L2",
           np.linalg.norm(fd - gv) / np.linalg.norm(gv))
