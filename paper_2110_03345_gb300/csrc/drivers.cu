@@ -74,6 +74,29 @@ fwi_status make_tensor_map_hist(const fwi_plan* P, const float* base, int nslots
   return FWI_OK;
 }
 
+// 5D tensor map over a 3D history buffer of nsteps x nslots padded fields:
+// dims (x, y, z, slot, step), box = box_w x box_h of one plane.
+fwi_status make_tensor_map_hist3d(const fwi_plan* P, const float* base, int nslots, int nsteps,
+                                  int box_w, int box_h, CUtensorMap* out) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  const cuuint64_t dims[5] = {(cuuint64_t)P->L.sx, (cuuint64_t)P->L.rows, (cuuint64_t)P->L.planes,
+                              (cuuint64_t)nslots, (cuuint64_t)nsteps};
+  const cuuint64_t strides[4] = {(cuuint64_t)P->L.sx * sizeof(float),
+                                 (cuuint64_t)P->L.sxy * sizeof(float),
+                                 (cuuint64_t)P->L.fstride * sizeof(float),
+                                 (cuuint64_t)P->L.fstride * nslots * sizeof(float)};
+  const cuuint32_t box[5] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1u, 1u, 1u};
+  const cuuint32_t estr[5] = {1u, 1u, 1u, 1u, 1u};
+  const CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<float*>(base), dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled (3D history) failed with code " + std::to_string((int)r));
+  return FWI_OK;
+}
+
 // 4D tensor map over nslots padded 3D fields: dims (x, y, z, slot); box = a
 // 48-float-wide (80 for the two-point kernels) x-y tile (16-byte aligned
 // start) with its y halo, one plane.
@@ -194,7 +217,16 @@ fwi_status launch_step(Call& c, const StepParams& p_in, bool adj) {
     const CUtensorMap* bxm = c.vd ? find_map(c, c.W.bx) : map;
     const CUtensorMap* bym = c.vd ? find_map(c, c.W.by) : map;
     if (!bxm || !bym) return fail(FWI_ERR_INVALID_ARG, "internal: no tensor map for b_x / b_y");
-    e = c.pl.x2 ? launch_step3d_x2(p, *map, *bxm, *bym, P->R, c.vd, adj, c.pl.shape, P->st)
+    // the two-point variable-density adjoint's operand maps (others ignore them)
+    const bool ops = c.pl.x2 && c.vd && adj;
+    const CUtensorMap* upm = ops ? find_map(c, p.up, 1) : map;
+    const CUtensorMap* kfm = ops ? find_map(c, c.W.kf, 1) : map;
+    const CUtensorMap* gm = ops ? find_map(c, c.W.G, 1) : map;
+    if (!upm || !kfm || !gm || (ops && p.image && !c.hmap_ok))
+      return fail(FWI_ERR_INVALID_ARG, "internal: no tensor map for the 3D adjoint's operands");
+    const CUtensorMap* hm = (ops && p.image) ? &c.hmap : map;
+    e = c.pl.x2 ? launch_step3d_x2(p, *map, *bxm, *bym, *upm, *kfm, *gm, *hm, P->R, c.vd, adj,
+                                   c.pl.shape, P->st)
                 : launch_step3d_tma(p, *map, *bxm, *bym, P->R, c.vd, adj, c.pl.shape, P->st);
   } else if (P->grid.ndim == 3) e = launch_step3d(p, P->R, c.vd, adj, c.pl.shape, P->st);
   else if (c.pl.tma) {
@@ -527,6 +559,23 @@ fwi_status begin_call(fwi_plan* P, const fwi_model* model, const fwi_geometry* g
         c.maps.push_back(mi);
       }
     }
+    if (three && c.vd && c.pl.x2 && c.pl.gradient) {
+      // the two-point variable-density adjoint reads lambda^{k+1}, k and g by
+      // TMA in 64 x BY plane tiles
+      const int by = tile3_variant(c.pl.shape).by;
+      for (float* buf : {c.W.U0, c.W.U1, c.W.F0, c.W.F1}) {
+        if (!buf) continue;
+        Call::MapEnt m{buf, {}, 1};
+        FWI_TRY(make_tensor_map_3d(P, buf, c.pl.B, c.pl.shape, true, &m.map, 64, by));
+        c.maps.push_back(m);
+      }
+      Call::MapEnt mk{c.W.kf, {}, 1};
+      FWI_TRY(make_tensor_map_3d(P, c.W.kf, 1, c.pl.shape, true, &mk.map, 64, by));
+      c.maps.push_back(mk);
+      Call::MapEnt mg{c.W.G, {}, 1};
+      FWI_TRY(make_tensor_map_3d(P, c.W.G, c.pl.B, c.pl.shape, true, &mg.map, 64, by));
+      c.maps.push_back(mg);
+    }
     if (three && c.vd) {
       // the two-point kernels stage b_x on the tile rows (80 x BY) and b_y on
       // the tile columns (64 x BY + 2R); the one-point kernels whole planes
@@ -744,6 +793,11 @@ fwi_status gradient_adjoint_batch(Call& c, int j, int shot0, int nb, const DevTa
   // the 2D leapfrog adjoint reads h^k by TMA through a map of this batch's
   // history buffer (nt - 1 steps, or one segment of K)
   c.hmap_ok = c.h2map_ok = false;
+  if (c.pl.tma && P->grid.ndim == 3 && c.pl.x2 && c.vd && !ext) {
+    FWI_TRY(make_tensor_map_hist3d(P, bb.H, B, K == 0 ? std::max(nt - 1, 1) : K, 64,
+                                   tile3_variant(c.pl.shape).by, &c.hmap));
+    c.hmap_ok = true;
+  }
   if (c.pl.tma && P->grid.ndim == 2) {
     const int nsteps = K == 0 ? std::max(nt - 1, 1) : K;
     FWI_TRY(make_tensor_map_hist(P, bb.H, B, nsteps, c.pl.shape, &c.hmap));

@@ -308,6 +308,10 @@ fwi_status check_on_device(const void* ptr, const char* name, int dev);
 // buffer of nsteps x nslots fields, box = one tile without halo
 fwi_status make_tensor_map_hist(const fwi_plan* P, const float* base, int nslots, int nsteps,
                                 int shape, CUtensorMap* out);
+// a 3D history buffer of nsteps x nslots fields: (x, y, z, slot, step), box
+// box_w x box_h x 1 x 1 x 1
+fwi_status make_tensor_map_hist3d(const fwi_plan* P, const float* base, int nslots, int nsteps,
+                                  int box_w, int box_h, CUtensorMap* out);
 fwi_status make_tensor_map(const fwi_plan* P, const float* base, int nslots, int shape,
                            CUtensorMap* out, bool interior = false);
 // box_w / box_h > 0 override the box's x extent and rows

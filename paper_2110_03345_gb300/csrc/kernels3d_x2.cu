@@ -17,7 +17,8 @@
 //    4D TMA copies into a ring of R+1+PF planes (the centre, the R planes up
 //    to the lead, PF planes in flight); the variable-density adjoint streams
 //    b_x on the tile rows and b_y on the tile columns through a second,
-//    four-stage ring (two trips).
+//    four-stage ring (two trips), and its per-plane operands (lambda^{k+1},
+//    k, h^k, g) through a third, so that no register holds them ahead.
 // Every mbarrier wait is bounded: on time-out the error flag is set and the
 // kernel carries on, so no thread skips a barrier.
 #include "fwi_internal.cuh"
@@ -57,12 +58,18 @@ struct GeoX2 {
   static constexpr int BYB = TXP * BYH;
   static constexpr int BSTAGE = BXB + BYB;
   static constexpr uint32_t BSTAGE_BYTES = BSTAGE * 4;
+  // variable-density adjoint: a stage of per-plane operands holds the
+  // column's lambda^{k+1}, k, h^k and g tiles (64 x BY each)
+  static constexpr int OPT = TXP * BY;
+  static constexpr int NOS = 4;             // operand stages: two loop trips
 };
 
 template <int R, bool VD, bool ADJ, int BY>
 __global__ void __launch_bounds__(32 * BY, ((VD && ADJ) ? 512 : 768) / (32 * BY))
 k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
-            const __grid_constant__ CUtensorMap bxmap, const __grid_constant__ CUtensorMap bymap) {
+            const __grid_constant__ CUtensorMap bxmap, const __grid_constant__ CUtensorMap bymap,
+            const __grid_constant__ CUtensorMap opup, const __grid_constant__ CUtensorMap opkf,
+            const __grid_constant__ CUtensorMap opg, const __grid_constant__ CUtensorMap oph) {
   pdl_trigger();
   using G = GeoX2<R, BY, VD && ADJ>;
   constexpr int TY = BY;
@@ -76,8 +83,11 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
   float* ring = smem3x;                       // [NSU][BYH][BXW]
   constexpr int NBS = 4;                      // b stages: two loop trips of two planes
   float* bring = ring + NSU * G::PLANE;       // PSI: [NBS stages][b_x [BY][BXW], b_y [BYH][TXP]]
+  constexpr int NOS = G::NOS;
+  float* ops = bring + NBS * G::BSTAGE;       // PSI: [NOS stages][lambda^{k+1}, k, h, g][BY][TXP]
   __shared__ uint64_t bar[NSU];
   __shared__ uint64_t bbar[NBS];
+  __shared__ uint64_t obar[NOS];
   __shared__ int s_pe[MAX_ZCHUNK + 1];        // first source entry of each plane of the chunk
 
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -100,6 +110,7 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
   if (tid == 0) {
     for (int k = 0; k < NSU; ++k) mbar_init(&bar[k], 1);
     for (int k = 0; k < NBS; ++k) mbar_init(&bbar[k], 1);
+    for (int k = 0; k < NOS; ++k) mbar_init(&obar[k], 1);
     fence_mbar_init();
   }
   // Source entries of the tile are sorted by tile-local index, which grows
@@ -132,7 +143,24 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
   }
   if (nz_c <= 0) return;
   __syncthreads();
+  // PSI: the operands of plane ii of the chunk into operand stage ii % NOS
+  const bool img = ADJ && p.image;
+  auto issue_ops = [&](int ii) {
+    const int st = ii % NOS;
+    float* o = ops + st * 4 * G::OPT;
+    const int xx = x0 + p.ox, yy = y0 + p.oy, zz = z0 + ii + p.oz;
+    mbar_arrive_expect_tx(&obar[st], (uint32_t)G::OPT * 4u * (img ? 4u : 2u));
+    tma_load_4d(o, &opup, &obar[st], xx, yy, zz, b);
+    tma_load_4d(o + G::OPT, &opkf, &obar[st], xx, yy, zz, 0);
+    if (img) {   // h^k is read once: evict first from L2
+      tma_load_5d_hint(o + 2 * G::OPT, &oph, &obar[st], xx, yy, zz, b, p.hstep,
+                       policy_evict_first());
+      tma_load_4d(o + 3 * G::OPT, &opg, &obar[st], xx, yy, zz, b);
+    }
+  };
   if (tid == 0) {
+    if (PSI)
+      for (int ii = 0; ii < NOS && ii < nz_c; ++ii) issue_ops(ii);
     for (int lp = 0; lp < NSU && lp < nplanes; ++lp) {
       mbar_arrive_expect_tx(&bar[lp], G::PLANE_BYTES);
       tma_load_4d(ring + lp * G::PLANE, &umap, &bar[lp], tmx, tmy, pz0 + lp, b);
@@ -200,6 +228,10 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
     Ops o{z2, z2, z2, z2, z2, z2, z2, z2, 0.f};
     o.sz = __ldg(p.spz + z0 + ii);
     const long long id = (long long)(z0 + ii + p.oz) * p.sxy + col;
+    if (PSI) {   // lambda^{k+1}, k, h, g come from the operand stages
+      o.bzl = ldg2(p.bz + (long long)(pz0 + ii + 2 * R) * p.sxy + col);
+      return o;
+    }
     o.uo = *reinterpret_cast<const float2*>(p.up + fo + id);
     o.kk = ldg2(p.kf + id);
     if (ADJ && p.image) {
@@ -322,10 +354,21 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
               acc.y = fmaf(p.inj_w[e], p.vals[p.inj_vidx[e] + p.step_off], acc.y);
           }
         }
+        float2 uo = cur.uo, kk = cur.kk, hv = cur.hv, gv = cur.gv;
+        if (PSI) {   // this plane's operand stage
+          if (!mbar_wait_bounded(&obar[i % NOS], (uint32_t)((i / NOS) & 1))) timed_out = true;
+          const float* o = ops + (i % NOS) * 4 * G::OPT + ty * G::TXP + 2 * tx;
+          uo = lds2(o);
+          kk = lds2(o + G::OPT);
+          if (img) {
+            hv = lds2(o + 2 * G::OPT);
+            gv = lds2(o + 3 * G::OPT);
+          }
+        }
         const float sz_ = cur.sz;
         const float2 a = make_float2(axy.x + sz_, axy.y + sz_);
-        const float2 h = __fmul2_rn(cur.kk, acc);
-        float2 t = __ffma2_rn(make_float2(-(1.f - a.x), -(1.f - a.y)), cur.uo,
+        const float2 h = __fmul2_rn(kk, acc);
+        float2 t = __ffma2_rn(make_float2(-(1.f - a.x), -(1.f - a.y)), uo,
                               make_float2(2.f * cen.x, 2.f * cen.y));
         t = __fadd2_rn(t, h);
         const float2 r = __fmul2_rn(t, make_float2(__frcp_rn(1.f + a.x), __frcp_rn(1.f + a.y)));
@@ -334,14 +377,14 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
           if (!ADJ) {
             if (p.hist) __stcs(reinterpret_cast<float2*>(p.hist + fo + idx), h);
           } else if (p.image) {
-            *reinterpret_cast<float2*>(p.g + fo + idx) = __ffma2_rn(neg2(cen), cur.hv, cur.gv);
+            *reinterpret_cast<float2*>(p.g + fo + idx) = __ffma2_rn(neg2(cen), hv, gv);
           }
         } else if (in0) {
           p.up[fo + idx] = r.x;
           if (!ADJ) {
             if (p.hist) __stcs(p.hist + fo + idx, h.x);
           } else if (p.image) {
-            p.g[fo + idx] = fmaf(-cen.x, cur.hv.x, cur.gv.x);
+            p.g[fo + idx] = fmaf(-cen.x, hv.x, gv.x);
           }
         }
       }
@@ -360,6 +403,10 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&bar[k], G::PLANE_BYTES);
             tma_load_4d(ring + k * G::PLANE, &umap, &bar[k], tmx, tmy, pz0 + nx_, b);
+          }
+          if (PSI && i + NOS < nz_c) {   // the stage of plane i takes plane i + NOS
+            fence_proxy_async_smem();
+            issue_ops(i + NOS);
           }
           if (PSI && i + NBS < nz_c) {
             const int st = i % NBS;
@@ -386,13 +433,13 @@ template <int R, bool VD, bool ADJ, int BY>
 constexpr size_t smem_bytes_x2() {
   using G = GeoX2<R, BY, VD && ADJ>;
   size_t n = (size_t)G::NSU * G::PLANE;
-  if (VD && ADJ) n += 4 * (size_t)G::BSTAGE;   // NBS = 4 stages of b_x, b_y
+  if (VD && ADJ) n += 4 * (size_t)G::BSTAGE + (size_t)G::NOS * 4 * G::OPT;   // b and operand stages
   return n * sizeof(float);
 }
 
 template <int R, bool VD, bool ADJ, int BY>
 cudaError_t launch_t(const StepParams& p, const CUtensorMap& um, const CUtensorMap& bxm,
-                     const CUtensorMap& bym, cudaStream_t st) {
+                     const CUtensorMap& bym, const CUtensorMap* const* om, cudaStream_t st) {
   constexpr size_t smem = smem_bytes_x2<R, VD, ADJ, BY>();
   static bool attr_set = false;
   if (!attr_set) {
@@ -406,31 +453,36 @@ cudaError_t launch_t(const StepParams& p, const CUtensorMap& um, const CUtensorM
     attr_set = true;
   }
   dim3 grid((p.nx + 63) / 64, (p.ny + BY - 1) / BY, p.B * p.nzc);
-  return launch_pdl(k_step3d_x2<R, VD, ADJ, BY>, grid, dim3(32, BY), smem, st, p, um, bxm, bym);
+  return launch_pdl(k_step3d_x2<R, VD, ADJ, BY>, grid, dim3(32, BY), smem, st, p, um, bxm, bym,
+                    *om[0], *om[1], *om[2], *om[3]);
 }
 
 template <int R, bool VD, bool ADJ>
 cudaError_t launch_tile(const StepParams& p, const CUtensorMap& um, const CUtensorMap& bxm,
-                        const CUtensorMap& bym, int tile, cudaStream_t st) {
-  return tile3_variant(tile).by == 8 ? launch_t<R, VD, ADJ, 8>(p, um, bxm, bym, st)
-                                     : launch_t<R, VD, ADJ, 16>(p, um, bxm, bym, st);
+                        const CUtensorMap& bym, const CUtensorMap* const* om, int tile,
+                        cudaStream_t st) {
+  return tile3_variant(tile).by == 8 ? launch_t<R, VD, ADJ, 8>(p, um, bxm, bym, om, st)
+                                     : launch_t<R, VD, ADJ, 16>(p, um, bxm, bym, om, st);
 }
 
 }  // namespace
 
 cudaError_t launch_step3d_x2(const StepParams& p, const CUtensorMap& um, const CUtensorMap& bxm,
-                             const CUtensorMap& bym, int R, bool vd, bool adj, int tile,
+                             const CUtensorMap& bym, const CUtensorMap& upm,
+                             const CUtensorMap& kfm, const CUtensorMap& gm,
+                             const CUtensorMap& hm, int R, bool vd, bool adj, int tile,
                              cudaStream_t st) {
+  const CUtensorMap* om[4] = {&upm, &kfm, &gm, &hm};
   if (R == 4) {
-    if (vd) return adj ? launch_tile<4, true, true>(p, um, bxm, bym, tile, st)
-                       : launch_tile<4, true, false>(p, um, bxm, bym, tile, st);
-    return adj ? launch_tile<4, false, true>(p, um, bxm, bym, tile, st)
-               : launch_tile<4, false, false>(p, um, bxm, bym, tile, st);
+    if (vd) return adj ? launch_tile<4, true, true>(p, um, bxm, bym, om, tile, st)
+                       : launch_tile<4, true, false>(p, um, bxm, bym, om, tile, st);
+    return adj ? launch_tile<4, false, true>(p, um, bxm, bym, om, tile, st)
+               : launch_tile<4, false, false>(p, um, bxm, bym, om, tile, st);
   }
-  if (vd) return adj ? launch_tile<5, true, true>(p, um, bxm, bym, tile, st)
-                     : launch_tile<5, true, false>(p, um, bxm, bym, tile, st);
-  return adj ? launch_tile<5, false, true>(p, um, bxm, bym, tile, st)
-             : launch_tile<5, false, false>(p, um, bxm, bym, tile, st);
+  if (vd) return adj ? launch_tile<5, true, true>(p, um, bxm, bym, om, tile, st)
+                     : launch_tile<5, true, false>(p, um, bxm, bym, om, tile, st);
+  return adj ? launch_tile<5, false, true>(p, um, bxm, bym, om, tile, st)
+             : launch_tile<5, false, false>(p, um, bxm, bym, om, tile, st);
 }
 
 }  // namespace fwi
