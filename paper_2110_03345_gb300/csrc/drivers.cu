@@ -217,13 +217,13 @@ fwi_status launch_step(Call& c, const StepParams& p_in, bool adj) {
     const CUtensorMap* bxm = c.vd ? find_map(c, c.W.bx) : map;
     const CUtensorMap* bym = c.vd ? find_map(c, c.W.by) : map;
     if (!bxm || !bym) return fail(FWI_ERR_INVALID_ARG, "internal: no tensor map for b_x / b_y");
-    // the two-point variable-density adjoint's operand maps (others ignore them)
-    const bool ops = c.pl.x2 && c.vd && adj;
+    // the two-point variable-density kernels' operand maps (others ignore them)
+    const bool ops = c.pl.x2 && c.vd;
     const CUtensorMap* upm = ops ? find_map(c, p.up, 1) : map;
     const CUtensorMap* kfm = ops ? find_map(c, c.W.kf, 1) : map;
-    const CUtensorMap* gm = ops ? find_map(c, c.W.G, 1) : map;
+    const CUtensorMap* gm = (ops && adj) ? find_map(c, c.W.G, 1) : map;
     if (!upm || !kfm || !gm || (ops && p.image && !c.hmap_ok))
-      return fail(FWI_ERR_INVALID_ARG, "internal: no tensor map for the 3D adjoint's operands");
+      return fail(FWI_ERR_INVALID_ARG, "internal: no tensor map for the 3D kernels' operands");
     const CUtensorMap* hm = (ops && p.image) ? &c.hmap : map;
     e = c.pl.x2 ? launch_step3d_x2(p, *map, *bxm, *bym, *upm, *kfm, *gm, *hm, P->R, c.vd, adj,
                                    c.pl.shape, P->st)
@@ -559,9 +559,9 @@ fwi_status begin_call(fwi_plan* P, const fwi_model* model, const fwi_geometry* g
         c.maps.push_back(mi);
       }
     }
-    if (three && c.vd && c.pl.x2 && c.pl.gradient) {
-      // the two-point variable-density adjoint reads lambda^{k+1}, k and g by
-      // TMA in 64 x BY plane tiles
+    if (three && c.vd && c.pl.x2) {
+      // the two-point variable-density kernels read u^{n-1} (lambda^{k+1}), k
+      // and g by TMA in 64 x BY plane tiles
       const int by = tile3_variant(c.pl.shape).by;
       for (float* buf : {c.W.U0, c.W.U1, c.W.F0, c.W.F1}) {
         if (!buf) continue;
@@ -572,9 +572,11 @@ fwi_status begin_call(fwi_plan* P, const fwi_model* model, const fwi_geometry* g
       Call::MapEnt mk{c.W.kf, {}, 1};
       FWI_TRY(make_tensor_map_3d(P, c.W.kf, 1, c.pl.shape, true, &mk.map, 64, by));
       c.maps.push_back(mk);
-      Call::MapEnt mg{c.W.G, {}, 1};
-      FWI_TRY(make_tensor_map_3d(P, c.W.G, c.pl.B, c.pl.shape, true, &mg.map, 64, by));
-      c.maps.push_back(mg);
+      if (c.W.G) {   // gradient slots (gradient plans)
+        Call::MapEnt mg{c.W.G, {}, 1};
+        FWI_TRY(make_tensor_map_3d(P, c.W.G, c.pl.B, c.pl.shape, true, &mg.map, 64, by));
+        c.maps.push_back(mg);
+      }
     }
     if (three && c.vd) {
       // the two-point kernels stage b_x on the tile rows (80 x BY) and b_y on

@@ -267,10 +267,10 @@ cudaError_t launch_step3d_tma(const StepParams& p, const CUtensorMap& um, const 
 int tma_box3d_rows(int R, int tile);
 // Two-point TMA-staged 3D kernels (kernels3d_x2.cu): 64 x BY columns, the
 // same tensor maps with an 80-float-wide box; bit-identical to the above.
-// The variable-density adjoint also reads its per-plane operands by TMA:
-// upm (p.up), kfm (k, one slot) and gm (the gradient slots) map (x, y, z,
-// slot) with a 64 x BY box, hm the history buffer as (x, y, z, slot, step),
-// step p.hstep (read when p.image); other launches ignore them.
+// The variable-density kernels also read per-plane operands by TMA: upm
+// (p.up) and kfm (k, one slot), in the adjoint also gm (the gradient slots),
+// map (x, y, z, slot) with a 64 x BY box, hm the history buffer as (x, y, z,
+// slot, step), step p.hstep (read when p.image); other launches ignore them.
 cudaError_t launch_step3d_x2(const StepParams& p, const CUtensorMap& um, const CUtensorMap& bxm,
                              const CUtensorMap& bym, const CUtensorMap& upm,
                              const CUtensorMap& kfm, const CUtensorMap& gm,

@@ -84,7 +84,11 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
   constexpr int NBS = 4;                      // b stages: two loop trips of two planes
   float* bring = ring + NSU * G::PLANE;       // PSI: [NBS stages][b_x [BY][BXW], b_y [BYH][TXP]]
   constexpr int NOS = G::NOS;
-  float* ops = bring + NBS * G::BSTAGE;       // PSI: [NOS stages][lambda^{k+1}, k, h, g][BY][TXP]
+  // operand stages (variable density): [NOS][lambda^{k+1}, k, h, g][BY][TXP]
+  // in the adjoint, [NOS][u^{n-1}, k][BY][TXP] in the forward
+  constexpr bool OPS = VD;
+  constexpr int OPN = ADJ ? 4 : 2;            // operand tiles per stage
+  float* ops = bring + (PSI ? NBS * G::BSTAGE : 0);
   __shared__ uint64_t bar[NSU];
   __shared__ uint64_t bbar[NBS];
   __shared__ uint64_t obar[NOS];
@@ -143,11 +147,11 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
   }
   if (nz_c <= 0) return;
   __syncthreads();
-  // PSI: the operands of plane ii of the chunk into operand stage ii % NOS
+  // OPS: the operands of plane ii of the chunk into operand stage ii % NOS
   const bool img = ADJ && p.image;
   auto issue_ops = [&](int ii) {
     const int st = ii % NOS;
-    float* o = ops + st * 4 * G::OPT;
+    float* o = ops + st * OPN * G::OPT;
     const int xx = x0 + p.ox, yy = y0 + p.oy, zz = z0 + ii + p.oz;
     mbar_arrive_expect_tx(&obar[st], (uint32_t)G::OPT * 4u * (img ? 4u : 2u));
     tma_load_4d(o, &opup, &obar[st], xx, yy, zz, b);
@@ -159,7 +163,7 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
     }
   };
   if (tid == 0) {
-    if (PSI)
+    if (OPS)
       for (int ii = 0; ii < NOS && ii < nz_c; ++ii) issue_ops(ii);
     for (int lp = 0; lp < NSU && lp < nplanes; ++lp) {
       mbar_arrive_expect_tx(&bar[lp], G::PLANE_BYTES);
@@ -232,8 +236,10 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
       o.bzl = ldg2(p.bz + (long long)(pz0 + ii + 2 * R) * p.sxy + col);
       return o;
     }
-    o.uo = *reinterpret_cast<const float2*>(p.up + fo + id);
-    o.kk = ldg2(p.kf + id);
+    if (!OPS) {   // (OPS: u^{n-1} and k come from the operand stages)
+      o.uo = *reinterpret_cast<const float2*>(p.up + fo + id);
+      o.kk = ldg2(p.kf + id);
+    }
     if (ADJ && p.image) {
       o.hv = __ldcs(reinterpret_cast<const float2*>(p.hist + fo + id));
       o.gv = *reinterpret_cast<const float2*>(p.g + fo + id);
@@ -355,9 +361,9 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
           }
         }
         float2 uo = cur.uo, kk = cur.kk, hv = cur.hv, gv = cur.gv;
-        if (PSI) {   // this plane's operand stage
+        if (OPS) {   // this plane's operand stage
           if (!mbar_wait_bounded(&obar[i % NOS], (uint32_t)((i / NOS) & 1))) timed_out = true;
-          const float* o = ops + (i % NOS) * 4 * G::OPT + ty * G::TXP + 2 * tx;
+          const float* o = ops + (i % NOS) * OPN * G::OPT + ty * G::TXP + 2 * tx;
           uo = lds2(o);
           kk = lds2(o + G::OPT);
           if (img) {
@@ -404,7 +410,7 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
             mbar_arrive_expect_tx(&bar[k], G::PLANE_BYTES);
             tma_load_4d(ring + k * G::PLANE, &umap, &bar[k], tmx, tmy, pz0 + nx_, b);
           }
-          if (PSI && i + NOS < nz_c) {   // the stage of plane i takes plane i + NOS
+          if (OPS && i + NOS < nz_c) {   // the stage of plane i takes plane i + NOS
             fence_proxy_async_smem();
             issue_ops(i + NOS);
           }
@@ -434,6 +440,7 @@ constexpr size_t smem_bytes_x2() {
   using G = GeoX2<R, BY, VD && ADJ>;
   size_t n = (size_t)G::NSU * G::PLANE;
   if (VD && ADJ) n += 4 * (size_t)G::BSTAGE + (size_t)G::NOS * 4 * G::OPT;   // b and operand stages
+  if (VD && !ADJ) n += (size_t)G::NOS * 2 * G::OPT;                         // operand stages
   return n * sizeof(float);
 }
 
