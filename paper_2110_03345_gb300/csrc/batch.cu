@@ -213,9 +213,14 @@ fwi_status fwi_batch_create(fwi_batch** out, int nprob, const fwi_problem* probs
     if (b->tma) {
       const CUtensorMap* m0 = find_map(c, c.W.U0);
       const CUtensorMap* m1 = find_map(c, c.W.U1);
-      if (!m0 || !m1) return bail(fail(FWI_ERR_INVALID_ARG, "internal: missing tensor maps"));
+      const CUtensorMap* i0 = find_map(c, c.W.U0, 1);
+      const CUtensorMap* i1 = find_map(c, c.W.U1, 1);
+      if (!m0 || !m1 || !i0 || !i1)
+        return bail(fail(FWI_ERR_INVALID_ARG, "internal: missing tensor maps"));
       desc[k].map0 = *m0;
       desc[k].map1 = *m1;
+      desc[k].imap0 = *i0;
+      desc[k].imap1 = *i1;
     }
     // units: one per tile and shot group (TMA kernels loop S shots in a CTA)
     const int groups = b->tma ? (p.B + p.S - 1) / p.S : p.B;

@@ -178,6 +178,8 @@ cudaError_t launch_att_prep(const Layout& L, const float* vp, int param, const f
 struct MultiDesc {
   CUtensorMap map0;   // TMA descriptors of U0 and U1 (TMA-staged kernels)
   CUtensorMap map1;
+  CUtensorMap imap0;  // and of their tiles without halo (u^{n-1} staged by TMA)
+  CUtensorMap imap1;
   StepParams p;
   float* U0;   // u^n for even n (then u^{n-1} for odd n), [B][fstride]
   float* U1;

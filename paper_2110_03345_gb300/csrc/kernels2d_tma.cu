@@ -70,9 +70,11 @@ k_step2d_tma_multi(const MultiDesc* __restrict__ descs, const MultiUnit* __restr
   }
   __syncthreads();
   const CUtensorMap* map = (n & 1) ? &d->map1 : &d->map0;
-  step2d_tma_tile<R, VD, false, RY, BY>(sp, UW ? wx : sp.wx, UW ? wy : sp.wy, map, nullptr, nullptr,
-                                        nullptr, nullptr, un.tx, un.ty,
-                                        d->gx, un.slot, un.rank, smem, bar);
+  const CUtensorMap* umap = (n & 1) ? &d->imap0 : &d->imap1;   // u^{n-1} = sp.up
+  step2d_tma_tile<R, VD, false, RY, BY, LEAP, false, true>(sp, UW ? wx : sp.wx, UW ? wy : sp.wy, map,
+                                                           umap, nullptr, nullptr, nullptr, un.tx,
+                                                           un.ty, d->gx, un.slot, un.rank, smem,
+                                                           bar);
 }
 
 template <int R, bool VD, bool ADJ, int RY, int BY, bool CROWD = false>
@@ -114,7 +116,7 @@ cudaError_t launch_tile(const StepParams& p, const CUtensorMap& map, const CUten
 template <int R, bool VD, int RY, int BY, bool UW>
 cudaError_t launch_multi_u(const MultiDesc* descs, const MultiUnit* units, int nunits, int n,
                            const AxisW* w, cudaStream_t st) {
-  constexpr size_t smem = smem_bytes<R, VD, false, RY, BY>();
+  constexpr size_t smem = smem_bytes<R, VD, false, RY, BY, LEAP, true>();
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_step2d_tma_multi<R, VD, RY, BY, UW>,
