@@ -261,6 +261,20 @@ fwi_status launch_step(Call& c, const StepParams& p_in, bool adj) {
 // boundary; the tensor map of the stencil input p.x) or kernels_ext.cu.
 cudaError_t ext_pass(const Call& c, const StepParams& p, bool adj, int mode) {
   const fwi_plan* P = c.P;
+  if (c.pl.tma && P->grid.ndim == 3) {
+    // the two-point plane ring: p.x's map, b_x / b_y and the operand maps
+    const CUtensorMap* xm = find_map(c, p.x);
+    if (!xm) return cudaErrorInvalidValue;
+    const CUtensorMap* bxm = c.vd ? find_map(c, c.W.bx) : xm;
+    const CUtensorMap* bym = c.vd ? find_map(c, c.W.by) : xm;
+    const CUtensorMap* upm = c.vd ? find_map(c, p.up, 1) : xm;
+    const CUtensorMap* kfm = c.vd ? find_map(c, c.W.kf, 1) : xm;
+    const CUtensorMap* gm = (c.vd && adj) ? find_map(c, c.W.G, 1) : xm;
+    const bool img = c.vd && adj && p.image;
+    if (!bxm || !bym || !upm || !kfm || !gm || (img && !c.hmap_ok)) return cudaErrorInvalidValue;
+    return launch_step3d_x2_ext(p, *xm, *bxm, *bym, *upm, *kfm, *gm, img ? c.hmap : *xm, P->R,
+                                c.vd, adj, mode, P->st);
+  }
   if (c.pl.tma) {
     // p.x with halo, p.up without, and the history fields the adjoint images with
     const CUtensorMap* map = find_map(c, p.x);
@@ -795,7 +809,7 @@ fwi_status gradient_adjoint_batch(Call& c, int j, int shot0, int nb, const DevTa
   // the 2D leapfrog adjoint reads h^k by TMA through a map of this batch's
   // history buffer (nt - 1 steps, or one segment of K)
   c.hmap_ok = c.h2map_ok = false;
-  if (c.pl.tma && P->grid.ndim == 3 && c.pl.x2 && c.vd && !ext) {
+  if (c.pl.tma && P->grid.ndim == 3 && c.pl.x2 && c.vd) {
     FWI_TRY(make_tensor_map_hist3d(P, bb.H, B, K == 0 ? std::max(nt - 1, 1) : K, 64,
                                    tile3_variant(c.pl.shape).by, &c.hmap));
     c.hmap_ok = true;

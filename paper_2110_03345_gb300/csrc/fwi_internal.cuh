@@ -111,6 +111,24 @@ struct StepParams {
 inline int sample_group(int ncorner) { return ncorner > 8 ? 32 : 1; }
 
 #ifdef __CUDACC__
+// First injection entry of each plane lz = 0 .. nplanes of a 3D bucket whose
+// entries sort by tile-local index ((lz * TY + y) * TX + x): pe[lz] (one
+// bisection per plane by the CTA's threads; visible after a barrier).
+__device__ __forceinline__ void plane_entries(const StepParams& p, int bucket, int nplanes,
+                                              int plane_pts, int tid, int nthreads, int* pe) {
+  const int e0 = p.inj_off[bucket], e1 = p.inj_off[bucket + 1];
+  for (int k = tid; k <= nplanes; k += nthreads) {
+    const int lim = k * plane_pts;
+    int lo = e0, hi = e1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (__ldg(p.inj_loc + mid) < lim) lo = mid + 1;
+      else hi = mid;
+    }
+    pe[k] = lo;
+  }
+}
+
 // Receiver sampling d = P u^n by a launch's first threads: thread gid serves
 // the sample (slot, receiver) = gid / G with the nodes c = gid % G + k G,
 // and a group of G > 1 lanes (a whole warp, gid aligned to it) sums its
@@ -278,6 +296,14 @@ cudaError_t launch_step3d_x2(const StepParams& p, const CUtensorMap& um, const C
                              const CUtensorMap& kfm, const CUtensorMap& gm,
                              const CUtensorMap& hm, int R, bool vd, bool adj, int tile,
                              cudaStream_t st);
+// The extended schemes on the same kernels (kernels3d_x2_ext.cu; tile
+// variant 12: 64 x 8 columns): mode = EXT_KW / EXT_T4 / EXT_ATT0, xm the map
+// of the stencil input p.x, the other maps as above.
+cudaError_t launch_step3d_x2_ext(const StepParams& p, const CUtensorMap& xm, const CUtensorMap& bxm,
+                                 const CUtensorMap& bym, const CUtensorMap& upm,
+                                 const CUtensorMap& kfm, const CUtensorMap& gm,
+                                 const CUtensorMap& hm, int R, bool vd, bool adj, int mode,
+                                 cudaStream_t st);
 
 // Auxiliary kernels (aux_kernels.cu)
 cudaError_t launch_model_prep(const Layout& L, const float* vp, const float* rho, double dt,

@@ -41,16 +41,6 @@ namespace {
 
 constexpr float INV12 = 1.f / 12.f;   // the 1/12 of the fourth-order terms, rounded once
 
-__device__ __forceinline__ float ext_inject(const StepParams& p, int tile, int loc, float acc) {
-  if (p.inj_off) {
-    const int e0 = p.inj_off[tile], e1 = p.inj_off[tile + 1];
-    for (int e = e0; e < e1; ++e)
-      if (p.inj_loc[e] == loc)
-        acc = fmaf(p.inj_scale * p.inj_w[e], p.vals[p.inj_vidx[e] + p.step_off], acc);
-  }
-  return acc;
-}
-
 // Update of one point: cen = x at the point, acc = (L x + injection), lap =
 // its plain Laplacian part, lc = lap(att x) (y = 2 adjoint), a0 = sponge.
 template <bool ADJ, int MODE>
@@ -445,6 +435,10 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_ext3d(const StepParams p) 
   const bool in_xy = (xg < p.nx) && (yg < p.ny);
   const int tile = b * p.ntiles + (zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   const int cx = tx + R, cy = ty + R;
+  // each plane scans only its own injection entries
+  __shared__ int s_pe[MAX_ZCHUNK + 1];
+  const bool has_inj = p.inj_off && p.inj_off[tile + 1] > p.inj_off[tile];
+  if (has_inj) plane_entries(p, tile, z1 - z0, TY * TX, tid, NT, s_pe);
 
   for (int z = z0; z < z1; ++z) {
     const long long pz = (long long)(z + p.oz) * p.sxy;
@@ -516,7 +510,12 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_ext3d(const StepParams p) 
         lc = fmaf(p.wz.w2[j], (qc[R + j] + qc[R - j]) - cc2, lc);
       }
     }
-    acc = ext_inject(p, tile, ((z - z0) * TY + ty) * TX + tx, acc);
+    if (has_inj) {
+      const int lz = z - z0, loc = (lz * TY + ty) * TX + tx;
+      for (int e = s_pe[lz], e1 = s_pe[lz + 1]; e < e1; ++e)
+        if (p.inj_loc[e] == loc)
+          acc = fmaf(p.inj_scale * p.inj_w[e], p.vals[p.inj_vidx[e] + p.step_off], acc);
+    }
     if (in_xy) ext_update<ADJ, MODE>(p, fo, idx, cen, acc, lap, lc, axy + p.spz[z]);
 #pragma unroll
     for (int j = 0; j < Q - 1; ++j) {

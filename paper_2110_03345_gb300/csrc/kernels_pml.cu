@@ -349,6 +349,11 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_pml3d(const StepParams p) 
   const bool in_xy = (xg < p.nx) && (yg < p.ny);
   const int tile = b * p.ntiles + (zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   const int cx = tx + R, cy = ty + R;
+  // each plane scans only its own injection entries
+  __shared__ int s_pe[MAX_ZCHUNK + 1];
+  const bool has_inj = (MODE == PML_U || MODE == PML_A) && p.inj_off &&
+                       p.inj_off[tile + 1] > p.inj_off[tile];
+  if (has_inj) plane_entries(p, tile, z1 - z0, TY * TX, tid, NT, s_pe);
 
   // z queues of this column: the stencil input (kc in PML_B); phi_z (PML_U);
   // q (PML_PHI); b_z phibar_z and g_z phibar_z (PML_A); b_z k c (PML_B, vd)
@@ -450,10 +455,9 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_pml3d(const StepParams p) 
       }
     }
     float inj = 0.f;
-    if ((MODE == PML_U || MODE == PML_A) && p.inj_off) {
-      const int e0 = p.inj_off[tile], e1 = p.inj_off[tile + 1];
-      const int loc = ((z - z0) * TY + ty) * TX + tx;
-      for (int e = e0; e < e1; ++e)
+    if (has_inj) {
+      const int lz = z - z0, loc = (lz * TY + ty) * TX + tx;
+      for (int e = s_pe[lz], e1 = s_pe[lz + 1]; e < e1; ++e)
         if (p.inj_loc[e] == loc) inj += p.inj_w[e] * p.vals[p.inj_vidx[e] + p.step_off];
     }
     if (in_xy) {

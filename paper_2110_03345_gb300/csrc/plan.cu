@@ -381,11 +381,15 @@ fwi_status choose_plan(const fwi_plan* P, const fwi_geometry* g, bool vd, bool g
     // the extended schemes have one tile shape: in 2D (sponge boundary) the
     // TMA shot-loop kernels of 128 x 16 tiles (variant 6), otherwise one
     // shot per CTA (kernels_ext.cu, kernels_pml.cu)
+    // in 3D the two-point plane-ring kernels take the fourth-order scheme and
+    // the y = 0 term (variant 12); y = 2 and the PML keep kernels_ext.cu /
+    // kernels_pml.cu
     const bool tma2 = P->grid.ndim == 2 && !sc.pml;
-    out.tile = tma2 ? 6 : 0;
-    out.shape = tma2 ? 1 : 0;
-    out.tma = tma2;
-    out.x2 = false;
+    const bool x2 = P->grid.ndim == 3 && !sc.pml && (sc.t4 || sc.att == 0);
+    out.tile = tma2 ? 6 : (x2 ? 12 : 0);
+    out.shape = tma2 ? 1 : (x2 ? 3 : 0);
+    out.tma = tma2 || x2;
+    out.x2 = x2;
   }
   // slots x z chunks go on grid.z, which CUDA limits to 65535 blocks
   B = std::min(B, std::max(1, 65535 / std::max(1, tile_geo(P, out.shape, out.tma, out.x2,
