@@ -533,7 +533,8 @@ def roofline(acc, steps, ms, vd, ndim, tile, scheme=""):
         bpu = SCHEME_BYTES[(scheme, kind)] + (4 if vd else 0)   # + ln rho
         # 2D sponge-boundary schemes run on the TMA shot-loop kernels
         kern = ("k_pml%dd" % ndim if scheme == "pml" else
-                "k_step2d_tma_ext" if ndim == 2 else "k_ext3d")
+                "k_step2d_tma_ext" if ndim == 2 else
+                "k_step3d_x2" if scheme in ("t4", "att0") else "k_ext3d")
         kname = "%s %s step (%s)" % (kern, "adjoint+imaging" if kind == "adj" else "forward+store",
                                      scheme)
     else:
@@ -640,14 +641,19 @@ STAT_KEYS = ("fwd_ms", "adj_ms", "fwd_launches", "adj_launches", "fwd_points", "
              "launches", "fwd_timed", "adj_timed")
 
 
-def skull3d_sample(shots=2, steps=2, warmup=1, **opts):
+def skull3d_sample(shots=2, steps=2, warmup=1, scheme="", **opts):
     """The 3D workload at full grid size and time axis (256^3, 0.25 mm,
     10th order, variable density, 2000 steps, 512 receivers) with `shots`
     of its 32 shots: gradient Gpts/s and the roofline of its dominant kernel,
-    device-timed like the main line (inputs resident)."""
+    device-timed like the main line (inputs resident).  `scheme`: an extended
+    scheme of SCHEMES (the fourth-order scheme on the same record at CFL
+    0.66)."""
     import torch
     from paper_2110_03345_gb300 import binding, inputs
     p = inputs.config_skull_3d(shots=list(range(0, 16 * shots, 16)))
+    sopts, satt = scheme_setup(scheme)
+    if scheme == "t4":
+        p = t4_time_axis(p)
     dev = torch.device("cuda", torch.cuda.current_device())
     f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
     vp, rho, wav = f32(p.vp), f32(p.rho), f32(p.wavelet)
@@ -655,9 +661,12 @@ def skull3d_sample(shots=2, steps=2, warmup=1, **opts):
     stream = torch.cuda.current_stream()
     plan = binding.Plan(p.shape, p.spacing, p.nt, p.dt, order=p.order, sponge=p.nb, c_ref=p.c_ref,
                         stream=stream)
+    plan.set_options(**sopts)
+    if satt is not None:
+        plan.set_attenuation(f32(np.full(p.shape, satt[0])), satt[1])
     obs = plan.forward(f32(p.vp_true), rho, geo, wav)
     grad = torch.empty(p.shape, device=dev, dtype=torch.float32)
-    plan.set_options(profile=PROFILE_EVERY, **opts)
+    plan.set_options(profile=PROFILE_EVERY, **sopts, **opts)
     for _ in range(warmup):
         plan.gradient(vp, rho, geo, wav, obs, grad=grad)
     acc = dict.fromkeys(STAT_KEYS, 0)
@@ -675,11 +684,14 @@ def skull3d_sample(shots=2, steps=2, warmup=1, **opts):
     st = plan.stats()
     plan.close()
     upd = useful_updates(p)
-    return {"workload": f"skull3d 256^3 x 2000 steps, {shots} of the 32 shots, vd, o10, 512 receivers",
-            "value": upd / (ms * 1e-3) / 1e9, "unit": "Gpts/s", "ms_per_gradient": ms,
-            "steps": steps, "warmup": warmup, "batch": st["batch"], "ckpt_every": st["ckpt_every"],
-            "tile": st["tile"], "gpu_launches": int(acc["launches"]),
-            "roofline": roofline(acc, steps, ms, True, 3, st["tile"])}
+    out = {"workload": f"skull3d 256^3 x 2000 steps, {shots} of the 32 shots, vd, o10, 512 receivers",
+           "value": upd / (ms * 1e-3) / 1e9, "unit": "Gpts/s", "ms_per_gradient": ms,
+           "steps": steps, "warmup": warmup, "batch": st["batch"], "ckpt_every": st["ckpt_every"],
+           "tile": st["tile"], "gpu_launches": int(acc["launches"]),
+           "roofline": roofline(acc, steps, ms, True, 3, st["tile"], scheme)}
+    if scheme:
+        out.update({"scheme": scheme, "nt": p.nt, "dt_ns": p.dt * 1e9})
+    return out
 
 
 def run_mine(args):
@@ -806,6 +818,8 @@ def run_mine(args):
         if args.workload == "breast2d" and not args.scheme:
             extras["skull3d"] = skull3d_sample()
             extras["schemes"] = {k: scheme_sample(k) for k in ("t4", "att0", "att2", "sinc", "pml")}
+            # the 3D schemes on the plane-ring kernels (one timed gradient each)
+            extras["schemes3d"] = {k: skull3d_sample(steps=1, scheme=k) for k in ("t4", "att0")}
         extras["batched"] = uneven_batch(nprob=16, seed=4, reps=1)
         extras["serving"] = serving_stream(nreq=80, warm=10, seed=5)
         try:                               # the full Sec. 3.2 loop: ~3 s on one GB300
