@@ -397,7 +397,7 @@ fwi_status forward_steps(Call& c, int nb, int shot0, const DevTable& src, float*
   p.inj_loc = src.loc;
   p.inj_vidx = src.vidx;
   p.inj_row = src.row;
-  p.inj_crowded = src.crowded;
+  p.inj_crowded = src.crowded || (P->grid.ndim == 3 && c.ncorner > 8);   // 3D: sinc points
   p.inj_w = src.w;
   p.vals = c.wavelet;
   p.smp_node = c.smp_node;
@@ -724,7 +724,7 @@ fwi_status gradient_adjoint_batch(Call& c, int j, int shot0, int nb, const DevTa
   p.inj_loc = c.rec_tab.loc;
   p.inj_vidx = c.rec_tab.vidx;
   p.inj_row = c.rec_tab.row;
-  p.inj_crowded = c.rec_tab.crowded;
+  p.inj_crowded = c.rec_tab.crowded || (P->grid.ndim == 3 && c.ncorner > 8);
   p.inj_w = c.rec_tab.w;
   p.vals = c.D;
   p.g = c.W.G;

@@ -69,7 +69,7 @@ struct StepParams {
   const int* inj_loc;    // tile-local linear index (2D: ly*TX+lx; 3D: (lz*TY+ly)*TX+lx)
   const int* inj_vidx;   // index into vals (before step_off)
   const int* inj_row;    // 2D: per bucket, entry range of each tile row (TY + 1 values)
-  int inj_crowded;       // 2D: some tile row holds more than 32 entries
+  int inj_crowded;       // some tile row (2D) holds more than 32 entries; 3D: sinc points
   int hstep;             // 2D TMA adjoint: step of hist within the history buffer's tensor map
   const float* inj_w;    // weight (source: w/dV; receiver residual: w)
   const float* vals;

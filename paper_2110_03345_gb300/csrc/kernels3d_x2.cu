@@ -27,32 +27,35 @@ namespace fwi {
 
 namespace {
 
-template <int R, bool VD, bool ADJ, int BY>
+template <int R, bool VD, bool ADJ, int BY, bool CROWD = false>
 cudaError_t launch_t(const StepParams& p, const CUtensorMap& um, const CUtensorMap& bxm,
                      const CUtensorMap& bym, const CUtensorMap* const* om, cudaStream_t st) {
   constexpr size_t smem = smem_bytes_x2<R, VD, ADJ, BY>();
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_step3d_x2<R, VD, ADJ, BY>,
+    cudaError_t e = cudaFuncSetAttribute(k_step3d_x2<R, VD, ADJ, BY, X2_LEAP, CROWD>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_step3d_x2<R, VD, ADJ, BY>,
+    e = cudaFuncSetAttribute(k_step3d_x2<R, VD, ADJ, BY, X2_LEAP, CROWD>,
                              cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   dim3 grid((p.nx + 63) / 64, (p.ny + BY - 1) / BY, p.B * p.nzc);
-  return launch_pdl(k_step3d_x2<R, VD, ADJ, BY>, grid, dim3(32, BY), smem, st, p, um, bxm, bym,
-                    *om[0], *om[1], *om[2], *om[3]);
+  return launch_pdl(k_step3d_x2<R, VD, ADJ, BY, X2_LEAP, CROWD>, grid, dim3(32, BY), smem, st, p,
+                    um, bxm, bym, *om[0], *om[1], *om[2], *om[3]);
 }
 
 template <int R, bool VD, bool ADJ>
 cudaError_t launch_tile(const StepParams& p, const CUtensorMap& um, const CUtensorMap& bxm,
                         const CUtensorMap& bym, const CUtensorMap* const* om, int tile,
                         cudaStream_t st) {
-  return tile3_variant(tile).by == 8 ? launch_t<R, VD, ADJ, 8>(p, um, bxm, bym, om, st)
-                                     : launch_t<R, VD, ADJ, 16>(p, um, bxm, bym, om, st);
+  // (the 64 x 8 columns of the default variant have a crowded-plane instantiation)
+  if (tile3_variant(tile).by == 8)
+    return p.inj_crowded ? launch_t<R, VD, ADJ, 8, true>(p, um, bxm, bym, om, st)
+                         : launch_t<R, VD, ADJ, 8>(p, um, bxm, bym, om, st);
+  return launch_t<R, VD, ADJ, 16>(p, um, bxm, bym, om, st);
 }
 
 }  // namespace

@@ -54,7 +54,10 @@ struct GeoX2 {
 constexpr int X2_LEAP = -1;
 constexpr float X2_INV12 = 1.f / 12.f;   // the fourth-order scheme's 1/12, rounded once
 
-template <int R, bool VD, bool ADJ, int BY, int MODE = X2_LEAP>
+// CROWD: the injection tables have planes of more than 32 entries in a tile
+// (the 64-node rows of sinc points), whose threads find their own pair's
+// entries by bisection (a separate instantiation).
+template <int R, bool VD, bool ADJ, int BY, int MODE = X2_LEAP, bool CROWD = false>
 __global__ void __launch_bounds__(32 * BY, ((VD && ADJ) ? 512 : 768) / (32 * BY))
 k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
             const __grid_constant__ CUtensorMap bxmap, const __grid_constant__ CUtensorMap bymap,
@@ -213,22 +216,28 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
   const int loc0 = ty * G::TXP + 2 * tx;    // entry location of the own pair in plane lz = 0
 
   constexpr bool KWM = MODE == EXT_KW, T4M = MODE == EXT_T4, A0M = MODE == EXT_ATT0;
+  // (the extended schemes' u^n (lambda^k), k w^k and damping: x[0..2], only
+  // in their instantiations)
+  constexpr int NX = (MODE == X2_LEAP) ? 1 : 3;
   struct Ops {
     float2 uo, kk, hv, gv, bx, by, bz, bzl;
-    float2 uc, h2, at;   // fourth order: u^n (lambda^k), k w^k; y = 0: the damping
+    float2 x[NX];
     float sz;   // sponge damping of the plane (z part)
   };
   auto ldg2 = [](const float* a) { return __ldg(reinterpret_cast<const float2*>(a)); };
   auto load_ops = [&](int ii) {
     const float2 z2 = make_float2(0.f, 0.f);
-    Ops o{z2, z2, z2, z2, z2, z2, z2, z2, z2, z2, z2, 0.f};
+    Ops o;
+    o.uo = o.kk = o.hv = o.gv = o.bx = o.by = o.bz = o.bzl = z2;
+#pragma unroll
+    for (int q = 0; q < NX; ++q) o.x[q] = z2;
     o.sz = __ldg(p.spz + z0 + ii);
     const long long id = (long long)(z0 + ii + p.oz) * p.sxy + col;
     if (T4M) {
-      o.uc = *reinterpret_cast<const float2*>(p.u + fo + id);
-      if (ADJ && p.image) o.h2 = __ldcs(reinterpret_cast<const float2*>(p.hist2 + fo + id));
+      o.x[0] = *reinterpret_cast<const float2*>(p.u + fo + id);
+      if (ADJ && p.image) o.x[1] = __ldcs(reinterpret_cast<const float2*>(p.hist2 + fo + id));
     }
-    if (A0M) o.at = ldg2(p.att + id);
+    if (A0M) o.x[2] = ldg2(p.att + id);
     if (PSI) {   // lambda^{k+1}, k, h, g come from the operand stages
       o.bzl = ldg2(p.bz + (long long)(pz0 + ii + 2 * R) * p.sxy + col);
       return o;
@@ -349,12 +358,43 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
         if (has_inj) {
           const int lz = z - z0;
           const int l0 = lz * (TY * G::TXP) + loc0;
-          const int pe1 = s_pe[lz + 1];
-          for (int e = s_pe[lz]; e < pe1; ++e) {
-            const int l = __ldg(p.inj_loc + e);
-            const float w = (MODE == X2_LEAP) ? p.inj_w[e] : p.inj_scale * p.inj_w[e];
-            if (l == l0) acc.x = fmaf(w, p.vals[p.inj_vidx[e] + p.step_off], acc.x);
-            else if (l == l0 + 1) acc.y = fmaf(w, p.vals[p.inj_vidx[e] + p.step_off], acc.y);
+          int e = s_pe[lz], pe1 = s_pe[lz + 1];
+          if (CROWD && pe1 - e > 32) {
+            // entries sort by position: this pair's [l0, l0 + 2) by two bisections
+            int a = e, bnd = pe1;
+            while (a < bnd) {
+              const int m = (a + bnd) >> 1;
+              if (__ldg(p.inj_loc + m) < l0) a = m + 1;
+              else bnd = m;
+            }
+            int c = a;
+            bnd = pe1;
+            while (c < bnd) {
+              const int m = (c + bnd) >> 1;
+              if (__ldg(p.inj_loc + m) < l0 + 2) c = m + 1;
+              else bnd = m;
+            }
+            e = a;
+            pe1 = c;
+          }
+          if constexpr (CROWD) {
+            for (; e < pe1; ++e) {
+              const int l = __ldg(p.inj_loc + e);
+              const float w = (MODE == X2_LEAP) ? p.inj_w[e] : p.inj_scale * p.inj_w[e];
+              if (l == l0) acc.x = fmaf(w, p.vals[p.inj_vidx[e] + p.step_off], acc.x);
+              else if (l == l0 + 1) acc.y = fmaf(w, p.vals[p.inj_vidx[e] + p.step_off], acc.y);
+            }
+          } else {
+            const int pe1c = s_pe[lz + 1];
+            for (int e2 = s_pe[lz]; e2 < pe1c; ++e2) {
+              const int l = __ldg(p.inj_loc + e2);
+              if (l == l0)
+                acc.x = fmaf(MODE == X2_LEAP ? p.inj_w[e2] : p.inj_scale * p.inj_w[e2],
+                             p.vals[p.inj_vidx[e2] + p.step_off], acc.x);
+              else if (l == l0 + 1)
+                acc.y = fmaf(MODE == X2_LEAP ? p.inj_w[e2] : p.inj_scale * p.inj_w[e2],
+                             p.vals[p.inj_vidx[e2] + p.step_off], acc.y);
+            }
           }
         }
         float2 uo = cur.uo, kk = cur.kk, hv = cur.hv, gv = cur.gv;
@@ -370,12 +410,13 @@ k_step3d_x2(const StepParams p, const __grid_constant__ CUtensorMap umap,
         }
         const float sz_ = cur.sz;
         const float2 a = make_float2(axy.x + sz_, axy.y + sz_);
-        if (MODE != X2_LEAP) {
+        if constexpr (MODE != X2_LEAP) {
           // the extended schemes' update, lane by lane (kernels_ext.cu's arithmetic)
           const float cn[2] = {cen.x, cen.y}, ac[2] = {acc.x, acc.y}, kv[2] = {kk.x, kk.y};
-          const float uov[2] = {uo.x, uo.y}, ucv[2] = {cur.uc.x, cur.uc.y};
-          const float hvv[2] = {hv.x, hv.y}, h2v[2] = {cur.h2.x, cur.h2.y};
-          const float gvv[2] = {gv.x, gv.y}, atv[2] = {cur.at.x, cur.at.y};
+          const float2 uc2 = cur.x[0], h22 = cur.x[NX > 1 ? 1 : 0], at2 = cur.x[NX > 2 ? 2 : 0];
+          const float uov[2] = {uo.x, uo.y}, ucv[2] = {uc2.x, uc2.y};
+          const float hvv[2] = {hv.x, hv.y}, h2v[2] = {h22.x, h22.y};
+          const float gvv[2] = {gv.x, gv.y}, atv[2] = {at2.x, at2.y};
           const float av[2] = {a.x, a.y};
           const bool inl[2] = {in0, in1};
 #pragma unroll
