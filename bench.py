@@ -409,7 +409,8 @@ def uneven_gradient(nprob=64, seed=4, lanes=4, **kw):
     them concurrently on `lanes` streams within the HBM budget and while their
     GPU-fill weights sum to at most one, one plan per problem with all its
     shots per launch; (b) one plan per problem, problems one after another;
-    (c) the plain solver with one shot per launch."""
+    (c) the plain solver with one shot per launch; (d) gradient batches (one
+    CUDA graph each)."""
     import torch
     from paper_2110_03345_gb300 import binding, inputs, serve
     ps = inputs.config_uneven_batch(nprob=nprob, seed=seed, **kw)
@@ -454,15 +455,66 @@ def uneven_gradient(nprob=64, seed=4, lanes=4, **kw):
         torch.cuda.synchronize()
         return time.perf_counter() - t0
 
+    def batched():
+        """(d) gradient batches: the problems, longest first, packed into
+        batches whose full histories fit the budget, each one CUDA graph with
+        one branch per problem (its forward, misfit, adjoint with imaging and
+        finalisation on a stream of its own); a problem whose history alone
+        exceeds the budget runs on its own (checkpointed) plan.  Batches are
+        prepared outside the timed region, as in the forward arm."""
+        stream = torch.cuda.current_stream()
+        est = []
+        for r in reqs:
+            pl = binding.Plan(r["shape"], r["spacing"], r["nt"], r["dt"], order=r["order"],
+                              sponge=r["sponge"], c_ref=r["c_ref"], stream=stream)
+            pl.set_options(batch=r["geometry"].nshots, ckpt_every=-1)
+            est.append(pl.estimate(r["geometry"], True))
+            pl.close()
+        order = sorted(range(len(reqs)), key=lambda i: -reqs[i]["nt"])
+        groups, alone, cur, used = [], [], [], 0
+        for i in order:
+            if est[i] > budget:
+                alone.append(i)
+            elif used + est[i] > budget:
+                groups.append(cur)
+                cur, used = [i], est[i]
+            else:
+                cur.append(i)
+                used += est[i]
+        if cur:
+            groups.append(cur)
+        t = 0.0
+        for gidx in groups:
+            b = binding.Batch([reqs[i] for i in gidx], budget=budget, gradient=True)
+            b.run()   # warm-up
+            b.run()
+            t += b.stats()["run_ms"] * 1e-3
+            b.close()
+            torch.cuda.empty_cache()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in alone:
+            r = reqs[i]
+            pl = binding.Plan(r["shape"], r["spacing"], r["nt"], r["dt"], order=r["order"],
+                              sponge=r["sponge"], c_ref=r["c_ref"], stream=stream, budget=budget)
+            pl.gradient(r["vp"], r["rho"], r["geometry"], r["wavelet"], r["observed"])
+            pl.close()
+        torch.cuda.synchronize()
+        return t + time.perf_counter() - t0, len(groups), len(alone)
+
     served()   # warm-up (allocator pool, kernel attributes)
     out = {}
     for name, fn in (("served", served), ("per_problem", lambda: sequential(0)),
                      ("plain", lambda: sequential(1))):
         t = fn()
         out[name] = {"shots_per_s": shots / t, "gpts": updates / t / 1e9, "s": t}
+    t, ngroups, nalone = batched()
+    out["batched"] = {"shots_per_s": shots / t, "gpts": updates / t / 1e9, "s": t,
+                      "graphs": ngroups, "problems_on_own_plan": nalone}
     out.update({"problems": nprob, "shots": shots, "updates": updates, "lanes": lanes,
                 "speedup": out["plain"]["s"] / out["served"]["s"],
-                "speedup_vs_per_problem": out["per_problem"]["s"] / out["served"]["s"]})
+                "speedup_vs_per_problem": out["per_problem"]["s"] / out["served"]["s"],
+                "batched_vs_per_problem": out["per_problem"]["s"] / out["batched"]["s"]})
     return out
 
 

@@ -236,9 +236,14 @@ fwi_status fwi_misfit_backward_ex(fwi_plan* plan, float* grad_m, float* grad_wav
 
 /* ---- Uneven batches (many independent problems in one CUDA graph) ---- */
 
-/* One independent forward-modelling problem of a batch: its own grid, time
- * axis, model, geometry, wavelets (device [nshots][nsrc][nt]) and traces
- * (device out [nshots][nrec][nt]); the arrays follow fwi_forward. */
+/* One independent problem of a batch: its own grid, time axis, model,
+ * geometry, wavelets (device [nshots][nsrc][nt]) and traces (device out
+ * [nshots][nrec][nt]); the arrays follow fwi_forward.  A gradient problem
+ * (Sec. 2.2, as fwi_gradient) also gives observed (device [nshots][nrec][nt]),
+ * grad_m (device out, N floats, dJ/dm with m = 1/vp^2) and misfit (host out,
+ * J, written by fwi_batch_run); traces may then be NULL.  A forward problem
+ * leaves observed, grad_m and misfit NULL.  The problems of one batch are all
+ * forward or all gradient problems. */
 typedef struct {
     fwi_grid grid;
     int nt;
@@ -247,6 +252,9 @@ typedef struct {
     fwi_geometry geom;
     const float* wavelet;
     float* traces;
+    const float* observed;
+    float* grad_m;
+    double* misfit;
 } fwi_problem;
 
 typedef struct {
@@ -270,8 +278,12 @@ typedef struct fwi_batch fwi_batch;
  * use_graph = 1 the whole sequence, including the final sampling and trace
  * transposition, is captured once into a CUDA graph.  opt (or NULL) selects
  * the kernel variant (tile, shots_per_cta; 2D TMA variants 5-8 or variant 1)
- * for every problem.  The problem arrays must stay valid until
- * fwi_batch_destroy. */
+ * for every problem.  A gradient batch runs each problem's gradient as
+ * fwi_gradient does (all its shots at once; the full wavefield history when
+ * it fits the budget left, else sqrt(nt) checkpoints), each problem on its
+ * own stream forked from the batch's: with use_graph = 1 the graph holds one
+ * independent branch per problem, which the GPU runs concurrently.  The
+ * problem arrays must stay valid until fwi_batch_destroy. */
 fwi_status fwi_batch_create(fwi_batch** batch, int nprob, const fwi_problem* probs,
                             const fwi_options* opt, size_t hbm_budget_bytes, void* stream,
                             int use_graph);

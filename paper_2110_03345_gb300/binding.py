@@ -62,7 +62,8 @@ class CGeometry(ctypes.Structure):
 class CProblem(ctypes.Structure):
     _fields_ = [("grid", CGrid), ("nt", ctypes.c_int), ("dt", ctypes.c_double),
                 ("model", CModel), ("geom", CGeometry), ("wavelet", ctypes.c_void_p),
-                ("traces", ctypes.c_void_p)]
+                ("traces", ctypes.c_void_p), ("observed", ctypes.c_void_p),
+                ("grad_m", ctypes.c_void_p), ("misfit", ctypes.POINTER(ctypes.c_double))]
 
 
 class CBatchStats(ctypes.Structure):
@@ -535,9 +536,13 @@ class Batch:
 
     problems: list of dicts with keys shape, spacing, nt, dt, order, sponge,
     c_ref, vp, rho (CUDA tensors or None), geometry (Geometry), wavelet (CUDA
-    tensor [shots][src][nt]).  Traces are allocated here (self.traces)."""
+    tensor [shots][src][nt]), and for a gradient batch observed (CUDA tensor
+    [shots][rec][nt]).  Traces are allocated here (self.traces); a gradient
+    batch also allocates self.grads (dJ/dm per problem) and fills
+    self.misfits at each run."""
 
-    def __init__(self, problems, budget=0, stream=None, use_graph=True, tile=0, shots_per_cta=0):
+    def __init__(self, problems, budget=0, stream=None, use_graph=True, tile=0, shots_per_cta=0,
+                 gradient=False):
         import torch
         lib = load()
         if stream is None:
@@ -545,6 +550,9 @@ class Batch:
         self.stream = stream
         self._keep = []
         self.traces = []
+        self.grads = []
+        self.gradient = bool(gradient)
+        self._misfit = (ctypes.c_double * len(problems))()
         arr = (CProblem * len(problems))()
         for i, pr in enumerate(problems):
             geo = pr["geometry"]
@@ -566,6 +574,16 @@ class Batch:
             arr[i].geom = geo.c
             arr[i].wavelet = _ptr(pr["wavelet"])
             arr[i].traces = _ptr(tr)
+            if self.gradient:
+                check_array(pr["observed"], geo.nshots * geo.nrec * int(pr["nt"]),
+                            f"problem {i} observed", dev)
+                g = torch.empty(tuple(int(v) for v in pr["shape"]), device=dev, dtype=torch.float32)
+                self.grads.append(g)
+                self._keep.append((pr["observed"], g))
+                arr[i].observed = _ptr(pr["observed"])
+                arr[i].grad_m = _ptr(g)
+                arr[i].misfit = ctypes.cast(ctypes.byref(self._misfit, i * ctypes.sizeof(ctypes.c_double)),
+                                            ctypes.POINTER(ctypes.c_double))
         self._arr = arr
         self._opts = COptions(0, 0, int(tile), 0, 0, int(shots_per_cta), 0, 0, 0)
         h = ctypes.c_void_p()
@@ -575,7 +593,10 @@ class Batch:
         self._h = h
 
     def run(self):
+        """Forward batch: the traces; gradient batch: (misfits, gradients)."""
         _check(load().fwi_batch_run(self._h))
+        if self.gradient:
+            return [float(v) for v in self._misfit], self.grads
         return self.traces
 
     def stats(self) -> dict:

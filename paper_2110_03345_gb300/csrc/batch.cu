@@ -1,6 +1,6 @@
-// Uneven batches of independent 2D problems (forward modelling): one
-// multi-problem stencil launch per time step, the whole run captured once
-// into a CUDA graph (fwi_batch_*).
+// Uneven batches of independent 2D problems (forward modelling or gradients):
+// one multi-problem stencil launch per time step, the whole run captured
+// once into a CUDA graph (fwi_batch_*).
 #include "fwi_plan.cuh"
 
 using namespace fwi;
@@ -48,6 +48,12 @@ struct fwi_batch {
   AxisW w[2] = {};          // {x, y} weights when uniform_w
   MultiDesc* d_desc = nullptr;
   MultiUnit* d_units = nullptr;
+  bool grad = false;                  // a gradient batch
+  // gradient batches: one stream per problem, forked from ws and joined back
+  // (independent branches of the graph that the GPU runs concurrently)
+  std::vector<cudaStream_t> bst;
+  std::vector<cudaEvent_t> bjoin;
+  cudaEvent_t fork = nullptr;
   std::vector<int> active_units;      // units of the problems still running at step n
   int max_steps = 0;
   cudaGraph_t graph = nullptr;
@@ -60,14 +66,18 @@ struct fwi_batch {
     if (graph) cudaGraphDestroy(graph);
     cudaFree(d_desc);
     cudaFree(d_units);
+    for (BatchProblem* b : items) {
+      if (b->P) b->P->st = st;   // (a gradient batch moved it to its branch stream)
+      fwi_plan_destroy(b->P);
+      delete b;
+    }
+    for (cudaEvent_t e : bjoin) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+    for (cudaStream_t s : bst) cudaStreamDestroy(s);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (ready) cudaEventDestroy(ready);
     if (ws) cudaStreamDestroy(ws);
-    for (BatchProblem* b : items) {
-      fwi_plan_destroy(b->P);
-      delete b;
-    }
   }
 };
 
@@ -75,7 +85,41 @@ namespace {
 
 // Every step of every problem (and the final sampling / trace transposition)
 // enqueued on b->st; captured into a graph when b->use_graph.
+// Gradient batches: each problem's whole gradient (the forward with its
+// history, misfit, adjoint with the imaging condition, finalisation; the
+// single-problem kernels of fwi_gradient) on its own stream, forked from ws
+// and joined back, so that a graph holds one independent branch per problem.
+fwi_status batch_enqueue_grad(fwi_batch* b) {
+  int64_t launches = 0, updates = 0;
+  CUDA_TRY(cudaEventRecord(b->fork, b->ws));
+  for (size_t i = 0; i < b->items.size(); ++i) {
+    BatchProblem* it = b->items[i];
+    Call& c = it->c;
+    fwi_plan* P = it->P;
+    const int ns = it->prob.geom.nshots;
+    const size_t fs = (size_t)P->L.fstride;
+    P->st = b->bst[i];
+    CUDA_TRY(cudaStreamWaitEvent(P->st, b->fork, 0));
+    CUDA_TRY(cudaMemsetAsync(P->d_flags, 0, sizeof(int) * 4, P->st));
+    CUDA_TRY(cudaMemsetAsync(c.W.G, 0, fs * ns * sizeof(float), P->st));
+    c.launches = 0;
+    FWI_TRY(gradient_forward_batch(c, 0, 0, ns, it->src, it->prob.observed, it->prob.traces));
+    FWI_TRY(gradient_adjoint_batch(c, 0, 0, ns, it->src));
+    cudaError_t e = launch_grad_finalize(P->L, c.W.G, (ns + c.pl.S - 1) / c.pl.S, 1.0 / (P->dt * P->dt),
+                                         it->prob.grad_m, P->d_flags, P->st);
+    if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
+    launches += c.launches + 1;
+    updates += 2 * (int64_t)ns * P->L.nx * P->L.ny * (it->prob.nt - 1);
+    CUDA_TRY(cudaEventRecord(b->bjoin[i], P->st));
+    CUDA_TRY(cudaStreamWaitEvent(b->ws, b->bjoin[i], 0));
+  }
+  b->stats.launches = launches;
+  b->stats.updates = updates;
+  return FWI_OK;
+}
+
 fwi_status batch_enqueue(fwi_batch* b) {
+  if (b->grad) return batch_enqueue_grad(b);
   int64_t launches = 0, updates = 0;
   for (int n = 0; n < b->max_steps; ++n) {
     cudaError_t e = b->tma ? launch_step2d_tma_multi(b->d_desc, b->d_units, b->active_units[n], n,
@@ -90,6 +134,7 @@ fwi_status batch_enqueue(fwi_batch* b) {
     Call& c = it->c;
     const int nt = it->prob.nt;
     const int ns = it->prob.geom.nshots;
+    const int nrec = it->prob.geom.nrec;
     float* last = ((nt - 1) & 1) ? c.W.U1 : c.W.U0;   // u^{nt-1}
     StepParams p = base_params(c);
     p.B = ns;
@@ -97,12 +142,11 @@ fwi_status batch_enqueue(fwi_batch* b) {
     p.smp_node = c.smp_node;
     p.smp_w = c.smp_w;
     p.smp_out = c.W.D;
-    p.nrec = it->prob.geom.nrec;
-    p.smp_off = (long long)(nt - 1) * c.pl.B * it->prob.geom.nrec;
+    p.nrec = nrec;
+    p.smp_off = (long long)(nt - 1) * c.pl.B * nrec;
     cudaError_t e = launch_sample(p, b->ws);
     if (e == cudaSuccess)
-      e = launch_traces_out(c.W.D, it->prob.traces, c.pl.B, 0, ns, it->prob.geom.nrec, nt,
-                            it->P->d_flags, b->ws);
+      e = launch_traces_out(c.W.D, it->prob.traces, c.pl.B, 0, ns, nrec, nt, it->P->d_flags, b->ws);
     if (e != cudaSuccess) return fail(FWI_ERR_CUDA, cudaGetErrorString(e));
     launches += 2;
     updates += (int64_t)ns * it->P->L.nx * it->P->L.ny * (nt - 1);
@@ -136,7 +180,12 @@ fwi_status fwi_batch_create(fwi_batch** out, int nprob, const fwi_problem* probs
     } else if (pr.grid.order / 2 != b->R || (pr.model.rho != nullptr) != b->vd) {
       return bail(fail(FWI_ERR_UNSUPPORTED, "a batch shares one stencil order and density mode"));
     }
-    if (!pr.traces || !pr.wavelet) return bail(fail(FWI_ERR_INVALID_ARG, "problem arrays are NULL"));
+    const bool g = pr.observed != nullptr;
+    if (i == 0) b->grad = g;
+    else if (g != b->grad)
+      return bail(fail(FWI_ERR_INVALID_ARG, "a batch holds only forward or only gradient problems"));
+    if (!pr.wavelet || (!g && !pr.traces) || (g && (!pr.grad_m || !pr.misfit)))
+      return bail(fail(FWI_ERR_INVALID_ARG, "problem arrays are NULL"));
     if (pr.model.alpha0 ||
         (opt && (opt->time_order == 4 || opt->interp != FWI_INTERP_LINEAR || opt->boundary != 0)))
       return bail(fail(FWI_ERR_UNSUPPORTED,
@@ -155,8 +204,8 @@ fwi_status fwi_batch_create(fwi_batch** out, int nprob, const fwi_problem* probs
     o.batch = pr.geom.nshots;   // every shot of the problem in one batch
     o.tile = opt ? opt->tile : 0;                  // 0: the default (TMA-staged) variant
     o.shots_per_cta = opt ? opt->shots_per_cta : 0;
-    it->P->opt = o;
-    FWI_TRY_B(begin_call(it->P, &it->prob.model, &it->prob.geom, pr.wavelet, false, it->c, it->tabC));
+    it->P->opt = o;   // (gradients: the full history if it fits the budget left, else checkpoints)
+    FWI_TRY_B(begin_call(it->P, &it->prob.model, &it->prob.geom, pr.wavelet, g, it->c, it->tabC));
     if (it->c.pl.B != pr.geom.nshots)
       return bail(fail(FWI_ERR_BUDGET, "problem " + std::to_string(i) + " does not fit the budget with all its shots"));
     if (i == 0) {
@@ -247,14 +296,25 @@ fwi_status fwi_batch_create(fwi_batch** out, int nprob, const fwi_problem* probs
   CUDA_TRY_B(cudaEventCreate(&b->e1));
   CUDA_TRY_B(cudaEventCreateWithFlags(&b->ready, cudaEventDisableTiming));
   CUDA_TRY_B(cudaStreamCreateWithFlags(&b->ws, cudaStreamNonBlocking));
+  if (b->grad) {
+    CUDA_TRY_B(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    for (size_t i = 0; i < b->items.size(); ++i) {
+      cudaStream_t s = nullptr;
+      cudaEvent_t e = nullptr;
+      CUDA_TRY_B(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+      b->bst.push_back(s);
+      CUDA_TRY_B(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      b->bjoin.push_back(e);
+    }
+  }
   CUDA_TRY_B(cudaStreamSynchronize(b->st));
   if (b->use_graph) {
     // set the kernels' attributes outside the capture (zero-unit launch), then
     // capture every launch of a run
     {
       cudaError_t e = b->tma ? launch_step2d_tma_multi(b->d_desc, b->d_units, 0, 0, b->R, b->vd,
-                                                       b->shape, b->uniform_w ? b->w : nullptr,
-                                                       b->ws)
+                                                       b->shape,
+                                                       b->uniform_w ? b->w : nullptr, b->ws)
                              : launch_step2d_multi(b->d_desc, b->d_units, 0, 0, b->R, b->vd, b->ws);
       if (e != cudaSuccess) return bail(fail(FWI_ERR_CUDA, cudaGetErrorString(e)));
     }
@@ -303,7 +363,9 @@ fwi_status fwi_batch_run(fwi_batch* b) {
   for (BatchProblem* it : b->items) {
     int flags[4];
     CUDA_TRY(cudaMemcpy(flags, it->P->d_flags, sizeof(flags), cudaMemcpyDeviceToHost));
-    if (flags[0]) return fail(FWI_ERR_NONFINITE, "non-finite traces in a batched problem");
+    if (flags[0]) return fail(FWI_ERR_NONFINITE, "non-finite values in a batched problem");
+    if (flags[1] & 2) return fail(FWI_ERR_TIMEOUT, "a bounded wait on a TMA copy timed out");
+    if (b->grad) CUDA_TRY(cudaMemcpy(it->prob.misfit, it->P->d_J, sizeof(double), cudaMemcpyDeviceToHost));
   }
   return FWI_OK;
 }

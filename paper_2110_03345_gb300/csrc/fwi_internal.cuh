@@ -249,7 +249,7 @@ cudaError_t launch_step2d(const StepParams& p, int R, bool vd, bool adj, int til
 cudaError_t launch_step3d(const StepParams& p, int R, bool vd, bool adj, int tile,
                           cudaStream_t st);
 size_t step2d_smem(int R, bool vd, bool adj, int tile);
-// Multi-problem forward step, TMA-staged (kernels2d_tma.cu); units are
+// Multi-problem forward step, TMA-staged (kernels2d_tma_multi.cu); units are
 // (problem, tile, shot group) with the tile shape tile2_tma_variant(tile).
 // w: {x, y} stencil weights shared by every problem, or null when they differ.
 cudaError_t launch_step2d_tma_multi(const MultiDesc* descs, const MultiUnit* units, int nunits,

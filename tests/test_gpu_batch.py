@@ -1,11 +1,14 @@
 """Uneven batches: many independent 2D problems advanced by one multi-problem
 launch per step, captured in one CUDA graph, against one plan per problem
-(bit for bit: the same kernel body and tile shape) and the FP64 oracle."""
+(bit for bit: the same kernel body and tile shape) and the FP64 oracle, for
+forward modelling and for gradients."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2110_03345_gb300 import binding, inputs
-from _helpers import TOL_TRACES, gpu_forward, oracle_forward, rel_l2, to_dev
+from _helpers import (TOL_GRAD, TOL_TRACES, gpu_forward, gpu_gradient, gpu_plan, oracle_forward,
+                      oracle_grid, rel_l2, strong_perturbation, to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -49,4 +52,60 @@ def test_batch_against_oracle():
     k = int(np.argmax([p.nshots for p in ps]))
     ref = oracle_forward(ps[k])
     assert rel_l2(got[k].cpu().numpy(), ref) <= TOL_TRACES
+    b.close()
+
+
+def gradient_entries(ps):
+    """Batch entries of gradient problems: observed data from a perturbed model
+    (one plan per problem, the default variant)."""
+    import torch
+    entries = as_batch_entries(ps)
+    obs = []
+    for p, e in zip(ps, entries):
+        plan = gpu_plan(p)
+        o = plan.forward(to_dev(strong_perturbation(p)), to_dev(p.rho),
+                         binding.Geometry(p.src_xyz, p.rec_xyz), to_dev(p.wavelet))
+        plan.close()
+        torch.cuda.synchronize()
+        e["observed"] = o
+        obs.append(o.cpu().numpy().astype(np.float64))
+    return entries, obs
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_gradient_batch_matches_single_problem_runs(use_graph):
+    """A gradient batch (forward with the history, misfits, one multi-problem
+    adjoint launch per step, imaging, finalisation) gives each problem's
+    misfit and gradient bit for bit as one plan per problem with its full
+    history (same kernel body, tile shape and shot groups)."""
+    ps = problems()
+    entries, obs = gradient_entries(ps)
+    b = binding.Batch(entries, use_graph=use_graph, gradient=True)
+    J, grads = b.run()
+    for p, o, Jb, gb in zip(ps, obs, J, grads):
+        plan = gpu_plan(p, batch=p.nshots, ckpt_every=-1)
+        Jr, gr, _, _ = gpu_gradient(p, o, plan=plan)
+        plan.close()
+        assert Jb == Jr
+        assert np.array_equal(gb.cpu().numpy().astype(np.float64), gr)
+    J2, grads2 = b.run()   # a second run (graph replay) gives the same results
+    assert J2 == J and all(torch_equal(a, g) for a, g in zip(grads2, grads))
+    b.close()
+
+
+def torch_equal(a, b):
+    return bool((a == b).all())
+
+
+def test_gradient_batch_against_oracle():
+    ps = problems(3)
+    entries, obs = gradient_entries(ps)
+    b = binding.Batch(entries, gradient=True)
+    J, grads = b.run()
+    k = int(np.argmax([p.nshots for p in ps]))
+    p = ps[k]
+    J_ref, g_ref, _ = oracle.gradient(oracle_grid(p), p.vp, p.rho, p.src_xyz, p.wavelet,
+                                      p.rec_xyz, obs[k])
+    assert abs(J[k] - J_ref) <= 1e-3 * abs(J_ref)
+    assert rel_l2(grads[k].cpu().numpy(), g_ref) <= TOL_GRAD
     b.close()
