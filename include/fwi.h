@@ -406,7 +406,8 @@ fwi_status fwi_vp_update(float* vp, const float* grad_m, const float* mask, long
  *     the largest error of interpolating cosines down to 4 points per
  *     wavelength, 1.3e-3); the point's weights are the products over the
  *     axes, (2r)^ndim nodes, the slowest axis varying slowest.  The solver
- *     does not use these weights yet.
+ *     injects and samples with these weights when fwi_options.interp is
+ *     FWI_INTERP_SINC.
  *   xyz:     host [ndim] metres, slowest axis first, inside the grid (sinc:
  *            at least r - 1 nodes inside every face).
  *   nodes:   host out [cap][ndim] grid indices, slowest axis first.
