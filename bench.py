@@ -456,8 +456,8 @@ def uneven_gradient(nprob=64, seed=4, lanes=4, **kw):
         return time.perf_counter() - t0
 
     def batched():
-        """(d) gradient batches: the problems, longest first, packed into
-        batches whose full histories fit the budget, each one CUDA graph with
+        """(d) gradient batches: the problems packed (first fit, largest
+        first) into batches whose full histories fit the budget, each one CUDA graph with
         one branch per problem (its forward, misfit, adjoint with imaging and
         finalisation on a stream of its own); a problem whose history alone
         exceeds the budget runs on its own (checkpointed) plan.  Batches are
@@ -470,19 +470,22 @@ def uneven_gradient(nprob=64, seed=4, lanes=4, **kw):
             pl.set_options(batch=r["geometry"].nshots, ckpt_every=-1)
             est.append(pl.estimate(r["geometry"], True))
             pl.close()
-        order = sorted(range(len(reqs)), key=lambda i: -reqs[i]["nt"])
-        groups, alone, cur, used = [], [], [], 0
+        # first-fit decreasing on the workspace sizes: few graphs, each with
+        # as many concurrent branches as the budget holds
+        order = sorted(range(len(reqs)), key=lambda i: -est[i])
+        groups, used, alone = [], [], []
         for i in order:
             if est[i] > budget:
                 alone.append(i)
-            elif used + est[i] > budget:
-                groups.append(cur)
-                cur, used = [i], est[i]
+                continue
+            for g in range(len(groups)):
+                if used[g] + est[i] <= budget:
+                    groups[g].append(i)
+                    used[g] += est[i]
+                    break
             else:
-                cur.append(i)
-                used += est[i]
-        if cur:
-            groups.append(cur)
+                groups.append([i])
+                used.append(est[i])
         t = 0.0
         for gidx in groups:
             b = binding.Batch([reqs[i] for i in gidx], budget=budget, gradient=True)

@@ -41,47 +41,71 @@ namespace {
 
 constexpr float INV12 = 1.f / 12.f;   // the 1/12 of the fourth-order terms, rounded once
 
+// Per-point operands of one plane of the 3D kernel, loaded at the top of the
+// plane's trip so that their latency overlaps the plane staging, the barrier
+// and the stencil (each point is read and written by its own thread only).
+template <bool VD, bool ADJ, int MODE>
+struct PointOps {
+  float k, uo, uc, at, qo, h, h2, g, bx, by, bz;
+  __device__ __forceinline__ void load(const StepParams& p, long long fo, long long pi) {
+    k = __ldg(p.kf + pi);
+    if (MODE != EXT_KW) uo = p.up[fo + pi];
+    if (MODE == EXT_T4) uc = p.u[fo + pi];
+    if (MODE == EXT_ATT0 || MODE == EXT_ATT2) at = __ldg(p.att + pi);
+    if (MODE == EXT_ATT2) qo = p.q[fo + pi];
+    if (ADJ && MODE != EXT_KW && p.image) {
+      h = p.hist[fo + pi];
+      if (MODE == EXT_T4) h2 = p.hist2[fo + pi];
+      g = p.g[fo + pi];
+    }
+    if (VD && !ADJ) {
+      bx = __ldg(p.bx + pi);
+      by = __ldg(p.by + pi);
+      bz = __ldg(p.bz + pi);
+    }
+  }
+};
+
 // Update of one point: cen = x at the point, acc = (L x + injection), lap =
-// its plain Laplacian part, lc = lap(att x) (y = 2 adjoint), a0 = sponge.
-template <bool ADJ, int MODE>
+// its plain Laplacian part, lc = lap(att x) (y = 2 adjoint), a0 = sponge,
+// o = the point's operands.
+template <bool VD, bool ADJ, int MODE>
 __device__ __forceinline__ void ext_update(const StepParams& p, long long fo, long long pi,
-                                           float cen, float acc, float lap, float lc, float a0) {
-  const float k = __ldg(p.kf + pi);
+                                           float cen, float acc, float lap, float lc, float a0,
+                                           const PointOps<VD, ADJ, MODE>& o) {
+  const float k = o.k;
   float* upp = p.up + fo + pi;
   if (MODE == EXT_KW) {
     p.out[fo + pi] = k * acc;
   } else if (MODE == EXT_T4) {
     const float F = fmaf(k * acc, INV12, cen);
-    const float uc = p.u[fo + pi];
-    const float uo = *upp;
-    *upp = (2.f * uc - (1.f - a0) * uo + F) * __frcp_rn(1.f + a0);
+    const float uc = o.uc;
+    *upp = (2.f * uc - (1.f - a0) * o.uo + F) * __frcp_rn(1.f + a0);
     if (!ADJ) {
       if (p.hist) {
         p.hist[fo + pi] = F;
         p.hist2[fo + pi] = cen;
       }
     } else if (p.image) {
-      float* gp = p.g + fo + pi;
-      *gp = *gp - fmaf(cen * p.hist2[fo + pi], INV12, uc * p.hist[fo + pi]);
+      p.g[fo + pi] = o.g - fmaf(cen * o.h2, INV12, uc * o.h);
     }
   } else if (MODE == EXT_ATT0) {
-    const float at = __ldg(p.att + pi);
+    const float at = o.at;
     const float a = a0 + at;
-    const float uo = *upp;
+    const float uo = o.uo;
     const float h = k * acc;
     const float r = (2.f * cen - (1.f - a) * uo + h) * __frcp_rn(1.f + a);
     *upp = r;
     if (!ADJ) {
       if (p.hist) p.hist[fo + pi] = h - 0.5f * at * (r - uo);
     } else if (p.image) {
-      float* gp = p.g + fo + pi;
-      *gp = fmaf(-cen, p.hist[fo + pi], *gp);
+      p.g[fo + pi] = fmaf(-cen, o.h, o.g);
     }
   } else {   // EXT_ATT2
-    const float cf = __ldg(p.att + pi);
-    float* qp = p.q + fo + pi;
-    const float qo = *qp;
+    const float cf = o.at;
+    const float qo = o.qo;
     float E, extra = 0.f;
+    float* qp = p.q + fo + pi;
     if (!ADJ) {
       const float dl = lap - qo;
       E = fmaf(cf, dl, acc);
@@ -92,13 +116,11 @@ __device__ __forceinline__ void ext_update(const StepParams& p, long long fo, lo
       *qp = lc;
     }
     const float h = k * E;
-    const float uo = *upp;
-    *upp = (2.f * cen - (1.f - a0) * uo + h) * __frcp_rn(1.f + a0);
+    *upp = (2.f * cen - (1.f - a0) * o.uo + h) * __frcp_rn(1.f + a0);
     if (!ADJ) {
       if (p.hist) p.hist[fo + pi] = h + extra;
     } else if (p.image) {
-      float* gp = p.g + fo + pi;
-      *gp = fmaf(-cen, p.hist[fo + pi], *gp);
+      p.g[fo + pi] = fmaf(-cen, o.h, o.g);
     }
   }
 }
@@ -442,6 +464,9 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_ext3d(const StepParams p) 
 
   for (int z = z0; z < z1; ++z) {
     const long long pz = (long long)(z + p.oz) * p.sxy;
+    const long long idx = col + pz;
+    PointOps<VD, ADJ, MODE> ops;
+    if (in_xy) ops.load(p, fo, idx);
     {
       const long long o = col + pz + (long long)R * p.sxy;
       q[Q - 1] = X[o];
@@ -450,23 +475,36 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_ext3d(const StepParams p) 
     }
     __syncthreads();   // the previous plane's readers are done with the shared tiles
     const long long pb = pz + (long long)(y0 + p.oy - R) * p.sx + (x0 + p.ox - R);
-    for (int i = tid; i < SH * SW; i += NT) {
-      const int r = i / SW, c = i - r * SW;
-      const long long o = pb + (long long)r * p.sx + c;
-      const float v = X[o];
-      s_x[r][c] = v;
-      if (CL) s_c[r][c] = __ldg(p.att + o) * v;
+    // fixed trip counts, unrolled: every thread's loads of the plane issue together
+#pragma unroll
+    for (int t = 0; t < (SH * SW + NT - 1) / NT; ++t) {
+      const int i = tid + t * NT;
+      if (i < SH * SW) {
+        const int r = i / SW, c = i - r * SW;
+        const long long o = pb + (long long)r * p.sx + c;
+        const float v = X[o];
+        s_x[r][c] = v;
+        if (CL) s_c[r][c] = __ldg(p.att + o) * v;
+      }
     }
     if (PSI) {
-      for (int i = tid; i < TY * SW; i += NT) {
-        const int r = i / SW, c = i - r * SW;
-        const long long o = pb + (long long)(r + R) * p.sx + c;
-        s_px[r][c] = __ldg(p.bx + o) * X[o];
+#pragma unroll
+      for (int t = 0; t < (TY * SW + NT - 1) / NT; ++t) {
+        const int i = tid + t * NT;
+        if (i < TY * SW) {
+          const int r = i / SW, c = i - r * SW;
+          const long long o = pb + (long long)(r + R) * p.sx + c;
+          s_px[r][c] = __ldg(p.bx + o) * X[o];
+        }
       }
-      for (int i = tid; i < SH * TX; i += NT) {
-        const int r = i / TX, c = i - r * TX;
-        const long long o = pb + (long long)r * p.sx + c + R;
-        s_py[r][c] = __ldg(p.by + o) * X[o];
+#pragma unroll
+      for (int t = 0; t < (SH * TX + NT - 1) / NT; ++t) {
+        const int i = tid + t * NT;
+        if (i < SH * TX) {
+          const int r = i / TX, c = i - r * TX;
+          const long long o = pb + (long long)r * p.sx + c + R;
+          s_py[r][c] = __ldg(p.by + o) * X[o];
+        }
       }
     }
     __syncthreads();
@@ -481,7 +519,6 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_ext3d(const StepParams p) 
       lap = fmaf(p.wz.w2[j], (q[R + j] + q[R - j]) - c2, lap);
     }
     float acc = lap;
-    const long long idx = col + pz;
     if (VD && !ADJ) {
       float dx = 0.f, dy = 0.f, dz = 0.f;
 #pragma unroll
@@ -490,7 +527,7 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_ext3d(const StepParams p) 
         dy = fmaf(p.wy.w1[j], s_x[cy + j][cx] - s_x[cy - j][cx], dy);
         dz = fmaf(p.wz.w1[j], q[R + j] - q[R - j], dz);
       }
-      acc -= __ldg(p.bx + idx) * dx + __ldg(p.by + idx) * dy + __ldg(p.bz + idx) * dz;
+      acc -= ops.bx * dx + ops.by * dy + ops.bz * dz;
     }
     if (PSI) {
 #pragma unroll
@@ -516,7 +553,7 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_ext3d(const StepParams p) 
         if (p.inj_loc[e] == loc)
           acc = fmaf(p.inj_scale * p.inj_w[e], p.vals[p.inj_vidx[e] + p.step_off], acc);
     }
-    if (in_xy) ext_update<ADJ, MODE>(p, fo, idx, cen, acc, lap, lc, axy + p.spz[z]);
+    if (in_xy) ext_update<VD, ADJ, MODE>(p, fo, idx, cen, acc, lap, lc, axy + p.spz[z], ops);
 #pragma unroll
     for (int j = 0; j < Q - 1; ++j) {
       q[j] = q[j + 1];
