@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(EXT_TX2 / 4 * EXT_TY2) k_ext2d(const StepParam
 }
 
 template <int R, bool VD, bool ADJ, int MODE>
-__global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_ext3d(const StepParams p) {
+__global__ void __launch_bounds__(EXT_TX * EXT_TY3, 3) k_ext3d(const StepParams p) {
   constexpr int TX = EXT_TX, TY = EXT_TY3;
   constexpr int SW = TX + 2 * R, SH = TY + 2 * R;
   constexpr int NT = TX * TY;
