@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(EXT_TX2 / 4 * EXT_TY2, 2) k_pml2d(const StepPa
 
 // 3D: 32 x 8 columns streamed along z, one point per thread.
 template <int R, bool VD, int MODE>
-__global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_pml3d(const StepParams p) {
+__global__ void __launch_bounds__(EXT_TX * EXT_TY3, 3) k_pml3d(const StepParams p) {
   constexpr int TX = EXT_TX, TY = EXT_TY3;
   constexpr int SW = TX + 2 * R, SH = TY + 2 * R;
   constexpr int NT = TX * TY;
@@ -377,12 +377,40 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_pml3d(const StepParams p) 
 
   for (int z = z0; z < z1; ++z) {
     const long long pz = (long long)(z + p.oz) * p.sxy;
+    const long long idx = col + pz;
+    // the point's own operands (read and written by this thread only), loaded
+    // ahead of the plane staging, the barrier and the stencil
+    float o_k = 0.f, o_up = 0.f, o_q = 0.f, o_h = 0.f, o_g = 0.f, o_c = 0.f;
+    float o_b[3] = {0.f, 0.f, 0.f}, o_f[3] = {0.f, 0.f, 0.f};
+    if (in_xy) {
+      if (MODE != PML_PHI) o_k = __ldg(p.kf + idx);
+      if (MODE != PML_PHI) o_up = p.up[fo + idx];
+      if (MODE == PML_U || MODE == PML_A) o_q = p.q[fo + idx];
+      if (MODE == PML_U && VD) {
+        o_b[0] = __ldg(p.bx + idx);
+        o_b[1] = __ldg(p.by + idx);
+        o_b[2] = __ldg(p.bz + idx);
+      }
+      if (MODE == PML_A) {
+        o_h = __ldcs(p.hist + fo + idx);
+        o_g = p.g[fo + idx];
+      }
+      if (MODE == PML_B) o_c = X[idx];
+      if (MODE == PML_PHI || (MODE == PML_B && near)) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) o_f[j] = p.ph[j][fo + idx];
+      }
+    }
     col_vals(z + R, q1[Q - 1], q2[Q - 1], q3[Q - 1]);
     const float Az = sp_at(p.spz, z, p.nz);
     __syncthreads();   // the previous plane's readers are done with the shared tiles
     const long long pb = pz + (long long)(y0 + p.oy - R) * p.sx + (x0 + p.ox - R);
+    // fixed trip counts, unrolled: every thread's loads of the plane issue together
     if (FULL || QQ) {
-      for (int i = tid; i < SH * SW; i += NT) {
+#pragma unroll
+      for (int t = 0; t < (SH * SW + NT - 1) / NT; ++t) {
+        const int i = tid + t * NT;
+        if (i >= SH * SW) break;
         const int r = i / SW, c = i - r * SW;
         const long long o = pb + (long long)r * p.sx + c;
         if (FULL) s_x[r][c] = (MODE == PML_B) ? __ldg(p.kf + o) * X[o] : X[o];
@@ -390,7 +418,10 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_pml3d(const StepParams p) 
       }
     }
     if (cross) {
-      for (int i = tid; i < TY * SW; i += NT) {
+#pragma unroll
+      for (int t = 0; t < (TY * SW + NT - 1) / NT; ++t) {
+        const int i = tid + t * NT;
+        if (i >= TY * SW) break;
         const int r = i / SW, c = i - r * SW;
         const long long o = pb + (long long)(r + R) * p.sx + c;
         if (MODE == PML_U) {
@@ -404,7 +435,10 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_pml3d(const StepParams p) 
           s_r[r][c] = __ldg(p.bx + o) * __ldg(p.kf + o) * X[o];
         }
       }
-      for (int i = tid; i < SH * TX; i += NT) {
+#pragma unroll
+      for (int t = 0; t < (SH * TX + NT - 1) / NT; ++t) {
+        const int i = tid + t * NT;
+        if (i >= SH * TX) break;
         const int r = i / TX, c = i - r * TX;
         const long long o = pb + (long long)r * p.sx + c + R;
         if (MODE == PML_U) {
@@ -421,7 +455,6 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_pml3d(const StepParams p) 
     }
     __syncthreads();
 
-    const long long idx = col + pz;
     float cen = 0.f, acc = 0.f, d1x = 0.f, d1y = 0.f, d1z = 0.f;
     if (FULL) {
       cen = q1[R];
@@ -439,7 +472,7 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_pml3d(const StepParams p) 
       }
     }
     if (MODE == PML_U && VD)
-      acc -= __ldg(p.bx + idx) * d1x + __ldg(p.by + idx) * d1y + __ldg(p.bz + idx) * d1z;
+      acc -= o_b[0] * d1x + o_b[1] * d1y + o_b[2] * d1z;
     float dr = 0.f, dr2 = 0.f;   // D1 of the cross tiles and queues
     if (cross) {
 #pragma unroll
@@ -461,15 +494,15 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_pml3d(const StepParams p) 
         if (p.inj_loc[e] == loc) inj += p.inj_w[e] * p.vals[p.inj_vidx[e] + p.step_off];
     }
     if (in_xy) {
-      const float k = __ldg(p.kf + idx);
+      const float k = o_k;
       const float a = Ax + Ay + Az;
       const float e = 4.f * (Ax * Ay + Ax * Az + Ay * Az);
       const float f = 8.f * Ax * Ay * Az / p.dt;
       if (MODE == PML_U) {
         const float E = (acc + inj) + dr;
         const float hv = k * E;
-        const float uo = p.up[fo + idx];
-        const float qv = p.q[fo + idx];
+        const float uo = o_up;
+        const float qv = o_q;
         const float r = (2.f * cen - (1.f - a) * uo - e * cen - f * qv + hv) / (1.f + a);
         p.up[fo + idx] = r;
         p.q[fo + idx] = qv + p.dt * r;
@@ -485,29 +518,25 @@ __global__ void __launch_bounds__(EXT_TX * EXT_TY3) k_pml3d(const StepParams p) 
         float* fx = p.ph[0] + fo + idx;
         float* fy = p.ph[1] + fo + idx;
         float* fz = p.ph[2] + fo + idx;
-        *fx = pml_p(Ax) * *fx + pml_b(Ax, Ay, Az) * d1x + pml_g(Ax, Ay, Az, p.dt) * dqx;
-        *fy = pml_p(Ay) * *fy + pml_b(Ay, Ax, Az) * d1y + pml_g(Ay, Ax, Az, p.dt) * dqy;
-        *fz = pml_p(Az) * *fz + pml_b(Az, Ax, Ay) * d1z + pml_g(Az, Ax, Ay, p.dt) * dqz;
+        *fx = pml_p(Ax) * o_f[0] + pml_b(Ax, Ay, Az) * d1x + pml_g(Ax, Ay, Az, p.dt) * dqx;
+        *fy = pml_p(Ay) * o_f[1] + pml_b(Ay, Ax, Az) * d1y + pml_g(Ay, Ax, Az, p.dt) * dqy;
+        *fz = pml_p(Az) * o_f[2] + pml_b(Az, Ax, Ay) * d1z + pml_g(Az, Ax, Ay, p.dt) * dqz;
       } else if (MODE == PML_A) {
-        const float qb = p.q[fo + idx] - dr2;
-        const float ub = (p.up[fo + idx] - dr) + p.dt * qb;
+        const float qb = o_q - dr2;
+        const float ub = (o_up - dr) + p.dt * qb;
         const float c = ub / (1.f + a);
         p.q[fo + idx] = qb - f * c;
         p.out[fo + idx] = c;
         p.up[fo + idx] = inj - (1.f - a) * c;
-        float* gp = p.g + fo + idx;
-        *gp = fmaf(-(k * c), __ldcs(p.hist + fo + idx), *gp);
+        p.g[fo + idx] = fmaf(-(k * c), o_h, o_g);
       } else {   // PML_B
-        const float c = X[idx];
+        const float c = o_c;
         const float LT = acc + (VD ? dr : 0.f);
-        p.up[fo + idx] = p.up[fo + idx] + ((2.f - e) * c + LT);
+        p.up[fo + idx] = o_up + ((2.f - e) * c + LT);
         if (near) {
-          float* fx = p.ph[0] + fo + idx;
-          float* fy = p.ph[1] + fo + idx;
-          float* fz = p.ph[2] + fo + idx;
-          *fx = pml_p(Ax) * *fx - d1x;
-          *fy = pml_p(Ay) * *fy - d1y;
-          *fz = pml_p(Az) * *fz - d1z;
+          p.ph[0][fo + idx] = pml_p(Ax) * o_f[0] - d1x;
+          p.ph[1][fo + idx] = pml_p(Ay) * o_f[1] - d1y;
+          p.ph[2][fo + idx] = pml_p(Az) * o_f[2] - d1z;
         }
       }
     }
