@@ -408,9 +408,10 @@ def uneven_gradient(nprob=64, seed=4, lanes=4, **kw):
     against zero data), (a) submitted at once to the serving loop, which runs
     them concurrently on `lanes` streams within the HBM budget and while their
     GPU-fill weights sum to at most one, one plan per problem with all its
-    shots per launch; (b) one plan per problem, problems one after another;
-    (c) the plain solver with one shot per launch; (d) gradient batches (one
-    CUDA graph each)."""
+    shots per launch; (b) one plan per problem, problems one after another
+    (each plan's own shots per CTA, and six); (c) the plain solver with one
+    shot per launch; (d) gradient batches (one CUDA graph each, shot groups
+    sized for the batch)."""
     import torch
     from paper_2110_03345_gb300 import binding, inputs, serve
     ps = inputs.config_uneven_batch(nprob=nprob, seed=seed, **kw)
@@ -441,7 +442,7 @@ def uneven_gradient(nprob=64, seed=4, lanes=4, **kw):
         server.close()
         return t
 
-    def sequential(per_launch):
+    def sequential(per_launch, spc=0):
         stream = torch.cuda.current_stream()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -449,7 +450,7 @@ def uneven_gradient(nprob=64, seed=4, lanes=4, **kw):
             pl = binding.Plan(r["shape"], r["spacing"], r["nt"], r["dt"], order=r["order"],
                               sponge=r["sponge"], c_ref=r["c_ref"], stream=stream,
                               budget=budget)
-            pl.set_options(batch=per_launch)
+            pl.set_options(batch=per_launch, shots_per_cta=spc)
             pl.gradient(r["vp"], r["rho"], r["geometry"], r["wavelet"], r["observed"])
             pl.close()
         torch.cuda.synchronize()
@@ -507,7 +508,10 @@ def uneven_gradient(nprob=64, seed=4, lanes=4, **kw):
 
     served()   # warm-up (allocator pool, kernel attributes)
     out = {}
+    # per_problem_s6: the same with six shots per CTA in every plan (the shot
+    # groups the batches take), against each plan's own choice
     for name, fn in (("served", served), ("per_problem", lambda: sequential(0)),
+                     ("per_problem_s6", lambda: sequential(0, 6)),
                      ("plain", lambda: sequential(1))):
         t = fn()
         out[name] = {"shots_per_s": shots / t, "gpts": updates / t / 1e9, "s": t}

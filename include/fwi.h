@@ -263,6 +263,7 @@ typedef struct {
     int64_t launches;    /* kernel launches (graph nodes) of one run */
     int64_t updates;     /* grid-point updates of one run */
     double run_ms;       /* device time of the last fwi_batch_run */
+    int shots_per_cta;   /* the largest shot group of one CTA in the batch's launches */
 } fwi_batch_stats;
 
 typedef struct fwi_batch fwi_batch;
@@ -282,8 +283,11 @@ typedef struct fwi_batch fwi_batch;
  * fwi_gradient does (all its shots at once; the full wavefield history when
  * it fits the budget left, else sqrt(nt) checkpoints), each problem on its
  * own stream forked from the batch's: with use_graph = 1 the graph holds one
- * independent branch per problem, which the GPU runs concurrently.  The
- * problem arrays must stay valid until fwi_batch_destroy. */
+ * independent branch per problem, which the GPU runs concurrently.  Unless
+ * opt fixes shots_per_cta, a gradient batch sizes the shot groups for the
+ * batch as a whole (the largest S <= 6 whose CTAs over all its problems make
+ * four waves of two per SM), not per problem.  The problem arrays must stay
+ * valid until fwi_batch_destroy. */
 fwi_status fwi_batch_create(fwi_batch** batch, int nprob, const fwi_problem* probs,
                             const fwi_options* opt, size_t hbm_budget_bytes, void* stream,
                             int use_graph);

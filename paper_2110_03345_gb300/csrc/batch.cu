@@ -223,6 +223,22 @@ fwi_status fwi_batch_create(fwi_batch** out, int nprob, const fwi_problem* probs
   }
   std::stable_sort(b->items.begin(), b->items.end(),
                    [](const BatchProblem* a, const BatchProblem* c) { return a->prob.nt > c->prob.nt; });
+  if (b->grad && b->tma && !(opt && opt->shots_per_cta > 0) && !b->items.empty()) {
+    // the problems' branches run concurrently, so the shot groups are sized
+    // for the batch as a whole: the largest S <= 6 whose CTAs over all the
+    // problems still make four waves of two per SM (each plan alone lowers S
+    // until its own problem does)
+    const int nsm = b->items[0]->P->nsm;
+    int S = 6;
+    for (; S > 1; --S) {
+      long long ctas = 0;
+      for (const BatchProblem* it : b->items)
+        ctas += it->c.T.ntiles() * (long long)((it->prob.geom.nshots + S - 1) / S);
+      if (ctas >= 8LL * nsm) break;
+    }
+    for (BatchProblem* it : b->items) it->c.pl.S = std::min(S, it->c.pl.B);
+  }
+  for (const BatchProblem* it : b->items) b->stats.shots_per_cta = std::max(b->stats.shots_per_cta, it->c.pl.S);
   if (!b->items.empty()) {
     b->w[0] = b->items[0]->P->wx;
     b->w[1] = b->items[0]->P->wy;

@@ -72,18 +72,21 @@ def gradient_entries(ps):
     return entries, obs
 
 
-@pytest.mark.parametrize("use_graph", [True, False])
-def test_gradient_batch_matches_single_problem_runs(use_graph):
-    """A gradient batch (forward with the history, misfits, one multi-problem
-    adjoint launch per step, imaging, finalisation) gives each problem's
-    misfit and gradient bit for bit as one plan per problem with its full
-    history (same kernel body, tile shape and shot groups)."""
+@pytest.mark.parametrize("use_graph,spc", [(True, 0), (False, 0), (True, 4)])
+def test_gradient_batch_matches_single_problem_runs(use_graph, spc):
+    """A gradient batch (each problem's forward with the history, misfit,
+    adjoint with imaging and finalisation on a branch of its own) gives each
+    problem's misfit and gradient bit for bit as one plan per problem with its
+    full history and the batch's shot groups (same kernels, tile shape and
+    summation order)."""
     ps = problems()
     entries, obs = gradient_entries(ps)
-    b = binding.Batch(entries, use_graph=use_graph, gradient=True)
+    b = binding.Batch(entries, use_graph=use_graph, gradient=True, shots_per_cta=spc)
     J, grads = b.run()
+    S = b.stats()["shots_per_cta"]   # spc, or sized for the whole batch
+    assert 1 <= S <= (spc or 6)
     for p, o, Jb, gb in zip(ps, obs, J, grads):
-        plan = gpu_plan(p, batch=p.nshots, ckpt_every=-1)
+        plan = gpu_plan(p, batch=p.nshots, ckpt_every=-1, shots_per_cta=spc or S)
         Jr, gr, _, _ = gpu_gradient(p, o, plan=plan)
         plan.close()
         assert Jb == Jr
