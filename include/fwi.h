@@ -316,10 +316,9 @@ void fwi_batch_destroy(fwi_batch* batch);
  *     returning.
  * The call runs on the current device; every device array must live there
  * (FWI_ERR_INVALID_ARG otherwise).  The first call on a device looks up the
- * scratch address (once per device, with that device current); make that
- * first call before any stream capture.  The address is kept for the life of
- * the process, so the entry point must not be used on a device after a
- * cudaDeviceReset of it.  All calls share the scratch and keep the last
+ * scratch address (once per device, with that device current).  The address
+ * is kept for the life of the process, so the entry point must not be used on
+ * a device after a cudaDeviceReset of it.  All calls share the scratch and keep the last
  * call's contents, so calls that overlap on the GPU race; each call clears
  * what must start at zero, and returns only when its own work on the scratch
  * has finished, on success and on error.

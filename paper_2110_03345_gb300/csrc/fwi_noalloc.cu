@@ -14,8 +14,7 @@
 // allocated until the process exits.  Its host-side name is only a stand-in:
 // host code must use the device address returned by cudaGetSymbolAddress,
 // which is looked up once per device, with that device current, on the first
-// call made on it (so make the first call before any stream capture).  The
-// address is kept for the life of the process: after a cudaDeviceReset the
+// call made on it.  The address is kept for the life of the process: after a cudaDeviceReset the
 // entry point must not be used on that device again.  Every call reuses the
 // same array: calls that overlap on the GPU (different streams, threads or
 // processes sharing a context) race on it.  Each call clears what must start
