@@ -264,6 +264,8 @@ typedef struct {
     int64_t updates;     /* grid-point updates of one run */
     double run_ms;       /* device time of the last fwi_batch_run */
     int shots_per_cta;   /* the largest shot group of one CTA in the batch's launches */
+    int checkpointed;    /* gradient batches: problems run with checkpoints (their
+                            full history did not fit the budget left to them) */
 } fwi_batch_stats;
 
 typedef struct fwi_batch fwi_batch;

@@ -69,7 +69,8 @@ class CProblem(ctypes.Structure):
 class CBatchStats(ctypes.Structure):
     _fields_ = [("problems", ctypes.c_int), ("units", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("updates", ctypes.c_int64),
-                ("run_ms", ctypes.c_double), ("shots_per_cta", ctypes.c_int)]
+                ("run_ms", ctypes.c_double), ("shots_per_cta", ctypes.c_int),
+                ("checkpointed", ctypes.c_int)]
 
 
 class COptions(ctypes.Structure):

@@ -238,7 +238,10 @@ fwi_status fwi_batch_create(fwi_batch** out, int nprob, const fwi_problem* probs
     }
     for (BatchProblem* it : b->items) it->c.pl.S = std::min(S, it->c.pl.B);
   }
-  for (const BatchProblem* it : b->items) b->stats.shots_per_cta = std::max(b->stats.shots_per_cta, it->c.pl.S);
+  for (const BatchProblem* it : b->items) {
+    b->stats.shots_per_cta = std::max(b->stats.shots_per_cta, it->c.pl.S);
+    if (it->c.pl.K > 0) b->stats.checkpointed++;
+  }
   if (!b->items.empty()) {
     b->w[0] = b->items[0]->P->wx;
     b->w[1] = b->items[0]->P->wy;

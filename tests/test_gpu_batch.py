@@ -1,7 +1,7 @@
-"""Uneven batches: many independent 2D problems advanced by one multi-problem
-launch per step, captured in one CUDA graph, against one plan per problem
-(bit for bit: the same kernel body and tile shape) and the FP64 oracle, for
-forward modelling and for gradients."""
+"""Uneven batches: many independent 2D problems in one CUDA graph (forward
+modelling: one multi-problem launch per step; gradients: one branch per
+problem), against one plan per problem (bit for bit: the same kernel body,
+tile shape and shot groups) and the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -93,6 +93,39 @@ def test_gradient_batch_matches_single_problem_runs(use_graph, spc):
         assert np.array_equal(gb.cpu().numpy().astype(np.float64), gr)
     J2, grads2 = b.run()   # a second run (graph replay) gives the same results
     assert J2 == J and all(torch_equal(a, g) for a, g in zip(grads2, grads))
+    b.close()
+
+
+def test_gradient_batch_with_checkpointed_problems():
+    """A budget that leaves the last problem too little room for its full
+    history: it runs with sqrt(nt) checkpoints inside the batch, and every
+    gradient still equals, bit for bit, one plan per problem with its full
+    history (the recomputed segments repeat the forward exactly)."""
+    ps = problems()
+    entries, obs = gradient_entries(ps)
+    S = 2
+
+    def est(p, ckpt):
+        plan = gpu_plan(p, batch=p.nshots, ckpt_every=ckpt, shots_per_cta=S)
+        n = plan.estimate(binding.Geometry(p.src_xyz, p.rec_xyz), True)
+        plan.close()
+        return n
+
+    full = [est(p, -1) for p in ps]
+    last = ps[-1]
+    K = max(2, int(np.ceil(np.sqrt(2.0 * max(last.nt, 2)))))
+    ck = est(last, K)
+    assert ck < full[-1]
+    budget = sum(full[:-1]) + ck + (full[-1] - ck) // 2
+    b = binding.Batch(entries, budget=budget, gradient=True, shots_per_cta=S)
+    assert b.stats()["checkpointed"] >= 1
+    J, grads = b.run()
+    for p, o, Jb, gb in zip(ps, obs, J, grads):
+        plan = gpu_plan(p, batch=p.nshots, ckpt_every=-1, shots_per_cta=S)
+        Jr, gr, _, _ = gpu_gradient(p, o, plan=plan)
+        plan.close()
+        assert Jb == Jr
+        assert np.array_equal(gb.cpu().numpy().astype(np.float64), gr)
     b.close()
 
 
