@@ -132,6 +132,11 @@ __device__ __forceinline__ void ext_epilogue(const StepParams& p, int s, int pix
   }
 }
 
+// Ask for the lines of a global address in L2 (a hint: no data returns).
+__device__ __forceinline__ void prefetch_l2(const void* q) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
+}
+
 // One tile (bxi, byi) for shot group grp (shots grp*S .. grp*S+S-1): the body
 // shared by the single-problem kernel and the multi-problem kernel.  tmap is
 // the tensor map of the wavefield buffer p.u (param or global memory);
@@ -221,6 +226,14 @@ __device__ __forceinline__ void step2d_tma_tile(const StepParams& p, const AxisW
     kk[iy] = ldg4(p.kf + pix[iy]);
     if (AT) atv[iy] = ldg4(p.att + pix[iy]);
     ay[iy] = p.spy[yg];
+  }
+  if (ADJ && MODE != EXT_KW && p.image) {
+    // the group's gradient slot is read once, after the S shots: its lines
+    // are requested in L2 now, so that the read-modify-write at the end hits
+    // L2 instead of waiting on DRAM
+    const float* gpre = p.g + (size_t)grp * p.fstride;
+#pragma unroll
+    for (int iy = 0; iy < RY; ++iy) prefetch_l2(gpre + pix[iy]);
   }
   if (VD && ADJ && ns > 0) {
     for (int i = tid; i < TY * SW; i += NT) {
