@@ -425,12 +425,12 @@ def uneven_gradient(nprob=64, seed=4, lanes=4, **kw):
     updates = sum(2 * p.nshots * p.npoints * (p.nt - 1) for p in ps)
     budget = int(0.7 * binding.mem_available())
 
-    def served():
+    def served(spc=0):
         # requests that each fill the GPU (>= 8 M points x shots) run one at a
         # time, and a request may take the whole budget (as in the sequential
         # arms), so no plan is pushed into checkpointing by a per-request cap
         server = serve.Server(budget_bytes=budget, lanes=lanes, fill_points=8 << 20,
-                              request_cap=budget)
+                              request_cap=budget, shots_per_cta=spc)
         objs = [serve.Request(**r) for r in reqs]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -510,7 +510,8 @@ def uneven_gradient(nprob=64, seed=4, lanes=4, **kw):
     out = {}
     # per_problem_s6: the same with six shots per CTA in every plan (the shot
     # groups the batches take), against each plan's own choice
-    for name, fn in (("served", served), ("per_problem", lambda: sequential(0)),
+    for name, fn in (("served", served), ("served_s6", lambda: served(6)),
+                     ("per_problem", lambda: sequential(0)),
                      ("per_problem_s6", lambda: sequential(0, 6)),
                      ("plain", lambda: sequential(1))):
         t = fn()

@@ -80,10 +80,14 @@ def estimate_bytes(req: Request, cap: int = 0, stream=None) -> int:
         plan.close()
 
 
-def run_request(req: Request, stream, budget=0):
-    """Solve one request on `stream` (used by the lanes and for 'alone' runs)."""
+def run_request(req: Request, stream, budget=0, shots_per_cta=0):
+    """Solve one request on `stream` (used by the lanes and for 'alone' runs);
+    shots_per_cta > 0 fixes the shot group of the 2D kernels (0: the plan's
+    own choice)."""
     with torch.cuda.stream(stream):
         plan = _make_plan(req, stream, budget=budget)
+        if shots_per_cta:
+            plan.set_options(shots_per_cta=shots_per_cta)
         try:
             if req.observed is None:
                 out = plan.forward(req.vp, req.rho, req.geometry, req.wavelet)
@@ -101,11 +105,17 @@ class Server:
     fill_points (optional): grid points x shots that fill the GPU.  A request
     then weighs min(1, its points x shots / fill_points) and requests run
     together only while their weights sum to at most 1 (one always runs), so
-    requests that each fill the GPU do not contend for it."""
+    requests that each fill the GPU do not contend for it.
+
+    shots_per_cta (optional): the shot group of every request's 2D launches.
+    Concurrent requests fill the GPU together, so each may take larger groups
+    than its plan alone would (which lowers S until its own launch fills the
+    GPU); a fixed value keeps each result the same alone and in the mix."""
 
     def __init__(self, budget_bytes: int, lanes: int = 4, device=None, request_cap: int = 0,
-                 fill_points: int = 0):
+                 fill_points: int = 0, shots_per_cta: int = 0):
         self.budget = int(budget_bytes)
+        self.shots_per_cta = int(shots_per_cta)
         self.lanes = lanes
         self.fill_points = int(fill_points)
         self._load = 0.0
@@ -191,7 +201,8 @@ class Server:
         stream = self._streams[lane]
         req.t_start = time.perf_counter()
         try:
-            req.result = run_request(req, stream, budget=req.bytes)
+            req.result = run_request(req, stream, budget=req.bytes,
+                                     shots_per_cta=self.shots_per_cta)
             req.t_done = time.perf_counter()
             fut.set_result(req)
         except Exception as e:   # noqa: BLE001 - handed to the caller's future

@@ -95,3 +95,26 @@ def test_fill_weights_serialise_large_requests():
         ref = serve.run_request(r, alone)
         torch.cuda.synchronize()
         assert results_equal(r.result, ref)
+
+
+def test_fixed_shot_groups_equal_alone():
+    """With a fixed shot group (Server(shots_per_cta=4)), multi-shot gradient
+    requests give in the mix what they give alone with that shot group."""
+    ps = inputs.config_uneven_batch(nprob=4, seed=7, side=(96, 200), nt=(60, 200), shots=(2, 5),
+                                    dx=0.4e-3, nelem=16, nb=12)
+    reqs = [serve.Request(p.shape, p.spacing, p.nt, p.dt, to_dev(p.vp), to_dev(p.rho),
+                          binding.Geometry(p.src_xyz, p.rec_xyz), to_dev(p.wavelet),
+                          to_dev(np.zeros((p.nshots, p.rec_xyz.shape[0], p.nt)) + 1e-6),
+                          order=p.order, sponge=p.nb, c_ref=p.c_ref) for p in ps]
+    assert max(r.shots for r in reqs) >= 3
+    server = serve.Server(budget_bytes=24 << 30, lanes=4, shots_per_cta=4)
+    futs = [server.submit(r) for r in reqs]
+    for f in futs:
+        f.result(timeout=300)
+    server.drain()
+    server.close()
+    alone = torch.cuda.Stream()
+    for r in reqs:
+        ref = serve.run_request(r, alone, shots_per_cta=4)
+        torch.cuda.synchronize()
+        assert results_equal(r.result, ref)
